@@ -1,0 +1,136 @@
+"""Pins for oracle B (MPS operations) against oracle A, library SVDs and
+exact properties of the fit (Eq. add_min) and of SVD truncation."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import fci
+from oracle import mps as om
+
+
+def _system(L, n_elec, two_sz, seed):
+    I = synth.make_integrals(L, seed=seed)
+    na, nb = (n_elec + two_sz) // 2, (n_elec - two_sz) // 2
+    return om.System.build(I.h, I.eri, na, nb)
+
+
+def test_determinant_mps_is_unit_vector():
+    occ = [3, 1, 0, 2, 3, 0]
+    m = om.from_determinant(occ)
+    na, nb = 3, 3
+    dets = fci.basis(6, na, nb)
+    v = om.to_sector(m, dets)
+    ref = np.zeros(len(dets))
+    ref[np.searchsorted(dets, np.uint64(fci.occupation_mask(occ)))] = 1.0
+    assert np.allclose(v, ref)
+    assert om.coefficient(m, occ) == 1.0
+
+
+def test_transfer_overlap_equals_vector_overlap_and_coefficients():
+    A, q = synth.random_mps(6, 6, 0, 12, seed=1)
+    B, qb = synth.random_mps(6, 6, 0, 9, seed=2)
+    a, b = om.from_arrays(A, q), om.from_arrays(B, qb)
+    va, vb = om.to_fock(a), om.to_fock(b)
+    assert abs(om.overlap(b, a) - np.vdot(vb, va)) < 1e-12 * np.linalg.norm(va) * np.linalg.norm(vb)
+    rng = np.random.default_rng(0)
+    dets = fci.basis(6, 3, 3)
+    for m in rng.choice(dets, 5):
+        occ = [((int(m) >> (2 * i)) & 1) + 2 * ((int(m) >> (2 * i + 1)) & 1) for i in range(6)]
+        idx = om.fock_index(np.array([m], dtype=np.uint64), 6)[0]
+        assert abs(om.coefficient(a, occ) - va[idx]) < 1e-13
+
+
+def test_compress_two_sites_is_library_svd():
+    # L = 2: one bond; truncation to D is the Eckart-Young truncation of the
+    # 4 x 4 coefficient matrix, computed here by numpy's SVD.
+    A, q = synth.random_mps(2, 2, 0, 4, seed=3)
+    m = om.from_arrays(A, q)
+    M = om.to_fock(m).reshape(4, 4)
+    s = np.linalg.svd(M, compute_uv=False)
+    for D in (1, 2):
+        c, disc = om.compress(m, D, 0.0)
+        err2 = np.linalg.norm(om.to_fock(c).reshape(4, 4) - M) ** 2
+        assert abs(err2 - np.sum(s[D:] ** 2)) < 1e-12
+        assert abs(disc - np.sum(s[D:] ** 2) / np.sum(s ** 2)) < 1e-12
+
+
+def test_compress_exact_and_single_bond_truncation_weight():
+    A, q = synth.random_mps(6, 5, 1, 30, seed=4)
+    m = om.from_arrays(A, q)
+    v = om.to_fock(m)
+    c, disc = om.compress(m, 10 ** 6, 0.0)
+    assert np.linalg.norm(om.to_fock(c) - v) < 1e-12 * np.linalg.norm(v)
+    assert disc < 1e-24
+    # normalised state, truncation only at the middle bond (others are small
+    # enough to stay exact): <psi'|psi'> = 1 - discarded, |psi - psi'|^2 = discarded
+    mn = om.scale(c, 1.0 / om.norm(c))
+    D = 6
+    t, disc = om.compress(mn, D, 0.0)
+    dims = t.bond_dims
+    assert max(dims) <= D
+    vn, vt = om.to_fock(mn), om.to_fock(t)
+    assert abs(np.vdot(vn - vt, vn - vt).real - (1 - np.vdot(vt, vt).real)) < 1e-12
+
+
+def test_truncation_rule_eps_D_and_clusters():
+    s = {(0, 0): np.array([1.0, 0.5, 0.1]), (1, 1): np.array([0.5 + 1e-13, 1e-3]),
+         (1, -1): np.array([1e-14])}
+    kept, disc, tot = om.truncation_rule(s, D=10, eps=0.0)
+    assert kept == {(0, 0): 3, (1, 1): 2, (1, -1): 0}          # zero floor
+    kept, disc, tot = om.truncation_rule(s, D=10, eps=2e-6 / tot)
+    assert kept == {(0, 0): 3, (1, 1): 1, (1, -1): 0}          # drops 1e-3 (weight 1e-6)
+    kept, _, _ = om.truncation_rule(s, D=2, eps=0.0)            # cut inside 0.5 cluster
+    assert kept == {(0, 0): 1, (1, 1): 0, (1, -1): 0}
+    kept, _, _ = om.truncation_rule(s, D=3, eps=0.0)
+    assert kept == {(0, 0): 2, (1, 1): 1, (1, -1): 0}
+
+
+@pytest.mark.parametrize("n_two", [3])
+def test_untruncated_apply_h_is_exact(n_two):
+    sys_ = _system(6, 6, 0, seed=5)
+    psi = om.from_determinant([3, 3, 0, 0, 1, 2])
+    sch = om.Schedule(D=500, eps=0.0, n_two_site=n_two, n_one_site=1)
+    c = om.apply_H(sys_, psi, 0.7 - 0.2j, sch)
+    ref = (0.7 - 0.2j) * (sys_.H @ sys_.vec(psi))
+    assert np.linalg.norm(sys_.vec(c) - ref) < 1e-12 * np.linalg.norm(ref)
+
+
+def test_untruncated_integrators_equal_full_ci_integrators():
+    sys_ = _system(6, 5, 1, seed=6)
+    psi = om.from_determinant(synth.hole_occupation(6, 6, 2))
+    sch = om.Schedule(D=500, eps=0.0, n_two_site=3, n_one_site=1)
+    v = sys_.vec(psi).astype(complex)
+    p = om.rk4_step(sys_, psi, 0.03, sch)
+    assert np.linalg.norm(sys_.vec(p) - fci.rk4_step(sys_.H, v, 0.03)) < 1e-11
+    k, c, N, Hk = om.krylov_step(sys_, p, 0.05, 5, sch)
+    ref = fci.krylov_step(sys_.H, sys_.vec(p), 0.05, 5)
+    assert np.linalg.norm(sys_.vec(k) - ref) < 1e-10
+    assert abs(om.norm(k) - om.norm(p)) < 1e-12
+    g = om.one_rdm(sys_, k)
+    assert np.allclose(g, fci.one_rdm(ref, sys_.dets, 6), atol=1e-10)
+
+
+def test_truncated_fit_residual_monotone_and_projection_property():
+    sys_ = _system(6, 6, 0, seed=7)
+    A, q = synth.random_mps(6, 6, 0, 24, seed=8)
+    psi = om.from_arrays(A, q)
+    psi = om.scale(psi, 1.0 / om.norm(psi))
+    info = om.FitInfo()
+    sch = om.Schedule(D=8, eps=0.0, n_two_site=1, n_one_site=4)
+    T = sys_.fock(sys_.H @ sys_.vec(psi))
+    c = om.fit(T, psi, sch.D, sch.eps, sch.n_two_site, sch.n_one_site, info)
+    r = info.residuals
+    assert all(r[i + 1] <= r[i] + 1e-12 for i in range(len(r) - 1))
+    # after the last local solve, C is the projection of T on its own tangent
+    # space: <C|C> = <C|T>, and the residual equals |T|^2 - |C|^2
+    vc = om.to_fock(c)
+    assert abs(np.vdot(vc, vc) - np.vdot(vc, T)) < 1e-12 * np.vdot(T, T).real
+    assert abs(np.vdot(T - vc, T - vc).real - r[-1]) < 1e-10 * np.vdot(T, T).real
+    assert max(c.bond_dims) <= 8
+
+
+def test_scale_uses_lth_root():
+    A, q = synth.random_mps(4, 4, 0, 6, seed=9)
+    m = om.from_arrays(A, q)
+    s = om.scale(m, -2.0 + 1.0j)
+    assert np.allclose(om.to_fock(s), (-2.0 + 1.0j) * om.to_fock(m))
