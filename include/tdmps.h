@@ -1,0 +1,213 @@
+/*
+ * tdmps.h -- C ABI of the GB300 library for MPS time evolution of the
+ * ab-initio electronic Schroedinger equation (Frahm & Pfannkuche,
+ * "Ultrafast ab-initio Quantum Chemistry Using Matrix Product States").
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Units: atomic units, hbar = 1.
+ * - Orbitals i = 0..L-1, spin orbitals ordered 0up, 0down, 1up, ... as in the
+ *   paper's Eq. (fci).  Local states of one orbital: 0 = |0>, 1 = |up>,
+ *   2 = |down>, 3 = |up down> (= c+_up c+_down |0>), charges (N, 2S_z) =
+ *   (0,0), (1,1), (1,-1), (2,0).
+ * - Hamiltonian, Eq. (hamil), with integrals read in chemist order:
+ *     H = sum_{ij,s} h_ij c+_is c_js
+ *       + 1/2 sum_{ijkl,s,t} (ij|kl) c+_is c+_kt c_lt c_js + e0.
+ * - Handles own their memory; device memory comes from the context's stream
+ *   ordered pool (cudaMallocAsync on the context stream).  Host arrays passed
+ *   in are borrowed for the duration of the call and copied.
+ * - All GPU work is enqueued on the context stream.  Calls that return host
+ *   scalars or host arrays synchronise that stream before returning.
+ * - Return value 0 on success, a negative TDMPS_ERR_* code otherwise; the
+ *   message of the last error of a context is returned by tdmps_last_error.
+ *   There is no CPU fallback: when a CUDA call fails the entry point returns
+ *   TDMPS_ERR_CUDA.  A handle whose call failed stays valid and unchanged
+ *   unless stated otherwise.
+ * - Complex numbers are passed as tdmps_complex {re, im} (layout of C99
+ *   double complex).
+ */
+#ifndef TDMPS_H
+#define TDMPS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct tdmps_ctx_s* tdmps_ctx_t;
+typedef struct tdmps_mpo_s* tdmps_mpo_t;
+typedef struct tdmps_mps_s* tdmps_mps_t;
+
+typedef struct {
+  double re, im;
+} tdmps_complex;
+
+enum {
+  TDMPS_OK = 0,
+  TDMPS_ERR_INVALID_ARG = -1,
+  TDMPS_ERR_SECTOR = -2,          /* quantum numbers of operands do not match */
+  TDMPS_ERR_KRYLOV_SINGULAR = -3, /* Krylov overlap matrix has rank < 2      */
+  TDMPS_ERR_NONFINITE = -4,       /* NaN or Inf in an input or a result      */
+  TDMPS_ERR_CUDA = -5,            /* a CUDA runtime call or kernel failed    */
+  TDMPS_ERR_OOM = -6,             /* device allocation failed                */
+  TDMPS_ERR_ZERO_STATE = -7,      /* a fit target vanished on its sweep      */
+  TDMPS_ERR_NUMERIC = -8          /* an iterative kernel did not converge    */
+};
+
+/* Arithmetic of the contractions (environments, local matvecs, sums).
+ * Factorisations (QR, SVD), Krylov algebra and all norms stay FP64. */
+enum {
+  TDMPS_FP64 = 0,   /* complex FP64 everywhere                               */
+  TDMPS_TF32 = 1,   /* TF32 tensor-core products, FP32 accumulation          */
+  TDMPS_TF32X3 = 2, /* split TF32 (hi*hi + hi*lo + lo*hi), FP32 accumulation */
+  TDMPS_BF16 = 3    /* BF16 tensor-core products, FP32 accumulation          */
+};
+
+/* ---------------------------------------------------------------- context */
+
+/* Create a context on the current CUDA device.  cuda_stream: a cudaStream_t
+ * (NULL = the legacy default stream).  precision: TDMPS_FP64 .. TDMPS_BF16.
+ * Errors: INVALID_ARG (bad precision, ctx == NULL), CUDA. */
+int tdmps_create(tdmps_ctx_t* ctx, void* cuda_stream, int precision);
+int tdmps_destroy(tdmps_ctx_t ctx);
+/* Message of the last failed call on ctx ("" if none).  Owned by ctx. */
+const char* tdmps_last_error(tdmps_ctx_t ctx);
+/* Message of the last failed tdmps_create on this thread. */
+const char* tdmps_create_error(void);
+int tdmps_set_precision(tdmps_ctx_t ctx, int precision);
+
+/* Sweep schedule of every variational fit (paper Sec. 2.2.1, "Operations on
+ * MPS", Eq. add_min; "after ~10 sweeps"): n_two_site two-site sweeps (each a
+ * left-to-right and a right-to-left half sweep, truncated SVD of every
+ * two-site tensor) followed by n_one_site one-site sweeps (QR / LQ gauge
+ * moves, bond dimensions fixed).  Defaults: 2 and 2.  Errors: INVALID_ARG if
+ * either is negative or both are 0. */
+int tdmps_set_schedule(tdmps_ctx_t ctx, int n_two_site, int n_one_site);
+
+/* ------------------------------------------------------------------- MPO */
+
+/* Matrix product operator of Eq. (hamil) (paper Sec. 2.2 "Time Evolution
+ * Methods").  h: L*L row-major, symmetric.  eri: L^4 row-major (ij|kl).
+ * n_elec: electrons of the states it will act on (only checked by later
+ * calls).  Terms are split at every bond into left and right operator
+ * strings; a channel carries either the left string (coefficient applied
+ * later) or the right string (coefficients already summed into the left
+ * operator), whichever side holds fewer operators, ties going to the left
+ * half of the chain; fermionic signs follow the Jordan-Wigner order of the
+ * spin orbitals.  Errors: INVALID_ARG (L < 1 or > 64, NULL arrays),
+ * NONFINITE, CUDA, OOM. */
+int tdmps_build_mpo(tdmps_ctx_t ctx, const double* h, const double* eri, int L,
+                    int n_elec, double e0, tdmps_mpo_t* out);
+/* ctx may be NULL: the MPO is then built on the host only (no GPU needed);
+ * its device tables are uploaded on first use by a context. */
+
+/* Channel count of every bond (bond_dims[L+1]) and total stored elements. */
+int tdmps_mpo_info(tdmps_mpo_t mpo, int* bond_dims, int64_t* n_elements);
+/* Host copy of the stored elements of W_site, 0 <= site < L: entry e is the
+ * matrix element <sig|W[w_in, w_out]|sigp> = v[e] between channel w_in of
+ * bond `site` and channel w_out of bond site+1.  *count is the capacity on
+ * entry and the number of elements on return; with win == NULL only the
+ * number is returned.  No GPU is needed. */
+int tdmps_mpo_elements(tdmps_mpo_t mpo, int site, int64_t* count, int* win, int* wout, int* sig,
+                       int* sigp, double* v);
+int tdmps_mpo_free(tdmps_mpo_t mpo);
+
+/* ------------------------------------------------------------------- MPS */
+
+/* Product state of one determinant (paper Eq. mps with bond dimension 1).
+ * occ[L]: 0 = empty, 1 = up, 2 = down, 3 = both.  Errors: INVALID_ARG. */
+int tdmps_mps_from_determinant(tdmps_ctx_t ctx, int L, const uint8_t* occ,
+                               tdmps_mps_t* out);
+
+/* Import dense site tensors with labelled bonds (Eq. mps).
+ * bond_dims[L+1]: dimensions D_0..D_L (D_0 = 1 with label (0,0)).
+ * labels: for k = 0..L, D_k pairs (N, 2S_z) concatenated (int32 pairs).
+ * tensors[i]: host array D_i x 4 x D_{i+1}, row-major, complex.
+ * Entries that violate charge conservation must be zero (INVALID_ARG
+ * otherwise, SECTOR if D_L is not 1). */
+int tdmps_mps_import(tdmps_ctx_t ctx, int L, const int* bond_dims, const int* labels,
+                     const tdmps_complex* const* tensors, tdmps_mps_t* out);
+/* Export: with tensors == NULL only bond_dims (L+1 entries) is written; then
+ * call again with labels (sum D_k pairs) and tensors[i] of D_i*4*D_{i+1}. */
+int tdmps_mps_export(tdmps_ctx_t ctx, tdmps_mps_t mps, int* bond_dims, int* labels,
+                     tdmps_complex* const* tensors);
+int tdmps_mps_info(tdmps_mps_t mps, int* L, int* n_elec, int* two_sz, int* max_bond);
+int tdmps_mps_copy(tdmps_ctx_t ctx, tdmps_mps_t in, tdmps_mps_t* out);
+int tdmps_mps_free(tdmps_mps_t mps);
+
+/* ---------------------------------------------------------- operations */
+
+/* out ~ alpha * H |in> by variational fitting (Sec. 2.2.1, Eq. add_min) at
+ * bond dimension <= D, discarding at most a relative weight eps per
+ * truncation; n_sweeps > 0 overrides the one-site sweep count of the
+ * schedule (n_sweeps <= 0 keeps it).  The initial guess is `in`.
+ * The result is right-canonical with its norm on site 0. */
+int tdmps_apply_H(tdmps_ctx_t ctx, tdmps_mpo_t mpo, tdmps_mps_t in, tdmps_complex alpha,
+                  int D, double eps, int n_sweeps, tdmps_mps_t* out);
+
+/* out ~ sum_k coefs[k] |terms[k]> (Eqs. sum_exact, add_min), guess terms[0]. */
+int tdmps_sum(tdmps_ctx_t ctx, int n_terms, const tdmps_complex* coefs,
+              const tdmps_mps_t* terms, int D, double eps, tdmps_mps_t* out);
+
+/* <bra|ket> (the contraction of two chains of Eq. mps). */
+int tdmps_overlap(tdmps_ctx_t ctx, tdmps_mps_t bra, tdmps_mps_t ket, tdmps_complex* out);
+
+/* <bra|H|ket> with the MPO (Sec. 2.2.3, H_ij of Eq. krylov_evo). */
+int tdmps_expectation(tdmps_ctx_t ctx, tdmps_mpo_t mpo, tdmps_mps_t bra, tdmps_mps_t ket,
+                      tdmps_complex* out);
+
+/* SVD compression in place (Sec. 2.1: keep the D largest singular values):
+ * right-canonicalise, one left-to-right pass of truncated SVDs, exact LQ pass
+ * back.  discarded_weight (may be NULL): sum over bonds of the relative
+ * discarded weight. */
+int tdmps_compress(tdmps_ctx_t ctx, tdmps_mps_t inout, int D, double eps,
+                   double* discarded_weight);
+
+/* One RK4 step in place (Sec. 2.2.2, stages k1..k4 with k = -i dt H(...),
+ * Eq. rk_add): four fitted H applications and four fitted sums. */
+int tdmps_rk4_step(tdmps_ctx_t ctx, tdmps_mpo_t mpo, tdmps_mps_t inout, double dt, int D,
+                   double eps);
+
+/* One Krylov step in place (Sec. 2.2.3) with m >= 2 basis vectors including
+ * phi_0 = psi.  orthogonal != 0: Eq. (kry_orth) (fit of H phi_k, then a
+ * fitted sum subtracting <phi_j|H|phi_k>/<phi_j|phi_j> phi_j); otherwise
+ * Eq. (kry_non).  Each new vector is normalised.  The new state is the fitted
+ * sum of Eq. (krylov_evo) with N and H measured exactly; exp(-i dt N^-1 H) e0
+ * uses canonical orthogonalisation of N (eigenvalues below 1e-12 * max are
+ * dropped; KRYLOV_SINGULAR if fewer than 2 remain, inout unchanged). */
+int tdmps_krylov_step(tdmps_ctx_t ctx, tdmps_mpo_t mpo, tdmps_mps_t inout, double dt, int m,
+                      int orthogonal, int D, double eps);
+
+/* gamma_ij = sum_s <psi| c+_is c_js |psi> (Sec. 3.2, the 1BRDM), not
+ * normalised by <psi|psi>.  gamma: host array L*L row-major. */
+int tdmps_one_rdm(tdmps_ctx_t ctx, tdmps_mps_t psi, tdmps_complex* gamma);
+
+/* ------------------------------------------------------------ statistics */
+
+/* Per-kernel-class timing with CUDA events on the context stream, and the
+ * algorithmic work of every launch (block-sparse FLOPs / bytes, padding
+ * excluded).  Classes: see TDMPS_KSTAT_*. */
+enum {
+  TDMPS_KSTAT_GEMM = 0,     /* block contractions (environments, matvecs)  */
+  TDMPS_KSTAT_WSTAGE = 1,   /* sparse MPO-tensor application                */
+  TDMPS_KSTAT_QR = 2,
+  TDMPS_KSTAT_SVD = 3,
+  TDMPS_KSTAT_OTHER = 4,
+  TDMPS_KSTAT_COUNT = 5
+};
+typedef struct {
+  int64_t launches;
+  double ms;        /* summed event time of those launches   */
+  double flops;     /* algorithmic real FLOPs                */
+  double bytes;     /* algorithmic bytes read + written      */
+} tdmps_kstat;
+int tdmps_stats_enable(tdmps_ctx_t ctx, int enable);
+int tdmps_stats_reset(tdmps_ctx_t ctx);
+int tdmps_stats_get(tdmps_ctx_t ctx, int kind, tdmps_kstat* out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TDMPS_H */

@@ -1,0 +1,324 @@
+"""Python binding of the tdmps CUDA library (GB300, sm_103a).
+
+Thin ctypes marshalling around the C ABI declared in ``include/tdmps.h``:
+every computation runs in the library's CUDA kernels.  PyTorch supplies the
+CUDA stream (``torch.cuda.current_stream()``) and device selection.  If the
+compiled library is missing, every entry point raises ``TdmpsError`` -- there
+is no Python or CPU fallback.
+
+Entry points keep the names of the C ABI without the ``tdmps_`` prefix
+(``tdmps_sum`` is ``mps_sum`` here, to avoid shadowing the builtin).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libtdmps.so")
+HEADER = os.path.join(os.path.dirname(_HERE), "include", "tdmps.h")
+
+FP64, TF32, TF32X3, BF16 = 0, 1, 2, 3
+PRECISION = {"fp64": FP64, "tf32": TF32, "tf32x3": TF32X3, "bf16": BF16}
+KSTAT = {"gemm": 0, "wstage": 1, "qr": 2, "svd": 3, "other": 4}
+ERRORS = {-1: "INVALID_ARG", -2: "SECTOR", -3: "KRYLOV_SINGULAR", -4: "NONFINITE",
+          -5: "CUDA", -6: "OOM", -7: "ZERO_STATE", -8: "NUMERIC"}
+
+
+class TdmpsError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s (%d): %s" % (ERRORS.get(code, "?"), code, msg))
+        self.code = code
+        self.name = ERRORS.get(code, "?")
+
+
+class Complex(ctypes.Structure):
+    _fields_ = [("re", ctypes.c_double), ("im", ctypes.c_double)]
+
+
+class KStat(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_int64), ("ms", ctypes.c_double),
+                ("flops", ctypes.c_double), ("bytes", ctypes.c_double)]
+
+
+_lib = None
+P = ctypes.c_void_p
+I = ctypes.c_int
+D = ctypes.c_double
+I64 = ctypes.c_int64
+_SIGS = {
+    "tdmps_create": (I, [ctypes.POINTER(P), P, I]),
+    "tdmps_destroy": (I, [P]),
+    "tdmps_last_error": (ctypes.c_char_p, [P]),
+    "tdmps_create_error": (ctypes.c_char_p, []),
+    "tdmps_set_precision": (I, [P, I]),
+    "tdmps_set_schedule": (I, [P, I, I]),
+    "tdmps_build_mpo": (I, [P, P, P, I, I, D, ctypes.POINTER(P)]),
+    "tdmps_mpo_info": (I, [P, P, ctypes.POINTER(I64)]),
+    "tdmps_mpo_elements": (I, [P, I, ctypes.POINTER(I64), P, P, P, P, P]),
+    "tdmps_mpo_free": (I, [P]),
+    "tdmps_mps_from_determinant": (I, [P, I, P, ctypes.POINTER(P)]),
+    "tdmps_mps_import": (I, [P, I, P, P, P, ctypes.POINTER(P)]),
+    "tdmps_mps_export": (I, [P, P, P, P, P]),
+    "tdmps_mps_info": (I, [P, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I),
+                           ctypes.POINTER(I)]),
+    "tdmps_mps_copy": (I, [P, P, ctypes.POINTER(P)]),
+    "tdmps_mps_free": (I, [P]),
+    "tdmps_apply_H": (I, [P, P, P, Complex, I, D, I, ctypes.POINTER(P)]),
+    "tdmps_sum": (I, [P, I, P, P, I, D, ctypes.POINTER(P)]),
+    "tdmps_overlap": (I, [P, P, P, ctypes.POINTER(Complex)]),
+    "tdmps_expectation": (I, [P, P, P, P, ctypes.POINTER(Complex)]),
+    "tdmps_compress": (I, [P, P, I, D, ctypes.POINTER(D)]),
+    "tdmps_rk4_step": (I, [P, P, P, D, I, D]),
+    "tdmps_krylov_step": (I, [P, P, P, D, I, I, I, D]),
+    "tdmps_one_rdm": (I, [P, P, P]),
+    "tdmps_stats_enable": (I, [P, I]),
+    "tdmps_stats_reset": (I, [P]),
+    "tdmps_stats_get": (I, [P, I, ctypes.POINTER(KStat)]),
+}
+
+
+def lib() -> ctypes.CDLL:
+    """The loaded C library (raises TdmpsError if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise TdmpsError(-5, "CUDA library %s is not built; run "
+                                 "paper_1902_08489_gb300.build.build()" % LIB_PATH)
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def header_symbols() -> list[str]:
+    """Entry points declared in include/tdmps.h."""
+    txt = open(HEADER).read()
+    return sorted(set(re.findall(r"^\s*(?:int|const char\*)\s+(tdmps_\w+)\(", txt, re.M)))
+
+
+def _check(code, ctx=None):
+    if code != 0:
+        msg = lib().tdmps_last_error(ctx.h if ctx is not None else None)
+        raise TdmpsError(code, (msg or b"").decode())
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+class Context:
+    """Library context bound to a CUDA stream (default: torch's current)."""
+
+    def __init__(self, precision="fp64", stream=None, device=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise TdmpsError(-5, "no CUDA device available")
+        if device is not None:
+            torch.cuda.set_device(device)
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        handle = getattr(stream, "cuda_stream", stream)
+        h = ctypes.c_void_p()
+        prec = PRECISION[precision] if isinstance(precision, str) else int(precision)
+        code = lib().tdmps_create(ctypes.byref(h), ctypes.c_void_p(handle), prec)
+        if code != 0:
+            raise TdmpsError(code, lib().tdmps_create_error().decode())
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().tdmps_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_precision(self, precision):
+        prec = PRECISION[precision] if isinstance(precision, str) else int(precision)
+        _check(lib().tdmps_set_precision(self.h, prec), self)
+
+    def set_schedule(self, n_two_site: int, n_one_site: int):
+        _check(lib().tdmps_set_schedule(self.h, n_two_site, n_one_site), self)
+
+    # statistics
+    def stats_enable(self, on=True):
+        _check(lib().tdmps_stats_enable(self.h, 1 if on else 0), self)
+
+    def stats_reset(self):
+        _check(lib().tdmps_stats_reset(self.h), self)
+
+    def stats(self) -> dict:
+        out = {}
+        for name, k in KSTAT.items():
+            s = KStat()
+            _check(lib().tdmps_stats_get(self.h, k, ctypes.byref(s)), self)
+            out[name] = dict(launches=s.launches, ms=s.ms, flops=s.flops, bytes=s.bytes)
+        return out
+
+
+class MPO:
+    def __init__(self, handle, L):
+        self.h = handle
+        self.L = L
+
+    def bond_dims(self):
+        d = np.zeros(self.L + 1, dtype=np.int32)
+        n = ctypes.c_int64()
+        _check(lib().tdmps_mpo_info(self.h, _ptr(d), ctypes.byref(n)))
+        return d, n.value
+
+    def elements(self, site: int):
+        n = ctypes.c_int64(0)
+        _check(lib().tdmps_mpo_elements(self.h, site, ctypes.byref(n), None, None, None, None, None))
+        a = [np.zeros(n.value, dtype=np.int32) for _ in range(4)]
+        v = np.zeros(n.value)
+        _check(lib().tdmps_mpo_elements(self.h, site, ctypes.byref(n), *[_ptr(x) for x in a], _ptr(v)))
+        return (*a, v)
+
+    def free(self):
+        if self.h:
+            lib().tdmps_mpo_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+class MPS:
+    def __init__(self, ctx: Context, handle):
+        self.ctx = ctx
+        self.h = handle
+
+    def info(self):
+        L, n, s, mb = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _check(lib().tdmps_mps_info(self.h, ctypes.byref(L), ctypes.byref(n), ctypes.byref(s),
+                                    ctypes.byref(mb)))
+        return dict(L=L.value, n_elec=n.value, two_sz=s.value, max_bond=mb.value)
+
+    def export(self):
+        """(tensors, labels) as dense complex arrays with bond labels."""
+        L = self.info()["L"]
+        dims = np.zeros(L + 1, dtype=np.int32)
+        _check(lib().tdmps_mps_export(self.ctx.h, self.h, _ptr(dims), None, None), self.ctx)
+        labels = np.zeros(2 * int(dims.sum()), dtype=np.int32)
+        tens = [np.zeros((dims[i], 4, dims[i + 1]), dtype=np.complex128) for i in range(L)]
+        arr = (ctypes.c_void_p * L)(*[t.ctypes.data for t in tens])
+        _check(lib().tdmps_mps_export(self.ctx.h, self.h, _ptr(dims), _ptr(labels), arr), self.ctx)
+        labs, off = [], 0
+        for k in range(L + 1):
+            labs.append(labels[2 * off:2 * (off + dims[k])].reshape(-1, 2).astype(np.int64))
+            off += dims[k]
+        return tens, labs
+
+    def copy(self):
+        h = ctypes.c_void_p()
+        _check(lib().tdmps_mps_copy(self.ctx.h, self.h, ctypes.byref(h)), self.ctx)
+        return MPS(self.ctx, h)
+
+    def free(self):
+        if self.h:
+            lib().tdmps_mps_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+# ---------------------------------------------------------------- entry points
+
+def build_mpo(ctx, h, eri, L=None, n_elec=0, e0=0.0) -> MPO:
+    """MPO of the Hamiltonian (h: L x L, eri: L^4 chemist order).  ctx may be
+    None for a host-only MPO (inspection without a GPU)."""
+    h = np.ascontiguousarray(h, dtype=np.float64)
+    eri = np.ascontiguousarray(eri, dtype=np.float64)
+    L = h.shape[0] if L is None else L
+    out = ctypes.c_void_p()
+    _check(lib().tdmps_build_mpo(ctx.h if ctx else None, _ptr(h), _ptr(eri), L, n_elec, e0,
+                                 ctypes.byref(out)), ctx)
+    return MPO(out, L)
+
+
+def mps_from_determinant(ctx, occ) -> MPS:
+    o = np.ascontiguousarray(occ, dtype=np.uint8)
+    out = ctypes.c_void_p()
+    _check(lib().tdmps_mps_from_determinant(ctx.h, len(o), _ptr(o), ctypes.byref(out)), ctx)
+    return MPS(ctx, out)
+
+
+def mps_import(ctx, tensors, labels) -> MPS:
+    L = len(tensors)
+    dims = np.array([len(q) for q in labels], dtype=np.int32)
+    lab = np.ascontiguousarray(np.concatenate([np.asarray(q).reshape(-1, 2) for q in labels]),
+                               dtype=np.int32)
+    tens = [np.ascontiguousarray(t, dtype=np.complex128) for t in tensors]
+    arr = (ctypes.c_void_p * L)(*[t.ctypes.data for t in tens])
+    out = ctypes.c_void_p()
+    _check(lib().tdmps_mps_import(ctx.h, L, _ptr(dims), _ptr(lab), arr, ctypes.byref(out)), ctx)
+    return MPS(ctx, out)
+
+
+def apply_H(ctx, mpo, mps, alpha=1.0, D=64, eps=0.0, n_sweeps=0) -> MPS:
+    out = ctypes.c_void_p()
+    a = complex(alpha)
+    _check(lib().tdmps_apply_H(ctx.h, mpo.h, mps.h, Complex(a.real, a.imag), D, eps, n_sweeps,
+                               ctypes.byref(out)), ctx)
+    return MPS(ctx, out)
+
+
+def mps_sum(ctx, coefs, terms, D=64, eps=0.0) -> MPS:
+    n = len(terms)
+    cs = (Complex * n)(*[Complex(complex(c).real, complex(c).imag) for c in coefs])
+    ts = (ctypes.c_void_p * n)(*[t.h.value if isinstance(t.h, ctypes.c_void_p) else t.h for t in terms])
+    out = ctypes.c_void_p()
+    _check(lib().tdmps_sum(ctx.h, n, cs, ts, D, eps, ctypes.byref(out)), ctx)
+    return MPS(ctx, out)
+
+
+def overlap(ctx, bra, ket) -> complex:
+    r = Complex()
+    _check(lib().tdmps_overlap(ctx.h, bra.h, ket.h, ctypes.byref(r)), ctx)
+    return complex(r.re, r.im)
+
+
+def expectation(ctx, mpo, bra, ket) -> complex:
+    r = Complex()
+    _check(lib().tdmps_expectation(ctx.h, mpo.h, bra.h, ket.h, ctypes.byref(r)), ctx)
+    return complex(r.re, r.im)
+
+
+def compress(ctx, mps, D, eps=0.0) -> float:
+    d = ctypes.c_double()
+    _check(lib().tdmps_compress(ctx.h, mps.h, D, eps, ctypes.byref(d)), ctx)
+    return d.value
+
+
+def rk4_step(ctx, mpo, mps, dt, D, eps=0.0):
+    _check(lib().tdmps_rk4_step(ctx.h, mpo.h, mps.h, dt, D, eps), ctx)
+
+
+def krylov_step(ctx, mpo, mps, dt, m, orthogonal=True, D=64, eps=0.0):
+    _check(lib().tdmps_krylov_step(ctx.h, mpo.h, mps.h, dt, m, 1 if orthogonal else 0, D, eps), ctx)
+
+
+def one_rdm(ctx, mps) -> np.ndarray:
+    L = mps.info()["L"]
+    g = np.zeros((L, L), dtype=np.complex128)
+    _check(lib().tdmps_one_rdm(ctx.h, mps.h, _ptr(g)), ctx)
+    return g

@@ -1,0 +1,1516 @@
+// Host engine: block-sparse planners and the paper's algorithms.
+//
+// Environment and local-tensor contractions (paper Sec. 2.2.1, "Operations
+// on MPS"): the local solution of Eq. (add_min) at site i in the
+// mixed-canonical gauge is
+//     C[a, s, b] = sum L[a, w, a'] W[w, w', s, s'] A[a', s', b'] R[b, w', b'],
+// evaluated as three stages on symmetry blocks:
+//   L-stage  X[a][w][s'][b'] = L[a][w][a'] A[a'][s'][b']        (block GEMM)
+//   W-stage  Y[a][s][w'][b'] = sum W[w,w',s,s'] X[a][w][s'][b']  (sparse)
+//   R-stage  C[a][s][b]      = sum_{w',b'} Y[a][s][w'][b'] R[b][w'][b']
+// and the environment updates reuse the first two stages
+//   L_new[b][w'][b'] = sum_{a,s} conj(C[a][s][b]) Y[a][s][w'][b'].
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "engine.hpp"
+
+namespace tdmps {
+
+// ------------------------------------------------------------------ memory, bonds
+
+DevMem::DevMem(size_t b, cudaStream_t s) : bytes(b), st(s) {
+  if (b == 0) return;
+  cudaError_t e = cudaMallocAsync(&p, b, s);
+  if (e != cudaSuccess) {
+    p = nullptr;
+    throw Error(e == cudaErrorMemoryAllocation ? TDMPS_ERR_OOM : TDMPS_ERR_CUDA,
+                std::string("cudaMallocAsync: ") + cudaGetErrorString(e));
+  }
+}
+DevMem::~DevMem() {
+  if (p) cudaFreeAsync(p, st);
+}
+DevPtr dev_alloc(size_t bytes, cudaStream_t st) { return std::make_shared<DevMem>(bytes, st); }
+
+int Bond::find(const QN& x) const {
+  auto it = std::lower_bound(q.begin(), q.end(), x);
+  if (it == q.end() || *it != x) return -1;
+  return (int)(it - q.begin());
+}
+int Bond::total() const {
+  int t = 0;
+  for (int v : d) t += v;
+  return t;
+}
+int MPOBond::find(const QN& x) const {
+  auto it = std::lower_bound(gq.begin(), gq.end(), x);
+  if (it == gq.end() || *it != x) return -1;
+  return (int)(it - gq.begin());
+}
+
+RowGroups RowGroups::from_bond(const Bond& b) {
+  RowGroups r;
+  r.q = b.q;
+  r.d = b.d;
+  for (int i = 0; i < b.nsec(); ++i) { r.sa.push_back(i); r.sig.push_back(-1); }
+  return r;
+}
+RowGroups RowGroups::fused(const Bond& b) {
+  RowGroups r;
+  for (int i = 0; i < b.nsec(); ++i)
+    for (int s = 0; s < 4; ++s) {
+      r.q.push_back(b.q[i] + SITE_Q[s]);
+      r.d.push_back(b.d[i]);
+      r.sa.push_back(i);
+      r.sig.push_back(s);
+    }
+  return r;
+}
+
+SiteT make_site(const RowGroups& rows, const Bond& right, cudaStream_t st, bool zero) {
+  SiteT t;
+  t.index.assign((size_t)rows.n() * 4, -1);
+  for (int r = 0; r < rows.n(); ++r)
+    for (int s = 0; s < 4; ++s) {
+      int sb = right.find(rows.q[r] + SITE_Q[s]);
+      if (sb < 0) continue;
+      t.index[(size_t)r * 4 + s] = (int)t.blocks.size();
+      t.blocks.push_back({r, s, sb, rows.d[r], right.d[sb], t.size});
+      t.size += (size_t)rows.d[r] * right.d[sb];
+    }
+  t.data = dev_alloc(std::max<size_t>(t.size, 1) * sizeof(double2), st);
+  if (zero) launch_zero((double2*)t.data->p, t.size, st);
+  return t;
+}
+
+void Inter::alloc(cudaStream_t st, bool zero) {
+  data = dev_alloc(std::max<size_t>(size, 1) * sizeof(double2), st);
+  if (zero) launch_zero((double2*)data->p, size, st);
+}
+
+// ------------------------------------------------------------------ context
+
+Context::Context(cudaStream_t s, int prec) : st(s), precision(prec) {
+  ring_cap = (size_t)64 << 20;
+  TD_CHECK_CUDA(cudaMallocHost((void**)&h_ring, ring_cap));
+  TD_CHECK_CUDA(cudaMalloc((void**)&d_ring, ring_cap));
+  status = dev_alloc(64, st);
+  TD_CHECK_CUDA(cudaMemsetAsync(status->p, 0, 64, st));
+}
+
+Context::~Context() {
+  cudaStreamSynchronize(st);
+  for (auto& p : pending) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
+  ident.reset();
+  rdm.reset();
+  status.reset();
+  cudaStreamSynchronize(st);
+  if (h_ring) cudaFreeHost(h_ring);
+  if (d_ring) cudaFree(d_ring);
+}
+
+const void* Context::stage(const void* src, size_t bytes) {
+  size_t need = (bytes + 255) & ~(size_t)255;
+  if (need > ring_cap) {
+    // oversize: dedicated buffer released after the stream passes it
+    DevPtr b = dev_alloc(need, st);
+    TD_CHECK_CUDA(cudaMemcpyAsync(b->p, src, bytes, cudaMemcpyHostToDevice, st));
+    TD_CHECK_CUDA(cudaStreamSynchronize(st));
+    static std::vector<DevPtr> keep;
+    keep.push_back(b);
+    return b->p;
+  }
+  if (ring_off + need > ring_cap) {
+    TD_CHECK_CUDA(cudaStreamSynchronize(st));
+    ring_off = 0;
+  }
+  std::memcpy(h_ring + ring_off, src, bytes);
+  TD_CHECK_CUDA(cudaMemcpyAsync(d_ring + ring_off, h_ring + ring_off, bytes,
+                                cudaMemcpyHostToDevice, st));
+  const void* out = d_ring + ring_off;
+  ring_off += need;
+  return out;
+}
+
+void Context::kbegin(int kind, cudaEvent_t* a) {
+  (void)kind;
+  *a = nullptr;
+  if (!stats) return;
+  TD_CHECK_CUDA(cudaEventCreate(a));
+  TD_CHECK_CUDA(cudaEventRecord(*a, st));
+}
+
+void Context::kend(int kind, cudaEvent_t a, double flops, double bytes) {
+  TD_CHECK_CUDA(cudaGetLastError());
+  if (!stats) return;
+  cudaEvent_t b;
+  TD_CHECK_CUDA(cudaEventCreate(&b));
+  TD_CHECK_CUDA(cudaEventRecord(b, st));
+  pending.push_back({kind, a, b});
+  kstat[kind].launches += 1;
+  kstat[kind].flops += flops;
+  kstat[kind].bytes += bytes;
+}
+
+void Context::collect_stats() {
+  TD_CHECK_CUDA(cudaStreamSynchronize(st));
+  for (auto& p : pending) {
+    float ms = 0.f;
+    TD_CHECK_CUDA(cudaEventElapsedTime(&ms, p.a, p.b));
+    kstat[p.kind].ms += ms;
+    cudaEventDestroy(p.a);
+    cudaEventDestroy(p.b);
+  }
+  pending.clear();
+}
+
+void Context::sync() { TD_CHECK_CUDA(cudaStreamSynchronize(st)); }
+
+const MPOd& Context::identity_mpo(int L) {
+  if (!ident || ident->L != L) {
+    ident.reset(new MPOd(build_identity_mpo(L)));
+    upload_mpo_tables(*ident, *this);
+  }
+  return *ident;
+}
+
+const MPOd& Context::rdm_mpo(int L) {
+  if (!rdm || rdm->L != L) {
+    rdm.reset(new MPOd(build_rdm_mpo(L)));
+    upload_mpo_tables(*rdm, *this);
+  }
+  return *rdm;
+}
+
+// ------------------------------------------------------------------ MPO tables
+
+void upload_mpo_tables(MPOd& m, Context& c) {
+  std::vector<int> rowptr, ent_w;
+  std::vector<double> ent_v;
+  m.tab_left.assign(m.L, {});
+  m.tab_right.assign(m.L, {});
+  m.tab_left_idx.assign(m.L, {});
+  m.tab_right_idx.assign(m.L, {});
+  for (int i = 0; i < m.L; ++i) {
+    const MPOBond& bi = m.bonds[i];
+    const MPOBond& bo = m.bonds[i + 1];
+    // left: key (sig, sigp, g_out) rows over w_out
+    std::map<std::array<int, 3>, std::vector<const WElem*>> L, R;
+    for (const WElem& e : m.W[i]) {
+      L[{e.sig, e.sigp, bo.ch_group[e.wout]}].push_back(&e);
+      R[{e.sig, e.sigp, bi.ch_group[e.win]}].push_back(&e);
+    }
+    for (auto& kv : L) {
+      int gout = kv.first[2];
+      int rows = bo.gsize[gout];
+      int gin = bi.ch_group[kv.second[0]->win];
+      std::vector<std::vector<std::pair<int, double>>> perrow(rows);
+      for (auto* e : kv.second) {
+        if (bi.ch_group[e->win] != gin) throw Error(TDMPS_ERR_SECTOR, "MPO charge inconsistency");
+        perrow[bo.ch_local[e->wout]].push_back({bi.ch_local[e->win], e->v});
+      }
+      WTable t{kv.first[0], kv.first[1], gout, gin, rows, (int)rowptr.size()};
+      for (int r = 0; r < rows; ++r) {
+        rowptr.push_back((int)ent_w.size());
+        for (auto& pv : perrow[r]) { ent_w.push_back(pv.first); ent_v.push_back(pv.second); }
+      }
+      rowptr.push_back((int)ent_w.size());
+      m.tab_left_idx[i][kv.first] = (int)m.tab_left[i].size();
+      m.tab_left[i].push_back(t);
+    }
+    for (auto& kv : R) {
+      int gin = kv.first[2];
+      int rows = bi.gsize[gin];
+      int gout = bo.ch_group[kv.second[0]->wout];
+      std::vector<std::vector<std::pair<int, double>>> perrow(rows);
+      for (auto* e : kv.second) {
+        if (bo.ch_group[e->wout] != gout) throw Error(TDMPS_ERR_SECTOR, "MPO charge inconsistency");
+        perrow[bi.ch_local[e->win]].push_back({bo.ch_local[e->wout], e->v});
+      }
+      WTable t{kv.first[0], kv.first[1], gout, gin, rows, (int)rowptr.size()};
+      for (int r = 0; r < rows; ++r) {
+        rowptr.push_back((int)ent_w.size());
+        for (auto& pv : perrow[r]) { ent_w.push_back(pv.first); ent_v.push_back(pv.second); }
+      }
+      rowptr.push_back((int)ent_w.size());
+      m.tab_right_idx[i][kv.first] = (int)m.tab_right[i].size();
+      m.tab_right[i].push_back(t);
+    }
+  }
+  m.rowptr = dev_alloc(std::max<size_t>(rowptr.size(), 1) * sizeof(int), c.st);
+  m.ent_w = dev_alloc(std::max<size_t>(ent_w.size(), 1) * sizeof(int), c.st);
+  m.ent_v = dev_alloc(std::max<size_t>(ent_v.size(), 1) * sizeof(double), c.st);
+  if (!rowptr.empty())
+    TD_CHECK_CUDA(cudaMemcpyAsync(m.rowptr->p, rowptr.data(), rowptr.size() * sizeof(int),
+                                  cudaMemcpyHostToDevice, c.st));
+  if (!ent_w.empty()) {
+    TD_CHECK_CUDA(cudaMemcpyAsync(m.ent_w->p, ent_w.data(), ent_w.size() * sizeof(int),
+                                  cudaMemcpyHostToDevice, c.st));
+    TD_CHECK_CUDA(cudaMemcpyAsync(m.ent_v->p, ent_v.data(), ent_v.size() * sizeof(double),
+                                  cudaMemcpyHostToDevice, c.st));
+  }
+  // host vectors must outlive the async copies
+  TD_CHECK_CUDA(cudaStreamSynchronize(c.st));
+}
+
+// ------------------------------------------------------------------ batches
+
+namespace {
+
+struct GemmBatch {
+  std::vector<GemmTask> tasks;
+  std::vector<GemmTerm> terms;
+  double flops = 0.0, bytes = 0.0;
+  void task(double2* C, int M, int N, int ldc, int opA, int opB, bool beta, cplx alpha,
+            const double2* aptr = nullptr, const double2* adiv = nullptr) {
+    GemmTask t{};
+    t.C = C;
+    t.alpha_ptr = aptr;
+    t.alpha_div = adiv;
+    t.alpha = make_double2(alpha.real(), alpha.imag());
+    t.M = M; t.N = N; t.ldc = ldc;
+    t.opA = opA; t.opB = opB; t.beta = beta ? 1 : 0;
+    t.term_begin = t.term_end = (int)terms.size();
+    tasks.push_back(t);
+    bytes += 16.0 * M * N * (beta ? 2.0 : 1.0);
+  }
+  void term(const double2* A, int lda, const double2* B, int ldb, int K) {
+    if (K <= 0) return;
+    GemmTask& t = tasks.back();
+    terms.push_back({A, B, K, lda, ldb, 0});
+    t.term_end = (int)terms.size();
+    flops += 8.0 * t.M * t.N * K;
+    bytes += 16.0 * ((double)t.M * K + (double)K * t.N);
+  }
+  void run(Context& c) {
+    std::vector<int> tile_task;
+    std::vector<GemmTask> tk;
+    for (auto& t : tasks) {
+      if (t.M <= 0 || t.N <= 0) continue;
+      t.tiles_m = (t.M + 31) / 32;
+      int tn = (t.N + 31) / 32;
+      t.tile_base = (int)tile_task.size();
+      int id = (int)tk.size();
+      tk.push_back(t);
+      for (int q = 0; q < t.tiles_m * tn; ++q) tile_task.push_back(id);
+    }
+    if (tile_task.empty()) return;
+    const GemmTask* dt = c.stage(tk);
+    const GemmTerm* dm = terms.empty() ? nullptr : c.stage(terms);
+    const int* dtt = c.stage(tile_task);
+    cudaEvent_t ev;
+    c.kbegin(TDMPS_KSTAT_GEMM, &ev);
+    launch_gemm(dt, (int)tk.size(), dm, dtt, (int)tile_task.size(), c.st);
+    c.kend(TDMPS_KSTAT_GEMM, ev, flops, bytes);
+  }
+};
+
+struct WBatch {
+  std::vector<WTask> tasks;
+  int64_t work = 0;
+  double flops = 0.0, bytes = 0.0;
+  void run(Context& c, const MPOd& m) {
+    if (tasks.empty() || work == 0) return;
+    const WTask* dt = c.stage(tasks);
+    cudaEvent_t ev;
+    c.kbegin(TDMPS_KSTAT_WSTAGE, &ev);
+    launch_wstage(dt, (int)tasks.size(), work, (const int*)m.rowptr->p, (const int*)m.ent_w->p,
+                  (const double*)m.ent_v->p, c.st);
+    c.kend(TDMPS_KSTAT_WSTAGE, ev, flops, bytes);
+  }
+};
+
+}  // namespace
+
+// ------------------------------------------------------------------ environments
+
+static Env env_left_boundary(Context& c, const MPSd& bra, const MPSd& ket, const MPOd& mpo) {
+  if (bra.bonds[0].nsec() != 1 || ket.bonds[0].nsec() != 1)
+    throw Error(TDMPS_ERR_SECTOR, "left boundary bond must be one-dimensional");
+  Env e;
+  e.rows = RowGroups::from_bond(bra.bonds[0]);
+  e.mb = &mpo.bonds[0];
+  e.ket_copy = ket.bonds[0];
+  e.t.add(0, -1, 0, 0, 1, 1, 1);
+  e.t.alloc(c.st, false);
+  double2 one = make_double2(1.0, 0.0);
+  TD_CHECK_CUDA(cudaMemcpyAsync(e.t.data->p, c.stage(&one, sizeof(one)), sizeof(one),
+                                cudaMemcpyDeviceToDevice, c.st));
+  return e;
+}
+
+static Env env_right_boundary(Context& c, const MPSd& bra, const MPSd& ket, const MPOd& mpo) {
+  int L = bra.L;
+  if (bra.tot != ket.tot) throw Error(TDMPS_ERR_SECTOR, "bra and ket have different (N, 2Sz)");
+  if (mpo.bonds[L].nch() != 1) throw Error(TDMPS_ERR_SECTOR, "MPO right boundary must have one channel");
+  Env e;
+  e.rows = RowGroups::from_bond(bra.bonds[L]);
+  e.mb = &mpo.bonds[L];
+  e.ket_copy = ket.bonds[L];
+  e.t.add(0, -1, 0, 0, 1, 1, 1);
+  e.t.alloc(c.st, false);
+  double2 one = make_double2(1.0, 0.0);
+  TD_CHECK_CUDA(cudaMemcpyAsync(e.t.data->p, c.stage(&one, sizeof(one)), sizeof(one),
+                                cudaMemcpyDeviceToDevice, c.st));
+  return e;
+}
+
+// X[rg][w][s'][b'] = E[rg][w][k] A[k][s'][b']
+static Inter lstage(Context& c, const Env& E, const SiteT& ket, const Bond& ket_right) {
+  Inter X;
+  std::vector<std::pair<int, int>> src;   // (env block, ket block) per X block
+  for (int b = 0; b < (int)E.t.blocks.size(); ++b) {
+    const Inter::Blk& eb = E.t.blocks[b];
+    for (int s = 0; s < 4; ++s) {
+      int kb = ket.block_of(eb.k, s);
+      if (kb < 0) continue;
+      int sb = ket.blocks[kb].sb;
+      X.add(eb.rg, s, eb.g, sb, eb.rows, eb.W, ket_right.d[sb]);
+      src.push_back({b, kb});
+    }
+  }
+  X.alloc(c.st, false);
+  GemmBatch gb;
+  for (int x = 0; x < (int)X.blocks.size(); ++x) {
+    const Inter::Blk& xb = X.blocks[x];
+    const Inter::Blk& eb = E.t.blocks[src[x].first];
+    gb.task(X.ptr(x), xb.rows * xb.W, xb.cols, xb.cols, OP_N, OP_N, false, 1.0);
+    gb.term(E.t.ptr(src[x].first), eb.cols, ket.ptr(src[x].second), xb.cols, eb.cols);
+  }
+  gb.run(c);
+  return X;
+}
+
+// Y[rg][s][w_out][b'] = sum_{s', w_in} W[w_in, w_out, s, s'] X[rg][w_in][s'][b']
+static Inter wstage_left(Context& c, const Inter& X, const MPOd& m, int site) {
+  if (m.identity) return X;
+  const MPOBond& bi = m.bonds[site];
+  const MPOBond& bo = m.bonds[site + 1];
+  std::map<std::pair<int, int>, std::array<int, 4>> groups;
+  for (int x = 0; x < (int)X.blocks.size(); ++x) {
+    auto key = std::make_pair(X.blocks[x].rg, X.blocks[x].k);
+    auto it = groups.find(key);
+    if (it == groups.end()) it = groups.emplace(key, std::array<int, 4>{-1, -1, -1, -1}).first;
+    it->second[X.blocks[x].sig] = x;
+  }
+  Inter Y;
+  struct P { int xs[4]; int tabs[4]; };
+  std::vector<P> pend;
+  for (auto& kv : groups) {
+    for (int s = 0; s < 4; ++s) {
+      P p;
+      int gout = -1;
+      bool any = false;
+      for (int sp = 0; sp < 4; ++sp) {
+        p.xs[sp] = -1;
+        p.tabs[sp] = -1;
+        int x = kv.second[sp];
+        if (x < 0) continue;
+        int go = bo.find(bi.gq[X.blocks[x].g] + SITE_Q[s] - SITE_Q[sp]);
+        if (go < 0) continue;
+        auto it = m.tab_left_idx[site].find({s, sp, go});
+        if (it == m.tab_left_idx[site].end()) continue;
+        gout = go;
+        p.xs[sp] = x;
+        p.tabs[sp] = it->second;
+        any = true;
+      }
+      if (!any) continue;
+      const Inter::Blk& x0 = X.blocks[kv.second[0] >= 0 ? kv.second[0] : (kv.second[1] >= 0 ? kv.second[1] : (kv.second[2] >= 0 ? kv.second[2] : kv.second[3]))];
+      Y.add(kv.first.first, s, gout, kv.first.second, x0.rows, bo.gsize[gout], x0.cols);
+      pend.push_back(p);
+    }
+  }
+  Y.alloc(c.st, false);
+  WBatch wb;
+  for (int y = 0; y < (int)Y.blocks.size(); ++y) {
+    const Inter::Blk& yb = Y.blocks[y];
+    WTask t{};
+    t.Y = Y.ptr(y);
+    t.rows = yb.rows;
+    t.wout = yb.W;
+    t.cols = yb.cols;
+    t.beta = 0;
+    t.work_base = wb.work;
+    for (int sp = 0; sp < 4; ++sp) {
+      int x = pend[y].xs[sp];
+      if (x < 0) { t.X[sp] = nullptr; t.win[sp] = 0; t.csr[sp] = -1; continue; }
+      t.X[sp] = X.ptr(x);
+      t.win[sp] = X.blocks[x].W;
+      const WTable& tb = m.tab_left[site][pend[y].tabs[sp]];
+      t.csr[sp] = tb.rowptr_off;
+      wb.bytes += 16.0 * X.blocks[x].rows * X.blocks[x].W * X.blocks[x].cols;
+    }
+    int64_t n = (int64_t)yb.rows * yb.W * yb.cols;
+    wb.work += n;
+    wb.bytes += 16.0 * n;
+    wb.flops += 4.0 * n;   // at least one real x complex MAC per output
+    wb.tasks.push_back(t);
+  }
+  wb.run(c, m);
+  return Y;
+}
+
+// Z'[rb][s][w_in][a'] = sum_{s', w_out} W[w_in, w_out, s, s'] Z[rb][w_out][s'][a']
+static Inter wstage_right(Context& c, const Inter& Z, const MPOd& m, int site) {
+  if (m.identity) return Z;
+  const MPOBond& bi = m.bonds[site];
+  const MPOBond& bo = m.bonds[site + 1];
+  std::map<std::pair<int, int>, std::array<int, 4>> groups;
+  for (int z = 0; z < (int)Z.blocks.size(); ++z) {
+    auto key = std::make_pair(Z.blocks[z].rg, Z.blocks[z].k);
+    auto it = groups.find(key);
+    if (it == groups.end()) it = groups.emplace(key, std::array<int, 4>{-1, -1, -1, -1}).first;
+    it->second[Z.blocks[z].sig] = z;
+  }
+  Inter Y;
+  struct P { int xs[4]; int tabs[4]; };
+  std::vector<P> pend;
+  for (auto& kv : groups) {
+    for (int s = 0; s < 4; ++s) {
+      P p;
+      int gin = -1;
+      bool any = false;
+      int first = -1;
+      for (int sp = 0; sp < 4; ++sp) {
+        p.xs[sp] = -1;
+        p.tabs[sp] = -1;
+        int z = kv.second[sp];
+        if (z < 0) continue;
+        int gi = bi.find(bo.gq[Z.blocks[z].g] - SITE_Q[s] + SITE_Q[sp]);
+        if (gi < 0) continue;
+        auto it = m.tab_right_idx[site].find({s, sp, gi});
+        if (it == m.tab_right_idx[site].end()) continue;
+        gin = gi;
+        p.xs[sp] = z;
+        p.tabs[sp] = it->second;
+        any = true;
+        if (first < 0) first = z;
+      }
+      if (!any) continue;
+      Y.add(kv.first.first, s, gin, kv.first.second, Z.blocks[first].rows, bi.gsize[gin],
+            Z.blocks[first].cols);
+      pend.push_back(p);
+    }
+  }
+  Y.alloc(c.st, false);
+  WBatch wb;
+  for (int y = 0; y < (int)Y.blocks.size(); ++y) {
+    const Inter::Blk& yb = Y.blocks[y];
+    WTask t{};
+    t.Y = Y.ptr(y);
+    t.rows = yb.rows;
+    t.wout = yb.W;
+    t.cols = yb.cols;
+    t.beta = 0;
+    t.work_base = wb.work;
+    for (int sp = 0; sp < 4; ++sp) {
+      int z = pend[y].xs[sp];
+      if (z < 0) { t.X[sp] = nullptr; t.win[sp] = 0; t.csr[sp] = -1; continue; }
+      t.X[sp] = Z.ptr(z);
+      t.win[sp] = Z.blocks[z].W;
+      t.csr[sp] = m.tab_right[site][pend[y].tabs[sp]].rowptr_off;
+      wb.bytes += 16.0 * Z.blocks[z].rows * Z.blocks[z].W * Z.blocks[z].cols;
+    }
+    int64_t n = (int64_t)yb.rows * yb.W * yb.cols;
+    wb.work += n;
+    wb.bytes += 16.0 * n;
+    wb.flops += 4.0 * n;
+    wb.tasks.push_back(t);
+  }
+  wb.run(c, m);
+  return Y;
+}
+
+// out[rg][s][b] (+)= alpha * sum_{w', b'} Y[rg][s][w'][b'] R[b][w'][b']
+static void rstage(Context& c, const Inter& Y, const Env& R, SiteT& out, cplx alpha,
+                   const double2* alpha_dev, bool accumulate) {
+  std::map<int, std::vector<int>> rblocks;   // bra sector -> R blocks
+  for (int b = 0; b < (int)R.t.blocks.size(); ++b) rblocks[R.t.blocks[b].rg].push_back(b);
+  GemmBatch gb;
+  for (int o = 0; o < (int)out.blocks.size(); ++o) {
+    const SiteT::Blk& ob = out.blocks[o];
+    gb.task(out.ptr(o), ob.rows, ob.cols, ob.cols, OP_N, OP_T, accumulate, alpha, alpha_dev);
+    auto it = rblocks.find(ob.sb);
+    if (it == rblocks.end()) continue;
+    for (int rb : it->second) {
+      const Inter::Blk& r = R.t.blocks[rb];
+      int y = Y.find(ob.r, ob.sig, r.g, r.k);
+      if (y < 0) continue;
+      int K = r.W * r.cols;
+      gb.term(Y.ptr(y), K, R.t.ptr(rb), K, K);
+    }
+  }
+  gb.run(c);
+}
+
+// L_new[b][w'][b'] = sum_{a, s} conj(C[a][s][b]) Y[a][s][w'][b']
+static Env env_from_Y_left(Context& c, const Inter& Y, const SiteT& bra, const Bond& bra_right,
+                           const MPOBond& mb, const Bond& ket_right) {
+  Env e;
+  e.rows = RowGroups::from_bond(bra_right);
+  e.mb = &mb;
+  e.ket_copy = ket_right;
+  // Y blocks by (rg, sig)
+  std::map<std::pair<int, int>, std::vector<int>> ybys;
+  for (int y = 0; y < (int)Y.blocks.size(); ++y)
+    ybys[{Y.blocks[y].rg, Y.blocks[y].sig}].push_back(y);
+  struct T { int bra, y; };
+  std::map<std::array<int, 2>, std::vector<T>> contrib;   // (sb, g') -> terms
+  for (int b = 0; b < (int)bra.blocks.size(); ++b) {
+    const SiteT::Blk& cb = bra.blocks[b];
+    auto it = ybys.find({cb.r, cb.sig});
+    if (it == ybys.end()) continue;
+    for (int y : it->second) contrib[{cb.sb, Y.blocks[y].g}].push_back({b, y});
+  }
+  for (auto& kv : contrib) {
+    int sb = kv.first[0], g = kv.first[1];
+    const Inter::Blk& y0 = Y.blocks[kv.second[0].y];
+    e.t.add(sb, -1, g, y0.k, bra_right.d[sb], y0.W, y0.cols);
+  }
+  e.t.alloc(c.st, false);
+  GemmBatch gb;
+  int id = 0;
+  for (auto& kv : contrib) {
+    const Inter::Blk& eb = e.t.blocks[id];
+    int N = eb.W * eb.cols;
+    gb.task(e.t.ptr(id), eb.rows, N, N, OP_C, OP_N, false, 1.0);
+    for (auto& tm : kv.second) {
+      const SiteT::Blk& cb = bra.blocks[tm.bra];
+      gb.term(bra.ptr(tm.bra), cb.cols, Y.ptr(tm.y), N, cb.rows);
+    }
+    ++id;
+  }
+  gb.run(c);
+  return e;
+}
+
+static Env env_update_left(Context& c, const Env& E, const SiteT& bra, const Bond& bra_right,
+                           const MPSd& ket, int site, const MPOd& m) {
+  Inter X = lstage(c, E, ket.sites[site], ket.bonds[site + 1]);
+  Inter Y = wstage_left(c, X, m, site);
+  return env_from_Y_left(c, Y, bra, bra_right, m.bonds[site + 1], ket.bonds[site + 1]);
+}
+
+// R at bond site+1 -> R at bond site
+static Env env_update_right(Context& c, const Env& R, const SiteT& bra, const Bond& bra_left,
+                            const MPSd& ket, int site, const MPOd& m) {
+  const SiteT& A = ket.sites[site];
+  const Bond& ket_left = ket.bonds[site];
+  // ket blocks by (right sector, sigma)
+  std::map<std::pair<int, int>, int> kby;
+  for (int b = 0; b < (int)A.blocks.size(); ++b) kby[{A.blocks[b].sb, A.blocks[b].sig}] = b;
+  Inter Z;
+  std::vector<std::pair<int, int>> src;
+  for (int rb = 0; rb < (int)R.t.blocks.size(); ++rb) {
+    const Inter::Blk& r = R.t.blocks[rb];
+    for (int s = 0; s < 4; ++s) {
+      auto it = kby.find({r.k, s});
+      if (it == kby.end()) continue;
+      const SiteT::Blk& ab = A.blocks[it->second];
+      Z.add(r.rg, s, r.g, ab.r, r.rows, r.W, ket_left.d[ab.r]);
+      src.push_back({rb, it->second});
+    }
+  }
+  Z.alloc(c.st, false);
+  {
+    GemmBatch gb;
+    for (int z = 0; z < (int)Z.blocks.size(); ++z) {
+      const Inter::Blk& zb = Z.blocks[z];
+      const Inter::Blk& r = R.t.blocks[src[z].first];
+      gb.task(Z.ptr(z), zb.rows * zb.W, zb.cols, zb.cols, OP_N, OP_T, false, 1.0);
+      gb.term(R.t.ptr(src[z].first), r.cols, A.ptr(src[z].second), r.cols, r.cols);
+    }
+    gb.run(c);
+  }
+  Inter Zp = wstage_right(c, Z, m, site);
+  // R_new[a][w][a'] = sum_{s, b} conj(C[a][s][b]) Z'[b][s][w][a']
+  std::map<std::pair<int, int>, std::vector<int>> zby;
+  for (int z = 0; z < (int)Zp.blocks.size(); ++z) zby[{Zp.blocks[z].rg, Zp.blocks[z].sig}].push_back(z);
+  struct T { int bra, z; };
+  std::map<std::array<int, 2>, std::vector<T>> contrib;
+  for (int b = 0; b < (int)bra.blocks.size(); ++b) {
+    const SiteT::Blk& cb = bra.blocks[b];
+    auto it = zby.find({cb.sb, cb.sig});
+    if (it == zby.end()) continue;
+    for (int z : it->second) contrib[{cb.r, Zp.blocks[z].g}].push_back({b, z});
+  }
+  Env e;
+  e.rows = RowGroups::from_bond(bra_left);
+  e.mb = &m.bonds[site];
+  e.ket_copy = ket_left;
+  for (auto& kv : contrib) {
+    const Inter::Blk& z0 = Zp.blocks[kv.second[0].z];
+    e.t.add(kv.first[0], -1, kv.first[1], z0.k, bra_left.d[kv.first[0]], z0.W, z0.cols);
+  }
+  e.t.alloc(c.st, false);
+  GemmBatch gb;
+  int id = 0;
+  for (auto& kv : contrib) {
+    const Inter::Blk& eb = e.t.blocks[id];
+    int N = eb.W * eb.cols;
+    gb.task(e.t.ptr(id), eb.rows, N, N, OP_J, OP_N, false, 1.0);
+    for (auto& tm : kv.second) {
+      const SiteT::Blk& cb = bra.blocks[tm.bra];
+      gb.term(bra.ptr(tm.bra), cb.cols, Zp.ptr(tm.z), N, cb.cols);
+    }
+    ++id;
+  }
+  gb.run(c);
+  return e;
+}
+
+// ------------------------------------------------------------------ factorisations
+
+namespace {
+
+struct FactWork {
+  DevPtr buf;
+  std::vector<FactTask> tasks;
+  std::vector<size_t> a_off, v_off, s_off;
+};
+
+// allocate m x n work matrices (+ n x n V / R, + n values) for a list of shapes
+FactWork fact_alloc(Context& c, const std::vector<std::pair<int, int>>& shapes) {
+  FactWork fw;
+  size_t off = 0;
+  for (auto& sh : shapes) {
+    fw.a_off.push_back(off);
+    off += (size_t)sh.first * sh.second * sizeof(double2);
+    off = (off + 255) & ~(size_t)255;
+    fw.v_off.push_back(off);
+    off += (size_t)sh.second * sh.second * sizeof(double2);
+    off = (off + 255) & ~(size_t)255;
+    fw.s_off.push_back(off);
+    off += (size_t)sh.second * sizeof(double);
+    off = (off + 255) & ~(size_t)255;
+  }
+  fw.buf = dev_alloc(std::max<size_t>(off, 256), c.st);
+  char* base = (char*)fw.buf->p;
+  for (size_t i = 0; i < shapes.size(); ++i)
+    fw.tasks.push_back({(double2*)(base + fw.a_off[i]), (double2*)(base + fw.v_off[i]),
+                        (double*)(base + fw.s_off[i]), shapes[i].first, shapes[i].second});
+  return fw;
+}
+
+void run_copy(Context& c, const std::vector<CopyTask>& t, int to_work) {
+  if (t.empty()) return;
+  const CopyTask* d = c.stage(t);
+  cudaEvent_t ev;
+  c.kbegin(TDMPS_KSTAT_OTHER, &ev);
+  launch_copy(d, (int)t.size(), to_work, c.st);
+  double bytes = 0.0;
+  for (auto& x : t) bytes += 32.0 * x.rows * x.cols;
+  c.kend(TDMPS_KSTAT_OTHER, ev, 0.0, bytes);
+}
+
+void run_qr(Context& c, FactWork& fw) {
+  if (fw.tasks.empty()) return;
+  double fl = 0.0;
+  for (auto& t : fw.tasks) {
+    if (t.m > QR_MAX_ROWS || t.n > QR_MAX_COLS)
+      throw Error(TDMPS_ERR_INVALID_ARG, "QR block exceeds the supported size");
+    fl += 16.0 * t.m * t.n * t.n;
+  }
+  const FactTask* d = c.stage(fw.tasks);
+  cudaEvent_t ev;
+  c.kbegin(TDMPS_KSTAT_QR, &ev);
+  launch_qr(d, (int)fw.tasks.size(), c.st);
+  c.kend(TDMPS_KSTAT_QR, ev, fl, 0.0);
+}
+
+void run_svd(Context& c, FactWork& fw) {
+  if (fw.tasks.empty()) return;
+  const FactTask* d = c.stage(fw.tasks);
+  cudaEvent_t ev;
+  c.kbegin(TDMPS_KSTAT_SVD, &ev);
+  launch_svd(d, (int)fw.tasks.size(), (int*)c.status->p, c.st);
+  double fl = 0.0;
+  for (auto& t : fw.tasks) fl += 8.0 * 8.0 * t.m * t.n * t.n;
+  c.kend(TDMPS_KSTAT_SVD, ev, fl, 0.0);
+}
+
+}  // namespace
+
+// Block (r, s) -> sb of a site tensor seen as a matrix per right sector:
+// rows = row groups r with their sigma, cols = d(sb).
+struct RowLayout {
+  std::vector<std::vector<std::pair<int, int>>> members;   // per sector: (block id, row offset)
+  std::vector<int> m;
+};
+static RowLayout rows_by_right(const SiteT& t, int nsec_right) {
+  RowLayout L;
+  L.members.assign(nsec_right, {});
+  L.m.assign(nsec_right, 0);
+  for (int b = 0; b < (int)t.blocks.size(); ++b) {
+    const SiteT::Blk& bl = t.blocks[b];
+    L.members[bl.sb].push_back({b, L.m[bl.sb]});
+    L.m[bl.sb] += bl.rows;
+  }
+  return L;
+}
+
+// One-site left-to-right gauge move: C -> Q (thin QR per right sector).
+// Returns the new site tensor and the new right bond.
+static std::pair<SiteT, Bond> qr_left(Context& c, const SiteT& C, const RowGroups& rows,
+                                      const Bond& right) {
+  RowLayout lay = rows_by_right(C, right.nsec());
+  std::vector<std::pair<int, int>> shapes;
+  std::vector<int> secs;
+  for (int s = 0; s < right.nsec(); ++s)
+    if (lay.m[s] > 0) { shapes.push_back({lay.m[s], right.d[s]}); secs.push_back(s); }
+  FactWork fw = fact_alloc(c, shapes);
+  std::vector<CopyTask> g;
+  for (size_t i = 0; i < secs.size(); ++i)
+    for (auto& mb : lay.members[secs[i]]) {
+      const SiteT::Blk& bl = C.blocks[mb.first];
+      g.push_back({C.ptr(mb.first), fw.tasks[i].A, bl.rows, bl.cols, bl.cols, shapes[i].first,
+                   mb.second, 0, 0, 0, make_double2(1.0, 0.0)});
+    }
+  run_copy(c, g, 1);
+  run_qr(c, fw);
+  Bond nb;
+  std::vector<int> kdim(right.nsec(), 0);
+  for (size_t i = 0; i < secs.size(); ++i) kdim[secs[i]] = std::min(shapes[i].first, shapes[i].second);
+  for (int s = 0; s < right.nsec(); ++s)
+    if (kdim[s] > 0) { nb.q.push_back(right.q[s]); nb.d.push_back(kdim[s]); }
+  SiteT Q = make_site(rows, nb, c.st, false);
+  std::vector<CopyTask> sc;
+  for (size_t i = 0; i < secs.size(); ++i) {
+    int ns = nb.find(right.q[secs[i]]);
+    for (auto& mb : lay.members[secs[i]]) {
+      const SiteT::Blk& bl = C.blocks[mb.first];
+      int qb = Q.block_of(bl.r, bl.sig);
+      (void)ns;
+      sc.push_back({Q.ptr(qb), fw.tasks[i].A, bl.rows, kdim[secs[i]], kdim[secs[i]],
+                    shapes[i].first, mb.second, 0, 0, 0, make_double2(1.0, 0.0)});
+    }
+  }
+  run_copy(c, sc, 0);
+  return {std::move(Q), nb};
+}
+
+// One-site right-to-left gauge move: C = Lf Q per left sector (QR of C^H).
+// Returns (Q site, new left bond); if absorb is given, also the factor work
+// (R' of C^H = Q' R', with Lf = R'^H) for absorbing into the left neighbour.
+struct LQResult {
+  SiteT Q;
+  Bond left;
+  FactWork fw;
+  std::vector<int> secs;   // old left sector per factor task
+};
+static LQResult lq_right(Context& c, const SiteT& C, const Bond& left, const Bond& right) {
+  // per left sector: cols = (sig, sb) blocks concatenated
+  std::vector<std::vector<std::pair<int, int>>> members(left.nsec());
+  std::vector<int> ncol(left.nsec(), 0);
+  for (int b = 0; b < (int)C.blocks.size(); ++b) {
+    const SiteT::Blk& bl = C.blocks[b];
+    members[bl.r].push_back({b, ncol[bl.r]});
+    ncol[bl.r] += bl.cols;
+  }
+  LQResult res;
+  std::vector<std::pair<int, int>> shapes;
+  for (int s = 0; s < left.nsec(); ++s)
+    if (ncol[s] > 0) { shapes.push_back({ncol[s], left.d[s]}); res.secs.push_back(s); }
+  res.fw = fact_alloc(c, shapes);
+  std::vector<CopyTask> g;
+  for (size_t i = 0; i < res.secs.size(); ++i)
+    for (auto& mb : members[res.secs[i]]) {
+      const SiteT::Blk& bl = C.blocks[mb.first];
+      // work = M^H (ncol x |sa|): block (i, j) of M at (0, off) -> conj_t
+      g.push_back({C.ptr(mb.first), res.fw.tasks[i].A, bl.rows, bl.cols, bl.cols,
+                   shapes[i].first, 0, mb.second, 1, 0, make_double2(1.0, 0.0)});
+    }
+  run_copy(c, g, 1);
+  run_qr(c, res.fw);
+  std::vector<int> kdim(left.nsec(), 0);
+  for (size_t i = 0; i < res.secs.size(); ++i)
+    kdim[res.secs[i]] = std::min(shapes[i].first, shapes[i].second);
+  for (int s = 0; s < left.nsec(); ++s)
+    if (kdim[s] > 0) { res.left.q.push_back(left.q[s]); res.left.d.push_back(kdim[s]); }
+  res.Q = make_site(RowGroups::from_bond(res.left), right, c.st, false);
+  std::vector<CopyTask> sc;
+  for (size_t i = 0; i < res.secs.size(); ++i) {
+    int s = res.secs[i];
+    int ns = res.left.find(left.q[s]);
+    for (auto& mb : members[s]) {
+      const SiteT::Blk& bl = C.blocks[mb.first];
+      int qb = res.Q.block_of(ns, bl.sig);
+      // Q block (k x |sb|) = conj transpose of Q' rows [off, off+|sb|), cols [0, k)
+      sc.push_back({res.Q.ptr(qb), res.fw.tasks[i].A, kdim[s], bl.cols, bl.cols, shapes[i].first,
+                    0, mb.second, 1, 0, make_double2(1.0, 0.0)});
+    }
+  }
+  run_copy(c, sc, 0);
+  return res;
+}
+
+// new_prev[a'][s][k] = prev[a'][s][a] * Lf[a][k] with Lf = R'^H from lq_right
+static SiteT absorb_left_factor(Context& c, const SiteT& prev, const RowGroups& rows,
+                                const Bond& old_mid, const LQResult& lq) {
+  SiteT out = make_site(rows, lq.left, c.st, false);
+  std::map<int, int> task_of;   // old sector -> factor task
+  for (size_t i = 0; i < lq.secs.size(); ++i) task_of[lq.secs[i]] = (int)i;
+  GemmBatch gb;
+  for (int o = 0; o < (int)out.blocks.size(); ++o) {
+    const SiteT::Blk& ob = out.blocks[o];
+    int old_sec = old_mid.find(lq.left.q[ob.sb]);
+    int pb = prev.block_of(ob.r, ob.sig);
+    gb.task(out.ptr(o), ob.rows, ob.cols, ob.cols, OP_N, OP_J, false, 1.0);
+    if (pb < 0 || old_sec < 0) continue;
+    const FactTask& ft = lq.fw.tasks[task_of.at(old_sec)];
+    // Lf[a][k] = conj(R[a*n + k]) with n = |sa| (leading dimension of R)
+    gb.term(prev.ptr(pb), prev.blocks[pb].cols, ft.V, ft.n, ft.n);
+  }
+  gb.run(c);
+  return out;
+}
+
+MPSd right_canonicalize(Context& c, const MPSd& m0) {
+  MPSd m = m0;   // shares device buffers; every modified site is replaced
+  for (int i = m.L - 1; i >= 1; --i) {
+    LQResult lq = lq_right(c, m.sites[i], m.bonds[i], m.bonds[i + 1]);
+    SiteT prev = absorb_left_factor(c, m.sites[i - 1], RowGroups::from_bond(m.bonds[i - 1]),
+                                    m.bonds[i], lq);
+    m.sites[i] = std::move(lq.Q);
+    m.sites[i - 1] = std::move(prev);
+    m.bonds[i] = lq.left;
+  }
+  return m;
+}
+
+// Truncated SVD split of a tensor Th[(rg)][s2][c] whose row groups carry the
+// middle charge.  Returns new left site (rows x middle), right site (middle x
+// right) and the middle bond.  absorb_right: singular values go right.
+struct SplitResult {
+  SiteT A, B;
+  Bond mid;
+  double disc = 0.0, total = 0.0;
+};
+static SplitResult svd_split(Context& c, const SiteT& Th, const RowGroups& rows,
+                             const RowGroups& left_rows_of_A, const Bond& right, int D, double eps,
+                             bool absorb_right, int nsig2 = 4) {
+  // middle charges
+  std::map<QN, std::vector<std::pair<int, int>>> rmem;   // Q -> (row group, row offset)
+  std::map<QN, int> mrows;
+  for (int r = 0; r < rows.n(); ++r) {
+    bool has = false;
+    for (int s = 0; s < 4; ++s) has |= Th.block_of(r, s) >= 0;
+    if (!has) continue;
+    rmem[rows.q[r]].push_back({r, mrows[rows.q[r]]});
+    mrows[rows.q[r]] += rows.d[r];
+  }
+  std::map<QN, std::vector<std::array<int, 3>>> cmem;    // Q -> (sig2, sc, col offset)
+  std::map<QN, int> ncols;
+  for (int s2 = 0; s2 < nsig2; ++s2)
+    for (int sc = 0; sc < right.nsec(); ++sc) {
+      QN Q = right.q[sc] - SITE_Q[s2];
+      if (!mrows.count(Q)) continue;
+      cmem[Q].push_back({s2, sc, ncols[Q]});
+      ncols[Q] += right.d[sc];
+    }
+  std::vector<QN> qs;
+  std::vector<std::pair<int, int>> shapes;
+  std::vector<int> trans;
+  for (auto& kv : mrows) {
+    if (!ncols.count(kv.first)) continue;
+    int m = kv.second, n = ncols[kv.first];
+    qs.push_back(kv.first);
+    bool t = n > m;
+    trans.push_back(t);
+    shapes.push_back(t ? std::make_pair(n, m) : std::make_pair(m, n));
+  }
+  SplitResult res;
+  if (qs.empty()) throw Error(TDMPS_ERR_ZERO_STATE, "two-site tensor has no admissible sector");
+  FactWork fw = fact_alloc(c, shapes);
+  std::vector<CopyTask> g;
+  for (size_t i = 0; i < qs.size(); ++i) {
+    const QN& Q = qs[i];
+    int ldw = shapes[i].first;
+    for (auto& rm : rmem[Q])
+      for (auto& cm : cmem[Q]) {
+        int b = Th.block_of(rm.first, cm[0]);
+        if (b < 0 || Th.blocks[b].sb != cm[1]) continue;
+        const SiteT::Blk& bl = Th.blocks[b];
+        g.push_back({Th.ptr(b), fw.tasks[i].A, bl.rows, bl.cols, bl.cols, ldw, rm.second, cm[2],
+                     trans[i], 0, make_double2(1.0, 0.0)});
+      }
+  }
+  // zero the work matrices first (blocks not present stay zero)
+  for (size_t i = 0; i < qs.size(); ++i)
+    launch_zero(fw.tasks[i].A, (size_t)shapes[i].first * shapes[i].second, c.st);
+  run_copy(c, g, 1);
+  run_svd(c, fw);
+  // truncation over all singular values of the bond
+  std::vector<int> secid;
+  int nv = 0;
+  int ntot = 0;
+  for (auto& sh : shapes) ntot += sh.second;
+  DevPtr svals = dev_alloc(sizeof(double) * std::max(1, ntot) * 2 + 64, c.st);
+  DevPtr sids = dev_alloc(sizeof(int) * std::max(1, ntot) * 2 + 64, c.st);
+  for (size_t i = 0; i < qs.size(); ++i) {
+    TD_CHECK_CUDA(cudaMemcpyAsync((double*)svals->p + nv, fw.tasks[i].s,
+                                  sizeof(double) * shapes[i].second, cudaMemcpyDeviceToDevice, c.st));
+    for (int k = 0; k < shapes[i].second; ++k) secid.push_back((int)i);
+    nv += shapes[i].second;
+  }
+  const int* dsec = c.stage(secid);
+  DevPtr kept = dev_alloc(sizeof(int) * (qs.size() + 2) + sizeof(double) * 4, c.st);
+  int* dkept = (int*)kept->p;
+  double* dw = (double*)((char*)kept->p + ((sizeof(int) * (qs.size() + 2) + 15) & ~(size_t)15));
+  {
+    cudaEvent_t ev;
+    c.kbegin(TDMPS_KSTAT_OTHER, &ev);
+    launch_trunc((const double*)svals->p, dsec, nv, (int)qs.size(), D, eps, dkept, dw,
+                 (double*)svals->p + ntot, (int*)sids->p, c.st);
+    c.kend(TDMPS_KSTAT_OTHER, ev, 0.0, 0.0);
+  }
+  std::vector<int> hk(qs.size());
+  double hw[2];
+  int hstat = 0;
+  TD_CHECK_CUDA(cudaMemcpyAsync(hk.data(), dkept, sizeof(int) * qs.size(), cudaMemcpyDeviceToHost, c.st));
+  TD_CHECK_CUDA(cudaMemcpyAsync(hw, dw, sizeof(double) * 2, cudaMemcpyDeviceToHost, c.st));
+  TD_CHECK_CUDA(cudaMemcpyAsync(&hstat, c.status->p, sizeof(int), cudaMemcpyDeviceToHost, c.st));
+  TD_CHECK_CUDA(cudaStreamSynchronize(c.st));
+  if (hstat) throw Error(TDMPS_ERR_NUMERIC, "Jacobi SVD did not converge");
+  if (!std::isfinite(hw[1])) throw Error(TDMPS_ERR_NONFINITE, "non-finite singular values");
+  res.disc = hw[0];
+  res.total = hw[1];
+  for (size_t i = 0; i < qs.size(); ++i)
+    if (hk[i] > 0) { res.mid.q.push_back(qs[i]); res.mid.d.push_back(hk[i]); }
+  if (res.mid.q.empty()) throw Error(TDMPS_ERR_ZERO_STATE, "fit target vanished on this sweep");
+  res.A = make_site(left_rows_of_A, res.mid, c.st, false);
+  res.B = make_site(RowGroups::from_bond(res.mid), right, c.st, false);
+  // scatter: A rows from U (or V' if transposed), B from V^H (or U'^H)
+  std::vector<ScatterTask> ss;
+  for (size_t i = 0; i < qs.size(); ++i) {
+    int k = hk[i];
+    if (k == 0) continue;
+    const QN& Q = qs[i];
+    int mid = res.mid.find(Q);
+    const FactTask& ft = fw.tasks[i];
+    const double2* usrc = trans[i] ? ft.V : ft.A;
+    int ulds = trans[i] ? ft.n : ft.m;
+    const double2* vsrc = trans[i] ? ft.A : ft.V;
+    int vlds = trans[i] ? ft.m : ft.n;
+    for (auto& rm : rmem[Q]) {
+      int r = rm.first;
+      int ab = res.A.block_of(rows.sa[r], rows.sig[r] < 0 ? 0 : rows.sig[r]);
+      if (rows.sig[r] < 0) ab = res.A.block_of(rows.sa[r], 0);
+      if (ab < 0 || res.A.blocks[ab].sb != mid) continue;
+      ss.push_back({res.A.ptr(ab), rows.d[r], k, k, usrc, ulds, rm.second, 0, 0,
+                    absorb_right ? 0 : 1, ft.s});
+    }
+    for (auto& cm : cmem[Q]) {
+      int bb = res.B.block_of(mid, cm[0]);
+      if (bb < 0 || res.B.blocks[bb].sb != cm[1]) continue;
+      ss.push_back({res.B.ptr(bb), k, right.d[cm[1]], right.d[cm[1]], vsrc, vlds, cm[2], 0, 1,
+                    absorb_right ? 2 : 0, ft.s});
+    }
+  }
+  if (!ss.empty()) {
+    const ScatterTask* d = c.stage(ss);
+    cudaEvent_t ev;
+    c.kbegin(TDMPS_KSTAT_OTHER, &ev);
+    launch_scatter(d, (int)ss.size(), c.st);
+    c.kend(TDMPS_KSTAT_OTHER, ev, 0.0, 0.0);
+  }
+  return res;
+}
+
+// ------------------------------------------------------------------ fit
+
+namespace {
+
+struct TermState {
+  const MPSd* ket;
+  const MPOd* mpo;
+  cplx coef;
+  const double2* coef_dev;
+  std::vector<Env> LE, RE;
+};
+
+void check_same_space(const MPSd& a, const MPSd& b) {
+  if (a.L != b.L) throw Error(TDMPS_ERR_INVALID_ARG, "MPS lengths differ");
+  if (a.tot != b.tot) throw Error(TDMPS_ERR_SECTOR, "MPS quantum numbers (N, 2Sz) differ");
+}
+
+// one-site local tensor at site i with bra bonds (bl, br)
+SiteT local_one(Context& c, std::vector<TermState>& ts, int i, const Bond& bl, const Bond& br) {
+  SiteT out = make_site(RowGroups::from_bond(bl), br, c.st, false);
+  for (size_t t = 0; t < ts.size(); ++t) {
+    TermState& s = ts[t];
+    Inter X = lstage(c, s.LE[i], s.ket->sites[i], s.ket->bonds[i + 1]);
+    Inter Y = wstage_left(c, X, *s.mpo, i);
+    rstage(c, Y, s.RE[i + 1], out, s.coef, s.coef_dev, t > 0);
+  }
+  return out;
+}
+
+// two-site local tensor at sites (i, i+1): rows = fused (a, s1)
+SiteT local_two(Context& c, std::vector<TermState>& ts, int i, const Bond& bl, const Bond& br) {
+  RowGroups fr = RowGroups::fused(bl);
+  SiteT out = make_site(fr, br, c.st, false);
+  for (size_t t = 0; t < ts.size(); ++t) {
+    TermState& s = ts[t];
+    Inter X1 = lstage(c, s.LE[i], s.ket->sites[i], s.ket->bonds[i + 1]);
+    Inter Y1 = wstage_left(c, X1, *s.mpo, i);
+    // view Y1 as an environment with fused rows (sa, s1) -> index sa*4+s1
+    Env E2;
+    E2.rows = fr;
+    E2.mb = &s.mpo->bonds[i + 1];
+    E2.ket_copy = s.ket->bonds[i + 1];
+    E2.t.data = Y1.data;
+    E2.t.size = Y1.size;
+    for (auto& b : Y1.blocks) {
+      int id = (int)E2.t.blocks.size();
+      E2.t.blocks.push_back({b.rg * 4 + b.sig, -1, b.g, b.k, b.rows, b.W, b.cols, b.off});
+      E2.t.index[{b.rg * 4 + b.sig, -1, b.g, b.k}] = id;
+    }
+    Inter X2 = lstage(c, E2, s.ket->sites[i + 1], s.ket->bonds[i + 2]);
+    Inter Y2 = wstage_left(c, X2, *s.mpo, i + 1);
+    rstage(c, Y2, s.RE[i + 2], out, s.coef, s.coef_dev, t > 0);
+  }
+  return out;
+}
+
+}  // namespace
+
+MPSd fit(Context& c, const std::vector<FitTerm>& terms, const MPSd& guess, const FitOpts& o) {
+  if (terms.empty()) throw Error(TDMPS_ERR_INVALID_ARG, "no fit terms");
+  if (o.D < 1) throw Error(TDMPS_ERR_INVALID_ARG, "D must be >= 1");
+  if (o.n_two_site < 0 || o.n_one_site < 0 || o.n_two_site + o.n_one_site < 1)
+    throw Error(TDMPS_ERR_INVALID_ARG, "invalid sweep schedule");
+  for (auto& t : terms) check_same_space(*t.ket, guess);
+  const int L = guess.L;
+  MPSd C = right_canonicalize(c, guess);
+  std::vector<TermState> ts(terms.size());
+  for (size_t t = 0; t < terms.size(); ++t) {
+    ts[t].ket = terms[t].ket;
+    ts[t].mpo = terms[t].mpo ? terms[t].mpo : &c.identity_mpo(L);
+    if (ts[t].mpo->L != L) throw Error(TDMPS_ERR_INVALID_ARG, "MPO length differs from MPS");
+    ts[t].coef = terms[t].coef;
+    ts[t].coef_dev = terms[t].coef_dev;
+    ts[t].LE.resize(L + 1);
+    ts[t].RE.resize(L + 1);
+    ts[t].LE[0] = env_left_boundary(c, C, *ts[t].ket, *ts[t].mpo);
+    ts[t].RE[L] = env_right_boundary(c, C, *ts[t].ket, *ts[t].mpo);
+    for (int i = L - 1; i >= 1; --i)
+      ts[t].RE[i] = env_update_right(c, ts[t].RE[i + 1], C.sites[i], C.bonds[i], *ts[t].ket, i,
+                                     *ts[t].mpo);
+  }
+  if (L == 1) {
+    C.sites[0] = local_one(c, ts, 0, C.bonds[0], C.bonds[1]);
+    return C;
+  }
+  double maxdisc = 0.0;
+  for (int sw = 0; sw < o.n_two_site; ++sw) {
+    for (int half = 0; half < 2; ++half) {
+      for (int step = 0; step < L - 1; ++step) {
+        int i = half == 0 ? step : L - 2 - step;
+        SiteT Th = local_two(c, ts, i, C.bonds[i], C.bonds[i + 2]);
+        SplitResult sp = svd_split(c, Th, RowGroups::fused(C.bonds[i]),
+                                   RowGroups::from_bond(C.bonds[i]), C.bonds[i + 2], o.D, o.eps,
+                                   half == 0);
+        if (sp.total > 0) maxdisc = std::max(maxdisc, sp.disc / sp.total);
+        C.sites[i] = std::move(sp.A);
+        C.sites[i + 1] = std::move(sp.B);
+        C.bonds[i + 1] = sp.mid;
+        for (auto& s : ts) {
+          if (half == 0)
+            s.LE[i + 1] = env_update_left(c, s.LE[i], C.sites[i], C.bonds[i + 1], *s.ket, i, *s.mpo);
+          else
+            s.RE[i + 1] = env_update_right(c, s.RE[i + 2], C.sites[i + 1], C.bonds[i + 1], *s.ket,
+                                           i + 1, *s.mpo);
+        }
+      }
+    }
+  }
+  for (int sw = 0; sw < o.n_one_site; ++sw) {
+    for (int i = 0; i < L; ++i) {
+      SiteT Ci = local_one(c, ts, i, C.bonds[i], C.bonds[i + 1]);
+      if (i < L - 1) {
+        auto qr = qr_left(c, Ci, RowGroups::from_bond(C.bonds[i]), C.bonds[i + 1]);
+        C.sites[i] = std::move(qr.first);
+        C.bonds[i + 1] = qr.second;
+        for (auto& s : ts)
+          s.LE[i + 1] = env_update_left(c, s.LE[i], C.sites[i], C.bonds[i + 1], *s.ket, i, *s.mpo);
+      } else {
+        C.sites[i] = std::move(Ci);
+      }
+    }
+    for (int i = L - 1; i >= 0; --i) {
+      SiteT Ci = local_one(c, ts, i, C.bonds[i], C.bonds[i + 1]);
+      if (i > 0) {
+        LQResult lq = lq_right(c, Ci, C.bonds[i], C.bonds[i + 1]);
+        C.sites[i] = std::move(lq.Q);
+        C.bonds[i] = lq.left;
+        for (auto& s : ts)
+          s.RE[i] = env_update_right(c, s.RE[i + 1], C.sites[i], C.bonds[i], *s.ket, i, *s.mpo);
+      } else {
+        C.sites[0] = std::move(Ci);
+      }
+    }
+  }
+  if (o.n_one_site == 0) {
+    // two-site sweeps end with the norm on site 0 already (U S absorbed left)
+  }
+  if (o.max_discarded) *o.max_discarded = std::max(*o.max_discarded, maxdisc);
+  return C;
+}
+
+// ------------------------------------------------------------------ sandwiches
+
+void sandwich_dev(Context& c, const MPOd* mpo, const MPSd& bra, const MPSd& ket, double2* out) {
+  check_same_space(bra, ket);
+  const MPOd& m = mpo ? *mpo : c.identity_mpo(bra.L);
+  Env E = env_left_boundary(c, bra, ket, m);
+  for (int i = 0; i < bra.L; ++i)
+    E = env_update_left(c, E, bra.sites[i], bra.bonds[i + 1], ket, i, m);
+  int b = -1;
+  for (int k = 0; k < (int)E.t.blocks.size(); ++k) b = k;
+  if (b < 0) {
+    TD_CHECK_CUDA(cudaMemsetAsync(out, 0, sizeof(double2), c.st));
+    return;
+  }
+  if (E.t.blocks.size() != 1 || E.t.blocks[0].rows != 1 || E.t.blocks[0].W != 1 ||
+      E.t.blocks[0].cols != 1)
+    throw Error(TDMPS_ERR_SECTOR, "final environment is not a scalar");
+  TD_CHECK_CUDA(cudaMemcpyAsync(out, E.t.ptr(0), sizeof(double2), cudaMemcpyDeviceToDevice, c.st));
+}
+
+cplx sandwich(Context& c, const MPOd* mpo, const MPSd& bra, const MPSd& ket) {
+  DevPtr d = dev_alloc(sizeof(double2), c.st);
+  sandwich_dev(c, mpo, bra, ket, (double2*)d->p);
+  double2 h;
+  TD_CHECK_CUDA(cudaMemcpyAsync(&h, d->p, sizeof(double2), cudaMemcpyDeviceToHost, c.st));
+  TD_CHECK_CUDA(cudaStreamSynchronize(c.st));
+  return cplx(h.x, h.y);
+}
+
+void normalize_center(Context& c, MPSd& m, double2* norm_out) {
+  cudaEvent_t ev;
+  c.kbegin(TDMPS_KSTAT_OTHER, &ev);
+  launch_normalize((double2*)m.sites[0].data->p, m.sites[0].size, norm_out, c.st);
+  c.kend(TDMPS_KSTAT_OTHER, ev, 0.0, 0.0);
+}
+
+// ------------------------------------------------------------------ compress
+
+double compress(Context& c, MPSd& m, int D, double eps) {
+  if (D < 1) throw Error(TDMPS_ERR_INVALID_ARG, "D must be >= 1");
+  MPSd C = right_canonicalize(c, m);
+  double disc_sum = 0.0;
+  for (int i = 0; i + 1 < C.L; ++i) {
+    // SVD of site i as (rows = (a, s)) x b per right sector: reuse svd_split
+    // with a one-site tensor whose "right" part is the bond itself.
+    RowGroups rows = RowGroups::from_bond(C.bonds[i]);
+    // build a tensor viewed as Th[(a,s)][s2=0][b]: express site i with fused
+    // rows and sigma2 = 0 (charge 0) by re-keying its blocks.
+    RowGroups fr = RowGroups::fused(C.bonds[i]);
+    SiteT Th;
+    Th.index.assign((size_t)fr.n() * 4, -1);
+    Th.data = C.sites[i].data;
+    Th.size = C.sites[i].size;
+    for (auto& b : C.sites[i].blocks) {
+      int r = b.r * 4 + b.sig;
+      Th.index[(size_t)r * 4 + 0] = (int)Th.blocks.size();
+      Th.blocks.push_back({r, 0, b.sb, b.rows, b.cols, b.off});
+    }
+    SplitResult sp = svd_split(c, Th, fr, rows, C.bonds[i + 1], D, eps, true, 1);
+    if (sp.total > 0) disc_sum += sp.disc / sp.total;
+    // sp.B is (mid x 0 x right bond) with sigma2 = 0: contract with site i+1
+    const SiteT& nxt = C.sites[i + 1];
+    SiteT out = make_site(RowGroups::from_bond(sp.mid), C.bonds[i + 2], c.st, false);
+    GemmBatch gb;
+    for (int o = 0; o < (int)out.blocks.size(); ++o) {
+      const SiteT::Blk& ob = out.blocks[o];
+      gb.task(out.ptr(o), ob.rows, ob.cols, ob.cols, OP_N, OP_N, false, 1.0);
+      // old middle sector with the same charge
+      int old = C.bonds[i + 1].find(sp.mid.q[ob.r]);
+      int sb = sp.B.block_of(ob.r, 0);
+      int nb = nxt.block_of(old, ob.sig);
+      if (sb < 0 || nb < 0) continue;
+      gb.term(sp.B.ptr(sb), sp.B.blocks[sb].cols, nxt.ptr(nb), ob.cols, sp.B.blocks[sb].cols);
+    }
+    gb.run(c);
+    C.sites[i] = std::move(sp.A);
+    C.sites[i + 1] = std::move(out);
+    C.bonds[i + 1] = sp.mid;
+  }
+  m = right_canonicalize(c, C);
+  return disc_sum;
+}
+
+// ------------------------------------------------------------------ integrators
+
+MPSd rk4_step(Context& c, const MPOd& H, const MPSd& psi, double dt, const FitOpts& o) {
+  const cplx a(0.0, -dt);
+  auto applyH = [&](const MPSd& x) { return fit(c, {{&x, &H, a}}, x, o); };
+  auto sum2 = [&](cplx cb, const MPSd& b) { return fit(c, {{&psi, nullptr, 1.0}, {&b, nullptr, cb}}, psi, o); };
+  MPSd k1 = applyH(psi);
+  MPSd s1 = sum2(0.5, k1);
+  MPSd k2 = applyH(s1);
+  MPSd s2 = sum2(0.5, k2);
+  MPSd k3 = applyH(s2);
+  MPSd s3 = sum2(1.0, k3);
+  MPSd k4 = applyH(s3);
+  return fit(c, {{&psi, nullptr, 1.0}, {&k1, nullptr, 1.0 / 6}, {&k2, nullptr, 1.0 / 3},
+                 {&k3, nullptr, 1.0 / 3}, {&k4, nullptr, 1.0 / 6}}, psi, o);
+}
+
+MPSd krylov_step(Context& c, const MPOd& H, const MPSd& psi, double dt, int m, bool orth,
+                 const FitOpts& o) {
+  if (m < 2 || m > 16) throw Error(TDMPS_ERR_INVALID_ARG, "Krylov dimension must be in [2, 16]");
+  std::vector<MPSd> phi;
+  phi.reserve(m);
+  phi.push_back(psi);
+  DevPtr mats = dev_alloc(sizeof(double2) * (2 * m * m + 2 * m + 8), c.st);
+  double2* Nd = (double2*)mats->p;
+  double2* Hd = Nd + m * m;
+  double2* cd = Hd + m * m;
+  double2* gs = cd + m;
+  TD_CHECK_CUDA(cudaMemsetAsync(mats->p, 0, sizeof(double2) * (2 * m * m + 2 * m + 8), c.st));
+  std::vector<char> haveN(m * m, 0), haveH(m * m, 0);
+  const MPOd& I = c.identity_mpo(psi.L);
+  for (int k = 0; k + 1 < m; ++k) {
+    MPSd u = fit(c, {{&phi[k], &H, 1.0}}, phi[k], o);
+    if (orth) {
+      std::vector<FitTerm> terms;
+      terms.push_back({&u, nullptr, 1.0});
+      for (int j = 0; j <= k; ++j) {
+        if (!haveH[j * m + k]) { sandwich_dev(c, &H, phi[j], phi[k], Hd + j * m + k); haveH[j * m + k] = 1; }
+        if (!haveN[j * m + j]) { sandwich_dev(c, &I, phi[j], phi[j], Nd + j * m + j); haveN[j * m + j] = 1; }
+      }
+      DevPtr cj = dev_alloc(sizeof(double2) * (k + 1), c.st);
+      for (int j = 0; j <= k; ++j) {
+        launch_scalar_div_neg(Hd + j * m + k, Nd + j * m + j, (double2*)cj->p + j, c.st);
+        terms.push_back({&phi[j], nullptr, 1.0, (double2*)cj->p + j});
+      }
+      MPSd v = fit(c, terms, u, o);
+      normalize_center(c, v, nullptr);
+      phi.push_back(std::move(v));
+      // keep coefficient buffer alive until the fit's kernels ran (stream order)
+      (void)cj;
+    } else {
+      normalize_center(c, u, nullptr);
+      phi.push_back(std::move(u));
+    }
+  }
+  for (int i = 0; i < m; ++i)
+    for (int j = i; j < m; ++j) {
+      if (!haveN[i * m + j]) sandwich_dev(c, &I, phi[i], phi[j], Nd + i * m + j);
+      if (!haveH[i * m + j]) sandwich_dev(c, &H, phi[i], phi[j], Hd + i * m + j);
+    }
+  int* st = (int*)c.status->p + 4;
+  launch_krylov_small(Nd, Hd, m, dt, cd, st, c.st);
+  int hs[2];
+  TD_CHECK_CUDA(cudaMemcpyAsync(hs, st, sizeof(hs), cudaMemcpyDeviceToHost, c.st));
+  TD_CHECK_CUDA(cudaStreamSynchronize(c.st));
+  if (hs[1]) throw Error(TDMPS_ERR_NONFINITE, "non-finite Krylov matrices");
+  if (m - hs[0] < 2) throw Error(TDMPS_ERR_KRYLOV_SINGULAR, "Krylov overlap matrix has rank < 2");
+  std::vector<FitTerm> terms;
+  for (int k = 0; k < m; ++k) terms.push_back({&phi[k], nullptr, 1.0, cd + k});
+  (void)gs;
+  return fit(c, terms, phi[0], o);
+}
+
+// ------------------------------------------------------------------ one-body RDM
+
+void one_rdm(Context& c, const MPSd& psi, cplx* gamma) {
+  const int L = psi.L;
+  const MPOd& I = c.identity_mpo(L);
+  const MPOd& G = c.rdm_mpo(L);
+  // right overlap environments
+  std::vector<Env> RO(L + 1);
+  RO[L] = env_right_boundary(c, psi, psi, I);
+  for (int i = L - 1; i >= 1; --i)
+    RO[i] = env_update_right(c, RO[i + 1], psi.sites[i], psi.bonds[i], psi, i, I);
+  DevPtr gd = dev_alloc(sizeof(double2) * (size_t)L * 2 * L, c.st);   // [j][2*i + s]
+  TD_CHECK_CUDA(cudaMemsetAsync(gd->p, 0, sizeof(double2) * (size_t)L * 2 * L, c.st));
+  Env E = env_left_boundary(c, psi, psi, G);
+  for (int j = 0; j < L; ++j) {
+    // readout operator: channels of G bond j -> closed channels (i, s), i <= j
+    MPOd R;
+    R.L = 1;
+    R.bonds.resize(2);
+    R.bonds[0] = G.bonds[j];
+    MPOBond& rb = R.bonds[1];
+    rb.gq = {QN()};
+    rb.gsize = {2 * (j + 1)};
+    for (int w = 0; w < 2 * (j + 1); ++w) { rb.ch_group.push_back(0); rb.ch_local.push_back(w); }
+    R.W.assign(1, {});
+    // local matrices: c_up |u>->|0>, |ud>->|d>; c_down |d>->|0>, |ud>->-|u>
+    for (int s = 0; s < 2; ++s) {
+      // channel of c+_{i s} at bond j: down spins 1 + i, up spins 1 + j + i
+      for (int i = 0; i < j; ++i) {
+        int win = s == 1 ? 1 + i : 1 + j + i;
+        int wout = 2 * i + s;
+        if (s == 0) { R.W[0].push_back({win, wout, 0, 1, 1.0}); R.W[0].push_back({win, wout, 2, 3, 1.0}); }
+        else { R.W[0].push_back({win, wout, 0, 2, 1.0}); R.W[0].push_back({win, wout, 1, 3, -1.0}); }
+      }
+      // diagonal: n_s on site j from the identity channel
+      int wout = 2 * j + s;
+      if (s == 0) { R.W[0].push_back({0, wout, 1, 1, 1.0}); R.W[0].push_back({0, wout, 3, 3, 1.0}); }
+      else { R.W[0].push_back({0, wout, 2, 2, 1.0}); R.W[0].push_back({0, wout, 3, 3, 1.0}); }
+    }
+    upload_mpo_tables(R, c);
+    // contract: E (bond j) with site j through the readout, then with RO[j+1]
+    Inter X = lstage(c, E, psi.sites[j], psi.bonds[j + 1]);
+    Inter Y = wstage_left(c, X, R, 0);
+    Env Eo = env_from_Y_left(c, Y, psi.sites[j], psi.bonds[j + 1], R.bonds[1], psi.bonds[j + 1]);
+    for (int b = 0; b < (int)Eo.t.blocks.size(); ++b) {
+      const Inter::Blk& eb = Eo.t.blocks[b];
+      int rb2 = RO[j + 1].t.find(eb.rg, -1, 0, eb.rg);
+      if (rb2 < 0) continue;
+      launch_trace_channels(Eo.t.ptr(b), eb.rows, eb.W, eb.cols, RO[j + 1].t.ptr(rb2),
+                            (double2*)gd->p + (size_t)j * 2 * L, c.st);
+    }
+    TD_CHECK_CUDA(cudaGetLastError());
+    if (j + 1 < L) E = env_update_left(c, E, psi.sites[j], psi.bonds[j + 1], psi, j, G);
+    // R tables must stay alive until the kernels above consumed them
+    c.sync();
+  }
+  std::vector<double2> h((size_t)L * 2 * L);
+  TD_CHECK_CUDA(cudaMemcpyAsync(h.data(), gd->p, sizeof(double2) * h.size(), cudaMemcpyDeviceToHost, c.st));
+  TD_CHECK_CUDA(cudaStreamSynchronize(c.st));
+  for (int i = 0; i < L * L; ++i) gamma[i] = 0.0;
+  for (int j = 0; j < L; ++j)
+    for (int i = 0; i <= j; ++i)
+      for (int s = 0; s < 2; ++s) {
+        double2 v = h[(size_t)j * 2 * L + 2 * i + s];
+        gamma[i * L + j] += cplx(v.x, v.y);
+      }
+  for (int j = 0; j < L; ++j)
+    for (int i = 0; i < j; ++i) gamma[j * L + i] = std::conj(gamma[i * L + j]);
+}
+
+// ------------------------------------------------------------------ MPS creation
+
+MPSd mps_determinant(Context& c, int L, const uint8_t* occ) {
+  if (L < 1 || L > 63) throw Error(TDMPS_ERR_INVALID_ARG, "L must be in [1, 63]");
+  MPSd m;
+  m.L = L;
+  m.bonds.resize(L + 1);
+  m.bonds[0].q = {QN()};
+  m.bonds[0].d = {1};
+  QN q;
+  for (int i = 0; i < L; ++i) {
+    if (occ[i] > 3) throw Error(TDMPS_ERR_INVALID_ARG, "occupation codes must be 0..3");
+    q = q + SITE_Q[occ[i]];
+    m.bonds[i + 1].q = {q};
+    m.bonds[i + 1].d = {1};
+  }
+  m.tot = q;
+  std::vector<double2> ones(L, make_double2(1.0, 0.0));
+  for (int i = 0; i < L; ++i) {
+    m.sites.push_back(make_site(RowGroups::from_bond(m.bonds[i]), m.bonds[i + 1], c.st, false));
+    TD_CHECK_CUDA(cudaMemcpyAsync(m.sites[i].data->p, c.stage(&ones[i], sizeof(double2)),
+                                  sizeof(double2), cudaMemcpyDeviceToDevice, c.st));
+  }
+  return m;
+}
+
+MPSd mps_import(Context& c, int L, const int* bond_dims, const int* labels,
+                const tdmps_complex* const* tensors) {
+  if (L < 1 || L > 63) throw Error(TDMPS_ERR_INVALID_ARG, "L must be in [1, 63]");
+  MPSd m;
+  m.L = L;
+  m.bonds.resize(L + 1);
+  // per bond: map basis index -> (sector, position)
+  std::vector<std::vector<std::pair<int, int>>> where(L + 1);
+  const int* lab = labels;
+  for (int k = 0; k <= L; ++k) {
+    int D = bond_dims[k];
+    if (D < 1) throw Error(TDMPS_ERR_INVALID_ARG, "bond dimensions must be >= 1");
+    std::map<QN, int> cnt;
+    std::vector<QN> qv(D);
+    for (int x = 0; x < D; ++x) { qv[x] = QN(lab[2 * x], lab[2 * x + 1]); cnt[qv[x]]++; }
+    lab += 2 * D;
+    for (auto& kv : cnt) { m.bonds[k].q.push_back(kv.first); m.bonds[k].d.push_back(kv.second); }
+    std::vector<int> pos(m.bonds[k].nsec(), 0);
+    where[k].resize(D);
+    for (int x = 0; x < D; ++x) {
+      int s = m.bonds[k].find(qv[x]);
+      where[k][x] = {s, pos[s]++};
+    }
+  }
+  if (m.bonds[0].nsec() != 1 || m.bonds[0].q[0] != QN() || m.bonds[0].d[0] != 1)
+    throw Error(TDMPS_ERR_INVALID_ARG, "bond 0 must be one-dimensional with label (0, 0)");
+  if (m.bonds[L].nsec() != 1 || m.bonds[L].d[0] != 1)
+    throw Error(TDMPS_ERR_SECTOR, "bond L must be one-dimensional");
+  m.tot = m.bonds[L].q[0];
+  for (int i = 0; i < L; ++i) {
+    SiteT t = make_site(RowGroups::from_bond(m.bonds[i]), m.bonds[i + 1], c.st, false);
+    std::vector<double2> h(t.size);
+    int Dl = bond_dims[i], Dr = bond_dims[i + 1];
+    const tdmps_complex* A = tensors[i];
+    for (int a = 0; a < Dl; ++a)
+      for (int s = 0; s < 4; ++s)
+        for (int b = 0; b < Dr; ++b) {
+          tdmps_complex v = A[((size_t)a * 4 + s) * Dr + b];
+          if (!std::isfinite(v.re) || !std::isfinite(v.im))
+            throw Error(TDMPS_ERR_NONFINITE, "MPS tensor contains NaN/Inf");
+          int sa = where[i][a].first, sb = where[i + 1][b].first;
+          int blk = t.block_of(sa, s);
+          if (blk < 0 || t.blocks[blk].sb != sb) {
+            if (v.re != 0.0 || v.im != 0.0)
+              throw Error(TDMPS_ERR_INVALID_ARG, "non-zero entry violates charge conservation");
+            continue;
+          }
+          const SiteT::Blk& bl = t.blocks[blk];
+          h[bl.off + (size_t)where[i][a].second * bl.cols + where[i + 1][b].second] =
+              make_double2(v.re, v.im);
+        }
+    if (t.size)
+      TD_CHECK_CUDA(cudaMemcpyAsync(t.data->p, h.data(), t.size * sizeof(double2),
+                                    cudaMemcpyHostToDevice, c.st));
+    TD_CHECK_CUDA(cudaStreamSynchronize(c.st));
+    m.sites.push_back(std::move(t));
+  }
+  return m;
+}
+
+void mps_export(Context& c, const MPSd& m, int* bond_dims, int* labels, tdmps_complex* const* tensors) {
+  for (int k = 0; k <= m.L; ++k) bond_dims[k] = m.bonds[k].total();
+  if (!tensors) return;
+  int* lab = labels;
+  for (int k = 0; k <= m.L; ++k)
+    for (int s = 0; s < m.bonds[k].nsec(); ++s)
+      for (int x = 0; x < m.bonds[k].d[s]; ++x) { *lab++ = m.bonds[k].q[s].n; *lab++ = m.bonds[k].q[s].s; }
+  for (int i = 0; i < m.L; ++i) {
+    const SiteT& t = m.sites[i];
+    std::vector<double2> h(t.size);
+    if (t.size)
+      TD_CHECK_CUDA(cudaMemcpyAsync(h.data(), t.data->p, t.size * sizeof(double2),
+                                    cudaMemcpyDeviceToHost, c.st));
+    TD_CHECK_CUDA(cudaStreamSynchronize(c.st));
+    int Dl = bond_dims[i], Dr = bond_dims[i + 1];
+    std::vector<int> offl(m.bonds[i].nsec() + 1, 0), offr(m.bonds[i + 1].nsec() + 1, 0);
+    for (int s = 0; s < m.bonds[i].nsec(); ++s) offl[s + 1] = offl[s] + m.bonds[i].d[s];
+    for (int s = 0; s < m.bonds[i + 1].nsec(); ++s) offr[s + 1] = offr[s] + m.bonds[i + 1].d[s];
+    tdmps_complex* A = tensors[i];
+    for (size_t e = 0; e < (size_t)Dl * 4 * Dr; ++e) A[e] = {0.0, 0.0};
+    for (auto& bl : t.blocks)
+      for (int a = 0; a < bl.rows; ++a)
+        for (int b = 0; b < bl.cols; ++b) {
+          double2 v = h[bl.off + (size_t)a * bl.cols + b];
+          A[((size_t)(offl[bl.r] + a) * 4 + bl.sig) * Dr + offr[bl.sb] + b] = {v.x, v.y};
+        }
+  }
+}
+
+MPSd mps_copy(Context& c, const MPSd& m) {
+  MPSd o = m;
+  for (int i = 0; i < m.L; ++i) {
+    o.sites[i].data = dev_alloc(std::max<size_t>(m.sites[i].size, 1) * sizeof(double2), c.st);
+    if (m.sites[i].size)
+      TD_CHECK_CUDA(cudaMemcpyAsync(o.sites[i].data->p, m.sites[i].data->p,
+                                    m.sites[i].size * sizeof(double2), cudaMemcpyDeviceToDevice, c.st));
+  }
+  return o;
+}
+
+}  // namespace tdmps

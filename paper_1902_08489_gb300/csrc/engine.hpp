@@ -1,0 +1,142 @@
+// Host engine of the tdmps library: context, block-sparse intermediates,
+// contraction planners and the algorithms of the paper built on them.
+#pragma once
+
+#include <complex>
+#include <functional>
+#include <map>
+#include <vector>
+
+#include "internal.hpp"
+#include "kernels.hpp"
+
+namespace tdmps {
+
+using cplx = std::complex<double>;
+
+// ------------------------------------------------------------------ context
+
+struct KStat {
+  int64_t launches = 0;
+  double ms = 0.0, flops = 0.0, bytes = 0.0;
+};
+
+struct Context {
+  cudaStream_t st = nullptr;
+  int precision = TDMPS_FP64;
+  int n_two_site = 2, n_one_site = 2;
+  std::string err;
+  // staging ring for task lists
+  char* h_ring = nullptr;
+  char* d_ring = nullptr;
+  size_t ring_cap = 0, ring_off = 0;
+  // statistics
+  bool stats = false;
+  KStat kstat[TDMPS_KSTAT_COUNT];
+  struct Pending { int kind; cudaEvent_t a, b; };
+  std::vector<Pending> pending;
+  // scratch for device status words
+  DevPtr status;   // int[8]
+  std::unique_ptr<MPOd> ident;   // identity MPO cache (by L)
+  std::unique_ptr<MPOd> rdm;     // density-matrix MPO cache (by L)
+
+  explicit Context(cudaStream_t s, int prec);
+  ~Context();
+
+  // copy a host array into device memory valid until the stream passes it
+  const void* stage(const void* src, size_t bytes);
+  template <class T> const T* stage(const std::vector<T>& v) {
+    return v.empty() ? nullptr : (const T*)stage(v.data(), v.size() * sizeof(T));
+  }
+  // kernel timing bracket
+  void kbegin(int kind, cudaEvent_t* a);
+  void kend(int kind, cudaEvent_t a, double flops, double bytes);
+  void collect_stats();
+  void sync();
+  const MPOd& identity_mpo(int L);
+  const MPOd& rdm_mpo(int L);
+};
+
+// ------------------------------------------------------------------ intermediates
+
+// Block-sparse tensor with blocks rows x W x cols keyed (row group, sigma,
+// channel group, column sector); sigma = -1 for environments.
+struct Inter {
+  struct Blk {
+    int rg, sig, g, k;
+    int rows, W, cols;
+    size_t off;
+  };
+  std::vector<Blk> blocks;
+  std::map<std::array<int, 4>, int> index;
+  size_t size = 0;
+  DevPtr data;
+  int find(int rg, int sig, int g, int k) const {
+    auto it = index.find({rg, sig, g, k});
+    return it == index.end() ? -1 : it->second;
+  }
+  int add(int rg, int sig, int g, int k, int rows, int W, int cols) {
+    int id = (int)blocks.size();
+    blocks.push_back({rg, sig, g, k, rows, W, cols, size});
+    index[{rg, sig, g, k}] = id;
+    size += (size_t)rows * W * cols;
+    return id;
+  }
+  double2* ptr(int b) const { return (double2*)data->p + blocks[b].off; }
+  void alloc(cudaStream_t st, bool zero);
+};
+
+// Environment E[a, w, a'] at one bond: rows = bra row groups, channels = MPO
+// bond groups, cols = ket bond sectors.  Block (rg, g) has ket sector
+// q_rg - q_g.
+struct Env {
+  RowGroups rows;
+  const MPOBond* mb = nullptr;
+  const Bond* ket = nullptr;
+  Bond ket_copy;
+  Inter t;
+};
+
+// MPS handle contents
+struct MPSh {
+  MPSd m;
+};
+
+// ------------------------------------------------------------------ engine API
+
+void upload_mpo_tables(MPOd& m, Context& c);
+MPSd mps_determinant(Context& c, int L, const uint8_t* occ);
+MPSd mps_import(Context& c, int L, const int* bond_dims, const int* labels,
+                const tdmps_complex* const* tensors);
+void mps_export(Context& c, const MPSd& m, int* bond_dims, int* labels, tdmps_complex* const* tensors);
+MPSd mps_copy(Context& c, const MPSd& m);
+
+// fit target term: coef * (H or identity) |ket>
+struct FitTerm {
+  const MPSd* ket;
+  const MPOd* mpo;           // nullptr -> identity
+  cplx coef = 1.0;
+  const double2* coef_dev = nullptr;   // multiplies coef when set
+};
+struct FitOpts {
+  int D = 0;
+  double eps = 0.0;
+  int n_two_site = 0, n_one_site = 0;
+  double* max_discarded = nullptr;
+};
+MPSd fit(Context& c, const std::vector<FitTerm>& terms, const MPSd& guess, const FitOpts& o);
+
+// <bra| O |ket> into a device scalar (O = mpo or identity)
+void sandwich_dev(Context& c, const MPOd* mpo, const MPSd& bra, const MPSd& ket, double2* out);
+cplx sandwich(Context& c, const MPOd* mpo, const MPSd& bra, const MPSd& ket);
+
+MPSd right_canonicalize(Context& c, const MPSd& m);
+double compress(Context& c, MPSd& m, int D, double eps);
+void normalize_center(Context& c, MPSd& m, double2* norm_out);
+
+MPSd rk4_step(Context& c, const MPOd& H, const MPSd& psi, double dt, const FitOpts& o);
+MPSd krylov_step(Context& c, const MPOd& H, const MPSd& psi, double dt, int m, bool orth,
+                 const FitOpts& o);
+void one_rdm(Context& c, const MPSd& psi, cplx* gamma);
+
+}  // namespace tdmps

@@ -1,0 +1,692 @@
+// FP64 device kernels of the tdmps library: grouped complex block GEMM, sparse
+// MPO-tensor application, block gather/scatter, one-sided Jacobi SVD, CGS2
+// QR, the truncation rule, and the small Krylov algebra.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+
+#include "kernels.hpp"
+
+namespace tdmps {
+
+// ------------------------------------------------------------------ complex helpers
+
+__device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ double2 cconj(double2 a) { return make_double2(a.x, -a.y); }
+__device__ __forceinline__ double2 cscale(double2 a, double s) { return make_double2(a.x * s, a.y * s); }
+__device__ __forceinline__ double cabs2(double2 a) { return a.x * a.x + a.y * a.y; }
+__device__ __forceinline__ double2 cfma(double2 a, double2 b, double2 c) {   // a*b + c
+  return make_double2(fma(a.x, b.x, fma(-a.y, b.y, c.x)), fma(a.x, b.y, fma(a.y, b.x, c.y)));
+}
+__device__ __forceinline__ double2 cdiv(double2 a, double2 b) {
+  double d = b.x * b.x + b.y * b.y;
+  return make_double2((a.x * b.x + a.y * b.y) / d, (a.y * b.x - a.x * b.y) / d);
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// ------------------------------------------------------------------ grouped GEMM
+
+constexpr int GT = 32;    // output tile edge
+constexpr int GK = 8;     // K chunk
+
+__device__ __forceinline__ double2 load_op(const double2* P, int ld, int op, int r, int c,
+                                           int R, int C) {
+  // element (r, c) of op(P) where op(P) is R x C
+  if (r >= R || c >= C) return make_double2(0.0, 0.0);
+  switch (op) {
+    case OP_N: return P[(size_t)r * ld + c];
+    case OP_T: return P[(size_t)c * ld + r];
+    case OP_C: return cconj(P[(size_t)c * ld + r]);
+    default: return cconj(P[(size_t)r * ld + c]);
+  }
+}
+
+__global__ void __launch_bounds__(256) k_gemm(const GemmTask* __restrict__ tasks,
+                                              const GemmTerm* __restrict__ terms,
+                                              const int* __restrict__ tile_task) {
+  __shared__ double2 As[GK][GT + 1];
+  __shared__ double2 Bs[GK][GT + 1];
+  const int ti = tile_task[blockIdx.x];
+  const GemmTask t = tasks[ti];
+  const int local = blockIdx.x - t.tile_base;
+  const int m0 = (local % t.tiles_m) * GT;
+  const int n0 = (local / t.tiles_m) * GT;
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  double2 acc[2][2];
+  for (int i = 0; i < 2; ++i)
+    for (int j = 0; j < 2; ++j) acc[i][j] = make_double2(0.0, 0.0);
+  for (int e = t.term_begin; e < t.term_end; ++e) {
+    const GemmTerm g = terms[e];
+    for (int k0 = 0; k0 < g.K; k0 += GK) {
+      {
+        int i = threadIdx.x >> 3, k = threadIdx.x & 7;      // A tile: 32 x 8
+        As[k][i] = load_op(g.A, g.lda, t.opA, m0 + i, k0 + k, t.M, g.K);
+        int kk = threadIdx.x >> 5, j = threadIdx.x & 31;    // B tile: 8 x 32
+        Bs[kk][j] = load_op(g.B, g.ldb, t.opB, k0 + kk, n0 + j, g.K, t.N);
+      }
+      __syncthreads();
+#pragma unroll
+      for (int k = 0; k < GK; ++k) {
+        double2 a0 = As[k][ty * 2], a1 = As[k][ty * 2 + 1];
+        double2 b0 = Bs[k][tx * 2], b1 = Bs[k][tx * 2 + 1];
+        acc[0][0] = cfma(a0, b0, acc[0][0]);
+        acc[0][1] = cfma(a0, b1, acc[0][1]);
+        acc[1][0] = cfma(a1, b0, acc[1][0]);
+        acc[1][1] = cfma(a1, b1, acc[1][1]);
+      }
+      __syncthreads();
+    }
+  }
+  double2 alpha = t.alpha;
+  if (t.alpha_ptr) alpha = cmul(alpha, *t.alpha_ptr);
+  if (t.alpha_div) alpha = cdiv(alpha, *t.alpha_div);
+  for (int i = 0; i < 2; ++i)
+    for (int j = 0; j < 2; ++j) {
+      int r = m0 + ty * 2 + i, c = n0 + tx * 2 + j;
+      if (r < t.M && c < t.N) {
+        double2* p = t.C + (size_t)r * t.ldc + c;
+        double2 v = cmul(alpha, acc[i][j]);
+        if (t.beta) v = cadd(v, *p);
+        *p = v;
+      }
+    }
+}
+
+void launch_gemm(const GemmTask* d_tasks, int ntasks, const GemmTerm* d_terms,
+                 const int* d_tile_task, int ntiles, cudaStream_t st) {
+  (void)ntasks;
+  if (ntiles <= 0) return;
+  k_gemm<<<ntiles, 256, 0, st>>>(d_tasks, d_terms, d_tile_task);
+}
+
+// ------------------------------------------------------------------ W stage
+
+__global__ void __launch_bounds__(256) k_wstage(const WTask* __restrict__ tasks, int ntasks,
+                                                int64_t total, const int* __restrict__ rowptr,
+                                                const int* __restrict__ ent_w,
+                                                const double* __restrict__ ent_v) {
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    int lo = 0, hi = ntasks - 1;
+    while (lo < hi) {
+      int mid = (lo + hi + 1) >> 1;
+      if (tasks[mid].work_base <= idx) lo = mid; else hi = mid - 1;
+    }
+    const WTask& t = tasks[lo];
+    int64_t loc = idx - t.work_base;
+    int b = (int)(loc % t.cols);
+    int64_t rw = loc / t.cols;
+    int w = (int)(rw % t.wout);
+    int a = (int)(rw / t.wout);
+    double2 acc = make_double2(0.0, 0.0);
+    for (int s = 0; s < 4; ++s) {
+      if (t.csr[s] < 0) continue;
+      const int* rp = rowptr + t.csr[s];
+      const double2* X = t.X[s];
+      int win = t.win[s];
+      for (int e = rp[w]; e < rp[w + 1]; ++e) {
+        double v = ent_v[e];
+        double2 x = X[((size_t)a * win + ent_w[e]) * t.cols + b];
+        acc.x = fma(v, x.x, acc.x);
+        acc.y = fma(v, x.y, acc.y);
+      }
+    }
+    double2* y = t.Y + ((size_t)a * t.wout + w) * t.cols + b;
+    if (t.beta) acc = cadd(acc, *y);
+    *y = acc;
+  }
+}
+
+void launch_wstage(const WTask* d_tasks, int ntasks, int64_t total_work, const int* d_rowptr,
+                   const int* d_ent_w, const double* d_ent_v, cudaStream_t st) {
+  if (total_work <= 0) return;
+  int64_t blocks = (total_work + 255) / 256;
+  if (blocks > 152 * 64) blocks = 152 * 64;
+  k_wstage<<<(int)blocks, 256, 0, st>>>(d_tasks, ntasks, total_work, d_rowptr, d_ent_w, d_ent_v);
+}
+
+// ------------------------------------------------------------------ gather / scatter
+
+__global__ void k_copy(const CopyTask* __restrict__ tasks, int to_work) {
+  const CopyTask t = tasks[blockIdx.x];
+  int n = t.rows * t.cols;
+  for (int e = threadIdx.x; e < n; e += blockDim.x) {
+    int i = e / t.cols, j = e % t.cols;
+    size_t w = t.conj_t ? (size_t)(t.row0 + i) * t.ldw + (t.col0 + j)
+                        : (size_t)(t.col0 + j) * t.ldw + (t.row0 + i);
+    double2* b = t.blk + (size_t)i * t.ld + j;
+    if (to_work) {
+      double2 v = cmul(t.scale, *b);
+      t.work[w] = t.conj_t ? cconj(v) : v;
+    } else {
+      double2 v = t.work[w];
+      if (t.conj_t) v = cconj(v);
+      *b = cmul(t.scale, v);
+    }
+  }
+}
+
+void launch_copy(const CopyTask* d_tasks, int ntasks, int to_work, cudaStream_t st) {
+  if (ntasks <= 0) return;
+  k_copy<<<ntasks, 256, 0, st>>>(d_tasks, to_work);
+}
+
+__global__ void k_scatter(const ScatterTask* __restrict__ tasks) {
+  const ScatterTask t = tasks[blockIdx.x];
+  int n = t.rows * t.cols;
+  for (int e = threadIdx.x; e < n; e += blockDim.x) {
+    int i = e / t.cols, j = e % t.cols;
+    double2 v = t.conj_t ? cconj(t.src[(size_t)(t.c0 + i) * t.lds + t.r0 + j])
+                         : t.src[(size_t)(t.c0 + j) * t.lds + t.r0 + i];
+    if (t.scale_dim == 1) v = cscale(v, t.s[j]);
+    else if (t.scale_dim == 2) v = cscale(v, t.s[i]);
+    t.blk[(size_t)i * t.ld + j] = v;
+  }
+}
+
+void launch_scatter(const ScatterTask* d_tasks, int ntasks, cudaStream_t st) {
+  if (ntasks <= 0) return;
+  k_scatter<<<ntasks, 256, 0, st>>>(d_tasks);
+}
+
+__global__ void k_zero(double2* p, size_t n) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * blockDim.x)
+    p[i] = make_double2(0.0, 0.0);
+}
+
+void launch_zero(double2* p, size_t n, cudaStream_t st) {
+  if (n == 0) return;
+  size_t blocks = (n + 255) / 256;
+  if (blocks > 152 * 32) blocks = 152 * 32;
+  k_zero<<<(unsigned)blocks, 256, 0, st>>>(p, n);
+}
+
+__global__ void k_scale(double2* x, size_t n, double2 a) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * blockDim.x)
+    x[i] = cmul(a, x[i]);
+}
+
+void launch_scale(double2* x, size_t n, double2 a, cudaStream_t st) {
+  if (n == 0) return;
+  size_t blocks = (n + 255) / 256;
+  if (blocks > 152 * 32) blocks = 152 * 32;
+  k_scale<<<(unsigned)blocks, 256, 0, st>>>(x, n, a);
+}
+
+// ------------------------------------------------------------------ Jacobi SVD
+
+// One-sided (Hestenes) Jacobi on the columns of a column-major m x n matrix
+// (n <= m): pairs of columns are rotated until mutually orthogonal to 1e-15
+// relative; round-robin pairing lets every warp rotate a disjoint pair.
+// Afterwards sigma_j = |a_j|, u_j = a_j / sigma_j, columns sorted descending.
+constexpr int SVD_THREADS = 512;
+constexpr int SVD_MAX_SWEEPS = 80;
+
+__global__ void __launch_bounds__(SVD_THREADS) k_svd(const FactTask* __restrict__ tasks,
+                                                     int* status) {
+  const FactTask t = tasks[blockIdx.x];
+  const int m = t.m, n = t.n;
+  double2* A = t.A;
+  double2* V = t.V;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  for (int e = threadIdx.x; e < n * n; e += blockDim.x)
+    V[e] = make_double2((e % n) == (e / n) ? 1.0 : 0.0, 0.0);
+  __shared__ int rotated;
+  __syncthreads();
+  const int np = (n + 1) & ~1;   // even number of players
+  int sweep = 0;
+  for (; sweep < SVD_MAX_SWEEPS; ++sweep) {
+    if (threadIdx.x == 0) rotated = 0;
+    __syncthreads();
+    for (int r = 0; r < np - 1; ++r) {
+      for (int k = warp; k < np / 2; k += nwarp) {
+        int pa = k, pb = np - 1 - k;
+        int p = pa == 0 ? 0 : ((pa - 1 + r) % (np - 1)) + 1;
+        int q = ((pb - 1 + r) % (np - 1)) + 1;
+        if (p >= n || q >= n) continue;
+        if (p > q) { int tmp = p; p = q; q = tmp; }
+        double2* ap = A + (size_t)p * m;
+        double2* aq = A + (size_t)q * m;
+        double al = 0.0, be = 0.0, gr = 0.0, gi = 0.0;
+        for (int i = lane; i < m; i += 32) {
+          double2 x = ap[i], y = aq[i];
+          al += cabs2(x);
+          be += cabs2(y);
+          gr += x.x * y.x + x.y * y.y;     // conj(x) * y
+          gi += x.x * y.y - x.y * y.x;
+        }
+        al = warp_sum(al); be = warp_sum(be); gr = warp_sum(gr); gi = warp_sum(gi);
+        double g = sqrt(gr * gr + gi * gi);
+        if (g == 0.0 || al == 0.0 || be == 0.0 || g <= 1e-15 * sqrt(al * be)) continue;
+        double zeta = (be - al) / (2.0 * g);
+        double tt = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+        double c = 1.0 / sqrt(1.0 + tt * tt), s = c * tt;
+        double2 ph = make_double2(gr / g, gi / g);          // e^{i phi}
+        double2 sph = cscale(ph, s);                         // s e^{i phi}
+        double2 sphc = cconj(sph);                           // s e^{-i phi}
+        for (int i = lane; i < m; i += 32) {
+          double2 x = ap[i], y = aq[i];
+          ap[i] = csub(cscale(x, c), cmul(sphc, y));
+          aq[i] = cadd(cmul(sph, x), cscale(y, c));
+        }
+        double2* vp = V + (size_t)p * n;
+        double2* vq = V + (size_t)q * n;
+        for (int i = lane; i < n; i += 32) {
+          double2 x = vp[i], y = vq[i];
+          vp[i] = csub(cscale(x, c), cmul(sphc, y));
+          vq[i] = cadd(cmul(sph, x), cscale(y, c));
+        }
+        if (lane == 0) rotated = 1;
+      }
+      __syncthreads();
+    }
+    __syncthreads();
+    int any = rotated;
+    __syncthreads();
+    if (!any) break;
+  }
+  if (threadIdx.x == 0 && sweep == SVD_MAX_SWEEPS) atomicExch(status, 1);
+  // singular values and normalisation
+  for (int j = warp; j < n; j += nwarp) {
+    double2* aj = A + (size_t)j * m;
+    double s2 = 0.0;
+    for (int i = lane; i < m; i += 32) s2 += cabs2(aj[i]);
+    s2 = warp_sum(s2);
+    double sv = sqrt(s2);
+    if (lane == 0) t.s[j] = sv;
+    double inv = sv > 0.0 ? 1.0 / sv : 0.0;
+    for (int i = lane; i < m; i += 32) aj[i] = cscale(aj[i], inv);
+  }
+  __syncthreads();
+  // selection sort, descending (stable for ties: lower index first)
+  __shared__ int sel;
+  for (int j = 0; j < n - 1; ++j) {
+    if (threadIdx.x == 0) {
+      int b = j;
+      for (int k = j + 1; k < n; ++k)
+        if (t.s[k] > t.s[b]) b = k;
+      sel = b;
+    }
+    __syncthreads();
+    int b = sel;
+    if (b != j) {
+      for (int i = threadIdx.x; i < m; i += blockDim.x) {
+        double2 x = A[(size_t)j * m + i];
+        A[(size_t)j * m + i] = A[(size_t)b * m + i];
+        A[(size_t)b * m + i] = x;
+      }
+      for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        double2 x = V[(size_t)j * n + i];
+        V[(size_t)j * n + i] = V[(size_t)b * n + i];
+        V[(size_t)b * n + i] = x;
+      }
+      if (threadIdx.x == 0) {
+        double x = t.s[j];
+        t.s[j] = t.s[b];
+        t.s[b] = x;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+void launch_svd(const FactTask* d_tasks, int ntasks, int* d_status, cudaStream_t st) {
+  if (ntasks <= 0) return;
+  k_svd<<<ntasks, SVD_THREADS, 0, st>>>(d_tasks, d_status);
+}
+
+// ------------------------------------------------------------------ CGS2 QR
+
+// Classical Gram-Schmidt with one re-orthogonalisation on a column-major
+// m x n matrix.  Columns whose residual norm falls to <= 1e-12 times the
+// largest input column norm are dependent: they add no new direction.  The
+// independent directions are stored compactly in the first columns (at most
+// k = min(m, n)), the remaining of the first k columns are zero.  R (k x n,
+// column-major, leading dimension n) holds the coefficients, so that
+// A = Q R.
+constexpr int QR_THREADS = 256;
+constexpr int QR_MAX_M = 4096;
+constexpr int QR_MAX_N = 2048;
+
+__global__ void __launch_bounds__(QR_THREADS) k_qr(const FactTask* __restrict__ tasks) {
+  extern __shared__ double2 sh[];
+  double2* v = sh;                 // m
+  double2* coef = sh + QR_MAX_M;   // up to n
+  const FactTask t = tasks[blockIdx.x];
+  const int m = t.m, n = t.n, kmax = m < n ? m : n;
+  double2* A = t.A;
+  double2* R = t.V;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  __shared__ double maxn, vn;
+  __shared__ int nq;
+  if (threadIdx.x == 0) { maxn = 0.0; nq = 0; }
+  for (int e = threadIdx.x; e < n * n; e += blockDim.x) R[e] = make_double2(0.0, 0.0);
+  __syncthreads();
+  for (int j = warp; j < n; j += nwarp) {
+    double s2 = 0.0;
+    for (int i = lane; i < m; i += 32) s2 += cabs2(A[(size_t)j * m + i]);
+    s2 = warp_sum(s2);
+    if (lane == 0) {
+      // non-negative doubles order like their bit patterns
+      atomicMax((unsigned long long*)&maxn, (unsigned long long)__double_as_longlong(sqrt(s2)));
+    }
+  }
+  __syncthreads();
+  const double tol = 1e-12 * maxn;
+  for (int j = 0; j < n; ++j) {
+    for (int i = threadIdx.x; i < m; i += blockDim.x) v[i] = A[(size_t)j * m + i];
+    __syncthreads();
+    const int q = nq;
+    for (int pass = 0; pass < 2; ++pass) {
+      for (int c = warp; c < q; c += nwarp) {
+        const double2* qc = A + (size_t)c * m;
+        double re = 0.0, im = 0.0;
+        for (int i = lane; i < m; i += 32) {
+          double2 a = qc[i], b = v[i];
+          re += a.x * b.x + a.y * b.y;   // conj(q) * v
+          im += a.x * b.y - a.y * b.x;
+        }
+        re = warp_sum(re); im = warp_sum(im);
+        if (lane == 0) coef[c] = make_double2(re, im);
+      }
+      __syncthreads();
+      for (int i = threadIdx.x; i < m; i += blockDim.x) {
+        double2 acc = v[i];
+        for (int c = 0; c < q; ++c) acc = csub(acc, cmul(coef[c], A[(size_t)c * m + i]));
+        v[i] = acc;
+      }
+      for (int c = threadIdx.x; c < q; c += blockDim.x) {
+        double2* rr = R + (size_t)j * n + c;   // R[c, j], leading dimension n
+        *rr = cadd(*rr, coef[c]);
+      }
+      __syncthreads();
+    }
+    if (warp == 0) {
+      double s2 = 0.0;
+      for (int i = lane; i < m; i += 32) s2 += cabs2(v[i]);
+      s2 = warp_sum(s2);
+      if (lane == 0) vn = sqrt(s2);
+    }
+    __syncthreads();
+    const double nrm = vn;
+    if (nrm > tol && q < kmax) {
+      double inv = 1.0 / nrm;
+      for (int i = threadIdx.x; i < m; i += blockDim.x) A[(size_t)q * m + i] = cscale(v[i], inv);
+      if (threadIdx.x == 0) {
+        R[(size_t)j * n + q] = make_double2(nrm, 0.0);
+        nq = q + 1;
+      }
+    }
+    __syncthreads();
+  }
+  const int nfin = nq;
+  for (int c = nfin; c < kmax; ++c)
+    for (int i = threadIdx.x; i < m; i += blockDim.x) A[(size_t)c * m + i] = make_double2(0.0, 0.0);
+}
+
+void launch_qr(const FactTask* d_tasks, int ntasks, cudaStream_t st) {
+  if (ntasks <= 0) return;
+  size_t shmem = sizeof(double2) * (QR_MAX_M + QR_MAX_N);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_qr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shmem);
+    attr = true;
+  }
+  k_qr<<<ntasks, QR_THREADS, shmem, st>>>(d_tasks);
+}
+
+// ------------------------------------------------------------------ truncation rule
+
+// Singular values of all sectors of one bond (each sector descending, sector
+// ids ascending): sort descending with ties by position; drop values <=
+// 1e-12 * max; keep at most D and the fewest whose discarded weight is <= eps
+// of the total; move a cut inside a cluster (gaps <= 1e-10 * max) down to the
+// cluster edge (up if the cluster starts at the top).
+__global__ void k_trunc(const double* __restrict__ s, const int* __restrict__ sec, int nv,
+                        int nsec, int D, double eps, int* kept, double* w, double* sorted,
+                        int* sorted_sec) {
+  for (int i = threadIdx.x; i < nv; i += blockDim.x) {
+    double si = s[i];
+    int rank = 0;
+    for (int j = 0; j < nv; ++j) {
+      double sj = s[j];
+      rank += (sj > si) || (sj == si && j < i);
+    }
+    sorted[rank] = si;
+    sorted_sec[rank] = sec[i];
+  }
+  for (int i = threadIdx.x; i < nsec; i += blockDim.x) kept[i] = 0;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double total = 0.0;
+    for (int i = nv - 1; i >= 0; --i) total += sorted[i] * sorted[i];
+    int k = 0;
+    double disc = total;
+    if (nv > 0 && sorted[0] > 0.0) {
+      const double smax = sorted[0];
+      int nz = 0;
+      while (nz < nv && sorted[nz] > 1e-12 * smax) ++nz;
+      // tail[j] = sum_{i >= j} sorted[i]^2
+      k = nz;
+      double tail = 0.0;
+      for (int i = nv - 1; i >= nz; --i) tail += sorted[i] * sorted[i];
+      // try dropping index k-1 while allowed
+      while (k > 1) {
+        double t2 = tail + sorted[k - 1] * sorted[k - 1];
+        if (t2 <= eps * total) { tail = t2; --k; } else break;
+      }
+      if (k > D) k = D;
+      if (k < nz) {
+        int j = k;
+        while (j > 0 && sorted[j - 1] - sorted[j] <= 1e-10 * smax) --j;
+        if (j > 0) k = j;
+        else
+          while (k < nz && sorted[k - 1] - sorted[k] <= 1e-10 * smax) ++k;
+      }
+      disc = 0.0;
+      for (int i = nv - 1; i >= k; --i) disc += sorted[i] * sorted[i];
+      for (int i = 0; i < k; ++i) kept[sorted_sec[i]] += 1;
+    }
+    w[0] = disc;
+    w[1] = total;
+  }
+}
+
+void launch_trunc(const double* d_s, const int* d_sec, int nv, int nsec, int D, double eps,
+                  int* d_kept, double* d_w, double* d_sorted, int* d_sorted_sec, cudaStream_t st) {
+  k_trunc<<<1, 1024, 0, st>>>(d_s, d_sec, nv, nsec, D, eps, d_kept, d_w, d_sorted, d_sorted_sec);
+}
+
+// ------------------------------------------------------------------ Krylov algebra
+
+constexpr int KMAX = 16;
+
+// Cyclic Jacobi eigen-decomposition of a Hermitian n x n matrix (row-major,
+// in place); eigenvectors in columns of V.
+__device__ void herm_eig(double2* A, double2* V, double* w, int n) {
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) V[i * n + j] = make_double2(i == j ? 1.0 : 0.0, 0.0);
+  for (int sweep = 0; sweep < 60; ++sweep) {
+    double off = 0.0, tot = 0.0;
+    for (int i = 0; i < n; ++i)
+      for (int j = 0; j < n; ++j) {
+        tot += cabs2(A[i * n + j]);
+        if (i != j) off += cabs2(A[i * n + j]);
+      }
+    if (off <= 1e-30 * tot || off == 0.0) break;
+    for (int p = 0; p < n - 1; ++p)
+      for (int q = p + 1; q < n; ++q) {
+        double2 apq = A[p * n + q];
+        double g = sqrt(cabs2(apq));
+        if (g == 0.0) continue;
+        double a = A[p * n + p].x, b = A[q * n + q].x;
+        double2 ph = make_double2(apq.x / g, apq.y / g);   // e^{i phi}
+        double zeta = (b - a) / (2.0 * g);
+        double tt = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+        double c = 1.0 / sqrt(1.0 + tt * tt), s = c * tt;
+        // J = [[c, s],[ -s e^{-i phi}, c e^{-i phi}]] on (p, q); A <- J^H A J, V <- V J
+        double2 phc = cconj(ph);
+        for (int k = 0; k < n; ++k) {   // columns: A J
+          double2 x = A[k * n + p], y = A[k * n + q];
+          A[k * n + p] = csub(cscale(x, c), cmul(cscale(phc, s), y));
+          A[k * n + q] = cadd(cscale(x, s), cmul(cscale(phc, c), y));
+          double2 vx = V[k * n + p], vy = V[k * n + q];
+          V[k * n + p] = csub(cscale(vx, c), cmul(cscale(phc, s), vy));
+          V[k * n + q] = cadd(cscale(vx, s), cmul(cscale(phc, c), vy));
+        }
+        for (int k = 0; k < n; ++k) {   // rows: J^H (A J)
+          double2 x = A[p * n + k], y = A[q * n + k];
+          A[p * n + k] = csub(cscale(x, c), cmul(cscale(ph, s), y));
+          A[q * n + k] = cadd(cscale(x, s), cmul(cscale(ph, c), y));
+        }
+        A[p * n + q] = make_double2(0.0, 0.0);
+        A[q * n + p] = make_double2(0.0, 0.0);
+      }
+  }
+  for (int i = 0; i < n; ++i) w[i] = A[i * n + i].x;
+}
+
+__global__ void k_krylov_small(const double2* Nm, const double2* Hm, int m, double dt,
+                               double2* c, int* status) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double2 A[KMAX * KMAX], V[KMAX * KMAX], X[KMAX * KMAX], M[KMAX * KMAX], U[KMAX * KMAX];
+  double w[KMAX], lam[KMAX];
+  int bad = 0;
+  for (int i = 0; i < m * m; ++i) {
+    if (!isfinite(Nm[i].x) || !isfinite(Nm[i].y) || !isfinite(Hm[i].x) || !isfinite(Hm[i].y)) bad = 1;
+  }
+  // Hermitian parts
+  for (int i = 0; i < m; ++i)
+    for (int j = 0; j < m; ++j) {
+      double2 a = Nm[i * m + j], b = cconj(Nm[j * m + i]);
+      A[i * m + j] = make_double2(0.5 * (a.x + b.x), 0.5 * (a.y + b.y));
+    }
+  herm_eig(A, V, w, m);
+  double wmax = 0.0;
+  for (int i = 0; i < m; ++i) wmax = fmax(wmax, w[i]);
+  int r = 0;
+  for (int k = 0; k < m; ++k)
+    if (w[k] > 1e-12 * wmax) {
+      double inv = 1.0 / sqrt(w[k]);
+      for (int i = 0; i < m; ++i) X[i * KMAX + r] = cscale(V[i * m + k], inv);
+      ++r;
+    }
+  // M = X^H H X  (r x r)
+  for (int a = 0; a < r; ++a)
+    for (int b = 0; b < r; ++b) {
+      double2 acc = make_double2(0.0, 0.0);
+      for (int i = 0; i < m; ++i)
+        for (int j = 0; j < m; ++j) {
+          double2 hij = cscale(cadd(Hm[i * m + j], cconj(Hm[j * m + i])), 0.5);
+          acc = cadd(acc, cmul(cmul(cconj(X[i * KMAX + a]), hij), X[j * KMAX + b]));
+        }
+      M[a * r + b] = acc;
+    }
+  if (r > 0) herm_eig(M, U, lam, r);
+  // b = X^H N e0
+  double2 bvec[KMAX], tmp[KMAX];
+  for (int a = 0; a < r; ++a) {
+    double2 acc = make_double2(0.0, 0.0);
+    for (int i = 0; i < m; ++i) acc = cadd(acc, cmul(cconj(X[i * KMAX + a]), Nm[i * m + 0]));
+    bvec[a] = acc;
+  }
+  for (int a = 0; a < r; ++a) {   // tmp = exp(-i dt lam) U^H b
+    double2 acc = make_double2(0.0, 0.0);
+    for (int b2 = 0; b2 < r; ++b2) acc = cadd(acc, cmul(cconj(U[b2 * r + a]), bvec[b2]));
+    double ph = -dt * lam[a];
+    tmp[a] = cmul(make_double2(cos(ph), sin(ph)), acc);
+  }
+  for (int i = 0; i < m; ++i) {
+    double2 acc = make_double2(0.0, 0.0);
+    for (int a = 0; a < r; ++a) {
+      double2 ua = make_double2(0.0, 0.0);
+      for (int b2 = 0; b2 < r; ++b2) ua = cadd(ua, cmul(U[a * r + b2], tmp[b2]));
+      acc = cadd(acc, cmul(X[i * KMAX + a], ua));
+    }
+    c[i] = acc;
+    if (!isfinite(acc.x) || !isfinite(acc.y)) bad = 1;
+  }
+  status[0] = m - r;
+  status[1] = bad;
+}
+
+void launch_krylov_small(const double2* d_N, const double2* d_H, int m, double dt, double2* d_c,
+                         int* d_status, cudaStream_t st) {
+  k_krylov_small<<<1, 32, 0, st>>>(d_N, d_H, m, dt, d_c, d_status);
+}
+
+// ------------------------------------------------------------------ scalar helpers
+
+__global__ void k_scalar_div_neg(const double2* num, const double2* den, double2* out) {
+  double2 q = cdiv(*num, *den);
+  *out = make_double2(-q.x, -q.y);
+}
+
+void launch_scalar_div_neg(const double2* num, const double2* den, double2* out, cudaStream_t st) {
+  k_scalar_div_neg<<<1, 1, 0, st>>>(num, den, out);
+}
+
+__global__ void k_normalize(double2* x, size_t n, double2* norm_out) {
+  __shared__ double part[32];
+  double s2 = 0.0;
+  for (size_t i = threadIdx.x; i < n; i += blockDim.x) s2 += cabs2(x[i]);
+  s2 = warp_sum(s2);
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = s2;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double v = threadIdx.x < (blockDim.x >> 5) ? part[threadIdx.x] : 0.0;
+    v = warp_sum(v);
+    if (threadIdx.x == 0) part[0] = v;
+  }
+  __syncthreads();
+  double nrm = sqrt(part[0]);
+  double inv = nrm > 0.0 ? 1.0 / nrm : 0.0;
+  for (size_t i = threadIdx.x; i < n; i += blockDim.x) x[i] = cscale(x[i], inv);
+  if (threadIdx.x == 0 && norm_out) *norm_out = make_double2(nrm, 0.0);
+}
+
+void launch_normalize(double2* x, size_t n, double2* d_norm_out, cudaStream_t st) {
+  k_normalize<<<1, 1024, 0, st>>>(x, n, d_norm_out);
+}
+
+// out[w] = sum_{a, b} E[a][w][b] * R[a][b]   (rows x nch x cols and rows x cols)
+__global__ void k_trace_channels(const double2* E, int rows, int nch, int cols, const double2* R,
+                                 double2* out) {
+  const int w = blockIdx.x;
+  double re = 0.0, im = 0.0;
+  for (int e = threadIdx.x; e < rows * cols; e += blockDim.x) {
+    int a = e / cols, b = e % cols;
+    double2 v = cmul(E[((size_t)a * nch + w) * cols + b], R[(size_t)a * cols + b]);
+    re += v.x;
+    im += v.y;
+  }
+  __shared__ double pr[32], pi[32];
+  re = warp_sum(re);
+  im = warp_sum(im);
+  if ((threadIdx.x & 31) == 0) { pr[threadIdx.x >> 5] = re; pi[threadIdx.x >> 5] = im; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double sr = 0.0, si = 0.0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) { sr += pr[k]; si += pi[k]; }
+    out[w] = cadd(out[w], make_double2(sr, si));
+  }
+}
+
+void launch_trace_channels(const double2* E, int rows, int nch, int cols, const double2* R,
+                           double2* out, cudaStream_t st) {
+  if (nch <= 0 || rows * cols == 0) return;
+  k_trace_channels<<<nch, 256, 0, st>>>(E, rows, nch, cols, R, out);
+}
+
+}  // namespace tdmps

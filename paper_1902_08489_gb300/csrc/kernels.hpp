@@ -1,0 +1,103 @@
+// Device kernel interfaces of the tdmps library.  All matrices are complex
+// double (double2) unless stated; blocks are row-major unless stated.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+namespace tdmps {
+
+// op codes for grouped GEMM operands
+enum : int { OP_N = 0, OP_T = 1, OP_C = 2, OP_J = 3 };   // none, transpose, conj-transpose, conj
+
+struct GemmTerm {
+  const double2* A;
+  const double2* B;
+  int K, lda, ldb, pad;
+};
+
+// C (M x N, ldc) = alpha * sum_terms op(A) op(B) + beta * C;
+// alpha = alpha_imm * (*alpha_ptr if non-null) * (alpha_inv ? 1 / *alpha_inv : 1).
+struct GemmTask {
+  double2* C;
+  const double2* alpha_ptr;
+  const double2* alpha_div;
+  double2 alpha;
+  int M, N, ldc;
+  int opA, opB, beta;
+  int term_begin, term_end;
+  int tiles_m, tile_base;
+};
+
+// Sparse MPO-tensor application.  Output block Y[r][w][c] (rows r, W_out
+// channels, c columns), Y[a][w][b] = sum over inputs s of
+//   sum_{(w_in, v) in CSR_s[w]} v * X_s[a][w_in][b]   (X_s has W_in_s channels)
+struct WTask {
+  double2* Y;
+  const double2* X[4];
+  int win[4];
+  int csr[4];          // row-pointer offset of the CSR for input s (-1: none)
+  int rows, wout, cols, beta;
+  int64_t work_base;   // first flat element index of this task
+};
+
+// Copy a (rows x cols, ld) row-major block into / out of a column-major work
+// matrix (ldw) at (row0, col0); conj_t: the work matrix holds the conjugate
+// transpose of the block.  scale multiplies on the way.
+struct CopyTask {
+  double2* blk;
+  double2* work;
+  int rows, cols, ld, ldw;
+  int row0, col0, conj_t, zero_fill;
+  double2 scale;
+};
+
+// One-sided Jacobi SVD / CGS2 QR on column-major matrices in global memory.
+// blk(i, j) = src(r0 + i, c0 + j)            (conj_t = 0, src column-major, lds)
+// blk(i, j) = conj(src(r0 + j, c0 + i))      (conj_t = 1)
+// times s[j] (scale_dim = 1) or s[i] (scale_dim = 2)
+struct ScatterTask {
+  double2* blk;
+  int rows, cols, ld;
+  const double2* src;
+  int lds, r0, c0, conj_t, scale_dim;
+  const double* s;
+};
+
+struct FactTask {
+  double2* A;       // m x n column-major (lda = m); overwritten by U (SVD) or Q (QR)
+  double2* V;       // SVD: n x n column-major right singular vectors; QR: R (n x n col-major)
+  double* s;        // SVD: n singular values (descending); QR: unused
+  int m, n;
+};
+
+void launch_gemm(const GemmTask* d_tasks, int ntasks, const GemmTerm* d_terms,
+                 const int* d_tile_task, int ntiles, cudaStream_t st);
+void launch_wstage(const WTask* d_tasks, int ntasks, int64_t total_work, const int* d_rowptr,
+                   const int* d_ent_w, const double* d_ent_v, cudaStream_t st);
+void launch_copy(const CopyTask* d_tasks, int ntasks, int to_work, cudaStream_t st);
+void launch_scatter(const ScatterTask* d_tasks, int ntasks, cudaStream_t st);
+void launch_zero(double2* p, size_t n, cudaStream_t st);
+void launch_svd(const FactTask* d_tasks, int ntasks, int* d_status, cudaStream_t st);
+void launch_qr(const FactTask* d_tasks, int ntasks, cudaStream_t st);
+// truncation rule over nv singular values (grouped by sector, each sector
+// descending; sector id per value): writes kept count per sector and the
+// discarded / total weight to out_w[0..1].
+void launch_trunc(const double* d_s, const int* d_sec, int nv, int nsec, int D, double eps,
+                  int* d_kept, double* d_w, double* d_sorted, int* d_sorted_sec, cudaStream_t st);
+constexpr int QR_MAX_ROWS = 4096;
+constexpr int QR_MAX_COLS = 2048;
+// Krylov: c = exp(-i dt N^-1 H) e_0 (canonical orthogonalisation of N);
+// status[0] = number of dropped directions, status[1] = 1 if non-finite.
+void launch_krylov_small(const double2* d_N, const double2* d_H, int m, double dt,
+                         double2* d_c, int* d_status, cudaStream_t st);
+// y[k] = a * x[k] / b[k] style scalar helpers on device scalars
+void launch_scalar_div_neg(const double2* num, const double2* den, double2* out, cudaStream_t st);
+// norm of a buffer (sqrt of sum |x|^2) and scaling of it by 1/norm
+void launch_normalize(double2* x, size_t n, double2* d_norm_out, cudaStream_t st);
+void launch_scale(double2* x, size_t n, double2 a, cudaStream_t st);
+void launch_trace_channels(const double2* E, int rows, int nch, int cols, const double2* R,
+                           double2* out, cudaStream_t st);
+
+}  // namespace tdmps

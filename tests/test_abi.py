@@ -1,0 +1,95 @@
+"""The C-ABI library loads without a GPU and exports every declared symbol;
+host-side MPO construction (no GPU) reproduces the full-CI Hamiltonian."""
+import os
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import fci
+from oracle import mps as om
+
+import paper_1902_08489_gb300 as td
+
+
+@pytest.fixture(scope="module")
+def built():
+    if not os.path.exists(td.LIB_PATH):
+        from paper_1902_08489_gb300 import build
+        build.build()
+    return td.lib()
+
+
+def test_exports_every_header_symbol(built):
+    syms = td.header_symbols()
+    assert len(syms) >= 20
+    missing = [s for s in syms if not hasattr(built, s)]
+    assert not missing, missing
+    for s in ["tdmps_build_mpo", "tdmps_mps_from_determinant", "tdmps_apply_H", "tdmps_overlap",
+              "tdmps_compress", "tdmps_rk4_step", "tdmps_krylov_step", "tdmps_one_rdm"]:
+        assert s in syms
+
+
+def test_invalid_arguments_are_rejected_without_gpu(built):
+    h = np.zeros((2, 2))
+    eri = np.zeros((2, 2, 2, 2))
+    with pytest.raises(td.TdmpsError) as e:
+        td.build_mpo(None, h, eri, L=0)
+    assert e.value.name == "INVALID_ARG"
+    h[0, 0] = np.nan
+    with pytest.raises(td.TdmpsError) as e:
+        td.build_mpo(None, h, eri)
+    assert e.value.name == "NONFINITE"
+
+
+def _dense_mpo(mpo, L):
+    """Contract W_0 ... W_{L-1} into the 4^L x 4^L operator (first site
+    slowest), from the host copy of the MPO elements."""
+    dims, _ = mpo.bond_dims()
+    Ws = []
+    for i in range(L):
+        win, wout, sig, sigp, v = mpo.elements(i)
+        W = np.zeros((dims[i], dims[i + 1], 4, 4))
+        np.add.at(W, (win, wout, sig, sigp), v)
+        Ws.append(W)
+    T = Ws[0][0]                       # (w1, 4, 4)
+    for i in range(1, L):
+        T = np.einsum("wab,wvcd->vacbd", T, Ws[i])
+        n = T.shape[1] * T.shape[2]
+        T = T.reshape(T.shape[0], n, n)
+    assert T.shape[0] == 1
+    return T[0]
+
+
+@pytest.mark.parametrize("L,seed", [(2, 0), (3, 1), (4, 2)])
+def test_host_mpo_equals_full_ci_hamiltonian(built, L, seed):
+    I = synth.make_integrals(L, seed=seed, n_chol=4)
+    mpo = td.build_mpo(None, I.h, I.eri, n_elec=L, e0=0.37)
+    Hm = _dense_mpo(mpo, L)
+    assert np.abs(Hm - Hm.T).max() < 1e-12
+    for na in range(L + 1):
+        for nb in range(L + 1):
+            dets = fci.basis(L, na, nb)
+            idx = om.fock_index(dets, L)
+            ref = fci.hamiltonian(I.h, I.eri, dets, e0=0.37)
+            assert np.allclose(Hm[np.ix_(idx, idx)], ref, atol=1e-12)
+    # no matrix elements between different (N, S_z) sectors
+    blocks = np.zeros_like(Hm)
+    for na in range(L + 1):
+        for nb in range(L + 1):
+            idx = om.fock_index(fci.basis(L, na, nb), L)
+            blocks[np.ix_(idx, idx)] = Hm[np.ix_(idx, idx)]
+    assert np.abs(Hm - blocks).max() == 0.0
+
+
+def test_mpo_bond_dimension_is_quadratic_in_the_smaller_side(built):
+    L = 16
+    I = synth.make_integrals(L, seed=0)
+    mpo = td.build_mpo(None, I.h, I.eri, n_elec=16)
+    dims, nel = mpo.bond_dims()
+    assert dims[0] == 1 and dims[L] == 1
+    # complementary-operator count: 2 + 4L singles + O(8 min(k, L-k)^2) pairs
+    for k in range(1, L):
+        m = min(k, L - k)
+        assert dims[k] <= 2 + 4 * L + 8 * m * m + 8 * m, (k, dims[k])
+    assert dims[L // 2] <= 600
