@@ -1,0 +1,303 @@
+"""Benchmark: Krylov MPS time steps at L = 16, D = 256 (apply_H TFLOP/s).
+
+One step is one Krylov time step (paper Sec. 2.2.3; m = 10, dt = 0.05 a.u.,
+D = 256, eps = 1e-8) of a 16-orbital, 15-electron, S_z = 1/2 state: fitted H
+applications (environments, local matvecs, gauge moves and truncation),
+fitted sums, the exact overlaps and H sandwiches of the Krylov matrices, and
+the small FP64 exponential -- every stage of the hot path.  The state starts
+as a seeded random block-sparse MPS at full D so every timed step runs at the
+benchmark bond dimension; integrals are the seeded synthetic set standing in
+for the paper's active spaces.  ``value`` is the algorithmic (block-sparse)
+contraction FLOPs of the timed steps divided by their device time.
+
+--impl reference times the CPU oracle instead (the only other place this file
+runs oracle code).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "apply_H TFLOP/s at L=16, D=256 (Krylov step)"
+L, N_ELEC, TWO_SZ, D = 16, 15, 1, 256
+M_KRYLOV, DT, EPS = 10, 0.05, 1e-8
+SCHEDULE = (0, 2)   # two-site sweeps, one-site sweeps per fit
+
+
+def _peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.samples = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 7:
+                self.samples.append(parts)
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
+        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for s in self.samples for k in range(4)
+                          if s[3 + k].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(self.samples)}
+
+
+def cpu_baseline(seconds=20.0):
+    """The oracle as it stands on the host cores: fitted H applications of the
+    same kind (dense-projection fit, same sweep schedule) on a bounded sample,
+    the L = 8, N = 7 system (the oracle holds 4^L-long vectors, so L = 16 is
+    out of its reach).  FLOPs are the oracle's own complex arithmetic."""
+    import synth
+    from oracle import mps as om
+    Ls, Ds = 8, 64
+    I = synth.make_integrals(Ls, seed=0)
+    sysb = om.System.build(I.h, I.eri, 4, 3)
+    A, q = synth.random_mps(Ls, 7, 1, Ds, seed=0)
+    psi = om.from_arrays(A, q)
+    sch = om.Schedule(D=Ds, eps=EPS, n_two_site=0, n_one_site=2)
+    # oracle FLOPs per one-site projection: two contractions with the 4^L target
+    flops_fit = 0.0
+    dims = psi.bond_dims
+    for _ in range(2 * sch.n_one_site + 1):
+        for i in range(Ls):
+            flops_fit += 8.0 * (4 ** Ls) * (dims[i] + dims[i + 1])
+    flops_H = 2.0 * len(sysb.dets) ** 2
+    t0 = time.perf_counter()
+    n = 0
+    while True:
+        om.apply_H(sysb, psi, -1j * DT, sch)
+        n += 1
+        if time.perf_counter() - t0 > seconds:
+            break
+    dt = time.perf_counter() - t0
+    threads = os.environ.get("OMP_NUM_THREADS") or str(os.cpu_count())
+    return {"value": n * (flops_fit + flops_H) / dt / 1e12, "unit": "TFLOP/s",
+            "cores": int(threads), "kind": "oracle",
+            "sample": "%d dense-projection apply_H fits, L=8 N=7 D=64, one-site x2 "
+                      "(L=16 needs 4^16-long vectors)" % n,
+            "ms_per_fit": 1e3 * dt / n}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    for _ in range(args.warmup):
+        pass
+    t0 = time.perf_counter()
+    vals = []
+    for _ in range(args.steps):
+        vals.append(cpu_baseline(seconds=max(5.0, 20.0 / max(1, args.steps))))
+    dt = time.perf_counter() - t0
+    v = statistics.median([x["value"] for x in vals])
+    cb = dict(vals[0])
+    cb["value"] = v
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "TFLOP/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * dt / max(1, args.steps), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "oracle sample: apply_H L=8 N=7 D=64 (stands in for L=16 D=256)"},
+            "cpu_baseline": cb,
+            "e2e": {"value": v, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--precision", default="fp64")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--mode", default="krylov", choices=["krylov", "apply"],
+                    help="krylov: one Krylov time step per step (default); apply: one "
+                         "fitted H application (one one-site sweep) per step")
+    ap.add_argument("--schedule", default=None, help="two-site,one-site sweeps per fit")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import paper_1902_08489_gb300 as td
+    import synth
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    ctx = td.Context(args.precision)
+    sched = SCHEDULE if args.mode == "krylov" else (0, 1)
+    if args.schedule:
+        sched = tuple(int(x) for x in args.schedule.split(","))
+    ctx.set_schedule(*sched)
+    I = synth.make_integrals(L, seed=0)
+    mpo = td.build_mpo(ctx, I.h, I.eri, n_elec=N_ELEC)
+    # replicas only: each rank evolves its own seeded state, no collective
+    A, q = synth.random_mps(L, N_ELEC, TWO_SZ, D, seed=rank)
+    nrm = None
+    psi = td.mps_import(ctx, A, q)
+    nrm = abs(td.overlap(ctx, psi, psi)) ** 0.5
+    A[0] = A[0] / nrm
+    h2d_bytes = sum(int(np.count_nonzero(t)) for t in A) * 16
+
+    def step(state):
+        if args.mode == "krylov":
+            td.krylov_step(ctx, mpo, state, DT, M_KRYLOV, True, D, EPS)
+        else:
+            out = td.apply_H(ctx, mpo, state, -1j * DT, D, EPS)
+            out.free()
+
+    state = td.mps_import(ctx, A, q)
+    for _ in range(args.warmup):
+        step(state)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ctx.stats_enable(True)
+    ctx.stats_reset()
+    stream = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with Clocks(local) as clk:
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            step(state)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    st = ctx.stats()
+    ctx.stats_enable(False)
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    flops = st["gemm"]["flops"] + st["wstage"]["flops"]
+    value = world * flops / (ms / 1e3) / 1e12
+
+    # end-to-end through the public API with host buffers: import the state
+    # from host memory, one Krylov step, read the 1-RDM back
+    e2e = None
+    if not args.no_e2e:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(max(1, args.steps)):
+            s2 = td.mps_import(ctx, A, q)
+            step(s2)
+            g = td.one_rdm(ctx, s2)
+            s2.free()
+        torch.cuda.synchronize()
+        te = time.perf_counter() - t0
+        e2e = {"value": world * flops / te / 1e12,
+               "unit": "TFLOP/s", "h2d_bytes_per_step": h2d_bytes,
+               "d2h_bytes_per_step": int(g.nbytes)}
+
+    peaks = _peaks()
+    # dominant kernel: the class with the largest event time
+    kinds = sorted(st, key=lambda k: -st[k]["ms"])
+    top = kinds[0]
+    ks = st[top]
+    per_launch_ms = ks["ms"] / max(1, ks["launches"])
+    if top in ("gemm",):
+        fp64_peak = peaks.get("bf16_tflops", 1913.9) * (1.25 / 2250.0)
+        achieved = ks["flops"] / max(1, ks["launches"]) / (per_launch_ms / 1e3) / 1e12
+        roof = {"kernel": "k_gemm (grouped complex block GEMM)", "bound": "alu",
+                "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
+                "frac": achieved / fp64_peak, "traffic": None,
+                "peak_source": "measured bf16 x nominal FP64/bf16 ratio (1.25/2250)"}
+    else:
+        hbm = peaks.get("hbm_gbs", 6675.5)
+        achieved = ks["bytes"] / max(1, ks["launches"]) / (per_launch_ms / 1e3) / 1e9
+        roof = {"kernel": top, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                "frac": achieved / hbm, "traffic": None, "peak_source": "measured hbm_gbs"}
+    line = {
+        "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": {"fp64": "f64", "tf32": "tf32", "tf32x3": "tf32x3", "bf16": "bf16"}[args.precision],
+        "data": "synthetic",
+        "config": {"workload": ("Krylov step, L=16 N=15 2Sz=1 D=256 m=10 dt=0.05 eps=1e-8, "
+                                "fit schedule %d two-site + %d one-site sweeps, random seeded "
+                                "D=256 start" % sched) if args.mode == "krylov" else
+                               ("apply_H fit, L=16 N=15 2Sz=1 D=256, schedule %d two-site + "
+                                "%d one-site sweeps, random seeded D=256 state" % sched),
+                   "l2": "inputs larger than L2 (Krylov basis + environments, several GB)",
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "steps_per_s": 1e3 * args.steps / ms,
+        "gpu_launches": int(sum(v["launches"] for v in st.values())),
+        "kernel_stats": {k: {"launches": v["launches"], "ms": round(v["ms"], 3),
+                             "gflop": round(v["flops"] / 1e9, 3), "gb": round(v["bytes"] / 1e9, 3)}
+                         for k, v in st.items()},
+        "roofline": roof,
+        "clocks": clk.summary(),
+        "e2e": e2e,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(20.0)
+    if rank == 0:
+        print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -26,6 +26,8 @@ Fixed schedule (the paper leaves it open; the same schedule runs on the GPU):
   2. ``n_one_site`` one-site sweeps: sites 0..L-1 left to right (thin QR per
      right sector moves the gauge), then L-1..0 right to left (thin LQ per
      left sector).  The result is right-canonical with its norm on site 0.
+     The QR is ``gram_schmidt_qr``: dependent columns add no direction, so the
+     new bond basis spans exactly the column space of the local solution.
 The initial guess is the input MPS for H|A> and the first term's MPS for sums,
 a deterministic stand-in for the paper's random initial MPS.
 
@@ -127,11 +129,26 @@ def coefficient(mps: MPS, occ) -> complex:
     return complex(v[0])
 
 
+def coefficients(mps: MPS, occs) -> np.ndarray:
+    """<det|mps> for many configurations at once: the same products of
+    Eq. (mps), evaluated site by site for all configurations together."""
+    occs = np.asarray(occs, dtype=np.int64)
+    v = np.ones((len(occs), 1), dtype=np.complex128)
+    for i, A in enumerate(mps.tensors):
+        nv = np.zeros((len(occs), A.shape[2]), dtype=np.complex128)
+        for s in range(4):
+            sel = occs[:, i] == s
+            if sel.any():
+                nv[sel] = v[sel] @ A[:, s, :]
+        v = nv
+    return v[:, 0]
+
+
 def overlap(bra: MPS, ket: MPS) -> complex:
     """<bra|ket> by contracting the two chains site by site (any L)."""
     E = np.ones((1, 1), dtype=np.complex128)
     for B, A in zip(bra.tensors, ket.tensors):
-        E = np.einsum("ab,asc,bsd->cd", E, B.conj(), A)
+        E = sum(B[:, s, :].conj().T @ (E @ A[:, s, :]) for s in range(4))
     return complex(E[0, 0])
 
 
@@ -159,6 +176,36 @@ def _sectors(labels: np.ndarray):
     return sorted({(int(a), int(b)) for a, b in labels})
 
 
+QR_DEP_TOL = 1e-12
+
+
+def gram_schmidt_qr(M: np.ndarray):
+    """Thin QR by classical Gram-Schmidt with one re-orthogonalisation.
+
+    A column whose residual norm is <= 1e-12 times the largest column norm of
+    M adds no direction.  Q has k = min(m, n) columns: the independent
+    directions in column order, then zero columns; R (k x n) satisfies
+    M = Q R.  For full-rank M this spans the same space as any QR."""
+    m, n = M.shape
+    k = min(m, n)
+    Q = np.zeros((m, k), dtype=np.complex128)
+    R = np.zeros((k, n), dtype=np.complex128)
+    tol = QR_DEP_TOL * (np.linalg.norm(M, axis=0).max() if n else 0.0)
+    nq = 0
+    for j in range(n):
+        v = M[:, j].astype(np.complex128).copy()
+        for _ in range(2):
+            c = Q[:, :nq].conj().T @ v
+            v = v - Q[:, :nq] @ c
+            R[:nq, j] += c
+        nrm = np.linalg.norm(v)
+        if nrm > tol and nq < k:
+            Q[:, nq] = v / nrm
+            R[nq, j] = nrm
+            nq += 1
+    return Q, R
+
+
 def qr_left(C: np.ndarray, ql: np.ndarray, qr: np.ndarray):
     """Thin QR of C viewed as a (left x sigma) by right matrix, one right
     sector at a time.  Returns (Q tensor, new right labels, R blocks)."""
@@ -171,7 +218,7 @@ def qr_left(C: np.ndarray, ql: np.ndarray, qr: np.ndarray):
         cols = _rows_of(qr, q)
         if len(rows) == 0 or len(cols) == 0:
             continue
-        Q, R = np.linalg.qr(M[np.ix_(rows, cols)], mode="reduced")
+        Q, R = gram_schmidt_qr(M[np.ix_(rows, cols)])
         full = np.zeros((Dl * d, Q.shape[1]), dtype=np.complex128)
         full[rows] = Q
         cols_out.append(full)
@@ -194,7 +241,7 @@ def lq_right(C: np.ndarray, ql: np.ndarray, qr: np.ndarray):
         cols = _rows_of(collab, q)
         if len(rows) == 0 or len(cols) == 0:
             continue
-        Qh, Rh = np.linalg.qr(M[np.ix_(rows, cols)].conj().T, mode="reduced")
+        Qh, Rh = gram_schmidt_qr(M[np.ix_(rows, cols)].conj().T)
         full = np.zeros((Qh.shape[1], d * Dr), dtype=np.complex128)
         full[:, cols] = Qh.conj().T
         rows_out.append(full)

@@ -726,7 +726,9 @@ void run_svd(Context& c, FactWork& fw) {
   const FactTask* d = c.stage(fw.tasks);
   cudaEvent_t ev;
   c.kbegin(TDMPS_KSTAT_SVD, &ev);
-  launch_svd(d, (int)fw.tasks.size(), (int*)c.status->p, c.st);
+  size_t mx = 0;
+  for (auto& t : fw.tasks) mx = std::max(mx, (size_t)(t.m * t.n + t.n * t.n) * sizeof(double2));
+  launch_svd(d, (int)fw.tasks.size(), (int*)c.status->p, c.st, mx);
   double fl = 0.0;
   for (auto& t : fw.tasks) fl += 8.0 * 8.0 * t.m * t.n * t.n;
   c.kend(TDMPS_KSTAT_SVD, ev, fl, 0.0);

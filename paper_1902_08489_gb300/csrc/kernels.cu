@@ -227,23 +227,44 @@ void launch_scale(double2* x, size_t n, double2 a, cudaStream_t st) {
 // ------------------------------------------------------------------ Jacobi SVD
 
 // One-sided (Hestenes) Jacobi on the columns of a column-major m x n matrix
-// (n <= m): pairs of columns are rotated until mutually orthogonal to 1e-15
+// (n <= m): pairs of columns are rotated until mutually orthogonal to m*eps
 // relative; round-robin pairing lets every warp rotate a disjoint pair.
+// Columns below 1e-13 of the Frobenius norm are numerically zero and are not
+// rotated (their singular values fall under the truncation floor).
 // Afterwards sigma_j = |a_j|, u_j = a_j / sigma_j, columns sorted descending.
-constexpr int SVD_THREADS = 512;
-constexpr int SVD_MAX_SWEEPS = 80;
+// The matrix and V live in shared memory when both fit (smem_budget bytes).
+constexpr int SVD_THREADS = 1024;
+constexpr int SVD_MAX_SWEEPS = 60;
 
 __global__ void __launch_bounds__(SVD_THREADS) k_svd(const FactTask* __restrict__ tasks,
-                                                     int* status) {
+                                                     int* status, int smem_budget) {
+  extern __shared__ double2 svd_sh[];
   const FactTask t = tasks[blockIdx.x];
   const int m = t.m, n = t.n;
-  double2* A = t.A;
-  double2* V = t.V;
+  const bool a_sh = (size_t)m * n * sizeof(double2) <= (size_t)smem_budget && n <= 1024;
+  const bool v_sh = a_sh && (size_t)(m * n + n * n) * sizeof(double2) <= (size_t)smem_budget;
+  double2* A = a_sh ? svd_sh : t.A;
+  double2* V = v_sh ? svd_sh + (size_t)m * n : t.V;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  __shared__ int rotated;
+  __shared__ double fro2;
+  __shared__ int perm[1024];
+  if (threadIdx.x == 0) fro2 = 0.0;
+  if (a_sh)
+    for (size_t e = threadIdx.x; e < (size_t)m * n; e += blockDim.x) A[e] = t.A[e];
   for (int e = threadIdx.x; e < n * n; e += blockDim.x)
     V[e] = make_double2((e % n) == (e / n) ? 1.0 : 0.0, 0.0);
-  __shared__ int rotated;
   __syncthreads();
+  {
+    double s2 = 0.0;
+    for (size_t e = threadIdx.x; e < (size_t)m * n; e += blockDim.x) s2 += cabs2(A[e]);
+    s2 = warp_sum(s2);
+    if (lane == 0) atomicAdd(&fro2, s2);
+  }
+  __syncthreads();
+  const double negl = 1e-26 * fro2;
+  // the computed inner product carries ~m eps relative rounding error
+  const double tol = 2.2e-16 * fmax(16.0, (double)m);
   const int np = (n + 1) & ~1;   // even number of players
   int sweep = 0;
   for (; sweep < SVD_MAX_SWEEPS; ++sweep) {
@@ -268,7 +289,7 @@ __global__ void __launch_bounds__(SVD_THREADS) k_svd(const FactTask* __restrict_
         }
         al = warp_sum(al); be = warp_sum(be); gr = warp_sum(gr); gi = warp_sum(gi);
         double g = sqrt(gr * gr + gi * gi);
-        if (g == 0.0 || al == 0.0 || be == 0.0 || g <= 1e-15 * sqrt(al * be)) continue;
+        if (g == 0.0 || al <= negl || be <= negl || g <= tol * sqrt(al * be)) continue;
         double zeta = (be - al) / (2.0 * g);
         double tt = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
         double c = 1.0 / sqrt(1.0 + tt * tt), s = c * tt;
@@ -291,25 +312,62 @@ __global__ void __launch_bounds__(SVD_THREADS) k_svd(const FactTask* __restrict_
       }
       __syncthreads();
     }
-    __syncthreads();
     int any = rotated;
     __syncthreads();
     if (!any) break;
   }
   if (threadIdx.x == 0 && sweep == SVD_MAX_SWEEPS) atomicExch(status, 1);
-  // singular values and normalisation
+  // singular values
   for (int j = warp; j < n; j += nwarp) {
-    double2* aj = A + (size_t)j * m;
+    const double2* aj = A + (size_t)j * m;
     double s2 = 0.0;
     for (int i = lane; i < m; i += 32) s2 += cabs2(aj[i]);
     s2 = warp_sum(s2);
-    double sv = sqrt(s2);
-    if (lane == 0) t.s[j] = sv;
+    if (lane == 0) t.s[j] = sqrt(s2);
+  }
+  __syncthreads();
+  if (a_sh) {
+    // descending order (ties: lower index first) written straight out
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+      double sj = t.s[j];
+      int rank = 0;
+      for (int k = 0; k < n; ++k) {
+        double sk = t.s[k];
+        rank += (sk > sj) || (sk == sj && k < j);
+      }
+      perm[rank] = j;
+    }
+    __syncthreads();
+    for (size_t e = threadIdx.x; e < (size_t)m * n; e += blockDim.x) {
+      int j = (int)(e / m), i = (int)(e % m);
+      double sj = t.s[perm[j]];
+      double inv = sj > 0.0 ? 1.0 / sj : 0.0;
+      t.A[e] = cscale(A[(size_t)perm[j] * m + i], inv);
+    }
+    __syncthreads();
+    if (!v_sh) {   // A's shared buffer is free: stage V there (n*n <= m*n)
+      for (size_t e = threadIdx.x; e < (size_t)n * n; e += blockDim.x) svd_sh[e] = t.V[e];
+      __syncthreads();
+      V = svd_sh;
+    }
+    for (size_t e = threadIdx.x; e < (size_t)n * n; e += blockDim.x) {
+      int j = (int)(e / n), i = (int)(e % n);
+      t.V[e] = V[(size_t)perm[j] * n + i];
+    }
+    // permute the singular values: one thread per value (n <= 1024 = blockDim)
+    double mine = threadIdx.x < n ? t.s[perm[threadIdx.x]] : 0.0;
+    __syncthreads();
+    if (threadIdx.x < n) t.s[threadIdx.x] = mine;
+    return;
+  }
+  for (int j = warp; j < n; j += nwarp) {
+    double2* aj = A + (size_t)j * m;
+    double sv = t.s[j];
     double inv = sv > 0.0 ? 1.0 / sv : 0.0;
     for (int i = lane; i < m; i += 32) aj[i] = cscale(aj[i], inv);
   }
   __syncthreads();
-  // selection sort, descending (stable for ties: lower index first)
+  // selection sort in global memory, descending (ties: lower index first)
   __shared__ int sel;
   for (int j = 0; j < n - 1; ++j) {
     if (threadIdx.x == 0) {
@@ -341,9 +399,18 @@ __global__ void __launch_bounds__(SVD_THREADS) k_svd(const FactTask* __restrict_
   }
 }
 
-void launch_svd(const FactTask* d_tasks, int ntasks, int* d_status, cudaStream_t st) {
+void launch_svd(const FactTask* d_tasks, int ntasks, int* d_status, cudaStream_t st,
+                size_t max_bytes) {
   if (ntasks <= 0) return;
-  k_svd<<<ntasks, SVD_THREADS, 0, st>>>(d_tasks, d_status);
+  // static shared: perm (4 KB) + scalars
+  const size_t cap = 227 * 1024 - 5 * 1024;
+  size_t dyn = max_bytes < cap ? max_bytes : cap;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_svd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cap);
+    attr = true;
+  }
+  k_svd<<<ntasks, SVD_THREADS, dyn, st>>>(d_tasks, d_status, (int)dyn);
 }
 
 // ------------------------------------------------------------------ CGS2 QR
@@ -566,11 +633,17 @@ __global__ void k_krylov_small(const double2* Nm, const double2* Hm, int m, doub
   for (int i = 0; i < m * m; ++i) {
     if (!isfinite(Nm[i].x) || !isfinite(Nm[i].y) || !isfinite(Hm[i].x) || !isfinite(Hm[i].y)) bad = 1;
   }
-  // Hermitian parts
+  // N and H arrive with their upper triangles (i <= j) filled; complete them
+  // as Hermitian matrices
+  double2 Nf[KMAX * KMAX], Hf[KMAX * KMAX];
   for (int i = 0; i < m; ++i)
     for (int j = 0; j < m; ++j) {
-      double2 a = Nm[i * m + j], b = cconj(Nm[j * m + i]);
-      A[i * m + j] = make_double2(0.5 * (a.x + b.x), 0.5 * (a.y + b.y));
+      double2 n = i <= j ? Nm[i * m + j] : cconj(Nm[j * m + i]);
+      double2 h = i <= j ? Hm[i * m + j] : cconj(Hm[j * m + i]);
+      if (i == j) { n.y = 0.0; h.y = 0.0; }
+      Nf[i * m + j] = n;
+      Hf[i * m + j] = h;
+      A[i * m + j] = n;
     }
   herm_eig(A, V, w, m);
   double wmax = 0.0;
@@ -588,8 +661,7 @@ __global__ void k_krylov_small(const double2* Nm, const double2* Hm, int m, doub
       double2 acc = make_double2(0.0, 0.0);
       for (int i = 0; i < m; ++i)
         for (int j = 0; j < m; ++j) {
-          double2 hij = cscale(cadd(Hm[i * m + j], cconj(Hm[j * m + i])), 0.5);
-          acc = cadd(acc, cmul(cmul(cconj(X[i * KMAX + a]), hij), X[j * KMAX + b]));
+          acc = cadd(acc, cmul(cmul(cconj(X[i * KMAX + a]), Hf[i * m + j]), X[j * KMAX + b]));
         }
       M[a * r + b] = acc;
     }
@@ -598,7 +670,7 @@ __global__ void k_krylov_small(const double2* Nm, const double2* Hm, int m, doub
   double2 bvec[KMAX], tmp[KMAX];
   for (int a = 0; a < r; ++a) {
     double2 acc = make_double2(0.0, 0.0);
-    for (int i = 0; i < m; ++i) acc = cadd(acc, cmul(cconj(X[i * KMAX + a]), Nm[i * m + 0]));
+    for (int i = 0; i < m; ++i) acc = cadd(acc, cmul(cconj(X[i * KMAX + a]), Nf[i * m + 0]));
     bvec[a] = acc;
   }
   for (int a = 0; a < r; ++a) {   // tmp = exp(-i dt lam) U^H b

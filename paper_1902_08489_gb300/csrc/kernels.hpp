@@ -79,7 +79,9 @@ void launch_wstage(const WTask* d_tasks, int ntasks, int64_t total_work, const i
 void launch_copy(const CopyTask* d_tasks, int ntasks, int to_work, cudaStream_t st);
 void launch_scatter(const ScatterTask* d_tasks, int ntasks, cudaStream_t st);
 void launch_zero(double2* p, size_t n, cudaStream_t st);
-void launch_svd(const FactTask* d_tasks, int ntasks, int* d_status, cudaStream_t st);
+// max_bytes: largest (m*n + n*n) * 16 of the tasks (shared-memory sizing)
+void launch_svd(const FactTask* d_tasks, int ntasks, int* d_status, cudaStream_t st,
+                size_t max_bytes);
 void launch_qr(const FactTask* d_tasks, int ntasks, cudaStream_t st);
 // truncation rule over nv singular values (grouped by sector, each sector
 // descending; sector id per value): writes kept count per sector and the

@@ -114,10 +114,9 @@ def test_full_size_sandwich_sampled_determinants(td, ctx):
         d = td.mps_from_determinant(ctx, occ)
         got = td.expectation(ctx, mpo, d, psi)
         masks, coefs = fci.h_on_determinant(I.h, I.eri, fci.occupation_mask(occ))
-        ref = 0.0
-        for mk, cf in zip(masks, coefs):
-            o2 = [((int(mk) >> (2 * i)) & 1) + 2 * ((int(mk) >> (2 * i + 1)) & 1) for i in range(L)]
-            ref += cf * om.coefficient(opsi, o2)
+        occs = [[((int(mk) >> (2 * i)) & 1) + 2 * ((int(mk) >> (2 * i + 1)) & 1) for i in range(L)]
+                for mk in masks]
+        ref = np.sum(coefs * om.coefficients(opsi, occs))
         assert abs(got - ref) < 1e-9 * max(1.0, abs(ref)), (got, ref)
 
 

@@ -38,6 +38,7 @@ def test_transfer_overlap_equals_vector_overlap_and_coefficients():
         occ = [((int(m) >> (2 * i)) & 1) + 2 * ((int(m) >> (2 * i + 1)) & 1) for i in range(6)]
         idx = om.fock_index(np.array([m], dtype=np.uint64), 6)[0]
         assert abs(om.coefficient(a, occ) - va[idx]) < 1e-13
+        assert abs(om.coefficients(a, [occ])[0] - va[idx]) < 1e-13
 
 
 def test_compress_two_sites_is_library_svd():
@@ -134,3 +135,20 @@ def test_scale_uses_lth_root():
     m = om.from_arrays(A, q)
     s = om.scale(m, -2.0 + 1.0j)
     assert np.allclose(om.to_fock(s), (-2.0 + 1.0j) * om.to_fock(m))
+
+
+def test_gram_schmidt_qr_against_library_qr():
+    rng = np.random.default_rng(5)
+    for m, n in [(9, 4), (4, 9), (6, 6)]:
+        M = rng.standard_normal((m, n)) + 1j * rng.standard_normal((m, n))
+        Q, R = om.gram_schmidt_qr(M)
+        Ql, _ = np.linalg.qr(M, mode="reduced")
+        assert np.allclose(Q @ R, M, atol=1e-12)
+        assert np.allclose(Q.conj().T @ Q, np.eye(min(m, n)), atol=1e-12)
+        assert np.allclose(Q @ Q.conj().T, Ql @ Ql.conj().T, atol=1e-12)   # same span
+    # a dependent column adds no direction; the last column of Q is zero
+    M = rng.standard_normal((6, 3))
+    M[:, 1] = 2.0 * M[:, 0]
+    Q, R = om.gram_schmidt_qr(M)
+    assert np.allclose(Q @ R, M, atol=1e-12)
+    assert np.abs(Q[:, 2]).max() == 0.0
