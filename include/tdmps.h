@@ -62,13 +62,16 @@ enum {
   TDMPS_FP64 = 0,   /* complex FP64 everywhere                               */
   TDMPS_TF32 = 1,   /* TF32 tensor-core products, FP32 accumulation          */
   TDMPS_TF32X3 = 2, /* split TF32 (hi*hi + hi*lo + lo*hi), FP32 accumulation */
-  TDMPS_BF16 = 3    /* BF16 tensor-core products, FP32 accumulation          */
+  TDMPS_BF16 = 3    /* reserved: BF16 tensor-core products (not in this build,
+                       INVALID_ARG)                                          */
 };
 
 /* ---------------------------------------------------------------- context */
 
 /* Create a context on the current CUDA device.  cuda_stream: a cudaStream_t
- * (NULL = the legacy default stream).  precision: TDMPS_FP64 .. TDMPS_BF16.
+ * (NULL = the legacy default stream).  precision: TDMPS_FP64, TDMPS_TF32 or
+ * TDMPS_TF32X3 (TF32 modes keep environments and intermediates in complex
+ * FP32 and run the block contractions on the tcgen05 tensor cores).
  * Errors: INVALID_ARG (bad precision, ctx == NULL), CUDA. */
 int tdmps_create(tdmps_ctx_t* ctx, void* cuda_stream, int precision);
 int tdmps_destroy(tdmps_ctx_t ctx);

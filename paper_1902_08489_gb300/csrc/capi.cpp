@@ -69,8 +69,9 @@ extern "C" {
 
 int tdmps_create(tdmps_ctx_t* ctx, void* cuda_stream, int precision) {
   if (!ctx) { g_create_err = "ctx is NULL"; return TDMPS_ERR_INVALID_ARG; }
-  if (precision < TDMPS_FP64 || precision > TDMPS_BF16) {
-    g_create_err = "unknown precision";
+  if (precision < TDMPS_FP64 || precision > TDMPS_TF32X3) {
+    g_create_err = precision == TDMPS_BF16 ? "BF16 contractions are not available in this build"
+                                           : "unknown precision";
     return TDMPS_ERR_INVALID_ARG;
   }
   try {
@@ -100,7 +101,9 @@ const char* tdmps_create_error(void) { return g_create_err.c_str(); }
 int tdmps_set_precision(tdmps_ctx_t ctx, int precision) {
   if (!ctx) return TDMPS_ERR_INVALID_ARG;
   return guard(ctx, [&] {
-    need(precision >= TDMPS_FP64 && precision <= TDMPS_BF16, "unknown precision");
+    need(precision >= TDMPS_FP64 && precision <= TDMPS_TF32X3,
+         precision == TDMPS_BF16 ? "BF16 contractions are not available in this build"
+                                 : "unknown precision");
     ctx->c->precision = precision;
   });
 }

@@ -86,8 +86,8 @@ SiteT make_site(const RowGroups& rows, const Bond& right, cudaStream_t st, bool 
 }
 
 void Inter::alloc(cudaStream_t st, bool zero) {
-  data = dev_alloc(std::max<size_t>(size, 1) * sizeof(double2), st);
-  if (zero) launch_zero((double2*)data->p, size, st);
+  data = dev_alloc(std::max<size_t>(size, 1) * esz(), st);
+  if (zero) TD_CHECK_CUDA(cudaMemsetAsync(data->p, 0, size * esz(), st));
 }
 
 // ------------------------------------------------------------------ context
@@ -166,7 +166,22 @@ void Context::collect_stats() {
   pending.clear();
 }
 
-void Context::sync() { TD_CHECK_CUDA(cudaStreamSynchronize(st)); }
+void Context::sync() {
+  TD_CHECK_CUDA(cudaStreamSynchronize(st));
+  check_device_errors();
+}
+
+// Error words written by kernels whose bounded waits ran out (read after a
+// stream synchronisation; sticky until reported).
+void Context::check_device_errors() {
+  int h[16];
+  TD_CHECK_CUDA(cudaMemcpyAsync(h, status->p, sizeof(h), cudaMemcpyDeviceToHost, st));
+  TD_CHECK_CUDA(cudaStreamSynchronize(st));
+  if (h[8]) {
+    TD_CHECK_CUDA(cudaMemsetAsync((int*)status->p + 8, 0, sizeof(int), st));
+    throw Error(TDMPS_ERR_NUMERIC, "a tensor-core barrier wait timed out");
+  }
+}
 
 const MPOd& Context::identity_mpo(int L) {
   if (!ident || ident->L != L) {
@@ -259,12 +274,20 @@ void upload_mpo_tables(MPOd& m, Context& c) {
 
 namespace {
 
+// One grouped GEMM launch.  FP64 contexts (and every gauge-move GEMM) use
+// the FP64 kernel; mixed-precision contexts use the tcgen05 kernel, which
+// reads complex double or complex float operands and writes either.
 struct GemmBatch {
+  Context& c;
+  bool fp64;
   std::vector<GemmTask> tasks;
   std::vector<GemmTerm> terms;
   double flops = 0.0, bytes = 0.0;
-  void task(double2* C, int M, int N, int ldc, int opA, int opB, bool beta, cplx alpha,
-            const double2* aptr = nullptr, const double2* adiv = nullptr) {
+  explicit GemmBatch(Context& ctx, bool force_fp64 = false)
+      : c(ctx), fp64(force_fp64 || ctx.precision == TDMPS_FP64) {}
+  void task(void* C, int tc, int M, int N, int ldc, int opA, int ta, int opB, int tb, bool beta,
+            cplx alpha, const double2* aptr = nullptr, const double2* adiv = nullptr) {
+    if (fp64 && (ta || tb || tc)) throw Error(TDMPS_ERR_INVALID_ARG, "FP64 GEMM on float data");
     GemmTask t{};
     t.C = C;
     t.alpha_ptr = aptr;
@@ -272,25 +295,28 @@ struct GemmBatch {
     t.alpha = make_double2(alpha.real(), alpha.imag());
     t.M = M; t.N = N; t.ldc = ldc;
     t.opA = opA; t.opB = opB; t.beta = beta ? 1 : 0;
+    t.ta = ta; t.tb = tb; t.tc = tc;
     t.term_begin = t.term_end = (int)terms.size();
     tasks.push_back(t);
-    bytes += 16.0 * M * N * (beta ? 2.0 : 1.0);
+    bytes += (tc ? 8.0 : 16.0) * M * N * (beta ? 2.0 : 1.0);
   }
-  void term(const double2* A, int lda, const double2* B, int ldb, int K) {
+  void term(const void* A, int lda, const void* B, int ldb, int K) {
     if (K <= 0) return;
     GemmTask& t = tasks.back();
     terms.push_back({A, B, K, lda, ldb, 0});
     t.term_end = (int)terms.size();
     flops += 8.0 * t.M * t.N * K;
-    bytes += 16.0 * ((double)t.M * K + (double)K * t.N);
+    bytes += (t.ta ? 8.0 : 16.0) * t.M * K + (t.tb ? 8.0 : 16.0) * K * t.N;
   }
-  void run(Context& c) {
+  void run() {
+    const int bm = fp64 ? 32 : tc_tile_m();
+    const int bn = fp64 ? 32 : tc_tile_n();
     std::vector<int> tile_task;
     std::vector<GemmTask> tk;
     for (auto& t : tasks) {
       if (t.M <= 0 || t.N <= 0) continue;
-      t.tiles_m = (t.M + 31) / 32;
-      int tn = (t.N + 31) / 32;
+      t.tiles_m = (t.M + bm - 1) / bm;
+      int tn = (t.N + bn - 1) / bn;
       t.tile_base = (int)tile_task.size();
       int id = (int)tk.size();
       tk.push_back(t);
@@ -302,7 +328,11 @@ struct GemmBatch {
     const int* dtt = c.stage(tile_task);
     cudaEvent_t ev;
     c.kbegin(TDMPS_KSTAT_GEMM, &ev);
-    launch_gemm(dt, (int)tk.size(), dm, dtt, (int)tile_task.size(), c.st);
+    if (fp64)
+      launch_gemm(dt, (int)tk.size(), dm, dtt, (int)tile_task.size(), c.st);
+    else
+      launch_gemm_tc(dt, dm, dtt, (int)tile_task.size(), c.precision == TDMPS_TF32X3 ? 1 : 0,
+                     c.tc_err(), c.st);
     c.kend(TDMPS_KSTAT_GEMM, ev, flops, bytes);
   }
 };
@@ -311,13 +341,14 @@ struct WBatch {
   std::vector<WTask> tasks;
   int64_t work = 0;
   double flops = 0.0, bytes = 0.0;
+  int et = 0;
   void run(Context& c, const MPOd& m) {
     if (tasks.empty() || work == 0) return;
     const WTask* dt = c.stage(tasks);
     cudaEvent_t ev;
     c.kbegin(TDMPS_KSTAT_WSTAGE, &ev);
     launch_wstage(dt, (int)tasks.size(), work, (const int*)m.rowptr->p, (const int*)m.ent_w->p,
-                  (const double*)m.ent_v->p, c.st);
+                  (const double*)m.ent_v->p, et, c.st);
     c.kend(TDMPS_KSTAT_WSTAGE, ev, flops, bytes);
   }
 };
@@ -334,10 +365,9 @@ static Env env_left_boundary(Context& c, const MPSd& bra, const MPSd& ket, const
   e.mb = &mpo.bonds[0];
   e.ket_copy = ket.bonds[0];
   e.t.add(0, -1, 0, 0, 1, 1, 1);
+  e.t.et = c.et();
   e.t.alloc(c.st, false);
-  double2 one = make_double2(1.0, 0.0);
-  TD_CHECK_CUDA(cudaMemcpyAsync(e.t.data->p, c.stage(&one, sizeof(one)), sizeof(one),
-                                cudaMemcpyDeviceToDevice, c.st));
+  launch_fill_one(e.t.data->p, e.t.et, c.st);
   return e;
 }
 
@@ -350,10 +380,9 @@ static Env env_right_boundary(Context& c, const MPSd& bra, const MPSd& ket, cons
   e.mb = &mpo.bonds[L];
   e.ket_copy = ket.bonds[L];
   e.t.add(0, -1, 0, 0, 1, 1, 1);
+  e.t.et = c.et();
   e.t.alloc(c.st, false);
-  double2 one = make_double2(1.0, 0.0);
-  TD_CHECK_CUDA(cudaMemcpyAsync(e.t.data->p, c.stage(&one, sizeof(one)), sizeof(one),
-                                cudaMemcpyDeviceToDevice, c.st));
+  launch_fill_one(e.t.data->p, e.t.et, c.st);
   return e;
 }
 
@@ -371,15 +400,16 @@ static Inter lstage(Context& c, const Env& E, const SiteT& ket, const Bond& ket_
       src.push_back({b, kb});
     }
   }
+  X.et = E.t.et;
   X.alloc(c.st, false);
-  GemmBatch gb;
+  GemmBatch gb(c);
   for (int x = 0; x < (int)X.blocks.size(); ++x) {
     const Inter::Blk& xb = X.blocks[x];
     const Inter::Blk& eb = E.t.blocks[src[x].first];
-    gb.task(X.ptr(x), xb.rows * xb.W, xb.cols, xb.cols, OP_N, OP_N, false, 1.0);
+    gb.task(X.ptr(x), X.et, xb.rows * xb.W, xb.cols, xb.cols, OP_N, E.t.et, OP_N, 0, false, 1.0);
     gb.term(E.t.ptr(src[x].first), eb.cols, ket.ptr(src[x].second), xb.cols, eb.cols);
   }
-  gb.run(c);
+  gb.run();
   return X;
 }
 
@@ -423,8 +453,10 @@ static Inter wstage_left(Context& c, const Inter& X, const MPOd& m, int site) {
       pend.push_back(p);
     }
   }
+  Y.et = X.et;
   Y.alloc(c.st, false);
   WBatch wb;
+  wb.et = Y.et;
   for (int y = 0; y < (int)Y.blocks.size(); ++y) {
     const Inter::Blk& yb = Y.blocks[y];
     WTask t{};
@@ -441,11 +473,11 @@ static Inter wstage_left(Context& c, const Inter& X, const MPOd& m, int site) {
       t.win[sp] = X.blocks[x].W;
       const WTable& tb = m.tab_left[site][pend[y].tabs[sp]];
       t.csr[sp] = tb.rowptr_off;
-      wb.bytes += 16.0 * X.blocks[x].rows * X.blocks[x].W * X.blocks[x].cols;
+      wb.bytes += (double)X.esz() * X.blocks[x].rows * X.blocks[x].W * X.blocks[x].cols;
     }
     int64_t n = (int64_t)yb.rows * yb.W * yb.cols;
     wb.work += n;
-    wb.bytes += 16.0 * n;
+    wb.bytes += (double)Y.esz() * n;
     wb.flops += 4.0 * n;   // at least one real x complex MAC per output
     wb.tasks.push_back(t);
   }
@@ -495,8 +527,10 @@ static Inter wstage_right(Context& c, const Inter& Z, const MPOd& m, int site) {
       pend.push_back(p);
     }
   }
+  Y.et = Z.et;
   Y.alloc(c.st, false);
   WBatch wb;
+  wb.et = Y.et;
   for (int y = 0; y < (int)Y.blocks.size(); ++y) {
     const Inter::Blk& yb = Y.blocks[y];
     WTask t{};
@@ -512,11 +546,11 @@ static Inter wstage_right(Context& c, const Inter& Z, const MPOd& m, int site) {
       t.X[sp] = Z.ptr(z);
       t.win[sp] = Z.blocks[z].W;
       t.csr[sp] = m.tab_right[site][pend[y].tabs[sp]].rowptr_off;
-      wb.bytes += 16.0 * Z.blocks[z].rows * Z.blocks[z].W * Z.blocks[z].cols;
+      wb.bytes += (double)Z.esz() * Z.blocks[z].rows * Z.blocks[z].W * Z.blocks[z].cols;
     }
     int64_t n = (int64_t)yb.rows * yb.W * yb.cols;
     wb.work += n;
-    wb.bytes += 16.0 * n;
+    wb.bytes += (double)Y.esz() * n;
     wb.flops += 4.0 * n;
     wb.tasks.push_back(t);
   }
@@ -529,10 +563,11 @@ static void rstage(Context& c, const Inter& Y, const Env& R, SiteT& out, cplx al
                    const double2* alpha_dev, bool accumulate) {
   std::map<int, std::vector<int>> rblocks;   // bra sector -> R blocks
   for (int b = 0; b < (int)R.t.blocks.size(); ++b) rblocks[R.t.blocks[b].rg].push_back(b);
-  GemmBatch gb;
+  GemmBatch gb(c);
   for (int o = 0; o < (int)out.blocks.size(); ++o) {
     const SiteT::Blk& ob = out.blocks[o];
-    gb.task(out.ptr(o), ob.rows, ob.cols, ob.cols, OP_N, OP_T, accumulate, alpha, alpha_dev);
+    gb.task(out.ptr(o), 0, ob.rows, ob.cols, ob.cols, OP_N, Y.et, OP_T, R.t.et, accumulate, alpha,
+            alpha_dev);
     auto it = rblocks.find(ob.sb);
     if (it == rblocks.end()) continue;
     for (int rb : it->second) {
@@ -543,7 +578,7 @@ static void rstage(Context& c, const Inter& Y, const Env& R, SiteT& out, cplx al
       gb.term(Y.ptr(y), K, R.t.ptr(rb), K, K);
     }
   }
-  gb.run(c);
+  gb.run();
 }
 
 // L_new[b][w'][b'] = sum_{a, s} conj(C[a][s][b]) Y[a][s][w'][b']
@@ -570,20 +605,21 @@ static Env env_from_Y_left(Context& c, const Inter& Y, const SiteT& bra, const B
     const Inter::Blk& y0 = Y.blocks[kv.second[0].y];
     e.t.add(sb, -1, g, y0.k, bra_right.d[sb], y0.W, y0.cols);
   }
+  e.t.et = Y.et;
   e.t.alloc(c.st, false);
-  GemmBatch gb;
+  GemmBatch gb(c);
   int id = 0;
   for (auto& kv : contrib) {
     const Inter::Blk& eb = e.t.blocks[id];
     int N = eb.W * eb.cols;
-    gb.task(e.t.ptr(id), eb.rows, N, N, OP_C, OP_N, false, 1.0);
+    gb.task(e.t.ptr(id), e.t.et, eb.rows, N, N, OP_C, 0, OP_N, Y.et, false, 1.0);
     for (auto& tm : kv.second) {
       const SiteT::Blk& cb = bra.blocks[tm.bra];
       gb.term(bra.ptr(tm.bra), cb.cols, Y.ptr(tm.y), N, cb.rows);
     }
     ++id;
   }
-  gb.run(c);
+  gb.run();
   return e;
 }
 
@@ -614,16 +650,17 @@ static Env env_update_right(Context& c, const Env& R, const SiteT& bra, const Bo
       src.push_back({rb, it->second});
     }
   }
+  Z.et = R.t.et;
   Z.alloc(c.st, false);
   {
-    GemmBatch gb;
+    GemmBatch gb(c);
     for (int z = 0; z < (int)Z.blocks.size(); ++z) {
       const Inter::Blk& zb = Z.blocks[z];
       const Inter::Blk& r = R.t.blocks[src[z].first];
-      gb.task(Z.ptr(z), zb.rows * zb.W, zb.cols, zb.cols, OP_N, OP_T, false, 1.0);
+      gb.task(Z.ptr(z), Z.et, zb.rows * zb.W, zb.cols, zb.cols, OP_N, R.t.et, OP_T, 0, false, 1.0);
       gb.term(R.t.ptr(src[z].first), r.cols, A.ptr(src[z].second), r.cols, r.cols);
     }
-    gb.run(c);
+    gb.run();
   }
   Inter Zp = wstage_right(c, Z, m, site);
   // R_new[a][w][a'] = sum_{s, b} conj(C[a][s][b]) Z'[b][s][w][a']
@@ -645,20 +682,21 @@ static Env env_update_right(Context& c, const Env& R, const SiteT& bra, const Bo
     const Inter::Blk& z0 = Zp.blocks[kv.second[0].z];
     e.t.add(kv.first[0], -1, kv.first[1], z0.k, bra_left.d[kv.first[0]], z0.W, z0.cols);
   }
+  e.t.et = Zp.et;
   e.t.alloc(c.st, false);
-  GemmBatch gb;
+  GemmBatch gb(c);
   int id = 0;
   for (auto& kv : contrib) {
     const Inter::Blk& eb = e.t.blocks[id];
     int N = eb.W * eb.cols;
-    gb.task(e.t.ptr(id), eb.rows, N, N, OP_J, OP_N, false, 1.0);
+    gb.task(e.t.ptr(id), e.t.et, eb.rows, N, N, OP_J, 0, OP_N, Zp.et, false, 1.0);
     for (auto& tm : kv.second) {
       const SiteT::Blk& cb = bra.blocks[tm.bra];
       gb.term(bra.ptr(tm.bra), cb.cols, Zp.ptr(tm.z), N, cb.cols);
     }
     ++id;
   }
-  gb.run(c);
+  gb.run();
   return e;
 }
 
@@ -855,18 +893,18 @@ static SiteT absorb_left_factor(Context& c, const SiteT& prev, const RowGroups& 
   SiteT out = make_site(rows, lq.left, c.st, false);
   std::map<int, int> task_of;   // old sector -> factor task
   for (size_t i = 0; i < lq.secs.size(); ++i) task_of[lq.secs[i]] = (int)i;
-  GemmBatch gb;
+  GemmBatch gb(c, true);
   for (int o = 0; o < (int)out.blocks.size(); ++o) {
     const SiteT::Blk& ob = out.blocks[o];
     int old_sec = old_mid.find(lq.left.q[ob.sb]);
     int pb = prev.block_of(ob.r, ob.sig);
-    gb.task(out.ptr(o), ob.rows, ob.cols, ob.cols, OP_N, OP_J, false, 1.0);
+    gb.task(out.ptr(o), 0, ob.rows, ob.cols, ob.cols, OP_N, 0, OP_J, 0, false, 1.0);
     if (pb < 0 || old_sec < 0) continue;
     const FactTask& ft = lq.fw.tasks[task_of.at(old_sec)];
     // Lf[a][k] = conj(R[a*n + k]) with n = |sa| (leading dimension of R)
     gb.term(prev.ptr(pb), prev.blocks[pb].cols, ft.V, ft.n, ft.n);
   }
-  gb.run(c);
+  gb.run();
   return out;
 }
 
@@ -975,7 +1013,7 @@ static SplitResult svd_split(Context& c, const SiteT& Th, const RowGroups& rows,
   TD_CHECK_CUDA(cudaMemcpyAsync(hk.data(), dkept, sizeof(int) * qs.size(), cudaMemcpyDeviceToHost, c.st));
   TD_CHECK_CUDA(cudaMemcpyAsync(hw, dw, sizeof(double) * 2, cudaMemcpyDeviceToHost, c.st));
   TD_CHECK_CUDA(cudaMemcpyAsync(&hstat, c.status->p, sizeof(int), cudaMemcpyDeviceToHost, c.st));
-  TD_CHECK_CUDA(cudaStreamSynchronize(c.st));
+  c.sync();
   if (hstat) throw Error(TDMPS_ERR_NUMERIC, "Jacobi SVD did not converge");
   if (!std::isfinite(hw[1])) throw Error(TDMPS_ERR_NONFINITE, "non-finite singular values");
   res.disc = hw[0];
@@ -1066,6 +1104,7 @@ SiteT local_two(Context& c, std::vector<TermState>& ts, int i, const Bond& bl, c
     E2.ket_copy = s.ket->bonds[i + 1];
     E2.t.data = Y1.data;
     E2.t.size = Y1.size;
+    E2.t.et = Y1.et;
     for (auto& b : Y1.blocks) {
       int id = (int)E2.t.blocks.size();
       E2.t.blocks.push_back({b.rg * 4 + b.sig, -1, b.g, b.k, b.rows, b.W, b.cols, b.off});
@@ -1180,7 +1219,7 @@ void sandwich_dev(Context& c, const MPOd* mpo, const MPSd& bra, const MPSd& ket,
   if (E.t.blocks.size() != 1 || E.t.blocks[0].rows != 1 || E.t.blocks[0].W != 1 ||
       E.t.blocks[0].cols != 1)
     throw Error(TDMPS_ERR_SECTOR, "final environment is not a scalar");
-  TD_CHECK_CUDA(cudaMemcpyAsync(out, E.t.ptr(0), sizeof(double2), cudaMemcpyDeviceToDevice, c.st));
+  launch_to_double(E.t.ptr(0), E.t.et, out, 1, c.st);
 }
 
 cplx sandwich(Context& c, const MPOd* mpo, const MPSd& bra, const MPSd& ket) {
@@ -1188,7 +1227,7 @@ cplx sandwich(Context& c, const MPOd* mpo, const MPSd& bra, const MPSd& ket) {
   sandwich_dev(c, mpo, bra, ket, (double2*)d->p);
   double2 h;
   TD_CHECK_CUDA(cudaMemcpyAsync(&h, d->p, sizeof(double2), cudaMemcpyDeviceToHost, c.st));
-  TD_CHECK_CUDA(cudaStreamSynchronize(c.st));
+  c.sync();
   return cplx(h.x, h.y);
 }
 
@@ -1226,10 +1265,10 @@ double compress(Context& c, MPSd& m, int D, double eps) {
     // sp.B is (mid x 0 x right bond) with sigma2 = 0: contract with site i+1
     const SiteT& nxt = C.sites[i + 1];
     SiteT out = make_site(RowGroups::from_bond(sp.mid), C.bonds[i + 2], c.st, false);
-    GemmBatch gb;
+    GemmBatch gb(c, true);
     for (int o = 0; o < (int)out.blocks.size(); ++o) {
       const SiteT::Blk& ob = out.blocks[o];
-      gb.task(out.ptr(o), ob.rows, ob.cols, ob.cols, OP_N, OP_N, false, 1.0);
+      gb.task(out.ptr(o), 0, ob.rows, ob.cols, ob.cols, OP_N, 0, OP_N, 0, false, 1.0);
       // old middle sector with the same charge
       int old = C.bonds[i + 1].find(sp.mid.q[ob.r]);
       int sb = sp.B.block_of(ob.r, 0);
@@ -1237,7 +1276,7 @@ double compress(Context& c, MPSd& m, int D, double eps) {
       if (sb < 0 || nb < 0) continue;
       gb.term(sp.B.ptr(sb), sp.B.blocks[sb].cols, nxt.ptr(nb), ob.cols, sp.B.blocks[sb].cols);
     }
-    gb.run(c);
+    gb.run();
     C.sites[i] = std::move(sp.A);
     C.sites[i + 1] = std::move(out);
     C.bonds[i + 1] = sp.mid;
@@ -1310,7 +1349,7 @@ MPSd krylov_step(Context& c, const MPOd& H, const MPSd& psi, double dt, int m, b
   launch_krylov_small(Nd, Hd, m, dt, cd, st, c.st);
   int hs[2];
   TD_CHECK_CUDA(cudaMemcpyAsync(hs, st, sizeof(hs), cudaMemcpyDeviceToHost, c.st));
-  TD_CHECK_CUDA(cudaStreamSynchronize(c.st));
+  c.sync();
   if (hs[1]) throw Error(TDMPS_ERR_NONFINITE, "non-finite Krylov matrices");
   if (m - hs[0] < 2) throw Error(TDMPS_ERR_KRYLOV_SINGULAR, "Krylov overlap matrix has rank < 2");
   std::vector<FitTerm> terms;
@@ -1367,7 +1406,7 @@ void one_rdm(Context& c, const MPSd& psi, cplx* gamma) {
       const Inter::Blk& eb = Eo.t.blocks[b];
       int rb2 = RO[j + 1].t.find(eb.rg, -1, 0, eb.rg);
       if (rb2 < 0) continue;
-      launch_trace_channels(Eo.t.ptr(b), eb.rows, eb.W, eb.cols, RO[j + 1].t.ptr(rb2),
+      launch_trace_channels(Eo.t.ptr(b), eb.rows, eb.W, eb.cols, RO[j + 1].t.ptr(rb2), Eo.t.et,
                             (double2*)gd->p + (size_t)j * 2 * L, c.st);
     }
     TD_CHECK_CUDA(cudaGetLastError());
@@ -1377,7 +1416,7 @@ void one_rdm(Context& c, const MPSd& psi, cplx* gamma) {
   }
   std::vector<double2> h((size_t)L * 2 * L);
   TD_CHECK_CUDA(cudaMemcpyAsync(h.data(), gd->p, sizeof(double2) * h.size(), cudaMemcpyDeviceToHost, c.st));
-  TD_CHECK_CUDA(cudaStreamSynchronize(c.st));
+  c.sync();
   for (int i = 0; i < L * L; ++i) gamma[i] = 0.0;
   for (int j = 0; j < L; ++j)
     for (int i = 0; i <= j; ++i)

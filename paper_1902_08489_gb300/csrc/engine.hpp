@@ -36,7 +36,7 @@ struct Context {
   struct Pending { int kind; cudaEvent_t a, b; };
   std::vector<Pending> pending;
   // scratch for device status words
-  DevPtr status;   // int[8]
+  DevPtr status;   // int[16]: [0] SVD convergence, [4..5] Krylov, [8] tensor-core waits
   std::unique_ptr<MPOd> ident;   // identity MPO cache (by L)
   std::unique_ptr<MPOd> rdm;     // density-matrix MPO cache (by L)
 
@@ -53,7 +53,10 @@ struct Context {
   void kend(int kind, cudaEvent_t a, double flops, double bytes);
   void collect_stats();
   void sync();
+  void check_device_errors();
   const MPOd& identity_mpo(int L);
+  int et() const { return precision == TDMPS_FP64 ? 0 : 1; }
+  int* tc_err() const { return (int*)status->p + 8; }
   const MPOd& rdm_mpo(int L);
 };
 
@@ -70,7 +73,9 @@ struct Inter {
   std::vector<Blk> blocks;
   std::map<std::array<int, 4>, int> index;
   size_t size = 0;
+  int et = 0;   // element type: 0 complex double, 1 complex float
   DevPtr data;
+  size_t esz() const { return et ? sizeof(float2) : sizeof(double2); }
   int find(int rg, int sig, int g, int k) const {
     auto it = index.find({rg, sig, g, k});
     return it == index.end() ? -1 : it->second;
@@ -82,7 +87,7 @@ struct Inter {
     size += (size_t)rows * W * cols;
     return id;
   }
-  double2* ptr(int b) const { return (double2*)data->p + blocks[b].off; }
+  void* ptr(int b) const { return (char*)data->p + blocks[b].off * esz(); }
   void alloc(cudaStream_t st, bool zero);
 };
 

@@ -69,9 +69,9 @@ __global__ void __launch_bounds__(256) k_gemm(const GemmTask* __restrict__ tasks
     for (int k0 = 0; k0 < g.K; k0 += GK) {
       {
         int i = threadIdx.x >> 3, k = threadIdx.x & 7;      // A tile: 32 x 8
-        As[k][i] = load_op(g.A, g.lda, t.opA, m0 + i, k0 + k, t.M, g.K);
+        As[k][i] = load_op((const double2*)g.A, g.lda, t.opA, m0 + i, k0 + k, t.M, g.K);
         int kk = threadIdx.x >> 5, j = threadIdx.x & 31;    // B tile: 8 x 32
-        Bs[kk][j] = load_op(g.B, g.ldb, t.opB, k0 + kk, n0 + j, g.K, t.N);
+        Bs[kk][j] = load_op((const double2*)g.B, g.ldb, t.opB, k0 + kk, n0 + j, g.K, t.N);
       }
       __syncthreads();
 #pragma unroll
@@ -93,7 +93,7 @@ __global__ void __launch_bounds__(256) k_gemm(const GemmTask* __restrict__ tasks
     for (int j = 0; j < 2; ++j) {
       int r = m0 + ty * 2 + i, c = n0 + tx * 2 + j;
       if (r < t.M && c < t.N) {
-        double2* p = t.C + (size_t)r * t.ldc + c;
+        double2* p = (double2*)t.C + (size_t)r * t.ldc + c;
         double2 v = cmul(alpha, acc[i][j]);
         if (t.beta) v = cadd(v, *p);
         *p = v;
@@ -110,6 +110,25 @@ void launch_gemm(const GemmTask* d_tasks, int ntasks, const GemmTerm* d_terms,
 
 // ------------------------------------------------------------------ W stage
 
+template <class T>
+__device__ __forceinline__ double2 ld2(const T* p, size_t i);
+template <>
+__device__ __forceinline__ double2 ld2<double2>(const double2* p, size_t i) { return p[i]; }
+template <>
+__device__ __forceinline__ double2 ld2<float2>(const float2* p, size_t i) {
+  float2 v = p[i];
+  return make_double2(v.x, v.y);
+}
+template <class T>
+__device__ __forceinline__ void st2(T* p, size_t i, double2 v);
+template <>
+__device__ __forceinline__ void st2<double2>(double2* p, size_t i, double2 v) { p[i] = v; }
+template <>
+__device__ __forceinline__ void st2<float2>(float2* p, size_t i, double2 v) {
+  p[i] = make_float2((float)v.x, (float)v.y);
+}
+
+template <class T>
 __global__ void __launch_bounds__(256) k_wstage(const WTask* __restrict__ tasks, int ntasks,
                                                 int64_t total, const int* __restrict__ rowptr,
                                                 const int* __restrict__ ent_w,
@@ -131,28 +150,53 @@ __global__ void __launch_bounds__(256) k_wstage(const WTask* __restrict__ tasks,
     for (int s = 0; s < 4; ++s) {
       if (t.csr[s] < 0) continue;
       const int* rp = rowptr + t.csr[s];
-      const double2* X = t.X[s];
+      const T* X = (const T*)t.X[s];
       int win = t.win[s];
       for (int e = rp[w]; e < rp[w + 1]; ++e) {
         double v = ent_v[e];
-        double2 x = X[((size_t)a * win + ent_w[e]) * t.cols + b];
+        double2 x = ld2(X, ((size_t)a * win + ent_w[e]) * t.cols + b);
         acc.x = fma(v, x.x, acc.x);
         acc.y = fma(v, x.y, acc.y);
       }
     }
-    double2* y = t.Y + ((size_t)a * t.wout + w) * t.cols + b;
-    if (t.beta) acc = cadd(acc, *y);
-    *y = acc;
+    size_t yo = ((size_t)a * t.wout + w) * t.cols + b;
+    if (t.beta) acc = cadd(acc, ld2((const T*)t.Y, yo));
+    st2((T*)t.Y, yo, acc);
   }
 }
 
 void launch_wstage(const WTask* d_tasks, int ntasks, int64_t total_work, const int* d_rowptr,
-                   const int* d_ent_w, const double* d_ent_v, cudaStream_t st) {
+                   const int* d_ent_w, const double* d_ent_v, int et, cudaStream_t st) {
   if (total_work <= 0) return;
   int64_t blocks = (total_work + 255) / 256;
   if (blocks > 152 * 64) blocks = 152 * 64;
-  k_wstage<<<(int)blocks, 256, 0, st>>>(d_tasks, ntasks, total_work, d_rowptr, d_ent_w, d_ent_v);
+  if (et == 0)
+    k_wstage<double2><<<(int)blocks, 256, 0, st>>>(d_tasks, ntasks, total_work, d_rowptr, d_ent_w, d_ent_v);
+  else
+    k_wstage<float2><<<(int)blocks, 256, 0, st>>>(d_tasks, ntasks, total_work, d_rowptr, d_ent_w, d_ent_v);
 }
+
+template <class T>
+__global__ void k_to_double(const T* in, double2* out, size_t n) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * blockDim.x)
+    out[i] = ld2(in, i);
+}
+
+void launch_to_double(const void* in, int et, double2* out, size_t n, cudaStream_t st) {
+  if (n == 0) return;
+  size_t blocks = (n + 255) / 256;
+  if (blocks > 152 * 32) blocks = 152 * 32;
+  if (et == 0) k_to_double<double2><<<(unsigned)blocks, 256, 0, st>>>((const double2*)in, out, n);
+  else k_to_double<float2><<<(unsigned)blocks, 256, 0, st>>>((const float2*)in, out, n);
+}
+
+__global__ void k_fill_one(void* p, int et) {
+  if (et == 0) *(double2*)p = make_double2(1.0, 0.0);
+  else *(float2*)p = make_float2(1.f, 0.f);
+}
+
+void launch_fill_one(void* p, int et, cudaStream_t st) { k_fill_one<<<1, 1, 0, st>>>(p, et); }
 
 // ------------------------------------------------------------------ gather / scatter
 
@@ -732,14 +776,15 @@ void launch_normalize(double2* x, size_t n, double2* d_norm_out, cudaStream_t st
   k_normalize<<<1, 1024, 0, st>>>(x, n, d_norm_out);
 }
 
-// out[w] = sum_{a, b} E[a][w][b] * R[a][b]   (rows x nch x cols and rows x cols)
-__global__ void k_trace_channels(const double2* E, int rows, int nch, int cols, const double2* R,
+// out[w] += sum_{a, b} E[a][w][b] * R[a][b]   (rows x nch x cols and rows x cols)
+template <class T>
+__global__ void k_trace_channels(const T* E, int rows, int nch, int cols, const T* R,
                                  double2* out) {
   const int w = blockIdx.x;
   double re = 0.0, im = 0.0;
   for (int e = threadIdx.x; e < rows * cols; e += blockDim.x) {
     int a = e / cols, b = e % cols;
-    double2 v = cmul(E[((size_t)a * nch + w) * cols + b], R[(size_t)a * cols + b]);
+    double2 v = cmul(ld2(E, ((size_t)a * nch + w) * cols + b), ld2(R, (size_t)a * cols + b));
     re += v.x;
     im += v.y;
   }
@@ -755,10 +800,13 @@ __global__ void k_trace_channels(const double2* E, int rows, int nch, int cols, 
   }
 }
 
-void launch_trace_channels(const double2* E, int rows, int nch, int cols, const double2* R,
+void launch_trace_channels(const void* E, int rows, int nch, int cols, const void* R, int et,
                            double2* out, cudaStream_t st) {
   if (nch <= 0 || rows * cols == 0) return;
-  k_trace_channels<<<nch, 256, 0, st>>>(E, rows, nch, cols, R, out);
+  if (et == 0)
+    k_trace_channels<double2><<<nch, 256, 0, st>>>((const double2*)E, rows, nch, cols, (const double2*)R, out);
+  else
+    k_trace_channels<float2><<<nch, 256, 0, st>>>((const float2*)E, rows, nch, cols, (const float2*)R, out);
 }
 
 }  // namespace tdmps

@@ -12,15 +12,15 @@ namespace tdmps {
 enum : int { OP_N = 0, OP_T = 1, OP_C = 2, OP_J = 3 };   // none, transpose, conj-transpose, conj
 
 struct GemmTerm {
-  const double2* A;
-  const double2* B;
+  const void* A;
+  const void* B;
   int K, lda, ldb, pad;
 };
 
 // C (M x N, ldc) = alpha * sum_terms op(A) op(B) + beta * C;
 // alpha = alpha_imm * (*alpha_ptr if non-null) * (alpha_inv ? 1 / *alpha_inv : 1).
 struct GemmTask {
-  double2* C;
+  void* C;
   const double2* alpha_ptr;
   const double2* alpha_div;
   double2 alpha;
@@ -28,14 +28,15 @@ struct GemmTask {
   int opA, opB, beta;
   int term_begin, term_end;
   int tiles_m, tile_base;
+  int ta, tb, tc, pad;   // element types of A, B, C: 0 double2, 1 float2 (tensor-core path)
 };
 
 // Sparse MPO-tensor application.  Output block Y[r][w][c] (rows r, W_out
 // channels, c columns), Y[a][w][b] = sum over inputs s of
 //   sum_{(w_in, v) in CSR_s[w]} v * X_s[a][w_in][b]   (X_s has W_in_s channels)
 struct WTask {
-  double2* Y;
-  const double2* X[4];
+  void* Y;
+  const void* X[4];
   int win[4];
   int csr[4];          // row-pointer offset of the CSR for input s (-1: none)
   int rows, wout, cols, beta;
@@ -74,8 +75,18 @@ struct FactTask {
 
 void launch_gemm(const GemmTask* d_tasks, int ntasks, const GemmTerm* d_terms,
                  const int* d_tile_task, int ntiles, cudaStream_t st);
+// et: element type of X and Y (0 double2, 1 float2)
 void launch_wstage(const WTask* d_tasks, int ntasks, int64_t total_work, const int* d_rowptr,
-                   const int* d_ent_w, const double* d_ent_v, cudaStream_t st);
+                   const int* d_ent_w, const double* d_ent_v, int et, cudaStream_t st);
+// tensor-core grouped GEMM (kernels_tc.cu); mode 0 TF32, 1 3xTF32; tiles of
+// tc_tile_m() rows x tc_tile_n() complex columns
+void launch_gemm_tc(const GemmTask* d_tasks, const GemmTerm* d_terms, const int* d_tile_task,
+                    int ntiles, int mode, int* d_err, cudaStream_t st);
+int tc_tile_m();
+int tc_tile_n();
+// out (double2) = in (element type et), n elements
+void launch_to_double(const void* in, int et, double2* out, size_t n, cudaStream_t st);
+void launch_fill_one(void* p, int et, cudaStream_t st);
 void launch_copy(const CopyTask* d_tasks, int ntasks, int to_work, cudaStream_t st);
 void launch_scatter(const ScatterTask* d_tasks, int ntasks, cudaStream_t st);
 void launch_zero(double2* p, size_t n, cudaStream_t st);
@@ -99,7 +110,7 @@ void launch_scalar_div_neg(const double2* num, const double2* den, double2* out,
 // norm of a buffer (sqrt of sum |x|^2) and scaling of it by 1/norm
 void launch_normalize(double2* x, size_t n, double2* d_norm_out, cudaStream_t st);
 void launch_scale(double2* x, size_t n, double2 a, cudaStream_t st);
-void launch_trace_channels(const double2* E, int rows, int nch, int cols, const double2* R,
+void launch_trace_channels(const void* E, int rows, int nch, int cols, const void* R, int et,
                            double2* out, cudaStream_t st);
 
 }  // namespace tdmps

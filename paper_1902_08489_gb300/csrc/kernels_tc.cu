@@ -1,0 +1,345 @@
+// Tensor-core (tcgen05, sm_103a) grouped complex block GEMM for the mixed
+// precision contractions: C (M x N) = alpha * sum_terms op(A) op(B) (+ C).
+//
+// Complex arithmetic on the real tensor pipe: with A read as a real M x 2K
+// matrix (re/im interleaved along K, the storage order of complex numbers)
+// and B expanded to its 2K x 2N real representation
+//     [ br  bi ]
+//     [ -bi br ]   per complex entry,
+// the real product is the complex product with re/im interleaved along N,
+// i.e. exactly the storage of C.  Each CTA computes a 128 x N' real tile
+// (N' <= 128, 64 complex columns) in TMEM; operands are staged by the CTA's
+// threads in the canonical K-major no-swizzle layout (8-row x 16-byte core
+// matrices) because the symmetry blocks are ragged and addressed through
+// arbitrary leading dimensions and operand modes; one elected thread issues
+// tcgen05.mma and commits to an mbarrier.  3xTF32 splits each operand into
+// a TF32 head and a TF32 tail and accumulates hi*hi + hi*lo + lo*hi.
+//
+// Every wait is bounded: a stuck barrier sets the error word, the CTA waits
+// (bounded) for its own MMAs, frees its TMEM and returns.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "kernels.hpp"
+
+namespace tdmps {
+
+namespace {
+
+constexpr int TC_BM = 128;        // rows per tile (TMEM lanes)
+constexpr int TC_BNC = 64;        // complex columns per tile
+constexpr int TC_BKC = 16;        // complex K per stage
+constexpr int TC_KR = 2 * TC_BKC; // real K per stage (32 tf32 = 4 MMA k-steps)
+constexpr int TC_NR = 2 * TC_BNC; // real N per tile
+constexpr int TC_TMEM_COLS = 128;
+constexpr uint32_t TC_SPIN_LIMIT = 1u << 22;
+
+// bytes of one staged operand tile (rows x 32 tf32)
+constexpr int TILE_A_BYTES = TC_BM * TC_KR * 4;   // 16 KB
+constexpr int TILE_B_BYTES = TC_NR * TC_KR * 4;   // 16 KB
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// canonical K-major, no-swizzle layout: element (r, k) of a rows x 32 tile
+__device__ __forceinline__ int canon_off(int r, int k) {
+  return ((r >> 3) * (TC_KR / 4) + (k >> 2)) * 128 + (r & 7) * 16 + (k & 3) * 4;
+}
+
+// shared-memory matrix descriptor: start address, leading byte offset (next
+// core matrix along K), stride byte offset (next 8-row group), version 1,
+// no swizzle
+__device__ __forceinline__ uint64_t make_desc(uint32_t saddr) {
+  const uint64_t lbo = 128, sbo = (TC_KR / 4) * 128;
+  return (uint64_t)((saddr >> 4) & 0x3FFF) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | (1ull << 46);
+}
+
+// instruction descriptor: F32 accumulator, TF32 A and B, both K-major
+__device__ __forceinline__ uint32_t make_idesc_tf32(int n_real) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n_real >> 3) << 17) |
+         ((uint32_t)(TC_BM >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t tmem, uint64_t da, uint64_t db, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n"
+      :
+      : "r"(tmem), "l"(da), "l"(db), "r"(idesc), "r"(accumulate));
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t mbar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n"
+               :
+               : "r"(mbar)
+               : "memory");
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t mbar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" : : "r"(mbar), "r"(count) : "memory");
+}
+
+// bounded wait on an mbarrier phase; returns false on timeout
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t phase) {
+  for (uint32_t it = 0; it < TC_SPIN_LIMIT; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(done)
+        : "r"(mbar), "r"(phase)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void fence_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+}
+
+__device__ __forceinline__ float to_tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;\n" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+        "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
+        "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
+        "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// element (r, c) of op(P) (R x C), P of element type t (0 double2, 1 float2)
+__device__ __forceinline__ float2 load_el(const void* P, int t, int ld, int op, int r, int c, int R,
+                                          int C) {
+  if (r >= R || c >= C) return make_float2(0.f, 0.f);
+  size_t idx;
+  bool conj = false;
+  switch (op) {
+    case OP_N: idx = (size_t)r * ld + c; break;
+    case OP_T: idx = (size_t)c * ld + r; break;
+    case OP_C: idx = (size_t)c * ld + r; conj = true; break;
+    default: idx = (size_t)r * ld + c; conj = true; break;
+  }
+  float2 v;
+  if (t == 0) {
+    double2 d = ((const double2*)P)[idx];
+    v = make_float2((float)d.x, (float)d.y);
+  } else {
+    v = ((const float2*)P)[idx];
+  }
+  if (conj) v.y = -v.y;
+  return v;
+}
+
+template <int MODE>   // 0: TF32, 1: 3xTF32
+__global__ void __launch_bounds__(128) k_gemm_tc(const GemmTask* __restrict__ tasks,
+                                                 const GemmTerm* __restrict__ terms,
+                                                 const int* __restrict__ tile_task, int* err) {
+  extern __shared__ __align__(1024) unsigned char sm[];
+  constexpr int NSPLIT = MODE == 0 ? 1 : 2;
+  unsigned char* sA = sm;                                   // NSPLIT tiles
+  unsigned char* sB = sm + NSPLIT * TILE_A_BYTES;           // NSPLIT tiles
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ uint32_t tmem_base;
+  __shared__ int abort_flag;
+
+  const int ti = tile_task[blockIdx.x];
+  const GemmTask t = tasks[ti];
+  const int local = blockIdx.x - t.tile_base;
+  const int m0 = (local % t.tiles_m) * TC_BM;
+  const int n0 = (local / t.tiles_m) * TC_BNC;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int ncols = min(TC_BNC, t.N - n0);
+  const int nreal = ((2 * ncols + 15) / 16) * 16;   // MMA N: multiple of 16
+  const uint32_t idesc = make_idesc_tf32(nreal);
+  const uint32_t mb = smem_u32(&mbar);
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n"
+                 :
+                 : "r"(smem_u32(&tmem_base)), "r"(TC_TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+  }
+  if (threadIdx.x == 0) {
+    mbar_init(mb, 1);
+    abort_flag = 0;
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_base;
+
+  uint32_t phase = 0;
+  bool first = true;
+  bool ok = true;
+  for (int e = t.term_begin; e < t.term_end && ok; ++e) {
+    const GemmTerm g = terms[e];
+    for (int k0 = 0; k0 < g.K && ok; k0 += TC_BKC) {
+      // ---- stage A: row r = thread, 16 complex along K
+      {
+        const int r = threadIdx.x;
+        for (int kk = 0; kk < TC_BKC; ++kk) {
+          float2 a = load_el(g.A, t.ta, g.lda, t.opA, m0 + r, k0 + kk, t.M, g.K);
+          float2 hi = make_float2(to_tf32(a.x), to_tf32(a.y));
+          *(float2*)(sA + canon_off(r, 2 * kk)) = hi;
+          if (MODE == 1) {
+            float2 lo = make_float2(to_tf32(a.x - hi.x), to_tf32(a.y - hi.y));
+            *(float2*)(sA + TILE_A_BYTES + canon_off(r, 2 * kk)) = lo;
+          }
+        }
+      }
+      // ---- stage B-tilde (K-major, rows = real N): thread -> column n, half of K
+      {
+        const int n = threadIdx.x & (TC_BNC - 1);
+        const int kh = threadIdx.x >> 6;   // 0 or 1
+        for (int j = 0; j < TC_BKC / 2; ++j) {
+          const int kk = kh * (TC_BKC / 2) + j;
+          float2 b = load_el(g.B, t.tb, g.ldb, t.opB, k0 + kk, n0 + n, g.K, t.N);
+          float2 hr = make_float2(to_tf32(b.x), to_tf32(-b.y));   // row 2n:   (br, -bi)
+          float2 hi2 = make_float2(to_tf32(b.y), to_tf32(b.x));   // row 2n+1: (bi,  br)
+          *(float2*)(sB + canon_off(2 * n, 2 * kk)) = hr;
+          *(float2*)(sB + canon_off(2 * n + 1, 2 * kk)) = hi2;
+          if (MODE == 1) {
+            float2 lr = make_float2(to_tf32(b.x - hr.x), to_tf32(-b.y - hr.y));
+            float2 li = make_float2(to_tf32(b.y - hi2.x), to_tf32(b.x - hi2.y));
+            *(float2*)(sB + TILE_B_BYTES + canon_off(2 * n, 2 * kk)) = lr;
+            *(float2*)(sB + TILE_B_BYTES + canon_off(2 * n + 1, 2 * kk)) = li;
+          }
+        }
+      }
+      fence_async_smem();
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        tc_fence_after();
+        const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
+#pragma unroll
+        for (int s = 0; s < TC_KR / 8; ++s) {
+          const uint32_t off = s * 256;   // two core matrices along K per step
+          mma_tf32(tmem, make_desc(a0 + off), make_desc(b0 + off), idesc, first ? 0u : 1u);
+          first = false;
+          if (MODE == 1) {
+            mma_tf32(tmem, make_desc(a0 + off), make_desc(b0 + TILE_B_BYTES + off), idesc, 1u);
+            mma_tf32(tmem, make_desc(a0 + TILE_A_BYTES + off), make_desc(b0 + off), idesc, 1u);
+          }
+        }
+        mma_commit(mb);
+      }
+      first = false;
+      // all threads wait for the MMAs (their smem reads) before restaging
+      if (!mbar_wait(mb, phase)) {
+        if (lane == 0) atomicExch(err, 2);
+        abort_flag = 1;
+      }
+      phase ^= 1u;
+      __syncthreads();
+      tc_fence_after();
+      if (abort_flag) ok = false;
+    }
+  }
+
+  if (ok) {
+    double2 alpha = t.alpha;
+    if (t.alpha_ptr) {
+      double2 p = *t.alpha_ptr;
+      alpha = make_double2(alpha.x * p.x - alpha.y * p.y, alpha.x * p.y + alpha.y * p.x);
+    }
+    if (t.alpha_div) {
+      double2 q = *t.alpha_div;
+      double d = q.x * q.x + q.y * q.y;
+      alpha = make_double2((alpha.x * q.x + alpha.y * q.y) / d, (alpha.y * q.x - alpha.x * q.y) / d);
+    }
+    const int r = m0 + warp * 32 + lane;
+    const bool have = !first;   // at least one MMA wrote the accumulator
+    for (int c0 = 0; c0 < 2 * ncols; c0 += 32) {
+      float v[32];
+      if (have) {
+        tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+      } else {
+#pragma unroll
+        for (int i = 0; i < 32; ++i) v[i] = 0.f;
+      }
+      if (r < t.M) {
+        for (int j = 0; j < 16; ++j) {
+          const int c = n0 + c0 / 2 + j;
+          if (c >= n0 + ncols) break;
+          const double re = v[2 * j], im = v[2 * j + 1];
+          double ore = alpha.x * re - alpha.y * im, oim = alpha.x * im + alpha.y * re;
+          const size_t o = (size_t)r * t.ldc + c;
+          if (t.tc == 0) {
+            double2* C = (double2*)t.C;
+            if (t.beta) { ore += C[o].x; oim += C[o].y; }
+            C[o] = make_double2(ore, oim);
+          } else {
+            float2* C = (float2*)t.C;
+            if (t.beta) { ore += C[o].x; oim += C[o].y; }
+            C[o] = make_float2((float)ore, (float)oim);
+          }
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n"
+                 :
+                 : "r"(tmem), "r"(TC_TMEM_COLS)
+                 : "memory");
+  }
+}
+
+}  // namespace
+
+void launch_gemm_tc(const GemmTask* d_tasks, const GemmTerm* d_terms, const int* d_tile_task,
+                    int ntiles, int mode, int* d_err, cudaStream_t st) {
+  if (ntiles <= 0) return;
+  if (mode == 0) {
+    const int smem = TILE_A_BYTES + TILE_B_BYTES;
+    static bool attr = false;
+    if (!attr) {
+      cudaFuncSetAttribute(k_gemm_tc<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+      attr = true;
+    }
+    k_gemm_tc<0><<<ntiles, 128, smem, st>>>(d_tasks, d_terms, d_tile_task, d_err);
+  } else {
+    const int smem = 2 * (TILE_A_BYTES + TILE_B_BYTES);
+    static bool attr = false;
+    if (!attr) {
+      cudaFuncSetAttribute(k_gemm_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+      attr = true;
+    }
+    k_gemm_tc<1><<<ntiles, 128, smem, st>>>(d_tasks, d_terms, d_tile_task, d_err);
+  }
+}
+
+int tc_tile_m() { return TC_BM; }
+int tc_tile_n() { return TC_BNC; }
+
+}  // namespace tdmps
