@@ -197,6 +197,7 @@ __global__ void __launch_bounds__(128) k_gemm_tc(const GemmTask* __restrict__ ta
   const uint32_t tmem = tmem_base;
 
   uint32_t phase = 0;
+  uint32_t failed_phase = 0;
   bool first = true;
   bool ok = true;
   for (int e = t.term_begin; e < t.term_end && ok; ++e) {
@@ -256,6 +257,7 @@ __global__ void __launch_bounds__(128) k_gemm_tc(const GemmTask* __restrict__ ta
       if (!mbar_wait(mb, phase)) {
         if (lane == 0) atomicExch(err, 2);
         abort_flag = 1;
+        failed_phase = phase;
       }
       phase ^= 1u;
       __syncthreads();
@@ -304,6 +306,11 @@ __global__ void __launch_bounds__(128) k_gemm_tc(const GemmTask* __restrict__ ta
         }
       }
     }
+  }
+  if (!ok) {
+    // give the MMAs of this CTA one more bounded chance to drain before the
+    // accumulator columns are released
+    mbar_wait(mb, failed_phase);
   }
   tc_fence_before();
   __syncthreads();

@@ -3,8 +3,10 @@ accumulation, FP64 factorisations) against the FP64 GPU path and the oracle.
 
 Tolerances follow from the arithmetic: a TF32 product carries a relative
 rounding of 2^-11 per operand, so sums of K ~ 10^3 terms land near 1e-3
-relative; the split 3xTF32 product keeps ~21 mantissa bits and FP32
-accumulation gives ~1e-6 relative.
+relative; the split 3xTF32 product keeps ~21 mantissa bits, and FP32
+accumulation plus FP32 storage of the environments (2^-24 per element,
+~sqrt(K) growth per contraction, chained over ~2L environment updates) bound
+a fitted state at ~2e-5 relative.
 """
 import numpy as np
 import pytest
@@ -15,7 +17,7 @@ from oracle import mps as om
 
 pytestmark = pytest.mark.gpu
 
-TOLS = {"tf32": 3e-3, "tf32x3": 2e-6}
+TOLS = {"tf32": 3e-3, "tf32x3": 2e-5}
 
 
 @pytest.fixture(scope="module")
