@@ -252,22 +252,31 @@ def main():
                "d2h_bytes_per_step": int(g.nbytes)}
 
     peaks = _peaks()
-    # dominant kernel: the class with the largest event time
-    kinds = sorted(st, key=lambda k: -st[k]["ms"])
-    top = kinds[0]
+    bf16 = peaks.get("bf16_tflops", 1913.9)
+    hbm = peaks.get("hbm_gbs", 6675.5)
+    # dominant kernel class: the largest live event time in the timed region
+    top = max(st, key=lambda k: st[k]["ms"])
     ks = st[top]
-    per_launch_ms = ks["ms"] / max(1, ks["launches"])
-    if top in ("gemm",):
-        fp64_peak = peaks.get("bf16_tflops", 1913.9) * (1.25 / 2250.0)
-        achieved = ks["flops"] / max(1, ks["launches"]) / (per_launch_ms / 1e3) / 1e12
-        roof = {"kernel": "k_gemm (grouped complex block GEMM)", "bound": "alu",
-                "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
-                "frac": achieved / fp64_peak, "traffic": None,
-                "peak_source": "measured bf16 x nominal FP64/bf16 ratio (1.25/2250)"}
+    per_launch_s = ks["ms"] / max(1, ks["launches"]) / 1e3
+    if top == "gemm":
+        if args.precision == "fp64":
+            peak, src = bf16 * 1.25 / 2250.0, "measured bf16 x nominal FP64/bf16 (1.25/2250)"
+            kern, bound = "k_gemm (FP64 grouped complex block GEMM)", "alu"
+        else:
+            tf32 = bf16 * (1100.0 / 2250.0)
+            if args.precision == "tf32x3":
+                peak, src = tf32 / 3.0, "measured bf16 x nominal TF32/bf16 (1.1/2.25), /3 for split TF32"
+            else:
+                peak, src = tf32, "measured bf16 x nominal TF32/bf16 (1.1/2.25)"
+            kern, bound = "k_gemm_tc (tcgen05 grouped complex block GEMM)", "tensor"
+        achieved = ks["flops"] / max(1, ks["launches"]) / per_launch_s / 1e12
+        roof = {"kernel": kern, "bound": bound, "achieved": achieved, "peak": peak,
+                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None, "peak_source": src}
     else:
-        hbm = peaks.get("hbm_gbs", 6675.5)
-        achieved = ks["bytes"] / max(1, ks["launches"]) / (per_launch_ms / 1e3) / 1e9
-        roof = {"kernel": top, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+        achieved = ks["bytes"] / max(1, ks["launches"]) / per_launch_s / 1e9
+        roof = {"kernel": {"wstage": "k_wstage", "qr": "k_qr_warp", "svd": "k_svd",
+                           "other": "k_copy/k_scatter"}[top],
+                "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                 "frac": achieved / hbm, "traffic": None, "peak_source": "measured hbm_gbs"}
     line = {
         "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world,

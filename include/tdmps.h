@@ -56,8 +56,11 @@ enum {
   TDMPS_ERR_NUMERIC = -8          /* an iterative kernel did not converge    */
 };
 
-/* Arithmetic of the contractions (environments, local matvecs, sums).
- * Factorisations (QR, SVD), Krylov algebra and all norms stay FP64. */
+/* Arithmetic of the fit contractions (environments, local matvecs, sums).
+ * Factorisations (QR, SVD), the Krylov algebra, the Krylov inner products
+ * <phi_i|phi_j> and <phi_i|H|phi_j> (Gram-Schmidt coefficients), and the
+ * observables (tdmps_overlap, tdmps_expectation, tdmps_one_rdm) always
+ * contract in FP64. */
 enum {
   TDMPS_FP64 = 0,   /* complex FP64 everywhere                               */
   TDMPS_TF32 = 1,   /* TF32 tensor-core products, FP32 accumulation          */

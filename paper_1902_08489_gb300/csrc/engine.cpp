@@ -300,10 +300,11 @@ struct GemmBatch {
     tasks.push_back(t);
     bytes += (tc ? 8.0 : 16.0) * M * N * (beta ? 2.0 : 1.0);
   }
-  void term(const void* A, int lda, const void* B, int ldb, int K) {
+  void term(const void* A, int lda, const void* B, int ldb, int K, cplx scale = 1.0,
+            const double2* scale_ptr = nullptr) {
     if (K <= 0) return;
     GemmTask& t = tasks.back();
-    terms.push_back({A, B, K, lda, ldb, 0});
+    terms.push_back({A, B, K, lda, ldb, 0, make_double2(scale.real(), scale.imag()), scale_ptr});
     t.term_end = (int)terms.size();
     flops += 8.0 * t.M * t.N * K;
     bytes += (t.ta ? 8.0 : 16.0) * t.M * K + (t.tb ? 8.0 : 16.0) * K * t.N;
@@ -338,11 +339,14 @@ struct GemmBatch {
 };
 
 struct WBatch {
+  const MPOd* mpo = nullptr;
   std::vector<WTask> tasks;
   int64_t work = 0;
   double flops = 0.0, bytes = 0.0;
   int et = 0;
-  void run(Context& c, const MPOd& m) {
+  void run(Context& c) {
+    if (!mpo) return;
+    const MPOd& m = *mpo;
     if (tasks.empty() || work == 0) return;
     const WTask* dt = c.stage(tasks);
     cudaEvent_t ev;
@@ -386,8 +390,12 @@ static Env env_right_boundary(Context& c, const MPSd& bra, const MPSd& ket, cons
   return e;
 }
 
+// ---- stage planners: each appends its work to a batch; callers run one
+// launch per stage for all terms of a fit or all pairs of a sandwich.
+
 // X[rg][w][s'][b'] = E[rg][w][k] A[k][s'][b']
-static Inter lstage(Context& c, const Env& E, const SiteT& ket, const Bond& ket_right) {
+static Inter plan_lstage(Context& c, const Env& E, const SiteT& ket, const Bond& ket_right,
+                         GemmBatch& gb) {
   Inter X;
   std::vector<std::pair<int, int>> src;   // (env block, ket block) per X block
   for (int b = 0; b < (int)E.t.blocks.size(); ++b) {
@@ -402,22 +410,28 @@ static Inter lstage(Context& c, const Env& E, const SiteT& ket, const Bond& ket_
   }
   X.et = E.t.et;
   X.alloc(c.st, false);
-  GemmBatch gb(c);
   for (int x = 0; x < (int)X.blocks.size(); ++x) {
     const Inter::Blk& xb = X.blocks[x];
     const Inter::Blk& eb = E.t.blocks[src[x].first];
     gb.task(X.ptr(x), X.et, xb.rows * xb.W, xb.cols, xb.cols, OP_N, E.t.et, OP_N, 0, false, 1.0);
     gb.term(E.t.ptr(src[x].first), eb.cols, ket.ptr(src[x].second), xb.cols, eb.cols);
   }
-  gb.run();
   return X;
 }
 
-// Y[rg][s][w_out][b'] = sum_{s', w_in} W[w_in, w_out, s, s'] X[rg][w_in][s'][b']
-static Inter wstage_left(Context& c, const Inter& X, const MPOd& m, int site) {
+// Sparse MPO-tensor stage, either direction.
+//   left:  Y[rg][s][w_out][b'] = sum_{s', w_in} W[w_in, w_out, s, s'] X[rg][w_in][s'][b']
+//   right: Y[rb][s][w_in][a']  = sum_{s', w_out} W[w_in, w_out, s, s'] X[rb][w_out][s'][a']
+static Inter plan_wstage(Context& c, const Inter& X, const MPOd& m, int site, bool left,
+                         WBatch& wb) {
   if (m.identity) return X;
+  if (wb.mpo && wb.mpo != &m) throw Error(TDMPS_ERR_INVALID_ARG, "mixed MPOs in one W batch");
+  wb.mpo = &m;
+  wb.et = X.et;
   const MPOBond& bi = m.bonds[site];
   const MPOBond& bo = m.bonds[site + 1];
+  const MPOBond& bx = left ? bi : bo;   // channels of the input
+  const MPOBond& by = left ? bo : bi;   // channels of the output
   std::map<std::pair<int, int>, std::array<int, 4>> groups;
   for (int x = 0; x < (int)X.blocks.size(); ++x) {
     auto key = std::make_pair(X.blocks[x].rg, X.blocks[x].k);
@@ -431,32 +445,33 @@ static Inter wstage_left(Context& c, const Inter& X, const MPOd& m, int site) {
   for (auto& kv : groups) {
     for (int s = 0; s < 4; ++s) {
       P p;
-      int gout = -1;
-      bool any = false;
+      int gy = -1, first = -1;
       for (int sp = 0; sp < 4; ++sp) {
         p.xs[sp] = -1;
         p.tabs[sp] = -1;
         int x = kv.second[sp];
         if (x < 0) continue;
-        int go = bo.find(bi.gq[X.blocks[x].g] + SITE_Q[s] - SITE_Q[sp]);
-        if (go < 0) continue;
-        auto it = m.tab_left_idx[site].find({s, sp, go});
-        if (it == m.tab_left_idx[site].end()) continue;
-        gout = go;
+        // charge of the output channel group
+        QN qy = left ? bx.gq[X.blocks[x].g] + SITE_Q[s] - SITE_Q[sp]
+                     : bx.gq[X.blocks[x].g] - SITE_Q[s] + SITE_Q[sp];
+        int g = by.find(qy);
+        if (g < 0) continue;
+        const auto& idx = left ? m.tab_left_idx[site] : m.tab_right_idx[site];
+        auto it = idx.find({s, sp, g});
+        if (it == idx.end()) continue;
+        gy = g;
         p.xs[sp] = x;
         p.tabs[sp] = it->second;
-        any = true;
+        if (first < 0) first = x;
       }
-      if (!any) continue;
-      const Inter::Blk& x0 = X.blocks[kv.second[0] >= 0 ? kv.second[0] : (kv.second[1] >= 0 ? kv.second[1] : (kv.second[2] >= 0 ? kv.second[2] : kv.second[3]))];
-      Y.add(kv.first.first, s, gout, kv.first.second, x0.rows, bo.gsize[gout], x0.cols);
+      if (first < 0) continue;
+      Y.add(kv.first.first, s, gy, kv.first.second, X.blocks[first].rows, by.gsize[gy],
+            X.blocks[first].cols);
       pend.push_back(p);
     }
   }
   Y.et = X.et;
   Y.alloc(c.st, false);
-  WBatch wb;
-  wb.et = Y.et;
   for (int y = 0; y < (int)Y.blocks.size(); ++y) {
     const Inter::Blk& yb = Y.blocks[y];
     WTask t{};
@@ -471,7 +486,7 @@ static Inter wstage_left(Context& c, const Inter& X, const MPOd& m, int site) {
       if (x < 0) { t.X[sp] = nullptr; t.win[sp] = 0; t.csr[sp] = -1; continue; }
       t.X[sp] = X.ptr(x);
       t.win[sp] = X.blocks[x].W;
-      const WTable& tb = m.tab_left[site][pend[y].tabs[sp]];
+      const WTable& tb = (left ? m.tab_left[site] : m.tab_right[site])[pend[y].tabs[sp]];
       t.csr[sp] = tb.rowptr_off;
       wb.bytes += (double)X.esz() * X.blocks[x].rows * X.blocks[x].W * X.blocks[x].cols;
     }
@@ -481,114 +496,74 @@ static Inter wstage_left(Context& c, const Inter& X, const MPOd& m, int site) {
     wb.flops += 4.0 * n;   // at least one real x complex MAC per output
     wb.tasks.push_back(t);
   }
-  wb.run(c, m);
   return Y;
 }
 
-// Z'[rb][s][w_in][a'] = sum_{s', w_out} W[w_in, w_out, s, s'] Z[rb][w_out][s'][a']
-static Inter wstage_right(Context& c, const Inter& Z, const MPOd& m, int site) {
-  if (m.identity) return Z;
-  const MPOBond& bi = m.bonds[site];
-  const MPOBond& bo = m.bonds[site + 1];
-  std::map<std::pair<int, int>, std::array<int, 4>> groups;
-  for (int z = 0; z < (int)Z.blocks.size(); ++z) {
-    auto key = std::make_pair(Z.blocks[z].rg, Z.blocks[z].k);
-    auto it = groups.find(key);
-    if (it == groups.end()) it = groups.emplace(key, std::array<int, 4>{-1, -1, -1, -1}).first;
-    it->second[Z.blocks[z].sig] = z;
-  }
-  Inter Y;
-  struct P { int xs[4]; int tabs[4]; };
-  std::vector<P> pend;
-  for (auto& kv : groups) {
-    for (int s = 0; s < 4; ++s) {
-      P p;
-      int gin = -1;
-      bool any = false;
-      int first = -1;
-      for (int sp = 0; sp < 4; ++sp) {
-        p.xs[sp] = -1;
-        p.tabs[sp] = -1;
-        int z = kv.second[sp];
-        if (z < 0) continue;
-        int gi = bi.find(bo.gq[Z.blocks[z].g] - SITE_Q[s] + SITE_Q[sp]);
-        if (gi < 0) continue;
-        auto it = m.tab_right_idx[site].find({s, sp, gi});
-        if (it == m.tab_right_idx[site].end()) continue;
-        gin = gi;
-        p.xs[sp] = z;
-        p.tabs[sp] = it->second;
-        any = true;
-        if (first < 0) first = z;
-      }
-      if (!any) continue;
-      Y.add(kv.first.first, s, gin, kv.first.second, Z.blocks[first].rows, bi.gsize[gin],
-            Z.blocks[first].cols);
-      pend.push_back(p);
-    }
-  }
-  Y.et = Z.et;
-  Y.alloc(c.st, false);
-  WBatch wb;
-  wb.et = Y.et;
-  for (int y = 0; y < (int)Y.blocks.size(); ++y) {
-    const Inter::Blk& yb = Y.blocks[y];
-    WTask t{};
-    t.Y = Y.ptr(y);
-    t.rows = yb.rows;
-    t.wout = yb.W;
-    t.cols = yb.cols;
-    t.beta = 0;
-    t.work_base = wb.work;
-    for (int sp = 0; sp < 4; ++sp) {
-      int z = pend[y].xs[sp];
-      if (z < 0) { t.X[sp] = nullptr; t.win[sp] = 0; t.csr[sp] = -1; continue; }
-      t.X[sp] = Z.ptr(z);
-      t.win[sp] = Z.blocks[z].W;
-      t.csr[sp] = m.tab_right[site][pend[y].tabs[sp]].rowptr_off;
-      wb.bytes += (double)Z.esz() * Z.blocks[z].rows * Z.blocks[z].W * Z.blocks[z].cols;
-    }
-    int64_t n = (int64_t)yb.rows * yb.W * yb.cols;
-    wb.work += n;
-    wb.bytes += (double)Y.esz() * n;
-    wb.flops += 4.0 * n;
-    wb.tasks.push_back(t);
-  }
-  wb.run(c, m);
-  return Y;
-}
+// One term of a local tensor: coef * contraction of (Y, environment).
+struct LocalTerm {
+  const Inter* Y;
+  const Env* E;
+  cplx coef;
+  const double2* coef_dev;
+};
 
-// out[rg][s][b] (+)= alpha * sum_{w', b'} Y[rg][s][w'][b'] R[b][w'][b']
-static void rstage(Context& c, const Inter& Y, const Env& R, SiteT& out, cplx alpha,
-                   const double2* alpha_dev, bool accumulate) {
-  std::map<int, std::vector<int>> rblocks;   // bra sector -> R blocks
-  for (int b = 0; b < (int)R.t.blocks.size(); ++b) rblocks[R.t.blocks[b].rg].push_back(b);
-  GemmBatch gb(c);
+// out[r][s][b] = sum_t coef_t sum_{w', b'} Y_t[r][s][w'][b'] R_t[b][w'][b']
+static void plan_rstage(const std::vector<LocalTerm>& ts, SiteT& out, GemmBatch& gb) {
+  std::vector<std::map<int, std::vector<int>>> rby(ts.size());
+  for (size_t t = 0; t < ts.size(); ++t)
+    for (int b = 0; b < (int)ts[t].E->t.blocks.size(); ++b)
+      rby[t][ts[t].E->t.blocks[b].rg].push_back(b);
   for (int o = 0; o < (int)out.blocks.size(); ++o) {
     const SiteT::Blk& ob = out.blocks[o];
-    gb.task(out.ptr(o), 0, ob.rows, ob.cols, ob.cols, OP_N, Y.et, OP_T, R.t.et, accumulate, alpha,
-            alpha_dev);
-    auto it = rblocks.find(ob.sb);
-    if (it == rblocks.end()) continue;
-    for (int rb : it->second) {
-      const Inter::Blk& r = R.t.blocks[rb];
-      int y = Y.find(ob.r, ob.sig, r.g, r.k);
-      if (y < 0) continue;
-      int K = r.W * r.cols;
-      gb.term(Y.ptr(y), K, R.t.ptr(rb), K, K);
+    gb.task(out.ptr(o), 0, ob.rows, ob.cols, ob.cols, OP_N, ts[0].Y->et, OP_T, ts[0].E->t.et,
+            false, 1.0);
+    for (size_t t = 0; t < ts.size(); ++t) {
+      auto it = rby[t].find(ob.sb);
+      if (it == rby[t].end()) continue;
+      const Inter& R = ts[t].E->t;
+      for (int rb : it->second) {
+        const Inter::Blk& r = R.blocks[rb];
+        int y = ts[t].Y->find(ob.r, ob.sig, r.g, r.k);
+        if (y < 0) continue;
+        int K = r.W * r.cols;
+        gb.term(ts[t].Y->ptr(y), K, R.ptr(rb), K, K, ts[t].coef, ts[t].coef_dev);
+      }
     }
   }
-  gb.run();
+}
+
+// out[a][s][b] = sum_t coef_t sum_{w, a'} L_t[a][w][a'] Zp_t[b][s][w][a']
+static void plan_lcontract(const std::vector<LocalTerm>& ts, SiteT& out, GemmBatch& gb) {
+  std::vector<std::map<int, std::vector<int>>> lby(ts.size());
+  for (size_t t = 0; t < ts.size(); ++t)
+    for (int b = 0; b < (int)ts[t].E->t.blocks.size(); ++b)
+      lby[t][ts[t].E->t.blocks[b].rg].push_back(b);
+  for (int o = 0; o < (int)out.blocks.size(); ++o) {
+    const SiteT::Blk& ob = out.blocks[o];
+    gb.task(out.ptr(o), 0, ob.rows, ob.cols, ob.cols, OP_N, ts[0].E->t.et, OP_T, ts[0].Y->et,
+            false, 1.0);
+    for (size_t t = 0; t < ts.size(); ++t) {
+      auto it = lby[t].find(ob.r);
+      if (it == lby[t].end()) continue;
+      const Inter& Lt = ts[t].E->t;
+      for (int lb : it->second) {
+        const Inter::Blk& l = Lt.blocks[lb];
+        int z = ts[t].Y->find(ob.sb, ob.sig, l.g, l.k);
+        if (z < 0) continue;
+        int K = l.W * l.cols;
+        gb.term(Lt.ptr(lb), K, ts[t].Y->ptr(z), K, K, ts[t].coef, ts[t].coef_dev);
+      }
+    }
+  }
 }
 
 // L_new[b][w'][b'] = sum_{a, s} conj(C[a][s][b]) Y[a][s][w'][b']
-static Env env_from_Y_left(Context& c, const Inter& Y, const SiteT& bra, const Bond& bra_right,
-                           const MPOBond& mb, const Bond& ket_right) {
+static Env plan_env_left(Context& c, const Inter& Y, const SiteT& bra, const Bond& bra_right,
+                         const MPOBond& mb, const Bond& ket_right, GemmBatch& gb) {
   Env e;
   e.rows = RowGroups::from_bond(bra_right);
   e.mb = &mb;
   e.ket_copy = ket_right;
-  // Y blocks by (rg, sig)
   std::map<std::pair<int, int>, std::vector<int>> ybys;
   for (int y = 0; y < (int)Y.blocks.size(); ++y)
     ybys[{Y.blocks[y].rg, Y.blocks[y].sig}].push_back(y);
@@ -601,13 +576,11 @@ static Env env_from_Y_left(Context& c, const Inter& Y, const SiteT& bra, const B
     for (int y : it->second) contrib[{cb.sb, Y.blocks[y].g}].push_back({b, y});
   }
   for (auto& kv : contrib) {
-    int sb = kv.first[0], g = kv.first[1];
     const Inter::Blk& y0 = Y.blocks[kv.second[0].y];
-    e.t.add(sb, -1, g, y0.k, bra_right.d[sb], y0.W, y0.cols);
+    e.t.add(kv.first[0], -1, kv.first[1], y0.k, bra_right.d[kv.first[0]], y0.W, y0.cols);
   }
   e.t.et = Y.et;
   e.t.alloc(c.st, false);
-  GemmBatch gb(c);
   int id = 0;
   for (auto& kv : contrib) {
     const Inter::Blk& eb = e.t.blocks[id];
@@ -619,24 +592,13 @@ static Env env_from_Y_left(Context& c, const Inter& Y, const SiteT& bra, const B
     }
     ++id;
   }
-  gb.run();
   return e;
 }
 
-static Env env_update_left(Context& c, const Env& E, const SiteT& bra, const Bond& bra_right,
-                           const MPSd& ket, int site, const MPOd& m) {
-  Inter X = lstage(c, E, ket.sites[site], ket.bonds[site + 1]);
-  Inter Y = wstage_left(c, X, m, site);
-  return env_from_Y_left(c, Y, bra, bra_right, m.bonds[site + 1], ket.bonds[site + 1]);
-}
-
-// R at bond site+1 -> R at bond site
-static Env env_update_right(Context& c, const Env& R, const SiteT& bra, const Bond& bra_left,
-                            const MPSd& ket, int site, const MPOd& m) {
-  const SiteT& A = ket.sites[site];
-  const Bond& ket_left = ket.bonds[site];
-  // ket blocks by (right sector, sigma)
-  std::map<std::pair<int, int>, int> kby;
+// Z[rb][w'][s'][a'] = sum_b' R[rb][w'][b'] A[a'][s'][b']
+static Inter plan_r1(Context& c, const Env& R, const SiteT& A, const Bond& ket_left,
+                     GemmBatch& gb) {
+  std::map<std::pair<int, int>, int> kby;   // (right sector, sigma) -> ket block
   for (int b = 0; b < (int)A.blocks.size(); ++b) kby[{A.blocks[b].sb, A.blocks[b].sig}] = b;
   Inter Z;
   std::vector<std::pair<int, int>> src;
@@ -652,18 +614,18 @@ static Env env_update_right(Context& c, const Env& R, const SiteT& bra, const Bo
   }
   Z.et = R.t.et;
   Z.alloc(c.st, false);
-  {
-    GemmBatch gb(c);
-    for (int z = 0; z < (int)Z.blocks.size(); ++z) {
-      const Inter::Blk& zb = Z.blocks[z];
-      const Inter::Blk& r = R.t.blocks[src[z].first];
-      gb.task(Z.ptr(z), Z.et, zb.rows * zb.W, zb.cols, zb.cols, OP_N, R.t.et, OP_T, 0, false, 1.0);
-      gb.term(R.t.ptr(src[z].first), r.cols, A.ptr(src[z].second), r.cols, r.cols);
-    }
-    gb.run();
+  for (int z = 0; z < (int)Z.blocks.size(); ++z) {
+    const Inter::Blk& zb = Z.blocks[z];
+    const Inter::Blk& r = R.t.blocks[src[z].first];
+    gb.task(Z.ptr(z), Z.et, zb.rows * zb.W, zb.cols, zb.cols, OP_N, R.t.et, OP_T, 0, false, 1.0);
+    gb.term(R.t.ptr(src[z].first), r.cols, A.ptr(src[z].second), r.cols, r.cols);
   }
-  Inter Zp = wstage_right(c, Z, m, site);
-  // R_new[a][w][a'] = sum_{s, b} conj(C[a][s][b]) Z'[b][s][w][a']
+  return Z;
+}
+
+// R_new[a][w][a'] = sum_{s, b} conj(C[a][s][b]) Zp[b][s][w][a']
+static Env plan_env_right(Context& c, const Inter& Zp, const SiteT& bra, const Bond& bra_left,
+                          const MPOBond& mb, const Bond& ket_left, GemmBatch& gb) {
   std::map<std::pair<int, int>, std::vector<int>> zby;
   for (int z = 0; z < (int)Zp.blocks.size(); ++z) zby[{Zp.blocks[z].rg, Zp.blocks[z].sig}].push_back(z);
   struct T { int bra, z; };
@@ -676,7 +638,7 @@ static Env env_update_right(Context& c, const Env& R, const SiteT& bra, const Bo
   }
   Env e;
   e.rows = RowGroups::from_bond(bra_left);
-  e.mb = &m.bonds[site];
+  e.mb = &mb;
   e.ket_copy = ket_left;
   for (auto& kv : contrib) {
     const Inter::Blk& z0 = Zp.blocks[kv.second[0].z];
@@ -684,7 +646,6 @@ static Env env_update_right(Context& c, const Env& R, const SiteT& bra, const Bo
   }
   e.t.et = Zp.et;
   e.t.alloc(c.st, false);
-  GemmBatch gb(c);
   int id = 0;
   for (auto& kv : contrib) {
     const Inter::Blk& eb = e.t.blocks[id];
@@ -696,7 +657,35 @@ static Env env_update_right(Context& c, const Env& R, const SiteT& bra, const Bo
     }
     ++id;
   }
-  gb.run();
+  return e;
+}
+
+// Single-term environment updates (density-matrix code, boundaries).
+static Env env_update_left(Context& c, const Env& E, const SiteT& bra, const Bond& bra_right,
+                           const MPSd& ket, int site, const MPOd& m) {
+  GemmBatch g1(c);
+  Inter X = plan_lstage(c, E, ket.sites[site], ket.bonds[site + 1], g1);
+  g1.run();
+  WBatch wb;
+  Inter Y = plan_wstage(c, X, m, site, true, wb);
+  wb.run(c);
+  GemmBatch g2(c);
+  Env e = plan_env_left(c, Y, bra, bra_right, m.bonds[site + 1], ket.bonds[site + 1], g2);
+  g2.run();
+  return e;
+}
+
+static Env env_update_right(Context& c, const Env& R, const SiteT& bra, const Bond& bra_left,
+                            const MPSd& ket, int site, const MPOd& m) {
+  GemmBatch g1(c);
+  Inter Z = plan_r1(c, R, ket.sites[site], ket.bonds[site], g1);
+  g1.run();
+  WBatch wb;
+  Inter Zp = plan_wstage(c, Z, m, site, false, wb);
+  wb.run(c);
+  GemmBatch g2(c);
+  Env e = plan_env_right(c, Zp, bra, bra_left, m.bonds[site], ket.bonds[site], g2);
+  g2.run();
   return e;
 }
 
@@ -747,15 +736,26 @@ void run_copy(Context& c, const std::vector<CopyTask>& t, int to_work) {
 void run_qr(Context& c, FactWork& fw) {
   if (fw.tasks.empty()) return;
   double fl = 0.0;
-  for (auto& t : fw.tasks) {
+  std::vector<int> small, big;
+  size_t smem = 0;
+  for (size_t i = 0; i < fw.tasks.size(); ++i) {
+    const FactTask& t = fw.tasks[i];
     if (t.m > QR_MAX_ROWS || t.n > QR_MAX_COLS)
       throw Error(TDMPS_ERR_INVALID_ARG, "QR block exceeds the supported size");
     fl += 16.0 * t.m * t.n * t.n;
+    size_t b = ((size_t)t.m * t.n + (size_t)t.n * t.n) * sizeof(double2);
+    if (b <= (size_t)qr_warp_max_bytes()) { small.push_back((int)i); smem = std::max(smem, b); }
+    else big.push_back((int)i);
   }
   const FactTask* d = c.stage(fw.tasks);
   cudaEvent_t ev;
   c.kbegin(TDMPS_KSTAT_QR, &ev);
-  launch_qr(d, (int)fw.tasks.size(), c.st);
+  if (!small.empty()) launch_qr_warp(d, c.stage(small), (int)small.size(), smem, c.st);
+  if (!big.empty()) {
+    std::vector<FactTask> bt;
+    for (int i : big) bt.push_back(fw.tasks[i]);
+    launch_qr(c.stage(bt), (int)bt.size(), c.st);
+  }
   c.kend(TDMPS_KSTAT_QR, ev, fl, 0.0);
 }
 
@@ -1077,48 +1077,79 @@ void check_same_space(const MPSd& a, const MPSd& b) {
   if (a.tot != b.tot) throw Error(TDMPS_ERR_SECTOR, "MPS quantum numbers (N, 2Sz) differ");
 }
 
-// one-site local tensor at site i with bra bonds (bl, br)
-SiteT local_one(Context& c, std::vector<TermState>& ts, int i, const Bond& bl, const Bond& br) {
-  SiteT out = make_site(RowGroups::from_bond(bl), br, c.st, false);
+// MPO stage for all terms: one launch per distinct (non-identity) MPO
+std::vector<Inter> wstage_all(Context& c, const std::vector<TermState>& ts,
+                              const std::vector<Inter>& X, int site, bool left) {
+  std::vector<Inter> Y(ts.size());
+  std::vector<WBatch> batches;
+  std::vector<const MPOd*> mpos;
   for (size_t t = 0; t < ts.size(); ++t) {
-    TermState& s = ts[t];
-    Inter X = lstage(c, s.LE[i], s.ket->sites[i], s.ket->bonds[i + 1]);
-    Inter Y = wstage_left(c, X, *s.mpo, i);
-    rstage(c, Y, s.RE[i + 1], out, s.coef, s.coef_dev, t > 0);
+    if (ts[t].mpo->identity) { Y[t] = X[t]; continue; }
+    size_t b = 0;
+    while (b < mpos.size() && mpos[b] != ts[t].mpo) ++b;
+    if (b == mpos.size()) { mpos.push_back(ts[t].mpo); batches.emplace_back(); }
+    Y[t] = plan_wstage(c, X[t], *ts[t].mpo, site, left, batches[b]);
   }
-  return out;
+  for (auto& wb : batches) wb.run(c);
+  return Y;
 }
 
-// two-site local tensor at sites (i, i+1): rows = fused (a, s1)
-SiteT local_two(Context& c, std::vector<TermState>& ts, int i, const Bond& bl, const Bond& br) {
-  RowGroups fr = RowGroups::fused(bl);
-  SiteT out = make_site(fr, br, c.st, false);
-  for (size_t t = 0; t < ts.size(); ++t) {
-    TermState& s = ts[t];
-    Inter X1 = lstage(c, s.LE[i], s.ket->sites[i], s.ket->bonds[i + 1]);
-    Inter Y1 = wstage_left(c, X1, *s.mpo, i);
-    // view Y1 as an environment with fused rows (sa, s1) -> index sa*4+s1
-    Env E2;
-    E2.rows = fr;
-    E2.mb = &s.mpo->bonds[i + 1];
-    E2.ket_copy = s.ket->bonds[i + 1];
-    E2.t.data = Y1.data;
-    E2.t.size = Y1.size;
-    E2.t.et = Y1.et;
-    for (auto& b : Y1.blocks) {
-      int id = (int)E2.t.blocks.size();
-      E2.t.blocks.push_back({b.rg * 4 + b.sig, -1, b.g, b.k, b.rows, b.W, b.cols, b.off});
-      E2.t.index[{b.rg * 4 + b.sig, -1, b.g, b.k}] = id;
-    }
-    Inter X2 = lstage(c, E2, s.ket->sites[i + 1], s.ket->bonds[i + 2]);
-    Inter Y2 = wstage_left(c, X2, *s.mpo, i + 1);
-    rstage(c, Y2, s.RE[i + 2], out, s.coef, s.coef_dev, t > 0);
+// right environments at bond i of all terms from bond i+1, bra site C[i]
+void right_env_step(Context& c, std::vector<TermState>& ts, const MPSd& C, int i,
+                    const std::vector<Inter>* zp = nullptr) {
+  std::vector<Inter> Zp;
+  if (!zp) {
+    GemmBatch g1(c);
+    std::vector<Inter> Z(ts.size());
+    for (size_t t = 0; t < ts.size(); ++t)
+      Z[t] = plan_r1(c, ts[t].RE[i + 1], ts[t].ket->sites[i], ts[t].ket->bonds[i], g1);
+    g1.run();
+    Zp = wstage_all(c, ts, Z, i, false);
+    zp = &Zp;
   }
-  return out;
+  GemmBatch g3(c);
+  for (size_t t = 0; t < ts.size(); ++t)
+    ts[t].RE[i] = plan_env_right(c, (*zp)[t], C.sites[i], C.bonds[i], ts[t].mpo->bonds[i],
+                                 ts[t].ket->bonds[i], g3);
+  g3.run();
+}
+
+void left_env_step(Context& c, std::vector<TermState>& ts, const MPSd& C, int i,
+                   const std::vector<Inter>& Y) {
+  GemmBatch g3(c);
+  for (size_t t = 0; t < ts.size(); ++t)
+    ts[t].LE[i + 1] = plan_env_left(c, Y[t], C.sites[i], C.bonds[i + 1], ts[t].mpo->bonds[i + 1],
+                                    ts[t].ket->bonds[i + 1], g3);
+  g3.run();
+}
+
+// Y_t = W_i (L_t[i] A_t[i]) for all terms
+std::vector<Inter> left_stages(Context& c, std::vector<TermState>& ts, int i) {
+  GemmBatch g1(c);
+  std::vector<Inter> X(ts.size());
+  for (size_t t = 0; t < ts.size(); ++t)
+    X[t] = plan_lstage(c, ts[t].LE[i], ts[t].ket->sites[i], ts[t].ket->bonds[i + 1], g1);
+  g1.run();
+  return wstage_all(c, ts, X, i, true);
+}
+
+// Zp_t = W_i^right (R_t[i+1] A_t[i]^T) for all terms
+std::vector<Inter> right_stages(Context& c, std::vector<TermState>& ts, int i) {
+  GemmBatch g1(c);
+  std::vector<Inter> Z(ts.size());
+  for (size_t t = 0; t < ts.size(); ++t)
+    Z[t] = plan_r1(c, ts[t].RE[i + 1], ts[t].ket->sites[i], ts[t].ket->bonds[i], g1);
+  g1.run();
+  return wstage_all(c, ts, Z, i, false);
 }
 
 }  // namespace
 
+// Variational fit of Eq. (add_min): sum_t coef_t O_t |ket_t> into an MPS of
+// bond dimension <= D, guess right-canonicalised first; schedule as in the
+// header.  Left-to-right one-site steps contract L, A, W, then R, and reuse
+// W(L A) for the new left environment; right-to-left steps contract R, A, W,
+// then L, and reuse W(R A) for the new right environment.
 MPSd fit(Context& c, const std::vector<FitTerm>& terms, const MPSd& guess, const FitOpts& o) {
   if (terms.empty()) throw Error(TDMPS_ERR_INVALID_ARG, "no fit terms");
   if (o.D < 1) throw Error(TDMPS_ERR_INVALID_ARG, "D must be >= 1");
@@ -1138,65 +1169,99 @@ MPSd fit(Context& c, const std::vector<FitTerm>& terms, const MPSd& guess, const
     ts[t].RE.resize(L + 1);
     ts[t].LE[0] = env_left_boundary(c, C, *ts[t].ket, *ts[t].mpo);
     ts[t].RE[L] = env_right_boundary(c, C, *ts[t].ket, *ts[t].mpo);
-    for (int i = L - 1; i >= 1; --i)
-      ts[t].RE[i] = env_update_right(c, ts[t].RE[i + 1], C.sites[i], C.bonds[i], *ts[t].ket, i,
-                                     *ts[t].mpo);
   }
+  for (int i = L - 1; i >= 1; --i) right_env_step(c, ts, C, i);
+  auto local_terms = [&](const std::vector<Inter>& Y, int env_bond, bool right_env) {
+    std::vector<LocalTerm> lt;
+    for (size_t t = 0; t < ts.size(); ++t)
+      lt.push_back({&Y[t], right_env ? &ts[t].RE[env_bond] : &ts[t].LE[env_bond], ts[t].coef,
+                    ts[t].coef_dev});
+    return lt;
+  };
   if (L == 1) {
-    C.sites[0] = local_one(c, ts, 0, C.bonds[0], C.bonds[1]);
+    std::vector<Inter> Y = left_stages(c, ts, 0);
+    SiteT out = make_site(RowGroups::from_bond(C.bonds[0]), C.bonds[1], c.st, false);
+    GemmBatch g(c);
+    plan_rstage(local_terms(Y, 1, true), out, g);
+    g.run();
+    C.sites[0] = std::move(out);
     return C;
   }
   double maxdisc = 0.0;
   for (int sw = 0; sw < o.n_two_site; ++sw) {
     for (int half = 0; half < 2; ++half) {
       for (int step = 0; step < L - 1; ++step) {
-        int i = half == 0 ? step : L - 2 - step;
-        SiteT Th = local_two(c, ts, i, C.bonds[i], C.bonds[i + 2]);
-        SplitResult sp = svd_split(c, Th, RowGroups::fused(C.bonds[i]),
-                                   RowGroups::from_bond(C.bonds[i]), C.bonds[i + 2], o.D, o.eps,
-                                   half == 0);
+        const int i = half == 0 ? step : L - 2 - step;
+        // two-site tensor: (L A_i W_i) viewed as an environment with fused
+        // rows (a, s1), then A_{i+1}, W_{i+1} and R_{i+2}
+        std::vector<Inter> Y1 = left_stages(c, ts, i);
+        RowGroups fr = RowGroups::fused(C.bonds[i]);
+        std::vector<Env> E2(ts.size());
+        for (size_t t = 0; t < ts.size(); ++t) {
+          E2[t].rows = fr;
+          E2[t].mb = &ts[t].mpo->bonds[i + 1];
+          E2[t].ket_copy = ts[t].ket->bonds[i + 1];
+          E2[t].t.data = Y1[t].data;
+          E2[t].t.size = Y1[t].size;
+          E2[t].t.et = Y1[t].et;
+          for (auto& b : Y1[t].blocks) {
+            int id = (int)E2[t].t.blocks.size();
+            E2[t].t.blocks.push_back({b.rg * 4 + b.sig, -1, b.g, b.k, b.rows, b.W, b.cols, b.off});
+            E2[t].t.index[{b.rg * 4 + b.sig, -1, b.g, b.k}] = id;
+          }
+        }
+        GemmBatch g2(c);
+        std::vector<Inter> X2(ts.size());
+        for (size_t t = 0; t < ts.size(); ++t)
+          X2[t] = plan_lstage(c, E2[t], ts[t].ket->sites[i + 1], ts[t].ket->bonds[i + 2], g2);
+        g2.run();
+        std::vector<Inter> Y2 = wstage_all(c, ts, X2, i + 1, true);
+        SiteT Th = make_site(fr, C.bonds[i + 2], c.st, false);
+        GemmBatch g3(c);
+        plan_rstage(local_terms(Y2, i + 2, true), Th, g3);
+        g3.run();
+        SplitResult sp = svd_split(c, Th, fr, RowGroups::from_bond(C.bonds[i]), C.bonds[i + 2],
+                                   o.D, o.eps, half == 0);
         if (sp.total > 0) maxdisc = std::max(maxdisc, sp.disc / sp.total);
         C.sites[i] = std::move(sp.A);
         C.sites[i + 1] = std::move(sp.B);
         C.bonds[i + 1] = sp.mid;
-        for (auto& s : ts) {
-          if (half == 0)
-            s.LE[i + 1] = env_update_left(c, s.LE[i], C.sites[i], C.bonds[i + 1], *s.ket, i, *s.mpo);
-          else
-            s.RE[i + 1] = env_update_right(c, s.RE[i + 2], C.sites[i + 1], C.bonds[i + 1], *s.ket,
-                                           i + 1, *s.mpo);
-        }
+        if (half == 0) left_env_step(c, ts, C, i, Y1);
+        else right_env_step(c, ts, C, i + 1);
       }
     }
   }
   for (int sw = 0; sw < o.n_one_site; ++sw) {
     for (int i = 0; i < L; ++i) {
-      SiteT Ci = local_one(c, ts, i, C.bonds[i], C.bonds[i + 1]);
+      std::vector<Inter> Y = left_stages(c, ts, i);
+      SiteT Ci = make_site(RowGroups::from_bond(C.bonds[i]), C.bonds[i + 1], c.st, false);
+      GemmBatch g(c);
+      plan_rstage(local_terms(Y, i + 1, true), Ci, g);
+      g.run();
       if (i < L - 1) {
         auto qr = qr_left(c, Ci, RowGroups::from_bond(C.bonds[i]), C.bonds[i + 1]);
         C.sites[i] = std::move(qr.first);
         C.bonds[i + 1] = qr.second;
-        for (auto& s : ts)
-          s.LE[i + 1] = env_update_left(c, s.LE[i], C.sites[i], C.bonds[i + 1], *s.ket, i, *s.mpo);
+        left_env_step(c, ts, C, i, Y);
       } else {
         C.sites[i] = std::move(Ci);
       }
     }
     for (int i = L - 1; i >= 0; --i) {
-      SiteT Ci = local_one(c, ts, i, C.bonds[i], C.bonds[i + 1]);
+      std::vector<Inter> Zp = right_stages(c, ts, i);
+      SiteT Ci = make_site(RowGroups::from_bond(C.bonds[i]), C.bonds[i + 1], c.st, false);
+      GemmBatch g(c);
+      plan_lcontract(local_terms(Zp, i, false), Ci, g);
+      g.run();
       if (i > 0) {
         LQResult lq = lq_right(c, Ci, C.bonds[i], C.bonds[i + 1]);
         C.sites[i] = std::move(lq.Q);
         C.bonds[i] = lq.left;
-        for (auto& s : ts)
-          s.RE[i] = env_update_right(c, s.RE[i + 1], C.sites[i], C.bonds[i], *s.ket, i, *s.mpo);
+        right_env_step(c, ts, C, i, &Zp);
       } else {
         C.sites[0] = std::move(Ci);
       }
     }
-  }
-  if (o.n_one_site == 0) {
-    // two-site sweeps end with the norm on site 0 already (U S absorbed left)
   }
   if (o.max_discarded) *o.max_discarded = std::max(*o.max_discarded, maxdisc);
   return C;
@@ -1204,22 +1269,60 @@ MPSd fit(Context& c, const std::vector<FitTerm>& terms, const MPSd& guess, const
 
 // ------------------------------------------------------------------ sandwiches
 
-void sandwich_dev(Context& c, const MPOd* mpo, const MPSd& bra, const MPSd& ket, double2* out) {
-  check_same_space(bra, ket);
-  const MPOd& m = mpo ? *mpo : c.identity_mpo(bra.L);
-  Env E = env_left_boundary(c, bra, ket, m);
-  for (int i = 0; i < bra.L; ++i)
-    E = env_update_left(c, E, bra.sites[i], bra.bonds[i + 1], ket, i, m);
-  int b = -1;
-  for (int k = 0; k < (int)E.t.blocks.size(); ++k) b = k;
-  if (b < 0) {
-    TD_CHECK_CUDA(cudaMemsetAsync(out, 0, sizeof(double2), c.st));
-    return;
+namespace {
+// Temporarily switch a context to FP64 contractions (Krylov inner products,
+// observables and norms stay FP64 in every precision mode).
+struct Fp64Scope {
+  Context& c;
+  int saved;
+  explicit Fp64Scope(Context& ctx) : c(ctx), saved(ctx.precision) { c.precision = TDMPS_FP64; }
+  ~Fp64Scope() { c.precision = saved; }
+};
+}  // namespace
+
+// <bra_p| O |ket_p> for many pairs, one launch per stage and site for all;
+// FP64 contractions.
+void sandwich_batch(Context& c, const MPOd* mpo,
+                    const std::vector<std::pair<const MPSd*, const MPSd*>>& pairs,
+                    const std::vector<double2*>& outs) {
+  if (pairs.empty()) return;
+  Fp64Scope fp64(c);
+  const int L = pairs[0].first->L;
+  for (auto& p : pairs) check_same_space(*p.first, *p.second);
+  const MPOd& m = mpo ? *mpo : c.identity_mpo(L);
+  std::vector<Env> E(pairs.size());
+  for (size_t p = 0; p < pairs.size(); ++p) E[p] = env_left_boundary(c, *pairs[p].first, *pairs[p].second, m);
+  for (int i = 0; i < L; ++i) {
+    GemmBatch g1(c);
+    std::vector<Inter> X(pairs.size());
+    for (size_t p = 0; p < pairs.size(); ++p)
+      X[p] = plan_lstage(c, E[p], pairs[p].second->sites[i], pairs[p].second->bonds[i + 1], g1);
+    g1.run();
+    WBatch wb;
+    std::vector<Inter> Y(pairs.size());
+    for (size_t p = 0; p < pairs.size(); ++p) Y[p] = plan_wstage(c, X[p], m, i, true, wb);
+    wb.run(c);
+    GemmBatch g2(c);
+    for (size_t p = 0; p < pairs.size(); ++p)
+      E[p] = plan_env_left(c, Y[p], pairs[p].first->sites[i], pairs[p].first->bonds[i + 1],
+                           m.bonds[i + 1], pairs[p].second->bonds[i + 1], g2);
+    g2.run();
   }
-  if (E.t.blocks.size() != 1 || E.t.blocks[0].rows != 1 || E.t.blocks[0].W != 1 ||
-      E.t.blocks[0].cols != 1)
-    throw Error(TDMPS_ERR_SECTOR, "final environment is not a scalar");
-  launch_to_double(E.t.ptr(0), E.t.et, out, 1, c.st);
+  for (size_t p = 0; p < pairs.size(); ++p) {
+    const Env& e = E[p];
+    if (e.t.blocks.empty()) {
+      TD_CHECK_CUDA(cudaMemsetAsync(outs[p], 0, sizeof(double2), c.st));
+      continue;
+    }
+    if (e.t.blocks.size() != 1 || e.t.blocks[0].rows != 1 || e.t.blocks[0].W != 1 ||
+        e.t.blocks[0].cols != 1)
+      throw Error(TDMPS_ERR_SECTOR, "final environment is not a scalar");
+    launch_to_double(e.t.ptr(0), e.t.et, outs[p], 1, c.st);
+  }
+}
+
+void sandwich_dev(Context& c, const MPOd* mpo, const MPSd& bra, const MPSd& ket, double2* out) {
+  sandwich_batch(c, mpo, {{&bra, &ket}}, {out});
 }
 
 cplx sandwich(Context& c, const MPOd* mpo, const MPSd& bra, const MPSd& ket) {
@@ -1312,20 +1415,49 @@ MPSd krylov_step(Context& c, const MPOd& H, const MPSd& psi, double dt, int m, b
   double2* Nd = (double2*)mats->p;
   double2* Hd = Nd + m * m;
   double2* cd = Hd + m * m;
-  double2* gs = cd + m;
   TD_CHECK_CUDA(cudaMemsetAsync(mats->p, 0, sizeof(double2) * (2 * m * m + 2 * m + 8), c.st));
   std::vector<char> haveN(m * m, 0), haveH(m * m, 0);
-  const MPOd& I = c.identity_mpo(psi.L);
+  // batched exact overlaps / H sandwiches for the pairs (i, j), i <= j, not yet known
+  auto fill = [&](const std::vector<std::pair<int, int>>& want, bool withH) {
+    std::vector<std::pair<const MPSd*, const MPSd*>> pn, ph;
+    std::vector<double2*> on, oh;
+    for (auto& ij : want) {
+      int i = ij.first, j = ij.second;
+      if (!haveN[i * m + j]) {
+        pn.push_back({&phi[i], &phi[j]});
+        on.push_back(Nd + i * m + j);
+        haveN[i * m + j] = 1;
+      }
+      if (withH && !haveH[i * m + j]) {
+        ph.push_back({&phi[i], &phi[j]});
+        oh.push_back(Hd + i * m + j);
+        haveH[i * m + j] = 1;
+      }
+    }
+    sandwich_batch(c, nullptr, pn, on);
+    sandwich_batch(c, &H, ph, oh);
+  };
   for (int k = 0; k + 1 < m; ++k) {
     MPSd u = fit(c, {{&phi[k], &H, 1.0}}, phi[k], o);
     if (orth) {
-      std::vector<FitTerm> terms;
-      terms.push_back({&u, nullptr, 1.0});
-      for (int j = 0; j <= k; ++j) {
-        if (!haveH[j * m + k]) { sandwich_dev(c, &H, phi[j], phi[k], Hd + j * m + k); haveH[j * m + k] = 1; }
-        if (!haveN[j * m + j]) { sandwich_dev(c, &I, phi[j], phi[j], Nd + j * m + j); haveN[j * m + j] = 1; }
+      // Eq. (kry_orth): c_j = <phi_j|H|phi_k> / <phi_j|phi_j>
+      std::vector<std::pair<int, int>> want;
+      for (int j = 0; j <= k; ++j) want.push_back({j, k});
+      for (int j = 0; j <= k; ++j) want.push_back({j, j});
+      {
+        // H sandwiches (j, k) and overlaps (j, j) in two batched sweeps
+        std::vector<std::pair<const MPSd*, const MPSd*>> pn, ph;
+        std::vector<double2*> on, oh;
+        for (int j = 0; j <= k; ++j) {
+          if (!haveH[j * m + k]) { ph.push_back({&phi[j], &phi[k]}); oh.push_back(Hd + j * m + k); haveH[j * m + k] = 1; }
+          if (!haveN[j * m + j]) { pn.push_back({&phi[j], &phi[j]}); on.push_back(Nd + j * m + j); haveN[j * m + j] = 1; }
+        }
+        sandwich_batch(c, &H, ph, oh);
+        sandwich_batch(c, nullptr, pn, on);
       }
       DevPtr cj = dev_alloc(sizeof(double2) * (k + 1), c.st);
+      std::vector<FitTerm> terms;
+      terms.push_back({&u, nullptr, 1.0});
       for (int j = 0; j <= k; ++j) {
         launch_scalar_div_neg(Hd + j * m + k, Nd + j * m + j, (double2*)cj->p + j, c.st);
         terms.push_back({&phi[j], nullptr, 1.0, (double2*)cj->p + j});
@@ -1333,18 +1465,15 @@ MPSd krylov_step(Context& c, const MPOd& H, const MPSd& psi, double dt, int m, b
       MPSd v = fit(c, terms, u, o);
       normalize_center(c, v, nullptr);
       phi.push_back(std::move(v));
-      // keep coefficient buffer alive until the fit's kernels ran (stream order)
-      (void)cj;
     } else {
       normalize_center(c, u, nullptr);
       phi.push_back(std::move(u));
     }
   }
+  std::vector<std::pair<int, int>> rest;
   for (int i = 0; i < m; ++i)
-    for (int j = i; j < m; ++j) {
-      if (!haveN[i * m + j]) sandwich_dev(c, &I, phi[i], phi[j], Nd + i * m + j);
-      if (!haveH[i * m + j]) sandwich_dev(c, &H, phi[i], phi[j], Hd + i * m + j);
-    }
+    for (int j = i; j < m; ++j) rest.push_back({i, j});
+  fill(rest, true);
   int* st = (int*)c.status->p + 4;
   launch_krylov_small(Nd, Hd, m, dt, cd, st, c.st);
   int hs[2];
@@ -1354,13 +1483,13 @@ MPSd krylov_step(Context& c, const MPOd& H, const MPSd& psi, double dt, int m, b
   if (m - hs[0] < 2) throw Error(TDMPS_ERR_KRYLOV_SINGULAR, "Krylov overlap matrix has rank < 2");
   std::vector<FitTerm> terms;
   for (int k = 0; k < m; ++k) terms.push_back({&phi[k], nullptr, 1.0, cd + k});
-  (void)gs;
   return fit(c, terms, phi[0], o);
 }
 
 // ------------------------------------------------------------------ one-body RDM
 
 void one_rdm(Context& c, const MPSd& psi, cplx* gamma) {
+  Fp64Scope fp64(c);
   const int L = psi.L;
   const MPOd& I = c.identity_mpo(L);
   const MPOd& G = c.rdm_mpo(L);
@@ -1399,9 +1528,15 @@ void one_rdm(Context& c, const MPSd& psi, cplx* gamma) {
     }
     upload_mpo_tables(R, c);
     // contract: E (bond j) with site j through the readout, then with RO[j+1]
-    Inter X = lstage(c, E, psi.sites[j], psi.bonds[j + 1]);
-    Inter Y = wstage_left(c, X, R, 0);
-    Env Eo = env_from_Y_left(c, Y, psi.sites[j], psi.bonds[j + 1], R.bonds[1], psi.bonds[j + 1]);
+    GemmBatch g1(c);
+    Inter X = plan_lstage(c, E, psi.sites[j], psi.bonds[j + 1], g1);
+    g1.run();
+    WBatch wb;
+    Inter Y = plan_wstage(c, X, R, 0, true, wb);
+    wb.run(c);
+    GemmBatch g2(c);
+    Env Eo = plan_env_left(c, Y, psi.sites[j], psi.bonds[j + 1], R.bonds[1], psi.bonds[j + 1], g2);
+    g2.run();
     for (int b = 0; b < (int)Eo.t.blocks.size(); ++b) {
       const Inter::Blk& eb = Eo.t.blocks[b];
       int rb2 = RO[j + 1].t.find(eb.rg, -1, 0, eb.rg);

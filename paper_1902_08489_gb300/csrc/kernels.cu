@@ -66,10 +66,12 @@ __global__ void __launch_bounds__(256) k_gemm(const GemmTask* __restrict__ tasks
     for (int j = 0; j < 2; ++j) acc[i][j] = make_double2(0.0, 0.0);
   for (int e = t.term_begin; e < t.term_end; ++e) {
     const GemmTerm g = terms[e];
+    double2 sc = g.scale;
+    if (g.scale_ptr) sc = cmul(sc, *g.scale_ptr);
     for (int k0 = 0; k0 < g.K; k0 += GK) {
       {
         int i = threadIdx.x >> 3, k = threadIdx.x & 7;      // A tile: 32 x 8
-        As[k][i] = load_op((const double2*)g.A, g.lda, t.opA, m0 + i, k0 + k, t.M, g.K);
+        As[k][i] = cmul(sc, load_op((const double2*)g.A, g.lda, t.opA, m0 + i, k0 + k, t.M, g.K));
         int kk = threadIdx.x >> 5, j = threadIdx.x & 31;    // B tile: 8 x 32
         Bs[kk][j] = load_op((const double2*)g.B, g.ldb, t.opB, k0 + kk, n0 + j, g.K, t.N);
       }
@@ -128,11 +130,18 @@ __device__ __forceinline__ void st2<float2>(float2* p, size_t i, double2 v) {
   p[i] = make_float2((float)v.x, (float)v.y);
 }
 
+// accumulation type of the MPO stage: FP64 for complex double data, FP32 for
+// complex float data (the FP64 pipe is the scarce unit on this part)
+template <class T> struct WAcc;
+template <> struct WAcc<double2> { using R = double; };
+template <> struct WAcc<float2> { using R = float; };
+
 template <class T>
 __global__ void __launch_bounds__(256) k_wstage(const WTask* __restrict__ tasks, int ntasks,
                                                 int64_t total, const int* __restrict__ rowptr,
                                                 const int* __restrict__ ent_w,
                                                 const double* __restrict__ ent_v) {
+  using R = typename WAcc<T>::R;
   for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
        idx += (int64_t)gridDim.x * blockDim.x) {
     int lo = 0, hi = ntasks - 1;
@@ -146,22 +155,23 @@ __global__ void __launch_bounds__(256) k_wstage(const WTask* __restrict__ tasks,
     int64_t rw = loc / t.cols;
     int w = (int)(rw % t.wout);
     int a = (int)(rw / t.wout);
-    double2 acc = make_double2(0.0, 0.0);
+    R ax = 0, ay = 0;
     for (int s = 0; s < 4; ++s) {
       if (t.csr[s] < 0) continue;
       const int* rp = rowptr + t.csr[s];
       const T* X = (const T*)t.X[s];
       int win = t.win[s];
       for (int e = rp[w]; e < rp[w + 1]; ++e) {
-        double v = ent_v[e];
-        double2 x = ld2(X, ((size_t)a * win + ent_w[e]) * t.cols + b);
-        acc.x = fma(v, x.x, acc.x);
-        acc.y = fma(v, x.y, acc.y);
+        R v = (R)ent_v[e];
+        T x = X[((size_t)a * win + ent_w[e]) * t.cols + b];
+        ax = fma(v, (R)x.x, ax);
+        ay = fma(v, (R)x.y, ay);
       }
     }
-    size_t yo = ((size_t)a * t.wout + w) * t.cols + b;
-    if (t.beta) acc = cadd(acc, ld2((const T*)t.Y, yo));
-    st2((T*)t.Y, yo, acc);
+    T* y = (T*)t.Y + ((size_t)a * t.wout + w) * t.cols + b;
+    if (t.beta) { ax += (R)y->x; ay += (R)y->y; }
+    y->x = ax;
+    y->y = ay;
   }
 }
 
@@ -469,19 +479,25 @@ void launch_svd(const FactTask* d_tasks, int ntasks, int* d_status, cudaStream_t
 constexpr int QR_THREADS = 256;
 constexpr int QR_MAX_M = 4096;
 constexpr int QR_MAX_N = 2048;
+constexpr int QR_SMEM = 200 * 1024;   // matrix held in shared memory when it fits
 
 __global__ void __launch_bounds__(QR_THREADS) k_qr(const FactTask* __restrict__ tasks) {
   extern __shared__ double2 sh[];
-  double2* v = sh;                 // m
-  double2* coef = sh + QR_MAX_M;   // up to n
   const FactTask t = tasks[blockIdx.x];
   const int m = t.m, n = t.n, kmax = m < n ? m : n;
-  double2* A = t.A;
-  double2* R = t.V;
+  // layout: [v: m][coef: n][A: m*n][R: n*n] when they fit
+  double2* v = sh;
+  double2* coef = sh + m;
+  const bool a_sh =
+      (size_t)(m + n + (size_t)m * n + (size_t)n * n) * sizeof(double2) <= (size_t)QR_SMEM;
+  double2* A = a_sh ? sh + m + n : t.A;
+  double2* R = a_sh ? sh + m + n + (size_t)m * n : t.V;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
   __shared__ double maxn, vn;
   __shared__ int nq;
   if (threadIdx.x == 0) { maxn = 0.0; nq = 0; }
+  if (a_sh)
+    for (size_t e = threadIdx.x; e < (size_t)m * n; e += blockDim.x) A[e] = t.A[e];
   for (int e = threadIdx.x; e < n * n; e += blockDim.x) R[e] = make_double2(0.0, 0.0);
   __syncthreads();
   for (int j = warp; j < n; j += nwarp) {
@@ -500,8 +516,8 @@ __global__ void __launch_bounds__(QR_THREADS) k_qr(const FactTask* __restrict__ 
     __syncthreads();
     const int q = nq;
     for (int pass = 0; pass < 2; ++pass) {
-      for (int c = warp; c < q; c += nwarp) {
-        const double2* qc = A + (size_t)c * m;
+      for (int cc = warp; cc < q; cc += nwarp) {
+        const double2* qc = A + (size_t)cc * m;
         double re = 0.0, im = 0.0;
         for (int i = lane; i < m; i += 32) {
           double2 a = qc[i], b = v[i];
@@ -509,17 +525,17 @@ __global__ void __launch_bounds__(QR_THREADS) k_qr(const FactTask* __restrict__ 
           im += a.x * b.y - a.y * b.x;
         }
         re = warp_sum(re); im = warp_sum(im);
-        if (lane == 0) coef[c] = make_double2(re, im);
+        if (lane == 0) coef[cc] = make_double2(re, im);
       }
       __syncthreads();
       for (int i = threadIdx.x; i < m; i += blockDim.x) {
         double2 acc = v[i];
-        for (int c = 0; c < q; ++c) acc = csub(acc, cmul(coef[c], A[(size_t)c * m + i]));
+        for (int cc = 0; cc < q; ++cc) acc = csub(acc, cmul(coef[cc], A[(size_t)cc * m + i]));
         v[i] = acc;
       }
-      for (int c = threadIdx.x; c < q; c += blockDim.x) {
-        double2* rr = R + (size_t)j * n + c;   // R[c, j], leading dimension n
-        *rr = cadd(*rr, coef[c]);
+      for (int cc = threadIdx.x; cc < q; cc += blockDim.x) {
+        double2* rr = R + (size_t)j * n + cc;   // R[c, j], leading dimension n
+        *rr = cadd(*rr, coef[cc]);
       }
       __syncthreads();
     }
@@ -542,20 +558,98 @@ __global__ void __launch_bounds__(QR_THREADS) k_qr(const FactTask* __restrict__ 
     __syncthreads();
   }
   const int nfin = nq;
-  for (int c = nfin; c < kmax; ++c)
-    for (int i = threadIdx.x; i < m; i += blockDim.x) A[(size_t)c * m + i] = make_double2(0.0, 0.0);
+  for (int cc = nfin; cc < kmax; ++cc)
+    for (int i = threadIdx.x; i < m; i += blockDim.x) A[(size_t)cc * m + i] = make_double2(0.0, 0.0);
+  if (a_sh) {
+    __syncthreads();
+    for (size_t e = threadIdx.x; e < (size_t)m * kmax; e += blockDim.x) t.A[e] = A[e];
+    for (size_t e = threadIdx.x; e < (size_t)n * n; e += blockDim.x) t.V[e] = R[e];
+  }
+}
+
+// Warp-sized variant for the small sector matrices of a bond (m*n*16 bytes
+// <= QRW_SMEM): one warp per matrix, no block barriers; Gram-Schmidt with one
+// re-orthogonalisation pass, each projection applied as soon as its inner
+// product is known (modified Gram-Schmidt order).  Same dependency rule and
+// outputs as k_qr.
+constexpr int QRW_SMEM = 96 * 1024;
+
+__global__ void __launch_bounds__(32) k_qr_warp(const FactTask* __restrict__ tasks,
+                                                const int* __restrict__ ids) {
+  extern __shared__ double2 shw[];
+  const FactTask t = tasks[ids[blockIdx.x]];
+  const int m = t.m, n = t.n, kmax = m < n ? m : n;
+  const int lane = threadIdx.x;
+  double2* A = shw;                       // m x n, column-major
+  double2* R = shw + (size_t)m * n;       // n x n, leading dimension n
+  for (int e = lane; e < m * n; e += 32) A[e] = t.A[e];
+  for (int e = lane; e < n * n; e += 32) R[e] = make_double2(0.0, 0.0);
+  __syncwarp();
+  double maxn = 0.0;
+  for (int j = 0; j < n; ++j) {
+    double s2 = 0.0;
+    for (int i = lane; i < m; i += 32) s2 += cabs2(A[(size_t)j * m + i]);
+    maxn = fmax(maxn, sqrt(warp_sum(s2)));
+  }
+  const double tol = 1e-12 * maxn;
+  int nq = 0;
+  for (int j = 0; j < n; ++j) {
+    double2* v = A + (size_t)j * m;
+    for (int pass = 0; pass < 2; ++pass) {
+      for (int cc = 0; cc < nq; ++cc) {
+        const double2* qc = A + (size_t)cc * m;
+        double re = 0.0, im = 0.0;
+        for (int i = lane; i < m; i += 32) {
+          double2 a = qc[i], b = v[i];
+          re += a.x * b.x + a.y * b.y;
+          im += a.x * b.y - a.y * b.x;
+        }
+        const double2 c = make_double2(warp_sum(re), warp_sum(im));
+        for (int i = lane; i < m; i += 32) v[i] = csub(v[i], cmul(c, qc[i]));
+        if (lane == 0) R[(size_t)j * n + cc] = cadd(R[(size_t)j * n + cc], c);
+        __syncwarp();
+      }
+    }
+    double s2 = 0.0;
+    for (int i = lane; i < m; i += 32) s2 += cabs2(v[i]);
+    const double nrm = sqrt(warp_sum(s2));
+    if (nrm > tol && nq < kmax) {
+      const double inv = 1.0 / nrm;
+      double2* q = A + (size_t)nq * m;
+      for (int i = lane; i < m; i += 32) q[i] = cscale(v[i], inv);   // nq <= j: in place or earlier
+      if (lane == 0) R[(size_t)j * n + nq] = make_double2(nrm, 0.0);
+      ++nq;
+    }
+    __syncwarp();
+  }
+  for (int cc = nq; cc < kmax; ++cc)
+    for (int i = lane; i < m; i += 32) A[(size_t)cc * m + i] = make_double2(0.0, 0.0);
+  __syncwarp();
+  for (int e = lane; e < m * kmax; e += 32) t.A[e] = A[e];
+  for (int e = lane; e < n * n; e += 32) t.V[e] = R[e];
 }
 
 void launch_qr(const FactTask* d_tasks, int ntasks, cudaStream_t st) {
   if (ntasks <= 0) return;
-  size_t shmem = sizeof(double2) * (QR_MAX_M + QR_MAX_N);
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(k_qr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shmem);
+    cudaFuncSetAttribute(k_qr, cudaFuncAttributeMaxDynamicSharedMemorySize, QR_SMEM);
     attr = true;
   }
-  k_qr<<<ntasks, QR_THREADS, shmem, st>>>(d_tasks);
+  k_qr<<<ntasks, QR_THREADS, QR_SMEM, st>>>(d_tasks);
 }
+
+void launch_qr_warp(const FactTask* d_tasks, const int* d_ids, int n, size_t smem, cudaStream_t st) {
+  if (n <= 0) return;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_qr_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, QRW_SMEM);
+    attr = true;
+  }
+  k_qr_warp<<<n, 32, smem, st>>>(d_tasks, d_ids);
+}
+
+int qr_warp_max_bytes() { return QRW_SMEM; }
 
 // ------------------------------------------------------------------ truncation rule
 

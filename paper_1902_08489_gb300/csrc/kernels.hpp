@@ -11,10 +11,14 @@ namespace tdmps {
 // op codes for grouped GEMM operands
 enum : int { OP_N = 0, OP_T = 1, OP_C = 2, OP_J = 3 };   // none, transpose, conj-transpose, conj
 
+// One product op(A) op(B) of a task; op(A) elements are multiplied by
+// scale * (*scale_ptr if non-null) while staged (per-term coefficients).
 struct GemmTerm {
   const void* A;
   const void* B;
   int K, lda, ldb, pad;
+  double2 scale;
+  const double2* scale_ptr;
 };
 
 // C (M x N, ldc) = alpha * sum_terms op(A) op(B) + beta * C;
@@ -94,6 +98,9 @@ void launch_zero(double2* p, size_t n, cudaStream_t st);
 void launch_svd(const FactTask* d_tasks, int ntasks, int* d_status, cudaStream_t st,
                 size_t max_bytes);
 void launch_qr(const FactTask* d_tasks, int ntasks, cudaStream_t st);
+// warp-per-matrix QR for the tasks listed in d_ids (m*n*16 <= qr_warp_max_bytes())
+void launch_qr_warp(const FactTask* d_tasks, const int* d_ids, int n, size_t smem, cudaStream_t st);
+int qr_warp_max_bytes();
 // truncation rule over nv singular values (grouped by sector, each sector
 // descending; sector id per value): writes kept count per sector and the
 // discarded / total weight to out_w[0..1].

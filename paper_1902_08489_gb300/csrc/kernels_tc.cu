@@ -202,12 +202,19 @@ __global__ void __launch_bounds__(128) k_gemm_tc(const GemmTask* __restrict__ ta
   bool ok = true;
   for (int e = t.term_begin; e < t.term_end && ok; ++e) {
     const GemmTerm g = terms[e];
+    double2 scd = g.scale;
+    if (g.scale_ptr) {
+      const double2 p = *g.scale_ptr;
+      scd = make_double2(scd.x * p.x - scd.y * p.y, scd.x * p.y + scd.y * p.x);
+    }
+    const float2 sc = make_float2((float)scd.x, (float)scd.y);
     for (int k0 = 0; k0 < g.K && ok; k0 += TC_BKC) {
       // ---- stage A: row r = thread, 16 complex along K
       {
         const int r = threadIdx.x;
         for (int kk = 0; kk < TC_BKC; ++kk) {
-          float2 a = load_el(g.A, t.ta, g.lda, t.opA, m0 + r, k0 + kk, t.M, g.K);
+          float2 a0 = load_el(g.A, t.ta, g.lda, t.opA, m0 + r, k0 + kk, t.M, g.K);
+          float2 a = make_float2(sc.x * a0.x - sc.y * a0.y, sc.x * a0.y + sc.y * a0.x);
           float2 hi = make_float2(to_tf32(a.x), to_tf32(a.y));
           *(float2*)(sA + canon_off(r, 2 * kk)) = hi;
           if (MODE == 1) {
@@ -279,6 +286,7 @@ __global__ void __launch_bounds__(128) k_gemm_tc(const GemmTask* __restrict__ ta
     }
     const int r = m0 + warp * 32 + lane;
     const bool have = !first;   // at least one MMA wrote the accumulator
+    const float fax = (float)alpha.x, fay = (float)alpha.y;
     for (int c0 = 0; c0 < 2 * ncols; c0 += 32) {
       float v[32];
       if (have) {
@@ -288,20 +296,23 @@ __global__ void __launch_bounds__(128) k_gemm_tc(const GemmTask* __restrict__ ta
         for (int i = 0; i < 32; ++i) v[i] = 0.f;
       }
       if (r < t.M) {
-        for (int j = 0; j < 16; ++j) {
-          const int c = n0 + c0 / 2 + j;
-          if (c >= n0 + ncols) break;
-          const double re = v[2 * j], im = v[2 * j + 1];
-          double ore = alpha.x * re - alpha.y * im, oim = alpha.x * im + alpha.y * re;
-          const size_t o = (size_t)r * t.ldc + c;
-          if (t.tc == 0) {
-            double2* C = (double2*)t.C;
-            if (t.beta) { ore += C[o].x; oim += C[o].y; }
-            C[o] = make_double2(ore, oim);
-          } else {
-            float2* C = (float2*)t.C;
-            if (t.beta) { ore += C[o].x; oim += C[o].y; }
-            C[o] = make_float2((float)ore, (float)oim);
+        const int jn = min(16, ncols - c0 / 2);
+        const size_t o0 = (size_t)r * t.ldc + n0 + c0 / 2;
+        if (t.tc == 0) {
+          double2* C = (double2*)t.C + o0;
+          for (int j = 0; j < jn; ++j) {
+            const double re = v[2 * j], im = v[2 * j + 1];
+            double ore = alpha.x * re - alpha.y * im, oim = alpha.x * im + alpha.y * re;
+            if (t.beta) { ore += C[j].x; oim += C[j].y; }
+            C[j] = make_double2(ore, oim);
+          }
+        } else {
+          float2* C = (float2*)t.C + o0;
+          for (int j = 0; j < jn; ++j) {
+            const float re = v[2 * j], im = v[2 * j + 1];
+            float ore = fax * re - fay * im, oim = fax * im + fay * re;
+            if (t.beta) { ore += C[j].x; oim += C[j].y; }
+            C[j] = make_float2(ore, oim);
           }
         }
       }
