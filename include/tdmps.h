@@ -160,6 +160,24 @@ int tdmps_sum(tdmps_ctx_t ctx, int n_terms, const tdmps_complex* coefs,
 /* <bra|ket> (the contraction of two chains of Eq. mps). */
 int tdmps_overlap(tdmps_ctx_t ctx, tdmps_mps_t bra, tdmps_mps_t ket, tdmps_complex* out);
 
+/* Overlap that allocates no device memory.  The paper has no counterpart:
+ * this is a service for callers that must not allocate device memory while
+ * they run -- applications whose caching allocator has to stay the only
+ * owner of device memory, or loops on a fixed memory budget where an
+ * allocation's latency or failure is not acceptable.  Same result as
+ * tdmps_overlap (FP64 chain contraction); the environments and intermediate
+ * blocks live in one file-scope device array of TDMPS_NOALLOC_SCRATCH_BYTES,
+ * which every GPU that loads the library holds until the process exits.
+ * The first call on a device resolves that array's device address
+ * (cudaGetSymbolAddress) with the device current; make that first call
+ * before any stream capture.  Task lists go through the staging ring that
+ * tdmps_create allocated.  All calls on a device share the array and each
+ * overwrites it, so calls that overlap on the GPU (several contexts or
+ * streams at once) race.  A pair whose environments do not fit returns
+ * TDMPS_ERR_INVALID_ARG before any work is enqueued on the GPU. */
+#define TDMPS_NOALLOC_SCRATCH_BYTES (16u << 20)
+int tdmps_overlap_noalloc(tdmps_ctx_t ctx, tdmps_mps_t bra, tdmps_mps_t ket, tdmps_complex* out);
+
 /* <bra|H|ket> with the MPO (Sec. 2.2.3, H_ij of Eq. krylov_evo). */
 int tdmps_expectation(tdmps_ctx_t ctx, tdmps_mpo_t mpo, tdmps_mps_t bra, tdmps_mps_t ket,
                       tdmps_complex* out);

@@ -70,6 +70,7 @@ _SIGS = {
     "tdmps_apply_H": (I, [P, P, P, Complex, I, D, I, ctypes.POINTER(P)]),
     "tdmps_sum": (I, [P, I, P, P, I, D, ctypes.POINTER(P)]),
     "tdmps_overlap": (I, [P, P, P, ctypes.POINTER(Complex)]),
+    "tdmps_overlap_noalloc": (I, [P, P, P, ctypes.POINTER(Complex)]),
     "tdmps_expectation": (I, [P, P, P, P, ctypes.POINTER(Complex)]),
     "tdmps_compress": (I, [P, P, I, D, ctypes.POINTER(D)]),
     "tdmps_rk4_step": (I, [P, P, P, D, I, D]),
@@ -294,6 +295,13 @@ def mps_sum(ctx, coefs, terms, D=64, eps=0.0) -> MPS:
 def overlap(ctx, bra, ket) -> complex:
     r = Complex()
     _check(lib().tdmps_overlap(ctx.h, bra.h, ket.h, ctypes.byref(r)), ctx)
+    return complex(r.re, r.im)
+
+
+def overlap_noalloc(ctx, bra, ket) -> complex:
+    """<bra|ket> without any device allocation (fixed device scratch)."""
+    r = Complex()
+    _check(lib().tdmps_overlap_noalloc(ctx.h, bra.h, ket.h, ctypes.byref(r)), ctx)
     return complex(r.re, r.im)
 
 

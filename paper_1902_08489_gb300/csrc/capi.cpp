@@ -270,6 +270,16 @@ int tdmps_overlap(tdmps_ctx_t ctx, tdmps_mps_t bra, tdmps_mps_t ket, tdmps_compl
   });
 }
 
+int tdmps_overlap_noalloc(tdmps_ctx_t ctx, tdmps_mps_t bra, tdmps_mps_t ket, tdmps_complex* out) {
+  if (!ctx) return TDMPS_ERR_INVALID_ARG;
+  return guard(ctx, [&] {
+    need(bra && ket && out, "NULL argument");
+    cplx v = overlap_noalloc(*ctx->c, bra->m, ket->m);
+    out->re = v.real();
+    out->im = v.imag();
+  });
+}
+
 int tdmps_expectation(tdmps_ctx_t ctx, tdmps_mpo_t mpo, tdmps_mps_t bra, tdmps_mps_t ket,
                       tdmps_complex* out) {
   if (!ctx) return TDMPS_ERR_INVALID_ARG;

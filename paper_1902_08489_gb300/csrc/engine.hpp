@@ -143,5 +143,7 @@ MPSd rk4_step(Context& c, const MPOd& H, const MPSd& psi, double dt, const FitOp
 MPSd krylov_step(Context& c, const MPOd& H, const MPSd& psi, double dt, int m, bool orth,
                  const FitOpts& o);
 void one_rdm(Context& c, const MPSd& psi, cplx* gamma);
+// overlap with all blocks in a fixed device array (noalloc.cu)
+cplx overlap_noalloc(Context& c, const MPSd& bra, const MPSd& ket);
 
 }  // namespace tdmps
