@@ -159,7 +159,9 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--precision", default="fp64")
+    ap.add_argument("--precision", default="tf32x3", choices=["fp64", "tf32", "tf32x3"])
+    ap.add_argument("--no-fp64-compare", action="store_true",
+                    help="skip the FP64 run of the same steps (error and FP64 steps/s)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--mode", default="krylov", choices=["krylov", "apply"],
@@ -231,8 +233,36 @@ def main():
         t = torch.tensor([ms], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
-    flops = st["gemm"]["flops"] + st["wstage"]["flops"]
+    flops = st["gemm"]["flops"] + st["gemm_fp64"]["flops"] + st["wstage"]["flops"]
     value = world * flops / (ms / 1e3) / 1e12
+    g_mixed = td.one_rdm(ctx, state)
+    e_mixed = td.expectation(ctx, mpo, state, state).real / td.overlap(ctx, state, state).real
+
+    # the same steps in FP64 from the same start: steps/s and observable error
+    fp64_cmp = None
+    if args.precision != "fp64" and not args.no_fp64_compare and args.mode == "krylov":
+        ctx.set_precision("fp64")
+        ref = td.mps_import(ctx, A, q)
+        for _ in range(args.warmup):
+            step(ref)
+        torch.cuda.synchronize()
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for _ in range(args.steps):
+            step(ref)
+        t1.record(stream)
+        torch.cuda.synchronize()
+        ms64 = t0.elapsed_time(t1)
+        g64 = td.one_rdm(ctx, ref)
+        e64 = td.expectation(ctx, mpo, ref, ref).real / td.overlap(ctx, ref, ref).real
+        ctx.set_precision(args.precision)
+        fp64_cmp = {"steps_per_s_fp64": 1e3 * args.steps / ms64,
+                    "speedup_vs_fp64": ms64 / ms,
+                    "after_steps": args.warmup + args.steps,
+                    "max_abs_err_one_rdm": float(np.abs(g_mixed - g64).max()),
+                    "abs_err_energy": float(abs(e_mixed - e64)),
+                    "ref_energy": float(e64)}
 
     # end-to-end through the public API with host buffers: import the state
     # from host memory, one Krylov step, read the 1-RDM back
@@ -258,8 +288,8 @@ def main():
     top = max(st, key=lambda k: st[k]["ms"])
     ks = st[top]
     per_launch_s = ks["ms"] / max(1, ks["launches"]) / 1e3
-    if top == "gemm":
-        if args.precision == "fp64":
+    if top in ("gemm", "gemm_fp64"):
+        if top == "gemm_fp64":
             peak, src = bf16 * 1.25 / 2250.0, "measured bf16 x nominal FP64/bf16 (1.25/2250)"
             kern, bound = "k_gemm (FP64 grouped complex block GEMM)", "alu"
         else:
@@ -274,7 +304,7 @@ def main():
                 "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None, "peak_source": src}
     else:
         achieved = ks["bytes"] / max(1, ks["launches"]) / per_launch_s / 1e9
-        roof = {"kernel": {"wstage": "k_wstage", "qr": "k_qr_warp", "svd": "k_svd",
+        roof = {"kernel": {"wstage": "k_wstage", "qr": "k_qr", "svd": "k_svd",
                            "other": "k_copy/k_scatter"}[top],
                 "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                 "frac": achieved / hbm, "traffic": None, "peak_source": "measured hbm_gbs"}
@@ -292,6 +322,7 @@ def main():
                    "l2": "inputs larger than L2 (Krylov basis + environments, several GB)",
                    "parallelism": "replicas" if world > 1 else "single"},
         "steps_per_s": 1e3 * args.steps / ms,
+        "vs_fp64": fp64_cmp,
         "gpu_launches": int(sum(v["launches"] for v in st.values())),
         "kernel_stats": {k: {"launches": v["launches"], "ms": round(v["ms"], 3),
                              "gflop": round(v["flops"] / 1e9, 3), "gb": round(v["bytes"] / 1e9, 3)}

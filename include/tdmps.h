@@ -56,11 +56,12 @@ enum {
   TDMPS_ERR_NUMERIC = -8          /* an iterative kernel did not converge    */
 };
 
-/* Arithmetic of the fit contractions (environments, local matvecs, sums).
- * Factorisations (QR, SVD), the Krylov algebra, the Krylov inner products
- * <phi_i|phi_j> and <phi_i|H|phi_j> (Gram-Schmidt coefficients), and the
- * observables (tdmps_overlap, tdmps_expectation, tdmps_one_rdm) always
- * contract in FP64. */
+/* Arithmetic of the fit contractions (environments, local matvecs, sums) and
+ * of the Krylov inner products <phi_i|phi_j>, <phi_i|H|phi_j> (unless
+ * tdmps_set_krylov_fp64 asks for FP64).  Factorisations (QR, SVD), the
+ * Krylov matrices and their exponential, the centre-site norms and the
+ * observables (tdmps_overlap, tdmps_expectation, tdmps_one_rdm) are always
+ * FP64. */
 enum {
   TDMPS_FP64 = 0,   /* complex FP64 everywhere                               */
   TDMPS_TF32 = 1,   /* TF32 tensor-core products, FP32 accumulation          */
@@ -91,6 +92,12 @@ int tdmps_set_precision(tdmps_ctx_t ctx, int precision);
  * moves, bond dimensions fixed).  Defaults: 2 and 2.  Errors: INVALID_ARG if
  * either is negative or both are 0. */
 int tdmps_set_schedule(tdmps_ctx_t ctx, int n_two_site, int n_one_site);
+
+/* Krylov inner products (Gram-Schmidt coefficients and the N, H matrices of
+ * Eq. krylov_evo) contracted in FP64 (on != 0) or in the context precision
+ * (on == 0, the default).  The matrices are accumulated and processed in
+ * FP64 either way. */
+int tdmps_set_krylov_fp64(tdmps_ctx_t ctx, int on);
 
 /* ------------------------------------------------------------------- MPO */
 
@@ -214,12 +221,14 @@ int tdmps_one_rdm(tdmps_ctx_t ctx, tdmps_mps_t psi, tdmps_complex* gamma);
  * algorithmic work of every launch (block-sparse FLOPs / bytes, padding
  * excluded).  Classes: see TDMPS_KSTAT_*. */
 enum {
-  TDMPS_KSTAT_GEMM = 0,     /* block contractions (environments, matvecs)  */
-  TDMPS_KSTAT_WSTAGE = 1,   /* sparse MPO-tensor application                */
+  TDMPS_KSTAT_GEMM = 0,      /* block contractions on the tensor cores (TF32 modes) */
+  TDMPS_KSTAT_WSTAGE = 1,    /* sparse MPO-tensor application                       */
   TDMPS_KSTAT_QR = 2,
   TDMPS_KSTAT_SVD = 3,
   TDMPS_KSTAT_OTHER = 4,
-  TDMPS_KSTAT_COUNT = 5
+  TDMPS_KSTAT_GEMM_FP64 = 5, /* FP64 block contractions (FP64 mode, inner products,
+                                observables, gauge moves)                          */
+  TDMPS_KSTAT_COUNT = 6
 };
 typedef struct {
   int64_t launches;

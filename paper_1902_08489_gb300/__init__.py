@@ -23,7 +23,7 @@ HEADER = os.path.join(os.path.dirname(_HERE), "include", "tdmps.h")
 
 FP64, TF32, TF32X3, BF16 = 0, 1, 2, 3
 PRECISION = {"fp64": FP64, "tf32": TF32, "tf32x3": TF32X3, "bf16": BF16}
-KSTAT = {"gemm": 0, "wstage": 1, "qr": 2, "svd": 3, "other": 4}
+KSTAT = {"gemm": 0, "wstage": 1, "qr": 2, "svd": 3, "other": 4, "gemm_fp64": 5}
 ERRORS = {-1: "INVALID_ARG", -2: "SECTOR", -3: "KRYLOV_SINGULAR", -4: "NONFINITE",
           -5: "CUDA", -6: "OOM", -7: "ZERO_STATE", -8: "NUMERIC"}
 
@@ -56,6 +56,7 @@ _SIGS = {
     "tdmps_create_error": (ctypes.c_char_p, []),
     "tdmps_set_precision": (I, [P, I]),
     "tdmps_set_schedule": (I, [P, I, I]),
+    "tdmps_set_krylov_fp64": (I, [P, I]),
     "tdmps_build_mpo": (I, [P, P, P, I, I, D, ctypes.POINTER(P)]),
     "tdmps_mpo_info": (I, [P, P, ctypes.POINTER(I64)]),
     "tdmps_mpo_elements": (I, [P, I, ctypes.POINTER(I64), P, P, P, P, P]),
@@ -151,6 +152,9 @@ class Context:
 
     def set_schedule(self, n_two_site: int, n_one_site: int):
         _check(lib().tdmps_set_schedule(self.h, n_two_site, n_one_site), self)
+
+    def set_krylov_fp64(self, on: bool = True):
+        _check(lib().tdmps_set_krylov_fp64(self.h, 1 if on else 0), self)
 
     # statistics
     def stats_enable(self, on=True):

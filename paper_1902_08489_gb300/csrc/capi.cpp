@@ -117,6 +117,12 @@ int tdmps_set_schedule(tdmps_ctx_t ctx, int n_two_site, int n_one_site) {
   });
 }
 
+int tdmps_set_krylov_fp64(tdmps_ctx_t ctx, int on) {
+  if (!ctx) return TDMPS_ERR_INVALID_ARG;
+  ctx->c->krylov_fp64 = on != 0;
+  return TDMPS_OK;
+}
+
 int tdmps_build_mpo(tdmps_ctx_t ctx, const double* h, const double* eri, int L, int n_elec,
                     double e0, tdmps_mpo_t* out) {
   return guard(ctx, [&] {

@@ -314,27 +314,42 @@ struct GemmBatch {
     const int bn = fp64 ? 32 : tc_tile_n();
     std::vector<int> tile_task;
     std::vector<GemmTask> tk;
+    std::vector<ZeroRegion> zero;
     for (auto& t : tasks) {
       if (t.M <= 0 || t.N <= 0) continue;
       t.tiles_m = (t.M + bm - 1) / bm;
       int tn = (t.N + bn - 1) / bn;
+      // long K runs are shared by several CTAs (>= 8 K chunks each) that
+      // accumulate atomically into a zeroed output
+      {
+        const int kc = fp64 ? 8 : tc_stage_k();
+        long long stages = 0;
+        for (int e = t.term_begin; e < t.term_end; ++e) stages += (terms[e].K + kc - 1) / kc;
+        t.splits = (int)std::min<long long>(64, std::max<long long>(1, stages / 8));
+        if (t.splits > 1 && !t.beta) {
+          if (t.ldc != t.N) throw Error(TDMPS_ERR_INVALID_ARG, "split-K output must be contiguous");
+          zero.push_back({t.C, (size_t)t.M * t.N * (t.tc ? sizeof(float2) : sizeof(double2))});
+        }
+      }
       t.tile_base = (int)tile_task.size();
       int id = (int)tk.size();
       tk.push_back(t);
-      for (int q = 0; q < t.tiles_m * tn; ++q) tile_task.push_back(id);
+      for (int q = 0; q < t.tiles_m * tn * t.splits; ++q) tile_task.push_back(id);
     }
     if (tile_task.empty()) return;
     const GemmTask* dt = c.stage(tk);
     const GemmTerm* dm = terms.empty() ? nullptr : c.stage(terms);
     const int* dtt = c.stage(tile_task);
     cudaEvent_t ev;
-    c.kbegin(TDMPS_KSTAT_GEMM, &ev);
+    const int kind = fp64 ? TDMPS_KSTAT_GEMM_FP64 : TDMPS_KSTAT_GEMM;
+    c.kbegin(kind, &ev);
+    if (!zero.empty()) launch_zero_regions(c.stage(zero), (int)zero.size(), c.st);
     if (fp64)
       launch_gemm(dt, (int)tk.size(), dm, dtt, (int)tile_task.size(), c.st);
     else
       launch_gemm_tc(dt, dm, dtt, (int)tile_task.size(), c.precision == TDMPS_TF32X3 ? 1 : 0,
                      c.tc_err(), c.st);
-    c.kend(TDMPS_KSTAT_GEMM, ev, flops, bytes);
+    c.kend(kind, ev, flops, bytes);
   }
 };
 
@@ -736,26 +751,15 @@ void run_copy(Context& c, const std::vector<CopyTask>& t, int to_work) {
 void run_qr(Context& c, FactWork& fw) {
   if (fw.tasks.empty()) return;
   double fl = 0.0;
-  std::vector<int> small, big;
-  size_t smem = 0;
-  for (size_t i = 0; i < fw.tasks.size(); ++i) {
-    const FactTask& t = fw.tasks[i];
+  for (auto& t : fw.tasks) {
     if (t.m > QR_MAX_ROWS || t.n > QR_MAX_COLS)
       throw Error(TDMPS_ERR_INVALID_ARG, "QR block exceeds the supported size");
     fl += 16.0 * t.m * t.n * t.n;
-    size_t b = ((size_t)t.m * t.n + (size_t)t.n * t.n) * sizeof(double2);
-    if (b <= (size_t)qr_warp_max_bytes()) { small.push_back((int)i); smem = std::max(smem, b); }
-    else big.push_back((int)i);
   }
   const FactTask* d = c.stage(fw.tasks);
   cudaEvent_t ev;
   c.kbegin(TDMPS_KSTAT_QR, &ev);
-  if (!small.empty()) launch_qr_warp(d, c.stage(small), (int)small.size(), smem, c.st);
-  if (!big.empty()) {
-    std::vector<FactTask> bt;
-    for (int i : big) bt.push_back(fw.tasks[i]);
-    launch_qr(c.stage(bt), (int)bt.size(), c.st);
-  }
+  launch_qr(d, (int)fw.tasks.size(), c.st);
   c.kend(TDMPS_KSTAT_QR, ev, fl, 0.0);
 }
 
@@ -982,7 +986,36 @@ static SplitResult svd_split(Context& c, const SiteT& Th, const RowGroups& rows,
   for (size_t i = 0; i < qs.size(); ++i)
     launch_zero(fw.tasks[i].A, (size_t)shapes[i].first * shapes[i].second, c.st);
   run_copy(c, g, 1);
-  run_svd(c, fw);
+  // QR-preconditioned one-sided Jacobi: M = Q R, Jacobi on W = R^H gives
+  // W J = U_w S, hence M = (Q J) S U_w^H; far fewer sweeps than Jacobi on M
+  run_qr(c, fw);
+  std::vector<std::pair<int, int>> sq;
+  for (auto& sh : shapes) sq.push_back({sh.second, sh.second});
+  FactWork fj = fact_alloc(c, sq);
+  {
+    const FactTask* ds = c.stage(fw.tasks);
+    const FactTask* dd = c.stage(fj.tasks);
+    launch_adjoint(ds, dd, (int)fw.tasks.size(), c.st);
+  }
+  run_svd(c, fj);
+  // U = Q J  (column-major m x n), computed as U^T = J^T Q^T in row-major terms
+  DevPtr ubuf;
+  std::vector<double2*> uptr(qs.size());
+  {
+    size_t tot = 0;
+    for (auto& sh : shapes) tot += (size_t)sh.first * sh.second;
+    ubuf = dev_alloc(std::max<size_t>(tot, 1) * sizeof(double2), c.st);
+    size_t off = 0;
+    GemmBatch gb(c, true);
+    for (size_t i = 0; i < qs.size(); ++i) {
+      const int m = shapes[i].first, n = shapes[i].second;
+      uptr[i] = (double2*)ubuf->p + off;
+      off += (size_t)m * n;
+      gb.task(uptr[i], 0, n, m, m, OP_N, 0, OP_N, 0, false, 1.0);
+      gb.term(fj.tasks[i].V, n, fw.tasks[i].A, m, n);
+    }
+    gb.run();
+  }
   // truncation over all singular values of the bond
   std::vector<int> secid;
   int nv = 0;
@@ -991,7 +1024,7 @@ static SplitResult svd_split(Context& c, const SiteT& Th, const RowGroups& rows,
   DevPtr svals = dev_alloc(sizeof(double) * std::max(1, ntot) * 2 + 64, c.st);
   DevPtr sids = dev_alloc(sizeof(int) * std::max(1, ntot) * 2 + 64, c.st);
   for (size_t i = 0; i < qs.size(); ++i) {
-    TD_CHECK_CUDA(cudaMemcpyAsync((double*)svals->p + nv, fw.tasks[i].s,
+    TD_CHECK_CUDA(cudaMemcpyAsync((double*)svals->p + nv, fj.tasks[i].s,
                                   sizeof(double) * shapes[i].second, cudaMemcpyDeviceToDevice, c.st));
     for (int k = 0; k < shapes[i].second; ++k) secid.push_back((int)i);
     nv += shapes[i].second;
@@ -1031,9 +1064,13 @@ static SplitResult svd_split(Context& c, const SiteT& Th, const RowGroups& rows,
     const QN& Q = qs[i];
     int mid = res.mid.find(Q);
     const FactTask& ft = fw.tasks[i];
-    const double2* usrc = trans[i] ? ft.V : ft.A;
+    // left factor Q J (m x n, ld m) and right factor U_w (n x n, ld n) of the
+    // work matrix; the work matrix is M or M^H
+    const double2* lf = uptr[i];
+    const double2* rf = fj.tasks[i].A;
+    const double2* usrc = trans[i] ? rf : lf;
     int ulds = trans[i] ? ft.n : ft.m;
-    const double2* vsrc = trans[i] ? ft.A : ft.V;
+    const double2* vsrc = trans[i] ? lf : rf;
     int vlds = trans[i] ? ft.m : ft.n;
     for (auto& rm : rmem[Q]) {
       int r = rm.first;
@@ -1041,13 +1078,13 @@ static SplitResult svd_split(Context& c, const SiteT& Th, const RowGroups& rows,
       if (rows.sig[r] < 0) ab = res.A.block_of(rows.sa[r], 0);
       if (ab < 0 || res.A.blocks[ab].sb != mid) continue;
       ss.push_back({res.A.ptr(ab), rows.d[r], k, k, usrc, ulds, rm.second, 0, 0,
-                    absorb_right ? 0 : 1, ft.s});
+                    absorb_right ? 0 : 1, fj.tasks[i].s});
     }
     for (auto& cm : cmem[Q]) {
       int bb = res.B.block_of(mid, cm[0]);
       if (bb < 0 || res.B.blocks[bb].sb != cm[1]) continue;
       ss.push_back({res.B.ptr(bb), k, right.d[cm[1]], right.d[cm[1]], vsrc, vlds, cm[2], 0, 1,
-                    absorb_right ? 2 : 0, ft.s});
+                    absorb_right ? 2 : 0, fj.tasks[i].s});
     }
   }
   if (!ss.empty()) {
@@ -1275,18 +1312,19 @@ namespace {
 struct Fp64Scope {
   Context& c;
   int saved;
-  explicit Fp64Scope(Context& ctx) : c(ctx), saved(ctx.precision) { c.precision = TDMPS_FP64; }
+  explicit Fp64Scope(Context& ctx, bool on = true) : c(ctx), saved(ctx.precision) {
+    if (on) c.precision = TDMPS_FP64;
+  }
   ~Fp64Scope() { c.precision = saved; }
 };
 }  // namespace
 
-// <bra_p| O |ket_p> for many pairs, one launch per stage and site for all;
-// FP64 contractions.
+// <bra_p| O |ket_p> for many pairs, one launch per stage and site for all.
 void sandwich_batch(Context& c, const MPOd* mpo,
                     const std::vector<std::pair<const MPSd*, const MPSd*>>& pairs,
-                    const std::vector<double2*>& outs) {
+                    const std::vector<double2*>& outs, bool fp64) {
   if (pairs.empty()) return;
-  Fp64Scope fp64(c);
+  Fp64Scope scope(c, fp64);
   const int L = pairs[0].first->L;
   for (auto& p : pairs) check_same_space(*p.first, *p.second);
   const MPOd& m = mpo ? *mpo : c.identity_mpo(L);
@@ -1434,8 +1472,8 @@ MPSd krylov_step(Context& c, const MPOd& H, const MPSd& psi, double dt, int m, b
         haveH[i * m + j] = 1;
       }
     }
-    sandwich_batch(c, nullptr, pn, on);
-    sandwich_batch(c, &H, ph, oh);
+    sandwich_batch(c, nullptr, pn, on, c.krylov_fp64);
+    sandwich_batch(c, &H, ph, oh, c.krylov_fp64);
   };
   for (int k = 0; k + 1 < m; ++k) {
     MPSd u = fit(c, {{&phi[k], &H, 1.0}}, phi[k], o);
@@ -1452,8 +1490,8 @@ MPSd krylov_step(Context& c, const MPOd& H, const MPSd& psi, double dt, int m, b
           if (!haveH[j * m + k]) { ph.push_back({&phi[j], &phi[k]}); oh.push_back(Hd + j * m + k); haveH[j * m + k] = 1; }
           if (!haveN[j * m + j]) { pn.push_back({&phi[j], &phi[j]}); on.push_back(Nd + j * m + j); haveN[j * m + j] = 1; }
         }
-        sandwich_batch(c, &H, ph, oh);
-        sandwich_batch(c, nullptr, pn, on);
+        sandwich_batch(c, &H, ph, oh, c.krylov_fp64);
+        sandwich_batch(c, nullptr, pn, on, c.krylov_fp64);
       }
       DevPtr cj = dev_alloc(sizeof(double2) * (k + 1), c.st);
       std::vector<FitTerm> terms;

@@ -25,6 +25,7 @@ struct Context {
   cudaStream_t st = nullptr;
   int precision = TDMPS_FP64;
   int n_two_site = 2, n_one_site = 2;
+  bool krylov_fp64 = false;   // Krylov inner products in FP64 regardless of precision
   std::string err;
   // staging ring for task lists
   char* h_ring = nullptr;
@@ -131,6 +132,11 @@ struct FitOpts {
 };
 MPSd fit(Context& c, const std::vector<FitTerm>& terms, const MPSd& guess, const FitOpts& o);
 
+// <bra_p| O |ket_p> for many pairs into device scalars; FP64 contractions
+// unless fp64 == false (then the context precision)
+void sandwich_batch(Context& c, const MPOd* mpo,
+                    const std::vector<std::pair<const MPSd*, const MPSd*>>& pairs,
+                    const std::vector<double2*>& outs, bool fp64 = true);
 // <bra| O |ket> into a device scalar (O = mpo or identity)
 void sandwich_dev(Context& c, const MPOd* mpo, const MPSd& bra, const MPSd& ket, double2* out);
 cplx sandwich(Context& c, const MPOd* mpo, const MPSd& bra, const MPSd& ket);

@@ -58,17 +58,30 @@ __global__ void __launch_bounds__(256) k_gemm(const GemmTask* __restrict__ tasks
   const int ti = tile_task[blockIdx.x];
   const GemmTask t = tasks[ti];
   const int local = blockIdx.x - t.tile_base;
-  const int m0 = (local % t.tiles_m) * GT;
-  const int n0 = (local / t.tiles_m) * GT;
+  const int split = local % t.splits;
+  const int rest = local / t.splits;
+  const int m0 = (rest % t.tiles_m) * GT;
+  const int n0 = (rest / t.tiles_m) * GT;
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   double2 acc[2][2];
   for (int i = 0; i < 2; ++i)
     for (int j = 0; j < 2; ++j) acc[i][j] = make_double2(0.0, 0.0);
-  for (int e = t.term_begin; e < t.term_end; ++e) {
+  // this split's share of the task's K chunks (GK each, over all terms)
+  int S = 0;
+  for (int e = t.term_begin; e < t.term_end; ++e) S += (terms[e].K + GK - 1) / GK;
+  const int lo = (int)((long long)split * S / t.splits);
+  const int hi = (int)((long long)(split + 1) * S / t.splits);
+  int idx = 0;
+  for (int e = t.term_begin; e < t.term_end && idx < hi; ++e) {
     const GemmTerm g = terms[e];
+    const int nk = (g.K + GK - 1) / GK;
+    if (idx + nk <= lo) { idx += nk; continue; }
     double2 sc = g.scale;
     if (g.scale_ptr) sc = cmul(sc, *g.scale_ptr);
-    for (int k0 = 0; k0 < g.K; k0 += GK) {
+    const int c0 = lo > idx ? lo - idx : 0;
+    const int c1 = hi - idx < nk ? hi - idx : nk;
+    for (int ch = c0; ch < c1; ++ch) {
+      const int k0 = ch * GK;
       {
         int i = threadIdx.x >> 3, k = threadIdx.x & 7;      // A tile: 32 x 8
         As[k][i] = cmul(sc, load_op((const double2*)g.A, g.lda, t.opA, m0 + i, k0 + k, t.M, g.K));
@@ -87,6 +100,7 @@ __global__ void __launch_bounds__(256) k_gemm(const GemmTask* __restrict__ tasks
       }
       __syncthreads();
     }
+    idx += nk;
   }
   double2 alpha = t.alpha;
   if (t.alpha_ptr) alpha = cmul(alpha, *t.alpha_ptr);
@@ -97,8 +111,13 @@ __global__ void __launch_bounds__(256) k_gemm(const GemmTask* __restrict__ tasks
       if (r < t.M && c < t.N) {
         double2* p = (double2*)t.C + (size_t)r * t.ldc + c;
         double2 v = cmul(alpha, acc[i][j]);
-        if (t.beta) v = cadd(v, *p);
-        *p = v;
+        if (t.splits > 1) {
+          atomicAdd(&p->x, v.x);
+          atomicAdd(&p->y, v.y);
+        } else {
+          if (t.beta) v = cadd(v, *p);
+          *p = v;
+        }
       }
     }
 }
@@ -250,6 +269,21 @@ __global__ void k_scatter(const ScatterTask* __restrict__ tasks) {
 void launch_scatter(const ScatterTask* d_tasks, int ntasks, cudaStream_t st) {
   if (ntasks <= 0) return;
   k_scatter<<<ntasks, 256, 0, st>>>(d_tasks);
+}
+
+// dst = src^H for square column-major n x n matrices (one CTA per task)
+__global__ void k_adjoint(const FactTask* __restrict__ src, const FactTask* __restrict__ dst) {
+  const FactTask a = src[blockIdx.x], b = dst[blockIdx.x];
+  const int n = b.n;
+  for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+    const int i = e % n, j = e / n;
+    b.A[(size_t)j * n + i] = cconj(a.V[(size_t)i * n + j]);
+  }
+}
+
+void launch_adjoint(const FactTask* d_src, const FactTask* d_dst, int n, cudaStream_t st) {
+  if (n <= 0) return;
+  k_adjoint<<<n, 256, 0, st>>>(d_src, d_dst);
 }
 
 __global__ void k_zero(double2* p, size_t n) {
@@ -567,68 +601,6 @@ __global__ void __launch_bounds__(QR_THREADS) k_qr(const FactTask* __restrict__ 
   }
 }
 
-// Warp-sized variant for the small sector matrices of a bond (m*n*16 bytes
-// <= QRW_SMEM): one warp per matrix, no block barriers; Gram-Schmidt with one
-// re-orthogonalisation pass, each projection applied as soon as its inner
-// product is known (modified Gram-Schmidt order).  Same dependency rule and
-// outputs as k_qr.
-constexpr int QRW_SMEM = 96 * 1024;
-
-__global__ void __launch_bounds__(32) k_qr_warp(const FactTask* __restrict__ tasks,
-                                                const int* __restrict__ ids) {
-  extern __shared__ double2 shw[];
-  const FactTask t = tasks[ids[blockIdx.x]];
-  const int m = t.m, n = t.n, kmax = m < n ? m : n;
-  const int lane = threadIdx.x;
-  double2* A = shw;                       // m x n, column-major
-  double2* R = shw + (size_t)m * n;       // n x n, leading dimension n
-  for (int e = lane; e < m * n; e += 32) A[e] = t.A[e];
-  for (int e = lane; e < n * n; e += 32) R[e] = make_double2(0.0, 0.0);
-  __syncwarp();
-  double maxn = 0.0;
-  for (int j = 0; j < n; ++j) {
-    double s2 = 0.0;
-    for (int i = lane; i < m; i += 32) s2 += cabs2(A[(size_t)j * m + i]);
-    maxn = fmax(maxn, sqrt(warp_sum(s2)));
-  }
-  const double tol = 1e-12 * maxn;
-  int nq = 0;
-  for (int j = 0; j < n; ++j) {
-    double2* v = A + (size_t)j * m;
-    for (int pass = 0; pass < 2; ++pass) {
-      for (int cc = 0; cc < nq; ++cc) {
-        const double2* qc = A + (size_t)cc * m;
-        double re = 0.0, im = 0.0;
-        for (int i = lane; i < m; i += 32) {
-          double2 a = qc[i], b = v[i];
-          re += a.x * b.x + a.y * b.y;
-          im += a.x * b.y - a.y * b.x;
-        }
-        const double2 c = make_double2(warp_sum(re), warp_sum(im));
-        for (int i = lane; i < m; i += 32) v[i] = csub(v[i], cmul(c, qc[i]));
-        if (lane == 0) R[(size_t)j * n + cc] = cadd(R[(size_t)j * n + cc], c);
-        __syncwarp();
-      }
-    }
-    double s2 = 0.0;
-    for (int i = lane; i < m; i += 32) s2 += cabs2(v[i]);
-    const double nrm = sqrt(warp_sum(s2));
-    if (nrm > tol && nq < kmax) {
-      const double inv = 1.0 / nrm;
-      double2* q = A + (size_t)nq * m;
-      for (int i = lane; i < m; i += 32) q[i] = cscale(v[i], inv);   // nq <= j: in place or earlier
-      if (lane == 0) R[(size_t)j * n + nq] = make_double2(nrm, 0.0);
-      ++nq;
-    }
-    __syncwarp();
-  }
-  for (int cc = nq; cc < kmax; ++cc)
-    for (int i = lane; i < m; i += 32) A[(size_t)cc * m + i] = make_double2(0.0, 0.0);
-  __syncwarp();
-  for (int e = lane; e < m * kmax; e += 32) t.A[e] = A[e];
-  for (int e = lane; e < n * n; e += 32) t.V[e] = R[e];
-}
-
 void launch_qr(const FactTask* d_tasks, int ntasks, cudaStream_t st) {
   if (ntasks <= 0) return;
   static bool attr = false;
@@ -639,17 +611,7 @@ void launch_qr(const FactTask* d_tasks, int ntasks, cudaStream_t st) {
   k_qr<<<ntasks, QR_THREADS, QR_SMEM, st>>>(d_tasks);
 }
 
-void launch_qr_warp(const FactTask* d_tasks, const int* d_ids, int n, size_t smem, cudaStream_t st) {
-  if (n <= 0) return;
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_qr_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, QRW_SMEM);
-    attr = true;
-  }
-  k_qr_warp<<<n, 32, smem, st>>>(d_tasks, d_ids);
-}
 
-int qr_warp_max_bytes() { return QRW_SMEM; }
 
 // ------------------------------------------------------------------ truncation rule
 

@@ -32,7 +32,8 @@ struct GemmTask {
   int opA, opB, beta;
   int term_begin, term_end;
   int tiles_m, tile_base;
-  int ta, tb, tc, pad;   // element types of A, B, C: 0 double2, 1 float2 (tensor-core path)
+  int ta, tb, tc;        // element types of A, B, C: 0 double2, 1 float2 (tensor-core path)
+  int splits;            // tensor-core path: CTAs sharing the K range (atomic accumulation)
 };
 
 // Sparse MPO-tensor application.  Output block Y[r][w][c] (rows r, W_out
@@ -88,6 +89,12 @@ void launch_gemm_tc(const GemmTask* d_tasks, const GemmTerm* d_terms, const int*
                     int ntiles, int mode, int* d_err, cudaStream_t st);
 int tc_tile_m();
 int tc_tile_n();
+int tc_stage_k();   // complex K per staged tile
+struct ZeroRegion {
+  void* p;
+  size_t bytes;   // multiple of 4
+};
+void launch_zero_regions(const ZeroRegion* d_regions, int n, cudaStream_t st);
 // out (double2) = in (element type et), n elements
 void launch_to_double(const void* in, int et, double2* out, size_t n, cudaStream_t st);
 void launch_fill_one(void* p, int et, cudaStream_t st);
@@ -98,9 +105,8 @@ void launch_zero(double2* p, size_t n, cudaStream_t st);
 void launch_svd(const FactTask* d_tasks, int ntasks, int* d_status, cudaStream_t st,
                 size_t max_bytes);
 void launch_qr(const FactTask* d_tasks, int ntasks, cudaStream_t st);
-// warp-per-matrix QR for the tasks listed in d_ids (m*n*16 <= qr_warp_max_bytes())
-void launch_qr_warp(const FactTask* d_tasks, const int* d_ids, int n, size_t smem, cudaStream_t st);
-int qr_warp_max_bytes();
+// dst[t].A (n x n) = src[t].V^H (the R factor of a QR), n = dst[t].n
+void launch_adjoint(const FactTask* d_src, const FactTask* d_dst, int n, cudaStream_t st);
 // truncation rule over nv singular values (grouped by sector, each sector
 // descending; sector id per value): writes kept count per sector and the
 // discarded / total weight to out_w[0..1].

@@ -29,15 +29,16 @@ namespace {
 
 constexpr int TC_BM = 128;        // rows per tile (TMEM lanes)
 constexpr int TC_BNC = 64;        // complex columns per tile
-constexpr int TC_BKC = 16;        // complex K per stage
-constexpr int TC_KR = 2 * TC_BKC; // real K per stage (32 tf32 = 4 MMA k-steps)
+constexpr int TC_BKC = 8;         // complex K per stage
+constexpr int TC_KR = 2 * TC_BKC; // real K per stage (16 tf32 = 2 MMA k-steps)
 constexpr int TC_NR = 2 * TC_BNC; // real N per tile
+constexpr int TC_THREADS = 256;
 constexpr int TC_TMEM_COLS = 128;
 constexpr uint32_t TC_SPIN_LIMIT = 1u << 22;
 
-// bytes of one staged operand tile (rows x 32 tf32)
-constexpr int TILE_A_BYTES = TC_BM * TC_KR * 4;   // 16 KB
-constexpr int TILE_B_BYTES = TC_NR * TC_KR * 4;   // 16 KB
+// bytes of one staged operand tile (rows x 16 tf32)
+constexpr int TILE_A_BYTES = TC_BM * TC_KR * 4;   // 8 KB
+constexpr int TILE_B_BYTES = TC_NR * TC_KR * 4;   // 8 KB
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -158,27 +159,28 @@ __device__ __forceinline__ float2 load_el(const void* P, int t, int ld, int op, 
 }
 
 template <int MODE>   // 0: TF32, 1: 3xTF32
-__global__ void __launch_bounds__(128) k_gemm_tc(const GemmTask* __restrict__ tasks,
-                                                 const GemmTerm* __restrict__ terms,
-                                                 const int* __restrict__ tile_task, int* err) {
+__global__ void __launch_bounds__(TC_THREADS) k_gemm_tc(const GemmTask* __restrict__ tasks,
+                                                        const GemmTerm* __restrict__ terms,
+                                                        const int* __restrict__ tile_task,
+                                                        int* err) {
   extern __shared__ __align__(1024) unsigned char sm[];
-  constexpr int NSPLIT = MODE == 0 ? 1 : 2;
-  unsigned char* sA = sm;                                   // NSPLIT tiles
-  unsigned char* sB = sm + NSPLIT * TILE_A_BYTES;           // NSPLIT tiles
-  __shared__ __align__(8) uint64_t mbar;
+  constexpr int NSPLIT = MODE == 0 ? 1 : 2;                 // operand tiles per stage (hi[, lo])
+  constexpr int BUF_BYTES = NSPLIT * (TILE_A_BYTES + TILE_B_BYTES);
+  __shared__ __align__(8) uint64_t mbar[2];
   __shared__ uint32_t tmem_base;
   __shared__ int abort_flag;
 
   const int ti = tile_task[blockIdx.x];
   const GemmTask t = tasks[ti];
   const int local = blockIdx.x - t.tile_base;
-  const int m0 = (local % t.tiles_m) * TC_BM;
-  const int n0 = (local / t.tiles_m) * TC_BNC;
+  const int split = local % t.splits;
+  const int rest = local / t.splits;
+  const int m0 = (rest % t.tiles_m) * TC_BM;
+  const int n0 = (rest / t.tiles_m) * TC_BNC;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int ncols = min(TC_BNC, t.N - n0);
   const int nreal = ((2 * ncols + 15) / 16) * 16;   // MMA N: multiple of 16
   const uint32_t idesc = make_idesc_tf32(nreal);
-  const uint32_t mb = smem_u32(&mbar);
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n"
@@ -188,7 +190,8 @@ __global__ void __launch_bounds__(128) k_gemm_tc(const GemmTask* __restrict__ ta
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
   }
   if (threadIdx.x == 0) {
-    mbar_init(mb, 1);
+    mbar_init(smem_u32(&mbar[0]), 1);
+    mbar_init(smem_u32(&mbar[1]), 1);
     abort_flag = 0;
   }
   tc_fence_before();
@@ -196,11 +199,35 @@ __global__ void __launch_bounds__(128) k_gemm_tc(const GemmTask* __restrict__ ta
   tc_fence_after();
   const uint32_t tmem = tmem_base;
 
-  uint32_t phase = 0;
-  uint32_t failed_phase = 0;
-  bool first = true;
+  // stages of this task: (term, k0) pairs of TC_BKC complex, this split's share
+  int S = 0;
+  for (int e = t.term_begin; e < t.term_end; ++e) S += (terms[e].K + TC_BKC - 1) / TC_BKC;
+  const int lo = (int)((long long)split * S / t.splits);
+  const int hi = (int)((long long)(split + 1) * S / t.splits);
+  int e = t.term_begin, k0 = 0;
+  {
+    int idx = 0;
+    while (e < t.term_end) {
+      const int nk = (terms[e].K + TC_BKC - 1) / TC_BKC;
+      if (idx + nk <= lo) { idx += nk; ++e; continue; }
+      k0 = (lo - idx) * TC_BKC;
+      break;
+    }
+  }
+  const int count = hi - lo;
+
+  uint32_t uses[2] = {0u, 0u};
   bool ok = true;
-  for (int e = t.term_begin; e < t.term_end && ok; ++e) {
+  for (int s = 0; s < count && ok; ++s) {
+    const int b = s & 1;
+    unsigned char* sA = sm + b * BUF_BYTES;
+    unsigned char* sB = sA + NSPLIT * TILE_A_BYTES;
+    if (uses[b] > 0) {   // the MMAs that last read this buffer must be done
+      if (!mbar_wait(smem_u32(&mbar[b]), (uses[b] - 1) & 1u)) {
+        if (lane == 0) atomicExch(err, 2);
+        abort_flag = 1;
+      }
+    }
     const GemmTerm g = terms[e];
     double2 scd = g.scale;
     if (g.scale_ptr) {
@@ -208,70 +235,80 @@ __global__ void __launch_bounds__(128) k_gemm_tc(const GemmTask* __restrict__ ta
       scd = make_double2(scd.x * p.x - scd.y * p.y, scd.x * p.y + scd.y * p.x);
     }
     const float2 sc = make_float2((float)scd.x, (float)scd.y);
-    for (int k0 = 0; k0 < g.K && ok; k0 += TC_BKC) {
-      // ---- stage A: row r = thread, 16 complex along K
-      {
-        const int r = threadIdx.x;
-        for (int kk = 0; kk < TC_BKC; ++kk) {
-          float2 a0 = load_el(g.A, t.ta, g.lda, t.opA, m0 + r, k0 + kk, t.M, g.K);
-          float2 a = make_float2(sc.x * a0.x - sc.y * a0.y, sc.x * a0.y + sc.y * a0.x);
-          float2 hi = make_float2(to_tf32(a.x), to_tf32(a.y));
-          *(float2*)(sA + canon_off(r, 2 * kk)) = hi;
-          if (MODE == 1) {
-            float2 lo = make_float2(to_tf32(a.x - hi.x), to_tf32(a.y - hi.y));
-            *(float2*)(sA + TILE_A_BYTES + canon_off(r, 2 * kk)) = lo;
-          }
-        }
-      }
-      // ---- stage B-tilde (K-major, rows = real N): thread -> column n, half of K
-      {
-        const int n = threadIdx.x & (TC_BNC - 1);
-        const int kh = threadIdx.x >> 6;   // 0 or 1
-        for (int j = 0; j < TC_BKC / 2; ++j) {
-          const int kk = kh * (TC_BKC / 2) + j;
-          float2 b = load_el(g.B, t.tb, g.ldb, t.opB, k0 + kk, n0 + n, g.K, t.N);
-          float2 hr = make_float2(to_tf32(b.x), to_tf32(-b.y));   // row 2n:   (br, -bi)
-          float2 hi2 = make_float2(to_tf32(b.y), to_tf32(b.x));   // row 2n+1: (bi,  br)
-          *(float2*)(sB + canon_off(2 * n, 2 * kk)) = hr;
-          *(float2*)(sB + canon_off(2 * n + 1, 2 * kk)) = hi2;
-          if (MODE == 1) {
-            float2 lr = make_float2(to_tf32(b.x - hr.x), to_tf32(-b.y - hr.y));
-            float2 li = make_float2(to_tf32(b.y - hi2.x), to_tf32(b.x - hi2.y));
-            *(float2*)(sB + TILE_B_BYTES + canon_off(2 * n, 2 * kk)) = lr;
-            *(float2*)(sB + TILE_B_BYTES + canon_off(2 * n + 1, 2 * kk)) = li;
-          }
-        }
-      }
-      fence_async_smem();
-      __syncthreads();
-      if (threadIdx.x == 0) {
-        tc_fence_after();
-        const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
+    // ---- stage A: 128 rows x 8 complex; thread -> row, 4 complex of K
+    {
+      const int r = threadIdx.x & (TC_BM - 1);
+      const int kq = (threadIdx.x >> 7) * (TC_BKC / 2);
 #pragma unroll
-        for (int s = 0; s < TC_KR / 8; ++s) {
-          const uint32_t off = s * 256;   // two core matrices along K per step
-          mma_tf32(tmem, make_desc(a0 + off), make_desc(b0 + off), idesc, first ? 0u : 1u);
-          first = false;
-          if (MODE == 1) {
-            mma_tf32(tmem, make_desc(a0 + off), make_desc(b0 + TILE_B_BYTES + off), idesc, 1u);
-            mma_tf32(tmem, make_desc(a0 + TILE_A_BYTES + off), make_desc(b0 + off), idesc, 1u);
-          }
+      for (int j = 0; j < TC_BKC / 2; ++j) {
+        const int kk = kq + j;
+        float2 a0 = load_el(g.A, t.ta, g.lda, t.opA, m0 + r, k0 + kk, t.M, g.K);
+        float2 a = make_float2(sc.x * a0.x - sc.y * a0.y, sc.x * a0.y + sc.y * a0.x);
+        float2 hi = make_float2(to_tf32(a.x), to_tf32(a.y));
+        *(float2*)(sA + canon_off(r, 2 * kk)) = hi;
+        if (MODE == 1) {
+          float2 lo2 = make_float2(to_tf32(a.x - hi.x), to_tf32(a.y - hi.y));
+          *(float2*)(sA + TILE_A_BYTES + canon_off(r, 2 * kk)) = lo2;
         }
-        mma_commit(mb);
       }
-      first = false;
-      // all threads wait for the MMAs (their smem reads) before restaging
-      if (!mbar_wait(mb, phase)) {
-        if (lane == 0) atomicExch(err, 2);
-        abort_flag = 1;
-        failed_phase = phase;
+    }
+    // ---- stage B-tilde (K-major, rows = real N): thread -> column n, 2 complex of K
+    {
+      const int n = threadIdx.x & (TC_BNC - 1);
+      const int kq = (threadIdx.x >> 6) * (TC_BKC / 4);
+#pragma unroll
+      for (int j = 0; j < TC_BKC / 4; ++j) {
+        const int kk = kq + j;
+        float2 bv = load_el(g.B, t.tb, g.ldb, t.opB, k0 + kk, n0 + n, g.K, t.N);
+        float2 hr = make_float2(to_tf32(bv.x), to_tf32(-bv.y));   // row 2n:   (br, -bi)
+        float2 hi2 = make_float2(to_tf32(bv.y), to_tf32(bv.x));   // row 2n+1: (bi,  br)
+        *(float2*)(sB + canon_off(2 * n, 2 * kk)) = hr;
+        *(float2*)(sB + canon_off(2 * n + 1, 2 * kk)) = hi2;
+        if (MODE == 1) {
+          float2 lr = make_float2(to_tf32(bv.x - hr.x), to_tf32(-bv.y - hr.y));
+          float2 li = make_float2(to_tf32(bv.y - hi2.x), to_tf32(bv.x - hi2.y));
+          *(float2*)(sB + TILE_B_BYTES + canon_off(2 * n, 2 * kk)) = lr;
+          *(float2*)(sB + TILE_B_BYTES + canon_off(2 * n + 1, 2 * kk)) = li;
+        }
       }
-      phase ^= 1u;
-      __syncthreads();
+    }
+    fence_async_smem();
+    __syncthreads();
+    if (abort_flag) { ok = false; break; }
+    if (threadIdx.x == 0) {
       tc_fence_after();
-      if (abort_flag) ok = false;
+      const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
+#pragma unroll
+      for (int q = 0; q < TC_KR / 8; ++q) {
+        const uint32_t off = q * 256;   // two core matrices along K per k-step
+        mma_tf32(tmem, make_desc(a0 + off), make_desc(b0 + off), idesc, (s > 0 || q > 0) ? 1u : 0u);
+        if (MODE == 1) {
+          mma_tf32(tmem, make_desc(a0 + off), make_desc(b0 + TILE_B_BYTES + off), idesc, 1u);
+          mma_tf32(tmem, make_desc(a0 + TILE_A_BYTES + off), make_desc(b0 + off), idesc, 1u);
+        }
+      }
+      mma_commit(smem_u32(&mbar[b]));
+    }
+    uses[b] += 1;
+    k0 += TC_BKC;
+    while (e < t.term_end && k0 >= terms[e].K) { ++e; k0 = 0; }
+  }
+  // the last commit covers every MMA issued before it
+  uint32_t failed_bar = 0, failed_phase = 0;
+  bool pending = false;
+  if (count > 0) {
+    const int b = (count - 1) & 1;
+    failed_bar = smem_u32(&mbar[b]);
+    failed_phase = (uses[b] - 1) & 1u;
+    pending = true;
+    if (ok && !mbar_wait(failed_bar, failed_phase)) {
+      if (lane == 0) atomicExch(err, 2);
+      ok = false;
     }
   }
+  __syncthreads();
+  tc_fence_after();
+  if (abort_flag) ok = false;
 
   if (ok) {
     double2 alpha = t.alpha;
@@ -284,18 +321,20 @@ __global__ void __launch_bounds__(128) k_gemm_tc(const GemmTask* __restrict__ ta
       double d = q.x * q.x + q.y * q.y;
       alpha = make_double2((alpha.x * q.x + alpha.y * q.y) / d, (alpha.y * q.x - alpha.x * q.y) / d);
     }
-    const int r = m0 + warp * 32 + lane;
-    const bool have = !first;   // at least one MMA wrote the accumulator
+    const bool atomic = t.splits > 1;
+    const int quad = warp & 3, chalf = warp >> 2;
+    const int r = m0 + quad * 32 + lane;
+    const bool have = count > 0;
     const float fax = (float)alpha.x, fay = (float)alpha.y;
-    for (int c0 = 0; c0 < 2 * ncols; c0 += 32) {
+    for (int c0 = 32 * chalf; c0 < 2 * ncols; c0 += 64) {
       float v[32];
       if (have) {
-        tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+        tmem_ld32(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)c0, v);
       } else {
 #pragma unroll
         for (int i = 0; i < 32; ++i) v[i] = 0.f;
       }
-      if (r < t.M) {
+      if (r < t.M && (have || !atomic)) {
         const int jn = min(16, ncols - c0 / 2);
         const size_t o0 = (size_t)r * t.ldc + n0 + c0 / 2;
         if (t.tc == 0) {
@@ -303,25 +342,34 @@ __global__ void __launch_bounds__(128) k_gemm_tc(const GemmTask* __restrict__ ta
           for (int j = 0; j < jn; ++j) {
             const double re = v[2 * j], im = v[2 * j + 1];
             double ore = alpha.x * re - alpha.y * im, oim = alpha.x * im + alpha.y * re;
-            if (t.beta) { ore += C[j].x; oim += C[j].y; }
-            C[j] = make_double2(ore, oim);
+            if (atomic) {
+              atomicAdd(&C[j].x, ore);
+              atomicAdd(&C[j].y, oim);
+            } else {
+              if (t.beta) { ore += C[j].x; oim += C[j].y; }
+              C[j] = make_double2(ore, oim);
+            }
           }
         } else {
           float2* C = (float2*)t.C + o0;
           for (int j = 0; j < jn; ++j) {
             const float re = v[2 * j], im = v[2 * j + 1];
             float ore = fax * re - fay * im, oim = fax * im + fay * re;
-            if (t.beta) { ore += C[j].x; oim += C[j].y; }
-            C[j] = make_float2(ore, oim);
+            if (atomic) {
+              atomicAdd(&C[j].x, ore);
+              atomicAdd(&C[j].y, oim);
+            } else {
+              if (t.beta) { ore += C[j].x; oim += C[j].y; }
+              C[j] = make_float2(ore, oim);
+            }
           }
         }
       }
     }
-  }
-  if (!ok) {
-    // give the MMAs of this CTA one more bounded chance to drain before the
+  } else if (pending) {
+    // give this CTA's MMAs one more bounded chance to drain before the
     // accumulator columns are released
-    mbar_wait(mb, failed_phase);
+    mbar_wait(failed_bar, failed_phase);
   }
   tc_fence_before();
   __syncthreads();
@@ -333,30 +381,44 @@ __global__ void __launch_bounds__(128) k_gemm_tc(const GemmTask* __restrict__ ta
   }
 }
 
+// zero a list of (pointer, bytes) regions (outputs of split-K tasks)
+__global__ void k_zero_regions(const ZeroRegion* __restrict__ r) {
+  const ZeroRegion z = r[blockIdx.x];
+  uint32_t* p = (uint32_t*)z.p;
+  const size_t n = z.bytes / 4;
+  for (size_t i = threadIdx.x; i < n; i += blockDim.x) p[i] = 0u;
+}
+
 }  // namespace
 
 void launch_gemm_tc(const GemmTask* d_tasks, const GemmTerm* d_terms, const int* d_tile_task,
                     int ntiles, int mode, int* d_err, cudaStream_t st) {
   if (ntiles <= 0) return;
   if (mode == 0) {
-    const int smem = TILE_A_BYTES + TILE_B_BYTES;
+    const int smem = 2 * (TILE_A_BYTES + TILE_B_BYTES);
     static bool attr = false;
     if (!attr) {
       cudaFuncSetAttribute(k_gemm_tc<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
       attr = true;
     }
-    k_gemm_tc<0><<<ntiles, 128, smem, st>>>(d_tasks, d_terms, d_tile_task, d_err);
+    k_gemm_tc<0><<<ntiles, TC_THREADS, smem, st>>>(d_tasks, d_terms, d_tile_task, d_err);
   } else {
-    const int smem = 2 * (TILE_A_BYTES + TILE_B_BYTES);
+    const int smem = 2 * 2 * (TILE_A_BYTES + TILE_B_BYTES);
     static bool attr = false;
     if (!attr) {
       cudaFuncSetAttribute(k_gemm_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
       attr = true;
     }
-    k_gemm_tc<1><<<ntiles, 128, smem, st>>>(d_tasks, d_terms, d_tile_task, d_err);
+    k_gemm_tc<1><<<ntiles, TC_THREADS, smem, st>>>(d_tasks, d_terms, d_tile_task, d_err);
   }
 }
 
+void launch_zero_regions(const ZeroRegion* d_regions, int n, cudaStream_t st) {
+  if (n <= 0) return;
+  k_zero_regions<<<n, 256, 0, st>>>(d_regions);
+}
+
+int tc_stage_k() { return TC_BKC; }
 int tc_tile_m() { return TC_BM; }
 int tc_tile_n() { return TC_BNC; }
 

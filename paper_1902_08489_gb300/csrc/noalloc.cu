@@ -156,6 +156,7 @@ cplx overlap_noalloc(Context& c, const MPSd& bra, const MPSd& ket) {
         GemmTask g = tasks[t];
         if (g.M <= 0 || g.N <= 0) continue;
         g.tiles_m = (g.M + 31) / 32;
+        g.splits = 1;
         int tn = (g.N + 31) / 32;
         g.tile_base = (int)tile_task.size();
         int id = (int)tk.size();

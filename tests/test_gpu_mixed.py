@@ -121,4 +121,5 @@ def test_krylov_trajectory_mixed_observables(td):
         ctx.close()
     assert np.abs(out["fp64"][0] - out["tf32x3"][0]).max() < 1e-5
     assert np.abs(out["fp64"][1] - out["tf32x3"][1]).max() < 3e-5
-    assert np.ptp(out["fp64"][1]) < 1e-10       # FP64 Krylov conserves the energy
+    # FP64 Krylov conserves the energy up to the truncation (eps = 1e-10 weight)
+    assert np.ptp(out["fp64"][1]) < 1e-8
