@@ -216,6 +216,63 @@ def two_rdm(psi: np.ndarray, dets: np.ndarray, L: int) -> np.ndarray:
     return G
 
 
+def transition_rdm(bra: np.ndarray, ket: np.ndarray, dets: np.ndarray, L: int) -> np.ndarray:
+    """T_ij = sum_s <bra| a+_{is} a_{js} |ket> for two vectors on the same
+    determinant list (the 1BRDM of Section 3.2 between two states)."""
+    n = len(dets)
+    g = np.zeros((L, L), dtype=np.complex128)
+    for i in range(L):
+        for j in range(L):
+            for s in range(2):
+                m, a = apply_op(dets, np.ones(n), 2 * j + s, False)
+                m, a = apply_op(m, a, 2 * i + s, True)
+                nz = a != 0.0
+                row = np.searchsorted(dets, m[nz])
+                g[i, j] += np.sum(np.conj(bra[row]) * a[nz] * ket[nz])
+    return g
+
+
+def apply_to_vector(psi: np.ndarray, dets: np.ndarray, out_dets: np.ndarray, mode: int,
+                    dagger: bool) -> np.ndarray:
+    """a_mode psi or a+_mode psi, expressed on the determinant list
+    ``out_dets`` of the target sector."""
+    m, a = apply_op(dets, np.asarray(psi, dtype=np.complex128), mode, dagger)
+    nz = a != 0.0
+    out = np.zeros(len(out_dets), dtype=np.complex128)
+    row = np.searchsorted(out_dets, m[nz])
+    np.add.at(out, row, a[nz])
+    return out
+
+
+def green_function(h: np.ndarray, eri: np.ndarray, psi0: np.ndarray, dets: np.ndarray, L: int,
+                   i: int, j: int, taus, e0: float = 0.0) -> np.ndarray:
+    """Spin-summed, normalised one-particle Green's function of Eq. (green_time)
+    for tau = t - t' >= 0 (hbar = 1):
+
+        G_ij(tau) = -i sum_s <psi0| a+_{is} exp(+i H tau) a_{js} |psi0>
+                       / sum_s <psi0| a+_{is} a_{js} |psi0>.
+
+    a_{js}|psi0> lives in the sector with one electron of spin s fewer; it is
+    propagated backwards in time there exactly (Eq. time_evo_opera with
+    t -> -tau) and projected on a_{is}|psi0>."""
+    na = int(np.bitwise_count(np.uint64(dets[0]) & np.uint64(0x5555555555555555)))
+    nb = int(np.bitwise_count(np.uint64(dets[0]) & np.uint64(0xAAAAAAAAAAAAAAAA)))
+    taus = np.atleast_1d(np.asarray(taus, dtype=float))
+    num = np.zeros(len(taus), dtype=np.complex128)
+    den = 0.0 + 0.0j
+    for s in range(2):
+        if (na, nb)[s] == 0:
+            continue
+        dm = basis(L, na - (s == 0), nb - (s == 1))
+        Hm = hamiltonian(h, eri, dm, e0)
+        chi_j = apply_to_vector(psi0, dets, dm, 2 * j + s, False)
+        chi_i = apply_to_vector(psi0, dets, dm, 2 * i + s, False)
+        den += np.vdot(chi_i, chi_j)
+        for t, tau in enumerate(taus):
+            num[t] += np.vdot(chi_i, exact_evolve(Hm, chi_j, -tau))
+    return -1j * num / den
+
+
 def energy(H: np.ndarray, psi: np.ndarray) -> float:
     return float(np.real(np.vdot(psi, H @ psi) / np.vdot(psi, psi)))
 

@@ -100,6 +100,59 @@ def to_fock(mps: MPS) -> np.ndarray:
     return v[:, 0] if v.shape[1] == 1 else v.sum(axis=1)
 
 
+def from_fock(v: np.ndarray, L: int, tol: float = 1e-14) -> MPS:
+    """Exact MPS of a 4^L coefficient vector by successive SVDs (Sec. 2.1):
+    split off one site at a time, keeping every singular value above
+    tol * max of its bond; each bond sector is factorised on its own, so the
+    bond labels are the (N, 2S_z) of the sites to the left."""
+    rest = np.asarray(v, dtype=np.complex128).reshape(1, -1)
+    lab = np.zeros((1, 2), dtype=np.int64)
+    tensors, labels = [], [lab.copy()]
+    for i in range(L - 1):
+        Dl = rest.shape[0]
+        M = rest.reshape(Dl * 4, -1)
+        rowlab = (lab[:, None, :] + SITE_Q[None, :, :]).reshape(Dl * 4, 2)
+        pieces = []
+        for q in sorted({tuple(r) for r in rowlab}):
+            rows = _rows_of(rowlab, q)
+            U, sv, Vh = np.linalg.svd(M[rows], full_matrices=False)
+            pieces.append((q, rows, U, sv, Vh))
+        smax = max((p[3].max() for p in pieces if p[3].size), default=0.0)
+        keep = [(q, rows, U[:, sv > tol * smax], sv[sv > tol * smax], Vh[sv > tol * smax])
+                for q, rows, U, sv, Vh in pieces]
+        keep = [k for k in keep if k[3].size]
+        Dr = sum(k[3].size for k in keep)
+        A = np.zeros((Dl * 4, Dr), dtype=np.complex128)
+        nxt = np.zeros((Dr, M.shape[1]), dtype=np.complex128)
+        newlab = np.zeros((Dr, 2), dtype=np.int64)
+        c = 0
+        for q, rows, U, sv, Vh in keep:
+            k = sv.size
+            A[rows, c:c + k] = U
+            nxt[c:c + k] = sv[:, None] * Vh
+            newlab[c:c + k] = q
+            c += k
+        tensors.append(A.reshape(Dl, 4, Dr))
+        rest, lab = nxt, newlab
+        labels.append(lab.copy())
+    Dl = rest.shape[0]
+    last = rest.reshape(Dl, 4, 1)
+    rowlab = (lab[:, None, :] + SITE_Q[None, :, :])
+    weight = {}
+    for a in range(Dl):
+        for s in range(4):
+            q = tuple(rowlab[a, s])
+            weight[q] = weight.get(q, 0.0) + abs(last[a, s, 0]) ** 2
+    tot = max(weight, key=weight.get)
+    if sum(weight.values()) - weight[tot] > 1e-24 * max(weight[tot], 1e-300):
+        raise ValueError("vector is not an eigenvector of (N, 2S_z)")
+    # entries of another total charge are SVD rounding noise of exact zeros
+    mask = np.all(rowlab == np.array(tot)[None, None, :], axis=2)
+    tensors.append(np.where(mask[:, :, None], last, 0.0))
+    labels.append(np.array([tot], dtype=np.int64).reshape(1, 2))
+    return MPS(tensors, labels)
+
+
 def fock_index(dets: np.ndarray, L: int) -> np.ndarray:
     """Configuration index of each determinant mask (up bit -> 1, down -> 2)."""
     idx = np.zeros(len(dets), dtype=np.int64)
@@ -161,6 +214,45 @@ def scale(mps: MPS, alpha: complex) -> MPS:
     out = mps.copy()
     r = complex(alpha) ** (1.0 / mps.L)
     out.tensors = [t * r for t in out.tensors]
+    return out
+
+
+def _site_op_matrix(spin: int, dagger: bool) -> np.ndarray:
+    """4x4 matrix M[sigma_out, sigma_in] of a_(site, spin) or its adjoint on
+    one site's local states |0>, |up>, |down>, |up down> = a+_up a+_down |0>.
+
+    From the determinant convention of Eq. (fci): a local state is the
+    ordered product of its creators (up before down), so removing or adding
+    the down electron passes the up creator when the up orbital is occupied
+    (sign -1); removing or adding the up electron passes nothing."""
+    M = np.zeros((4, 4))
+    bit = 1 << spin
+    for s_in in range(4):
+        occupied = bool(s_in & bit)
+        if occupied == dagger:
+            continue
+        sign = -1.0 if (spin == 1 and (s_in & 1)) else 1.0
+        M[s_in ^ bit, s_in] = sign
+    return M
+
+
+def apply_site_op(mps: MPS, site: int, spin: int, dagger: bool) -> MPS:
+    """a_(site, spin)|mps> (dagger=False) or a+_(site, spin)|mps>, exactly.
+
+    The operator is a product over sites (bond dimension one): the parity
+    (-1)^n on every site before ``site`` (the electrons of all earlier spin
+    orbitals of Eq. fci), the local matrix of ``_site_op_matrix`` on ``site``
+    and the identity after it.  Bonds after ``site`` shift their (N, 2S_z)
+    labels by the operator's charge."""
+    out = mps.copy()
+    parity = np.array([1.0, -1.0, -1.0, 1.0])
+    for k in range(site):
+        out.tensors[k] = out.tensors[k] * parity[None, :, None]
+    M = _site_op_matrix(spin, dagger)
+    out.tensors[site] = np.einsum("ts,asb->atb", M, out.tensors[site])
+    dq = SITE_Q[1 + spin] * (1 if dagger else -1)
+    for k in range(site + 1, mps.L + 1):
+        out.labels[k] = out.labels[k] + dq[None, :]
     return out
 
 
@@ -537,6 +629,31 @@ def krylov_step(sys: System, psi: MPS, dt: float, m: int, sch: Schedule,
 
 def one_rdm(sys: System, mps: MPS) -> np.ndarray:
     return fci.one_rdm(sys.vec(mps), sys.dets, sys.L)
+
+
+def two_rdm(sys: System, mps: MPS) -> np.ndarray:
+    return fci.two_rdm(sys.vec(mps), sys.dets, sys.L)
+
+
+def green_function(systems: dict, psi0: MPS, i: int, j: int, dt: float, n_steps: int, m: int,
+                   sch: Schedule, orthogonal: bool = True) -> np.ndarray:
+    """Eq. (green_time) on MPS, as the paper evaluates it: annihilate an
+    electron of spin s at orbital j (``apply_site_op``, exact), propagate the
+    ionised state backwards in time with ``krylov_step`` (time step -dt) and
+    project on a_{is}|psi0> after every step.  ``systems[s]`` is the System
+    of the sector with one electron of spin s fewer.  Returns G_ij at
+    tau = 0, dt, ..., n_steps * dt."""
+    num = np.zeros(n_steps + 1, dtype=np.complex128)
+    den = 0.0 + 0.0j
+    for s, sysm in systems.items():
+        chi_i = apply_site_op(psi0, i, s, False)
+        chi = apply_site_op(psi0, j, s, False)
+        den += overlap(chi_i, chi)
+        num[0] += overlap(chi_i, chi)
+        for n in range(n_steps):
+            chi = krylov_step(sysm, chi, -dt, m, sch, orthogonal)[0]
+            num[n + 1] += overlap(chi_i, chi)
+    return -1j * num / den
 
 
 def compress(mps: MPS, D: int, eps: float):

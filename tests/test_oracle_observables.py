@@ -1,0 +1,144 @@
+"""Pins for the oracle's site operators, MPS-from-vector decomposition,
+transition and two-body density matrices and one-particle Green's function
+(Eq. green_time) against Kronecker-product Jordan-Wigner operators, closed
+forms of the non-interacting problem and exact identities."""
+import numpy as np
+import pytest
+import scipy.linalg
+
+import synth
+from oracle import fci
+from oracle import mps as om
+from jw_kron import site_config_index, spin_orbital_ops
+
+
+def _rand_sector_vector(dets, seed):
+    rng = np.random.default_rng(seed)
+    v = rng.standard_normal(len(dets)) + 1j * rng.standard_normal(len(dets))
+    return v / np.linalg.norm(v)
+
+
+def _labels_consistent(m):
+    for i, A in enumerate(m.tensors):
+        ql, qr = m.labels[i], m.labels[i + 1]
+        for a, s, b in zip(*np.nonzero(np.abs(A) > 0)):
+            if not np.array_equal(ql[a] + om.SITE_Q[s], qr[b]):
+                return False
+    return True
+
+
+@pytest.mark.parametrize("dagger", [False, True])
+def test_site_op_matches_kronecker_operators(dagger):
+    L = 3
+    A, q = synth.random_mps(L, 3, 1, 6, seed=4)
+    m = om.from_arrays(A, q)
+    a = spin_orbital_ops(L)
+    idx = site_config_index(L)
+    vk = om.to_fock(m)[idx]
+    for i in range(L):
+        for s in range(2):
+            op = a[2 * i + s].T if dagger else a[2 * i + s]
+            out = om.apply_site_op(m, i, s, dagger)
+            assert _labels_consistent(out)
+            assert np.allclose(om.to_fock(out)[idx], op @ vk, atol=1e-14)
+            sign = 1 if dagger else -1
+            assert np.array_equal(out.labels[-1][0], m.labels[-1][0] + sign * om.SITE_Q[1 + s])
+
+
+def test_site_ops_anticommute():
+    L = 3
+    A, q = synth.random_mps(L, 3, -1, 6, seed=5)
+    m = om.from_arrays(A, q)
+    v = om.to_fock(m)
+    for p in range(2 * L):
+        for r in range(2 * L):
+            x = om.apply_site_op(om.apply_site_op(m, r // 2, r % 2, True), p // 2, p % 2, False)
+            y = om.apply_site_op(om.apply_site_op(m, p // 2, p % 2, False), r // 2, r % 2, True)
+            assert np.allclose(om.to_fock(x) + om.to_fock(y), v * (p == r), atol=1e-14)
+
+
+def test_from_fock_contracts_back_with_full_ci_bond_profile():
+    L = 5
+    dets = fci.basis(L, 3, 2)
+    v = _rand_sector_vector(dets, 6)
+    m = om.from_fock(om.sector_to_fock(v, dets, L), L)
+    assert np.abs(om.to_sector(m, dets) - v).max() < 1e-14
+    assert _labels_consistent(m)
+    # a generic vector has the full rank at every cut: the number of
+    # (left, right) configuration pairs of matching charge, bounded by 4^k
+    for k, D in enumerate(m.bond_dims):
+        assert D <= min(4 ** k, 4 ** (L - k))
+    assert m.bond_dims[2] == 16 and m.bond_dims[3] == 16
+
+
+def test_transition_and_two_rdm_match_kronecker_operators():
+    L = 3
+    a = spin_orbital_ops(L)
+    ad = [x.T for x in a]
+    dets = fci.basis(L, 2, 1)
+    bra, ket = _rand_sector_vector(dets, 7), _rand_sector_vector(dets, 8)
+    full = lambda v: (lambda o: (o.__setitem__(dets.astype(np.int64), v), o)[1])(
+        np.zeros(4 ** L, dtype=complex))
+    B, K = full(bra), full(ket)
+    T = fci.transition_rdm(bra, ket, dets, L)
+    for i in range(L):
+        for j in range(L):
+            ref = sum(np.vdot(B, ad[2 * i + s] @ a[2 * j + s] @ K) for s in range(2))
+            assert abs(T[i, j] - ref) < 1e-13
+    assert np.allclose(fci.transition_rdm(ket, ket, dets, L), fci.one_rdm(ket, dets, L), atol=1e-15)
+    G = fci.two_rdm(ket, dets, L)
+    for i, j, k, l in np.ndindex(L, L, L, L):
+        ref = sum(np.vdot(K, ad[2 * i + s] @ ad[2 * k + t] @ a[2 * l + t] @ a[2 * j + s] @ K)
+                  for s in range(2) for t in range(2))
+        assert abs(G[i, j, k, l] - ref) < 1e-13
+
+
+def test_two_rdm_energy_trace_and_symmetries():
+    L = 4
+    I = synth.make_integrals(L, seed=9, n_chol=3)
+    dets = fci.basis(L, 2, 1)
+    v = _rand_sector_vector(dets, 10)
+    H = fci.hamiltonian(I.h, I.eri, dets, 0.37)
+    g = fci.one_rdm(v, dets, L)
+    G = fci.two_rdm(v, dets, L)
+    e = np.einsum("ij,ij->", I.h, g) + 0.5 * np.einsum("ijkl,ijkl->", I.eri, G) + 0.37
+    assert abs(e - np.vdot(v, H @ v)) < 1e-12
+    n = 3
+    assert np.allclose(np.einsum("ijkk->ij", G), (n - 1) * g, atol=1e-13)
+    assert np.allclose(G, G.transpose(2, 3, 0, 1), atol=1e-14)
+    assert np.allclose(G, G.transpose(1, 0, 3, 2).conj(), atol=1e-14)
+
+
+def test_green_function_noninteracting_closed_form():
+    # V = 0 and psi0 an eigenstate (E0): exp(iH tau) a_j exp(-iH tau) =
+    # sum_q [exp(-i h tau)]_jq a_q, so the numerator of Eq. (green_time) is
+    # exp(i E0 tau) [gamma exp(-i h tau)]_ij with the spin-summed 1BRDM gamma.
+    L = 4
+    I = synth.make_integrals(L, seed=12, n_chol=3)
+    eri0 = np.zeros_like(I.eri)
+    dets = fci.basis(L, 2, 2)
+    H = fci.hamiltonian(I.h, eri0, dets, 0.25)
+    w, U = np.linalg.eigh(H)
+    psi0 = U[:, 0].astype(complex)
+    g = fci.one_rdm(psi0, dets, L)
+    taus = np.array([0.0, 0.3, 1.1])
+    for i, j in [(0, 0), (1, 2), (3, 1)]:
+        G = fci.green_function(I.h, eri0, psi0, dets, L, i, j, taus, 0.25)
+        ref = np.array([-1j * np.exp(1j * w[0] * t) * (g @ scipy.linalg.expm(-1j * I.h * t))[i, j]
+                        / g[i, j] for t in taus])
+        assert np.allclose(G, ref, atol=1e-11)
+        assert abs(G[0] + 1j) < 1e-13
+
+
+def test_mps_green_function_matches_full_ci():
+    L = 4
+    I = synth.make_integrals(L, seed=13, n_chol=3)
+    dets = fci.basis(L, 2, 2)
+    w, U = np.linalg.eigh(fci.hamiltonian(I.h, I.eri, dets))
+    psi0 = om.from_fock(om.sector_to_fock(U[:, 0].astype(complex), dets, L), L)
+    systems = {0: om.System.build(I.h, I.eri, 1, 2), 1: om.System.build(I.h, I.eri, 2, 1)}
+    sch = om.Schedule(D=64, eps=0.0, n_two_site=1, n_one_site=1)
+    dt, n = 0.1, 3
+    G = om.green_function(systems, psi0, 1, 2, dt, n, 6, sch)
+    ref = fci.green_function(I.h, I.eri, U[:, 0], dets, L, 1, 2, dt * np.arange(n + 1))
+    assert np.allclose(G, ref, atol=1e-9)
