@@ -60,8 +60,8 @@ enum {
  * of the Krylov inner products <phi_i|phi_j>, <phi_i|H|phi_j> (unless
  * tdmps_set_krylov_fp64 asks for FP64).  Factorisations (QR, SVD), the
  * Krylov matrices and their exponential, the centre-site norms and the
- * observables (tdmps_overlap, tdmps_expectation, tdmps_one_rdm) are always
- * FP64. */
+ * observables (tdmps_overlap, tdmps_expectation, tdmps_one_rdm,
+ * tdmps_transition_rdm, tdmps_two_rdm) are always FP64. */
 enum {
   TDMPS_FP64 = 0,   /* complex FP64 everywhere                               */
   TDMPS_TF32 = 1,   /* TF32 tensor-core products, FP32 accumulation          */
@@ -214,6 +214,53 @@ int tdmps_krylov_step(tdmps_ctx_t ctx, tdmps_mpo_t mpo, tdmps_mps_t inout, doubl
 /* gamma_ij = sum_s <psi| c+_is c_js |psi> (Sec. 3.2, the 1BRDM), not
  * normalised by <psi|psi>.  gamma: host array L*L row-major. */
 int tdmps_one_rdm(tdmps_ctx_t ctx, tdmps_mps_t psi, tdmps_complex* gamma);
+
+/* T_ij = sum_s <bra| c+_is c_js |ket>: the 1BRDM between two states of the
+ * same (N, 2S_z) (TDMPS_ERR_SECTOR otherwise), not normalised.  T: host
+ * array L*L row-major.  FP64. */
+int tdmps_transition_rdm(tdmps_ctx_t ctx, tdmps_mps_t bra, tdmps_mps_t ket, tdmps_complex* T);
+
+/* Gamma_ijkl = sum_{s,t} <psi| c+_is c+_kt c_lt c_js |psi>, the partner of
+ * the chemist-order integral (ij|kl) in Eq. hamil, so that
+ * <psi|H|psi> = sum h_ij gamma_ij + 1/2 sum (ij|kl) Gamma_ijkl + e0 <psi|psi>
+ * and dE/dh_ij = gamma_ij, dE/d(ij|kl) = Gamma_ijkl / 2.  Not normalised.
+ * Gamma: host array L^4 row-major (index ((i*L + j)*L + k)*L + l).  Computed
+ * as sum_s T[c_is psi, c_js psi]_kl from 2 L^2 transition 1BRDMs of the
+ * exactly ionised states (tdmps_apply_site_op).  FP64. */
+int tdmps_two_rdm(tdmps_ctx_t ctx, tdmps_mps_t psi, tdmps_complex* Gamma);
+
+/* ------------------------------------------------------- site operators */
+
+/* out = c_(site, spin)|in> (dagger = 0) or c+_(site, spin)|in> (dagger = 1),
+ * exactly (no fit: the operator has bond dimension one).  spin: 0 up,
+ * 1 down; site in [0, L).  Jordan-Wigner order 1up, 1down, 2up, ... (Eq.
+ * fci): the parity (-1)^n of every earlier site and, for spin down, of the
+ * up electron on the same site.  The result has (N -+ 1, 2S_z -+ 1 for up,
+ * 2S_z +- 1 for down) and keeps the bond dimensions of `in`; it is neither
+ * normalised nor canonical.  This is the ionisation step of the one-particle
+ * Green's function (Eq. green_time: c_js|psi0>, propagated with a negative
+ * time step, projected on c_is|psi0>).  Returns TDMPS_ERR_ZERO_STATE, with
+ * *out untouched, when the operator annihilates every configuration of
+ * `in` (for example c_up on a state with that orbital empty). */
+int tdmps_apply_site_op(tdmps_ctx_t ctx, tdmps_mps_t in, int site, int spin, int dagger,
+                        tdmps_mps_t* out);
+
+/* One-particle Green's function of Eq. (green_time), spin-summed and
+ * normalised, at tau = n dt for n = 0..n_steps:
+ *   G_ij(tau) = -i sum_s <psi0| c+_is exp(+i H tau) c_js |psi0>
+ *                  / sum_s <psi0| c+_is c_js |psi0>   (hbar = 1).
+ * As in the paper: c_js|psi0> exactly (tdmps_apply_site_op), propagated
+ * backwards in time (time step -dt) with method 0 = Krylov
+ * (tdmps_krylov_step with m, orthogonal) or 1 = RK4 (tdmps_rk4_step; m and
+ * orthogonal ignored), fitted at D / eps, and projected on c_is|psi0> after
+ * every step (FP64 overlaps).  The MPO does not depend on the electron
+ * number, so the MPO of psi0's Hamiltonian serves the ionised sectors.
+ * G: host array of n_steps + 1 values.  Errors: INVALID_ARG (site, method,
+ * n_steps < 0), ZERO_STATE (the denominator vanishes), and those of the
+ * integrator. */
+int tdmps_green_function(tdmps_ctx_t ctx, tdmps_mpo_t mpo, tdmps_mps_t psi0, int i, int j,
+                         double dt, int n_steps, int method, int m, int orthogonal, int D,
+                         double eps, tdmps_complex* G);
 
 /* ------------------------------------------------------------ statistics */
 

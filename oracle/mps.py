@@ -636,11 +636,11 @@ def two_rdm(sys: System, mps: MPS) -> np.ndarray:
 
 
 def green_function(systems: dict, psi0: MPS, i: int, j: int, dt: float, n_steps: int, m: int,
-                   sch: Schedule, orthogonal: bool = True) -> np.ndarray:
+                   sch: Schedule, orthogonal: bool = True, method: str = "krylov") -> np.ndarray:
     """Eq. (green_time) on MPS, as the paper evaluates it: annihilate an
     electron of spin s at orbital j (``apply_site_op``, exact), propagate the
-    ionised state backwards in time with ``krylov_step`` (time step -dt) and
-    project on a_{is}|psi0> after every step.  ``systems[s]`` is the System
+    ionised state backwards in time with ``krylov_step`` or ``rk4_step``
+    (time step -dt) and project on a_{is}|psi0> after every step.  ``systems[s]`` is the System
     of the sector with one electron of spin s fewer.  Returns G_ij at
     tau = 0, dt, ..., n_steps * dt."""
     num = np.zeros(n_steps + 1, dtype=np.complex128)
@@ -651,7 +651,10 @@ def green_function(systems: dict, psi0: MPS, i: int, j: int, dt: float, n_steps:
         den += overlap(chi_i, chi)
         num[0] += overlap(chi_i, chi)
         for n in range(n_steps):
-            chi = krylov_step(sysm, chi, -dt, m, sch, orthogonal)[0]
+            if method == "krylov":
+                chi = krylov_step(sysm, chi, -dt, m, sch, orthogonal)[0]
+            else:
+                chi = rk4_step(sysm, chi, -dt, sch)
             num[n + 1] += overlap(chi_i, chi)
     return -1j * num / den
 

@@ -77,6 +77,10 @@ _SIGS = {
     "tdmps_rk4_step": (I, [P, P, P, D, I, D]),
     "tdmps_krylov_step": (I, [P, P, P, D, I, I, I, D]),
     "tdmps_one_rdm": (I, [P, P, P]),
+    "tdmps_transition_rdm": (I, [P, P, P, P]),
+    "tdmps_two_rdm": (I, [P, P, P]),
+    "tdmps_apply_site_op": (I, [P, P, I, I, I, ctypes.POINTER(P)]),
+    "tdmps_green_function": (I, [P, P, P, I, I, D, I, I, I, I, I, D, P]),
     "tdmps_stats_enable": (I, [P, I]),
     "tdmps_stats_reset": (I, [P]),
     "tdmps_stats_get": (I, [P, I, ctypes.POINTER(KStat)]),
@@ -333,4 +337,38 @@ def one_rdm(ctx, mps) -> np.ndarray:
     L = mps.info()["L"]
     g = np.zeros((L, L), dtype=np.complex128)
     _check(lib().tdmps_one_rdm(ctx.h, mps.h, _ptr(g)), ctx)
+    return g
+
+
+def transition_rdm(ctx, bra, ket) -> np.ndarray:
+    """T_ij = sum_s <bra| c+_is c_js |ket>."""
+    L = bra.info()["L"]
+    g = np.zeros((L, L), dtype=np.complex128)
+    _check(lib().tdmps_transition_rdm(ctx.h, bra.h, ket.h, _ptr(g)), ctx)
+    return g
+
+
+def two_rdm(ctx, mps) -> np.ndarray:
+    """Gamma_ijkl = sum_st <psi| c+_is c+_kt c_lt c_js |psi> (L^4)."""
+    L = mps.info()["L"]
+    g = np.zeros((L, L, L, L), dtype=np.complex128)
+    _check(lib().tdmps_two_rdm(ctx.h, mps.h, _ptr(g)), ctx)
+    return g
+
+
+def apply_site_op(ctx, mps, site, spin, dagger=False) -> MPS:
+    """c_(site, spin)|mps> or c+_(site, spin)|mps> exactly (spin 0 up, 1 down)."""
+    out = ctypes.c_void_p()
+    _check(lib().tdmps_apply_site_op(ctx.h, mps.h, site, spin, 1 if dagger else 0,
+                                     ctypes.byref(out)), ctx)
+    return MPS(ctx, out)
+
+
+def green_function(ctx, mpo, psi0, i, j, dt, n_steps, method="krylov", m=10, orthogonal=True,
+                   D=64, eps=0.0) -> np.ndarray:
+    """G_ij(n dt), n = 0..n_steps, of Eq. (green_time) (backward propagation)."""
+    g = np.zeros(n_steps + 1, dtype=np.complex128)
+    meth = {"krylov": 0, "rk4": 1}[method]
+    _check(lib().tdmps_green_function(ctx.h, mpo.h, psi0.h, i, j, dt, n_steps, meth, m,
+                                      1 if orthogonal else 0, D, eps, _ptr(g)), ctx)
     return g

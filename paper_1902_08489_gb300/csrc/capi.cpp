@@ -1,4 +1,5 @@
 // extern "C" boundary of the tdmps library (declared in include/tdmps.h).
+#include <cmath>
 #include <cstring>
 #include <memory>
 #include <string>
@@ -344,6 +345,57 @@ int tdmps_one_rdm(tdmps_ctx_t ctx, tdmps_mps_t psi, tdmps_complex* gamma) {
     std::vector<cplx> g((size_t)psi->m.L * psi->m.L);
     one_rdm(*ctx->c, psi->m, g.data());
     for (size_t i = 0; i < g.size(); ++i) gamma[i] = {g[i].real(), g[i].imag()};
+  });
+}
+
+int tdmps_transition_rdm(tdmps_ctx_t ctx, tdmps_mps_t bra, tdmps_mps_t ket, tdmps_complex* T) {
+  if (!ctx) return TDMPS_ERR_INVALID_ARG;
+  return guard(ctx, [&] {
+    need(bra && ket && T, "NULL argument");
+    std::vector<cplx> g((size_t)bra->m.L * bra->m.L);
+    transition_rdm(*ctx->c, bra->m, ket->m, g.data());
+    for (size_t i = 0; i < g.size(); ++i) T[i] = {g[i].real(), g[i].imag()};
+  });
+}
+
+int tdmps_two_rdm(tdmps_ctx_t ctx, tdmps_mps_t psi, tdmps_complex* Gamma) {
+  if (!ctx) return TDMPS_ERR_INVALID_ARG;
+  return guard(ctx, [&] {
+    need(psi && Gamma, "NULL argument");
+    size_t L2 = (size_t)psi->m.L * psi->m.L;
+    std::vector<cplx> g(L2 * L2);
+    two_rdm(*ctx->c, psi->m, g.data());
+    for (size_t i = 0; i < g.size(); ++i) Gamma[i] = {g[i].real(), g[i].imag()};
+  });
+}
+
+int tdmps_apply_site_op(tdmps_ctx_t ctx, tdmps_mps_t in, int site, int spin, int dagger,
+                        tdmps_mps_t* out) {
+  if (!ctx) return TDMPS_ERR_INVALID_ARG;
+  return guard(ctx, [&] {
+    need(in && out, "NULL argument");
+    auto m = std::make_unique<tdmps_mps_s>();
+    if (!apply_site_op(*ctx->c, in->m, site, spin, dagger != 0, m->m))
+      throw Error(TDMPS_ERR_ZERO_STATE, "the operator annihilates the state");
+    *out = m.release();
+  });
+}
+
+int tdmps_green_function(tdmps_ctx_t ctx, tdmps_mpo_t mpo, tdmps_mps_t psi0, int i, int j,
+                         double dt, int n_steps, int method, int m, int orthogonal, int D,
+                         double eps, tdmps_complex* G) {
+  if (!ctx) return TDMPS_ERR_INVALID_ARG;
+  return guard(ctx, [&] {
+    need(mpo && psi0 && G, "NULL argument");
+    need(mpo->m.L == psi0->m.L, "MPO and MPS lengths differ");
+    need(i >= 0 && i < psi0->m.L && j >= 0 && j < psi0->m.L, "orbital index out of range");
+    need(std::isfinite(dt), "dt must be finite");
+    if (method == 0) need(m >= 2 && m <= 16, "Krylov dimension must be in [2, 16]");
+    ensure_uploaded(ctx, mpo);
+    std::vector<cplx> g((size_t)std::max(n_steps, 0) + 1);
+    green_function(*ctx->c, mpo->m, psi0->m, i, j, dt, n_steps, method, m, orthogonal != 0,
+                   opts(ctx, D, eps), g.data());
+    for (size_t k = 0; k < g.size(); ++k) G[k] = {g[k].real(), g[k].imag()};
   });
 }
 

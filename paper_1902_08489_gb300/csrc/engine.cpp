@@ -1524,24 +1524,17 @@ MPSd krylov_step(Context& c, const MPOd& H, const MPSd& psi, double dt, int m, b
   return fit(c, terms, phi[0], o);
 }
 
-// ------------------------------------------------------------------ one-body RDM
+// ------------------------------------------------------------------ density matrices
 
-void one_rdm(Context& c, const MPSd& psi, cplx* gamma) {
-  Fp64Scope fp64(c);
-  const int L = psi.L;
-  const MPOd& I = c.identity_mpo(L);
-  const MPOd& G = c.rdm_mpo(L);
-  // right overlap environments
-  std::vector<Env> RO(L + 1);
-  RO[L] = env_right_boundary(c, psi, psi, I);
-  for (int i = L - 1; i >= 1; --i)
-    RO[i] = env_update_right(c, RO[i + 1], psi.sites[i], psi.bonds[i], psi, i, I);
-  DevPtr gd = dev_alloc(sizeof(double2) * (size_t)L * 2 * L, c.st);   // [j][2*i + s]
-  TD_CHECK_CUDA(cudaMemsetAsync(gd->p, 0, sizeof(double2) * (size_t)L * 2 * L, c.st));
-  Env E = env_left_boundary(c, psi, psi, G);
+// Readout operators of the density-matrix MPO: at bond j they close the open
+// creator channels c+_{is} (i < j) and the identity channel with c_{js} on
+// site j into one channel per (i, s), i <= j.
+const std::vector<MPOd>& Context::rdm_readouts(int L) {
+  if (rdm_read && (int)rdm_read->size() == L) return *rdm_read;
+  const MPOd& G = rdm_mpo(L);
+  auto v = std::make_unique<std::vector<MPOd>>(L);
   for (int j = 0; j < L; ++j) {
-    // readout operator: channels of G bond j -> closed channels (i, s), i <= j
-    MPOd R;
+    MPOd& R = (*v)[j];
     R.L = 1;
     R.bonds.resize(2);
     R.bonds[0] = G.bonds[j];
@@ -1564,29 +1557,59 @@ void one_rdm(Context& c, const MPSd& psi, cplx* gamma) {
       if (s == 0) { R.W[0].push_back({0, wout, 1, 1, 1.0}); R.W[0].push_back({0, wout, 3, 3, 1.0}); }
       else { R.W[0].push_back({0, wout, 2, 2, 1.0}); R.W[0].push_back({0, wout, 3, 3, 1.0}); }
     }
-    upload_mpo_tables(R, c);
-    // contract: E (bond j) with site j through the readout, then with RO[j+1]
+    upload_mpo_tables(R, *this);
+  }
+  rdm_read = std::move(v);
+  return *rdm_read;
+}
+
+// out[j][2 i + s] += <bra| c+_{is} c_{js} |ket> for i <= j (device, FP64 in
+// the caller's scope).  Left environments carry the open creator channels of
+// the density-matrix MPO; at every bond j the readout closes them with c_{js}
+// and the result is traced against the right overlap environment.
+static void rdm_upper(Context& c, const MPSd& bra, const MPSd& ket, double2* out) {
+  const int L = bra.L;
+  const MPOd& I = c.identity_mpo(L);
+  const MPOd& G = c.rdm_mpo(L);
+  const std::vector<MPOd>& R = c.rdm_readouts(L);
+  std::vector<Env> RO(L + 1);
+  RO[L] = env_right_boundary(c, bra, ket, I);
+  for (int i = L - 1; i >= 1; --i)
+    RO[i] = env_update_right(c, RO[i + 1], bra.sites[i], bra.bonds[i], ket, i, I);
+  Env E = env_left_boundary(c, bra, ket, G);
+  for (int j = 0; j < L; ++j) {
     GemmBatch g1(c);
-    Inter X = plan_lstage(c, E, psi.sites[j], psi.bonds[j + 1], g1);
+    Inter X = plan_lstage(c, E, ket.sites[j], ket.bonds[j + 1], g1);
     g1.run();
     WBatch wb;
-    Inter Y = plan_wstage(c, X, R, 0, true, wb);
+    Inter Y = plan_wstage(c, X, R[j], 0, true, wb);
     wb.run(c);
     GemmBatch g2(c);
-    Env Eo = plan_env_left(c, Y, psi.sites[j], psi.bonds[j + 1], R.bonds[1], psi.bonds[j + 1], g2);
+    Env Eo = plan_env_left(c, Y, bra.sites[j], bra.bonds[j + 1], R[j].bonds[1], ket.bonds[j + 1], g2);
     g2.run();
     for (int b = 0; b < (int)Eo.t.blocks.size(); ++b) {
       const Inter::Blk& eb = Eo.t.blocks[b];
-      int rb2 = RO[j + 1].t.find(eb.rg, -1, 0, eb.rg);
+      int rb2 = RO[j + 1].t.find(eb.rg, -1, 0, eb.k);
       if (rb2 < 0) continue;
       launch_trace_channels(Eo.t.ptr(b), eb.rows, eb.W, eb.cols, RO[j + 1].t.ptr(rb2), Eo.t.et,
-                            (double2*)gd->p + (size_t)j * 2 * L, c.st);
+                            out + (size_t)j * 2 * L, c.st);
     }
     TD_CHECK_CUDA(cudaGetLastError());
-    if (j + 1 < L) E = env_update_left(c, E, psi.sites[j], psi.bonds[j + 1], psi, j, G);
-    // R tables must stay alive until the kernels above consumed them
-    c.sync();
+    if (j + 1 < L) E = env_update_left(c, E, bra.sites[j], bra.bonds[j + 1], ket, j, G);
   }
+}
+
+static void check_rdm_pair(const MPSd& bra, const MPSd& ket) {
+  if (bra.L != ket.L) throw Error(TDMPS_ERR_INVALID_ARG, "MPS lengths differ");
+  if (bra.tot != ket.tot) throw Error(TDMPS_ERR_SECTOR, "bra and ket have different (N, 2Sz)");
+}
+
+void one_rdm(Context& c, const MPSd& psi, cplx* gamma) {
+  Fp64Scope fp64(c);
+  const int L = psi.L;
+  DevPtr gd = dev_alloc(sizeof(double2) * (size_t)L * 2 * L, c.st);   // [j][2*i + s]
+  TD_CHECK_CUDA(cudaMemsetAsync(gd->p, 0, sizeof(double2) * (size_t)L * 2 * L, c.st));
+  rdm_upper(c, psi, psi, (double2*)gd->p);
   std::vector<double2> h((size_t)L * 2 * L);
   TD_CHECK_CUDA(cudaMemcpyAsync(h.data(), gd->p, sizeof(double2) * h.size(), cudaMemcpyDeviceToHost, c.st));
   c.sync();
@@ -1599,6 +1622,166 @@ void one_rdm(Context& c, const MPSd& psi, cplx* gamma) {
       }
   for (int j = 0; j < L; ++j)
     for (int i = 0; i < j; ++i) gamma[j * L + i] = std::conj(gamma[i * L + j]);
+}
+
+void transition_rdm(Context& c, const MPSd& bra, const MPSd& ket, cplx* T) {
+  check_rdm_pair(bra, ket);
+  Fp64Scope fp64(c);
+  const int L = bra.L;
+  const size_t n = (size_t)L * 2 * L;
+  DevPtr gd = dev_alloc(sizeof(double2) * 2 * n, c.st);
+  TD_CHECK_CUDA(cudaMemsetAsync(gd->p, 0, sizeof(double2) * 2 * n, c.st));
+  // upper triangle from <bra|..|ket>, lower from the conjugate of <ket|..|bra>
+  rdm_upper(c, bra, ket, (double2*)gd->p);
+  rdm_upper(c, ket, bra, (double2*)gd->p + n);
+  std::vector<double2> h(2 * n);
+  TD_CHECK_CUDA(cudaMemcpyAsync(h.data(), gd->p, sizeof(double2) * h.size(), cudaMemcpyDeviceToHost, c.st));
+  c.sync();
+  for (int i = 0; i < L * L; ++i) T[i] = 0.0;
+  for (int j = 0; j < L; ++j)
+    for (int i = 0; i <= j; ++i)
+      for (int s = 0; s < 2; ++s) {
+        double2 u = h[(size_t)j * 2 * L + 2 * i + s];
+        T[i * L + j] += cplx(u.x, u.y);
+        if (i < j) {
+          double2 v = h[n + (size_t)j * 2 * L + 2 * i + s];
+          T[j * L + i] += cplx(v.x, -v.y);
+        }
+      }
+}
+
+// Gamma_ijkl = sum_{s,t} <psi| c+_is c+_kt c_lt c_js |psi>
+//            = sum_s T[c_is psi, c_js psi]_kl
+// with T the spin-summed transition 1BRDM of the two ionised states.
+void two_rdm(Context& c, const MPSd& psi, cplx* Gam) {
+  Fp64Scope fp64(c);
+  const int L = psi.L;
+  const size_t L2 = (size_t)L * L, n = (size_t)L * 2 * L;
+  for (size_t e = 0; e < L2 * L2; ++e) Gam[e] = 0.0;
+  for (int s = 0; s < 2; ++s) {
+    std::vector<MPSd> chi(L);
+    std::vector<char> nz(L, 0);
+    for (int i = 0; i < L; ++i) nz[i] = apply_site_op(c, psi, i, s, false, chi[i]);
+    DevPtr gd = dev_alloc(sizeof(double2) * L2 * n, c.st);   // [(i, j)][l][2 k + t]
+    TD_CHECK_CUDA(cudaMemsetAsync(gd->p, 0, sizeof(double2) * L2 * n, c.st));
+    for (int i = 0; i < L; ++i)
+      for (int j = 0; j < L; ++j)
+        if (nz[i] && nz[j]) rdm_upper(c, chi[i], chi[j], (double2*)gd->p + ((size_t)i * L + j) * n);
+    std::vector<double2> h(L2 * n);
+    TD_CHECK_CUDA(cudaMemcpyAsync(h.data(), gd->p, sizeof(double2) * h.size(), cudaMemcpyDeviceToHost, c.st));
+    c.sync();
+    auto at = [&](int i, int j, int k, int l) {   // <chi_i| c+_k c_l |chi_j>, k <= l, spin-summed
+      const double2* g = h.data() + ((size_t)i * L + j) * n + (size_t)l * 2 * L + 2 * k;
+      return cplx(g[0].x + g[1].x, g[0].y + g[1].y);
+    };
+    for (int i = 0; i < L; ++i)
+      for (int j = 0; j < L; ++j)
+        for (int k = 0; k < L; ++k)
+          for (int l = 0; l < L; ++l) {
+            cplx v = k <= l ? at(i, j, k, l) : std::conj(at(j, i, l, k));
+            Gam[((size_t)i * L + j) * L2 + (size_t)k * L + l] += v;
+          }
+  }
+}
+
+// ------------------------------------------------------------------ Green's function
+
+// Eq. (green_time) for tau = n dt, n = 0..n_steps:
+//   G_ij(tau) = -i sum_s <psi0| c+_is exp(+i H tau) c_js |psi0>
+//                  / sum_s <psi0| c+_is c_js |psi0>,
+// evaluated as the paper does: ionise exactly (c_js|psi0>), propagate the
+// ionised state backwards in time with the integrator (time step -dt) and
+// project on c_is|psi0> after every step.  Overlaps in FP64.
+void green_function(Context& c, const MPOd& H, const MPSd& psi0, int i, int j, double dt,
+                    int n_steps, int method, int m, bool orth, const FitOpts& o, cplx* G) {
+  if (n_steps < 0) throw Error(TDMPS_ERR_INVALID_ARG, "n_steps must be >= 0");
+  if (method != 0 && method != 1) throw Error(TDMPS_ERR_INVALID_ARG, "method must be 0 (Krylov) or 1 (RK4)");
+  std::vector<cplx> num(n_steps + 1, 0.0);
+  cplx den = 0.0;
+  for (int s = 0; s < 2; ++s) {
+    MPSd chi_i, chi;
+    bool nzi = apply_site_op(c, psi0, i, s, false, chi_i);
+    bool nzj = apply_site_op(c, psi0, j, s, false, chi);
+    if (!nzi || !nzj) continue;
+    cplx ov = sandwich(c, nullptr, chi_i, chi);
+    den += ov;
+    num[0] += ov;
+    for (int n = 0; n < n_steps; ++n) {
+      chi = method == 0 ? krylov_step(c, H, chi, -dt, m, orth, o) : rk4_step(c, H, chi, -dt, o);
+      num[n + 1] += sandwich(c, nullptr, chi_i, chi);
+    }
+  }
+  if (den == 0.0)
+    throw Error(TDMPS_ERR_ZERO_STATE, "sum_s <psi0|c+_is c_js|psi0> vanishes");
+  for (int n = 0; n <= n_steps; ++n) G[n] = cplx(0.0, -1.0) * num[n] / den;
+}
+
+// ------------------------------------------------------------------ site operators
+
+// a_(site, spin)|in> or a+_(site, spin)|in>: a product operator (bond
+// dimension one) -- the parity (-1)^n on every earlier site (Jordan-Wigner
+// string over the spin orbitals before it), the local matrix on `site`, the
+// identity after it.  Bonds right of `site` shift their charges by the
+// operator's, which keeps their sector order.  Returns false when no block
+// survives (the state is exactly zero).
+bool apply_site_op(Context& c, const MPSd& in, int site, int spin, bool dagger, MPSd& out) {
+  if (site < 0 || site >= in.L) throw Error(TDMPS_ERR_INVALID_ARG, "site out of range");
+  if (spin < 0 || spin > 1) throw Error(TDMPS_ERR_INVALID_ARG, "spin must be 0 (up) or 1 (down)");
+  const QN dq = dagger ? SITE_Q[1 + spin] : -SITE_Q[1 + spin];
+  out = MPSd();
+  out.L = in.L;
+  out.tot = in.tot + dq;
+  out.bonds = in.bonds;
+  for (int k = site + 1; k <= in.L; ++k)
+    for (auto& q : out.bonds[k].q) q = q + dq;
+  const int bit = 1 << spin;
+  std::vector<CopyTask> tasks;
+  auto copy_block = [&](const SiteT& a, int b, const SiteT& o, int ob, double sign) {
+    if (ob < 0 || o.blocks[ob].rows != a.blocks[b].rows || o.blocks[ob].cols != a.blocks[b].cols)
+      throw Error(TDMPS_ERR_SECTOR, "site tensor blocks do not match their bonds");
+    CopyTask t{};
+    size_t n = (size_t)a.blocks[b].rows * a.blocks[b].cols;
+    if (n > (size_t)INT32_MAX) throw Error(TDMPS_ERR_INVALID_ARG, "block too large");
+    t.blk = a.ptr(b);
+    t.work = o.ptr(ob);
+    t.rows = 1;
+    t.cols = (int)n;
+    t.ld = (int)n;
+    t.ldw = 1;
+    t.scale = make_double2(sign, 0.0);
+    tasks.push_back(t);
+  };
+  bool any = false;
+  for (int k = 0; k < in.L; ++k) {
+    const SiteT& a = in.sites[k];
+    SiteT o = make_site(RowGroups::from_bond(out.bonds[k]), out.bonds[k + 1], c.st, k == site);
+    for (int b = 0; b < (int)a.blocks.size(); ++b) {
+      const SiteT::Blk& ab = a.blocks[b];
+      if (k != site) {
+        double sign = (k < site && (ab.sig == 1 || ab.sig == 2)) ? -1.0 : 1.0;
+        copy_block(a, b, o, o.block_of(ab.r, ab.sig), sign);
+      } else {
+        bool occupied = (ab.sig & bit) != 0;
+        if (occupied == dagger) continue;   // annihilated local state
+        // the down operator passes the up creator of the same site
+        double sign = (spin == 1 && (ab.sig & 1)) ? -1.0 : 1.0;
+        copy_block(a, b, o, o.block_of(ab.r, ab.sig ^ bit), sign);
+        any = true;
+      }
+    }
+    out.sites.push_back(std::move(o));
+  }
+  if (!tasks.empty()) {
+    const CopyTask* d = c.stage(tasks);
+    cudaEvent_t ev;
+    c.kbegin(TDMPS_KSTAT_OTHER, &ev);
+    launch_copy(d, (int)tasks.size(), 1, c.st);
+    TD_CHECK_CUDA(cudaGetLastError());
+    double bytes = 0.0;
+    for (auto& t : tasks) bytes += 32.0 * t.cols;
+    c.kend(TDMPS_KSTAT_OTHER, ev, 0.0, bytes);
+  }
+  return any;
 }
 
 // ------------------------------------------------------------------ MPS creation

@@ -40,6 +40,7 @@ struct Context {
   DevPtr status;   // int[16]: [0] SVD convergence, [4..5] Krylov, [8] tensor-core waits
   std::unique_ptr<MPOd> ident;   // identity MPO cache (by L)
   std::unique_ptr<MPOd> rdm;     // density-matrix MPO cache (by L)
+  std::unique_ptr<std::vector<MPOd>> rdm_read;   // its per-bond readouts (by L)
 
   explicit Context(cudaStream_t s, int prec);
   ~Context();
@@ -59,6 +60,7 @@ struct Context {
   int et() const { return precision == TDMPS_FP64 ? 0 : 1; }
   int* tc_err() const { return (int*)status->p + 8; }
   const MPOd& rdm_mpo(int L);
+  const std::vector<MPOd>& rdm_readouts(int L);
 };
 
 // ------------------------------------------------------------------ intermediates
@@ -149,6 +151,15 @@ MPSd rk4_step(Context& c, const MPOd& H, const MPSd& psi, double dt, const FitOp
 MPSd krylov_step(Context& c, const MPOd& H, const MPSd& psi, double dt, int m, bool orth,
                  const FitOpts& o);
 void one_rdm(Context& c, const MPSd& psi, cplx* gamma);
+// T_ij = sum_s <bra| c+_is c_js |ket> (L*L row-major)
+void transition_rdm(Context& c, const MPSd& bra, const MPSd& ket, cplx* T);
+// Gamma_ijkl = sum_st <psi| c+_is c+_kt c_lt c_js |psi> (L^4 row-major)
+void two_rdm(Context& c, const MPSd& psi, cplx* Gam);
+// a_(site, spin)|in> (dagger false) or its adjoint, exactly; false if zero
+bool apply_site_op(Context& c, const MPSd& in, int site, int spin, bool dagger, MPSd& out);
+// Eq. (green_time) at tau = 0, dt, ..., n_steps dt (method 0 Krylov, 1 RK4)
+void green_function(Context& c, const MPOd& H, const MPSd& psi0, int i, int j, double dt,
+                    int n_steps, int method, int m, bool orth, const FitOpts& o, cplx* G);
 // overlap with all blocks in a fixed device array (noalloc.cu)
 cplx overlap_noalloc(Context& c, const MPSd& bra, const MPSd& ket);
 
