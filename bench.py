@@ -153,6 +153,109 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def roofline(st, precision):
+    """Roofline entry of the kernel class with the largest live event time:
+    achieved = its algorithmic work per launch / its average launch time."""
+    peaks = _peaks()
+    # the kernels run inside seconds-long steps: the sustained bf16 figure
+    bf16 = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops", 1716.0))
+    hbm = peaks.get("hbm_gbs", 6675.5)
+    fp64_peak = bf16 * 1.25 / 2250.0
+    top = max(st, key=lambda k: st[k]["ms"])
+    ks = st[top]
+    per_launch_s = ks["ms"] / max(1, ks["launches"]) / 1e3
+    per_launch = lambda x: x / max(1, ks["launches"])
+    src64 = "measured sustained bf16 x nominal FP64/bf16 (1.25/2250)"
+    if top == "gemm":
+        tf32 = bf16 * (1100.0 / 2250.0)
+        if precision == "tf32x3":
+            peak, src = tf32 / 3.0, "measured sustained bf16 x nominal TF32/bf16 (1.1/2.25), /3 for split TF32"
+        else:
+            peak, src = tf32, "measured sustained bf16 x nominal TF32/bf16 (1.1/2.25)"
+        kern, bound, unit = "k_gemm_tc (tcgen05 grouped complex block GEMM)", "tensor", "TFLOP/s"
+        achieved = per_launch(ks["flops"]) / per_launch_s / 1e12
+    elif top in ("gemm_fp64", "qr", "svd"):
+        kern = {"gemm_fp64": "k_gemm (FP64 grouped complex block GEMM)",
+                "qr": "k_qr (FP64 Gram-Schmidt QR, one classical pass counted)",
+                "svd": "k_svd (FP64 one-sided Jacobi SVD)"}[top]
+        peak, src, bound, unit = fp64_peak, src64, "alu", "TFLOP/s"
+        achieved = per_launch(ks["flops"]) / per_launch_s / 1e12
+    else:
+        kern = {"wstage": "k_wstage (sparse MPO-tensor stage)", "other": "k_copy/k_scatter"}[top]
+        peak, src, bound, unit = hbm, "measured hbm_gbs", "hbm", "GB/s"
+        achieved = per_launch(ks["bytes"]) / per_launch_s / 1e9
+    return {"kernel": kern, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
+            "frac": achieved / peak, "traffic": None, "peak_source": src,
+            "share_of_timed_device_time": ks["ms"] / max(1e-9, sum(v["ms"] for v in st.values()))}
+
+
+def batch_instances(n=64):
+    """The uneven-instance workload: seeds 0..n-1, L uniform in {8,10,12,14}
+    and D uniform in {32,64,128} drawn with default_rng(1000 + seed),
+    electrons = L, S_z = 0."""
+    out = []
+    for seed in range(n):
+        r = np.random.default_rng(1000 + seed)
+        out.append((seed, int(r.choice([8, 10, 12, 14])), int(r.choice([32, 64, 128]))))
+    return out
+
+
+def run_batch(args, td, ctx, torch, local):
+    import synth
+    sched = (0, 2) if not args.schedule else tuple(int(x) for x in args.schedule.split(","))
+    ctx.set_schedule(*sched)
+    inst = batch_instances()
+    mpos, states, Ds = [], [], []
+    for seed, Lb, Db in inst:
+        I = synth.make_integrals(Lb, seed=seed)
+        mpos.append(td.build_mpo(ctx, I.h, I.eri, n_elec=Lb))
+        A, q = synth.random_mps(Lb, Lb, 0, Db, seed=seed)
+        s0 = td.mps_import(ctx, A, q)
+        nrm = abs(td.overlap(ctx, s0, s0)) ** 0.5
+        A[0] = A[0] / nrm
+        s0.free()
+        states.append(td.mps_import(ctx, A, q))
+        Ds.append(Db)
+    dtb = 0.01
+    for _ in range(args.warmup):
+        td.evolve_batch(ctx, mpos, states, dtb, 1, Ds, method="rk4", n_workers=args.workers)
+    torch.cuda.synchronize()
+    ctx.stats_enable(True)
+    ctx.stats_reset()
+    stream = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with Clocks(local) as clk:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            td.evolve_batch(ctx, mpos, states, dtb, 1, Ds, method="rk4", n_workers=args.workers)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+    ms = ev0.elapsed_time(ev1)
+    st = ctx.stats()
+    ctx.stats_enable(False)
+    flops = st["gemm"]["flops"] + st["gemm_fp64"]["flops"] + st["wstage"]["flops"]
+    n = len(inst)
+    line = {"metric": "instance RK4 steps/s, 64 uneven instances", "value": n * args.steps / (ms / 1e3),
+            "unit": "instance-steps/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": {"fp64": "f64", "tf32": "tf32", "tf32x3": "tf32x3"}[args.precision],
+            "data": "synthetic",
+            "config": {"workload": "64 instances, seeds 0..63, L in {8,10,12,14}, N = L, D in "
+                                   "{32,64,128}, RK4 dt=0.01, schedule %d two-site + %d one-site "
+                                   "sweeps, random seeded start at D" % sched,
+                       "workers": args.workers,
+                       "l2": "inputs larger than L2 (64 states + environments)"},
+            "tflops": flops / (ms / 1e3) / 1e12, "host_wall_s_per_step": wall / args.steps,
+            "gpu_launches": int(sum(v["launches"] for v in st.values())),
+            "kernel_stats": {k: {"launches": v["launches"], "ms_summed_over_streams": round(v["ms"], 3),
+                                 "gflop": round(v["flops"] / 1e9, 3)} for k, v in st.items()},
+            "clocks": clk.summary()}
+    print(json.dumps(line))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -164,9 +267,12 @@ def main():
                     help="skip the FP64 run of the same steps (error and FP64 steps/s)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--mode", default="krylov", choices=["krylov", "apply"],
+    ap.add_argument("--mode", default="krylov", choices=["krylov", "apply", "batch"],
                     help="krylov: one Krylov time step per step (default); apply: one "
-                         "fitted H application (one one-site sweep) per step")
+                         "fitted H application (one one-site sweep) per step; batch: one "
+                         "RK4 step of each of 64 uneven instances (L in {8..14}, "
+                         "D in {32, 64, 128}) on worker streams")
+    ap.add_argument("--workers", type=int, default=16, help="batch mode: worker streams")
     ap.add_argument("--schedule", default=None, help="two-site,one-site sweeps per fit")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -186,6 +292,8 @@ def main():
         dist.init_process_group("nccl")
 
     ctx = td.Context(args.precision)
+    if args.mode == "batch":
+        return run_batch(args, td, ctx, torch, local)
     sched = SCHEDULE if args.mode == "krylov" else (0, 1)
     if args.schedule:
         sched = tuple(int(x) for x in args.schedule.split(","))
@@ -281,33 +389,8 @@ def main():
                "unit": "TFLOP/s", "h2d_bytes_per_step": h2d_bytes,
                "d2h_bytes_per_step": int(g.nbytes)}
 
-    peaks = _peaks()
-    bf16 = peaks.get("bf16_tflops", 1913.9)
-    hbm = peaks.get("hbm_gbs", 6675.5)
     # dominant kernel class: the largest live event time in the timed region
-    top = max(st, key=lambda k: st[k]["ms"])
-    ks = st[top]
-    per_launch_s = ks["ms"] / max(1, ks["launches"]) / 1e3
-    if top in ("gemm", "gemm_fp64"):
-        if top == "gemm_fp64":
-            peak, src = bf16 * 1.25 / 2250.0, "measured bf16 x nominal FP64/bf16 (1.25/2250)"
-            kern, bound = "k_gemm (FP64 grouped complex block GEMM)", "alu"
-        else:
-            tf32 = bf16 * (1100.0 / 2250.0)
-            if args.precision == "tf32x3":
-                peak, src = tf32 / 3.0, "measured bf16 x nominal TF32/bf16 (1.1/2.25), /3 for split TF32"
-            else:
-                peak, src = tf32, "measured bf16 x nominal TF32/bf16 (1.1/2.25)"
-            kern, bound = "k_gemm_tc (tcgen05 grouped complex block GEMM)", "tensor"
-        achieved = ks["flops"] / max(1, ks["launches"]) / per_launch_s / 1e12
-        roof = {"kernel": kern, "bound": bound, "achieved": achieved, "peak": peak,
-                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None, "peak_source": src}
-    else:
-        achieved = ks["bytes"] / max(1, ks["launches"]) / per_launch_s / 1e9
-        roof = {"kernel": {"wstage": "k_wstage", "qr": "k_qr", "svd": "k_svd",
-                           "other": "k_copy/k_scatter"}[top],
-                "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                "frac": achieved / hbm, "traffic": None, "peak_source": "measured hbm_gbs"}
+    roof = roofline(st, args.precision)
     line = {
         "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,

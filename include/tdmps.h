@@ -56,9 +56,9 @@ enum {
   TDMPS_ERR_NUMERIC = -8          /* an iterative kernel did not converge    */
 };
 
-/* Arithmetic of the fit contractions (environments, local matvecs, sums) and
- * of the Krylov inner products <phi_i|phi_j>, <phi_i|H|phi_j> (unless
- * tdmps_set_krylov_fp64 asks for FP64).  Factorisations (QR, SVD), the
+/* Arithmetic of the fit contractions (environments, local matvecs, sums)
+ * and, if tdmps_set_krylov_fp64(ctx, 0) asks for it, of the Krylov inner
+ * products <phi_i|phi_j>, <phi_i|H|phi_j>.  Factorisations (QR, SVD), the
  * Krylov matrices and their exponential, the centre-site norms and the
  * observables (tdmps_overlap, tdmps_expectation, tdmps_one_rdm,
  * tdmps_transition_rdm, tdmps_two_rdm) are always FP64. */
@@ -94,9 +94,10 @@ int tdmps_set_precision(tdmps_ctx_t ctx, int precision);
 int tdmps_set_schedule(tdmps_ctx_t ctx, int n_two_site, int n_one_site);
 
 /* Krylov inner products (Gram-Schmidt coefficients and the N, H matrices of
- * Eq. krylov_evo) contracted in FP64 (on != 0) or in the context precision
- * (on == 0, the default).  The matrices are accumulated and processed in
- * FP64 either way. */
+ * Eq. krylov_evo) contracted in FP64 (on != 0, the default) or in the
+ * context precision (on == 0: faster in the TF32 modes, but the canonical
+ * orthogonalisation then sees the TF32 rounding of N and H).  The matrices
+ * are accumulated and processed in FP64 either way. */
 int tdmps_set_krylov_fp64(tdmps_ctx_t ctx, int on);
 
 /* ------------------------------------------------------------------- MPO */
@@ -261,6 +262,28 @@ int tdmps_apply_site_op(tdmps_ctx_t ctx, tdmps_mps_t in, int site, int spin, int
 int tdmps_green_function(tdmps_ctx_t ctx, tdmps_mpo_t mpo, tdmps_mps_t psi0, int i, int j,
                          double dt, int n_steps, int method, int m, int orthogonal, int D,
                          double eps, tdmps_complex* G);
+
+/* ------------------------------------------------------- instance batch */
+
+/* Many independent time evolutions at once: item k advances states[k] in
+ * place by n_steps[k] steps of dt[k] under mpos[k], fitted at D[k] / eps[k]
+ * (method 0 = Krylov with m and orthogonal as in tdmps_krylov_step, 1 = RK4).
+ * Items may differ in L, electrons and bond dimension; they may share MPOs
+ * but not states.  n_workers host threads (<= 0: min(8, n)), each with its
+ * own CUDA stream, staging ring and caches, take the next unfinished item
+ * from a shared counter, so the kernels of several items overlap on the GPU.
+ * The context's stream is ordered before the first and after the last
+ * kernel of the batch; the context's precision and sweep schedule apply to
+ * every item.  Results equal those of separate tdmps_rk4_step /
+ * tdmps_krylov_step calls up to the summation order of split-K partial
+ * products.  status (may be NULL): n codes, 0 for every item that finished;
+ * a failed item keeps its input state.  Returns 0 when every item finished,
+ * else the code of the first failed item (message in tdmps_last_error with
+ * its index).  The worker streams are created on the first call and live as
+ * long as the context. */
+int tdmps_evolve_batch(tdmps_ctx_t ctx, int n, const tdmps_mpo_t* mpos, tdmps_mps_t* states,
+                       const double* dt, const int* n_steps, const int* D, const double* eps,
+                       int method, int m, int orthogonal, int n_workers, int* status);
 
 /* ------------------------------------------------------------ statistics */
 

@@ -81,6 +81,7 @@ _SIGS = {
     "tdmps_two_rdm": (I, [P, P, P]),
     "tdmps_apply_site_op": (I, [P, P, I, I, I, ctypes.POINTER(P)]),
     "tdmps_green_function": (I, [P, P, P, I, I, D, I, I, I, I, I, D, P]),
+    "tdmps_evolve_batch": (I, [P, I, P, P, P, P, P, P, I, I, I, I, P]),
     "tdmps_stats_enable": (I, [P, I]),
     "tdmps_stats_reset": (I, [P]),
     "tdmps_stats_get": (I, [P, I, ctypes.POINTER(KStat)]),
@@ -372,3 +373,23 @@ def green_function(ctx, mpo, psi0, i, j, dt, n_steps, method="krylov", m=10, ort
     _check(lib().tdmps_green_function(ctx.h, mpo.h, psi0.h, i, j, dt, n_steps, meth, m,
                                       1 if orthogonal else 0, D, eps, _ptr(g)), ctx)
     return g
+
+
+def evolve_batch(ctx, mpos, states, dt, n_steps, D, eps=0.0, method="rk4", m=10,
+                 orthogonal=True, n_workers=0, raise_on_error=True) -> np.ndarray:
+    """Advance many independent states in place (per-item dt, n_steps, D,
+    eps may be scalars or sequences).  Returns the per-item status codes;
+    with raise_on_error, raises TdmpsError for the first failed item after
+    all items ran."""
+    n = len(states)
+    arr = lambda x, dt_: np.ascontiguousarray(np.broadcast_to(np.asarray(x), (n,)), dtype=dt_)
+    dts, ns, Ds, es = arr(dt, np.float64), arr(n_steps, np.int32), arr(D, np.int32), arr(eps, np.float64)
+    hm = (ctypes.c_void_p * n)(*[p.h.value if isinstance(p.h, ctypes.c_void_p) else p.h for p in mpos])
+    hs = (ctypes.c_void_p * n)(*[p.h.value if isinstance(p.h, ctypes.c_void_p) else p.h for p in states])
+    status = np.zeros(n, dtype=np.int32)
+    meth = {"krylov": 0, "rk4": 1}[method]
+    rc = lib().tdmps_evolve_batch(ctx.h, n, hm, hs, _ptr(dts), _ptr(ns), _ptr(Ds), _ptr(es), meth,
+                                  m, 1 if orthogonal else 0, n_workers, _ptr(status))
+    if raise_on_error:
+        _check(rc, ctx)
+    return status

@@ -16,7 +16,8 @@ SRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT, "libtdmps.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["kernels.cu", "kernels_tc.cu", "noalloc.cu", "engine.cpp", "mpo_build.cpp", "capi.cpp"]
+SOURCES = ["kernels.cu", "kernels_tc.cu", "noalloc.cu", "engine.cpp", "batch.cpp", "mpo_build.cpp",
+           "capi.cpp"]
 
 
 def nvcc() -> str:

@@ -399,6 +399,41 @@ int tdmps_green_function(tdmps_ctx_t ctx, tdmps_mpo_t mpo, tdmps_mps_t psi0, int
   });
 }
 
+int tdmps_evolve_batch(tdmps_ctx_t ctx, int n, const tdmps_mpo_t* mpos, tdmps_mps_t* states,
+                       const double* dt, const int* n_steps, const int* D, const double* eps,
+                       int method, int m, int orthogonal, int n_workers, int* status) {
+  if (!ctx) return TDMPS_ERR_INVALID_ARG;
+  int first = TDMPS_OK;
+  int rc = guard(ctx, [&] {
+    need(n >= 0, "n must be >= 0");
+    if (n == 0) return;
+    need(mpos && states && dt && n_steps && D && eps, "NULL argument");
+    need(method == 0 || method == 1, "method must be 0 (Krylov) or 1 (RK4)");
+    if (method == 0) need(m >= 2 && m <= 16, "Krylov dimension must be in [2, 16]");
+    std::vector<BatchItem> items(n);
+    for (int k = 0; k < n; ++k) {
+      need(mpos[k] && states[k], "NULL MPO or state in the batch");
+      need(mpos[k]->m.L == states[k]->m.L, "MPO and MPS lengths differ");
+      need(n_steps[k] >= 0, "n_steps must be >= 0");
+      need(std::isfinite(dt[k]), "dt must be finite");
+      opts(ctx, D[k], eps[k]);   // argument checks
+      for (int q = 0; q < k; ++q) need(states[q] != states[k], "a state appears twice in the batch");
+      ensure_uploaded(ctx, mpos[k]);
+      items[k] = {&mpos[k]->m, &states[k]->m, dt[k], n_steps[k], D[k], eps[k]};
+    }
+    std::vector<int> st(n, TDMPS_OK);
+    std::vector<std::string> msgs;
+    evolve_batch(*ctx->c, items, method, m, orthogonal != 0, n_workers, st.data(), msgs);
+    if (status) for (int k = 0; k < n; ++k) status[k] = st[k];
+    for (int k = 0; k < n; ++k)
+      if (st[k] != TDMPS_OK) {
+        first = st[k];
+        throw Error(st[k], "batch item " + std::to_string(k) + ": " + msgs[k]);
+      }
+  });
+  return rc != TDMPS_OK ? rc : first;
+}
+
 int tdmps_stats_enable(tdmps_ctx_t ctx, int enable) {
   if (!ctx) return TDMPS_ERR_INVALID_ARG;
   return guard(ctx, [&] {

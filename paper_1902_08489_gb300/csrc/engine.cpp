@@ -92,8 +92,10 @@ void Inter::alloc(cudaStream_t st, bool zero) {
 
 // ------------------------------------------------------------------ context
 
-Context::Context(cudaStream_t s, int prec) : st(s), precision(prec) {
-  ring_cap = (size_t)64 << 20;
+Context::Context(cudaStream_t s, int prec, size_t ring_bytes) : st(s), precision(prec) {
+  ring_cap = ring_bytes;
+  TD_CHECK_CUDA(cudaGetDevice(&device));
+  TD_CHECK_CUDA(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, device));
   TD_CHECK_CUDA(cudaMallocHost((void**)&h_ring, ring_cap));
   TD_CHECK_CUDA(cudaMalloc((void**)&d_ring, ring_cap));
   status = dev_alloc(64, st);
@@ -101,6 +103,7 @@ Context::Context(cudaStream_t s, int prec) : st(s), precision(prec) {
 }
 
 Context::~Context() {
+  workers.clear();
   cudaStreamSynchronize(st);
   for (auto& p : pending) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
   ident.reset();
@@ -118,8 +121,9 @@ const void* Context::stage(const void* src, size_t bytes) {
     DevPtr b = dev_alloc(need, st);
     TD_CHECK_CUDA(cudaMemcpyAsync(b->p, src, bytes, cudaMemcpyHostToDevice, st));
     TD_CHECK_CUDA(cudaStreamSynchronize(st));
-    static std::vector<DevPtr> keep;
-    keep.push_back(b);
+    // its stream-ordered free is enqueued when the last holder lets go, so
+    // keeping it here until the context's next synchronisation is enough
+    oversize.push_back(b);
     return b->p;
   }
   if (ring_off + need > ring_cap) {
@@ -168,6 +172,7 @@ void Context::collect_stats() {
 
 void Context::sync() {
   TD_CHECK_CUDA(cudaStreamSynchronize(st));
+  oversize.clear();
   check_device_errors();
 }
 
@@ -315,17 +320,31 @@ struct GemmBatch {
     std::vector<int> tile_task;
     std::vector<GemmTask> tk;
     std::vector<ZeroRegion> zero;
-    for (auto& t : tasks) {
+    // Split-K: long K runs are shared by several CTAs that accumulate
+    // atomically into a zeroed output.  The chunk count per CTA is chosen so
+    // that the launch has about `per_sm` work units per SM (the FP64 pipe
+    // and the tensor pipe are per-SM resources; a launch with fewer units
+    // than SMs leaves the rest idle), with at least `min_chunks` K chunks
+    // per unit to amortise the atomic epilogue.
+    const int kc = fp64 ? 8 : tc_stage_k();
+    const int per_sm = fp64 ? 4 : 3, min_chunks = fp64 ? 2 : 4;
+    std::vector<long long> stages(tasks.size(), 0);
+    long long total = 0;
+    for (size_t i = 0; i < tasks.size(); ++i) {
+      const GemmTask& t = tasks[i];
+      if (t.M <= 0 || t.N <= 0) continue;
+      for (int e = t.term_begin; e < t.term_end; ++e) stages[i] += (terms[e].K + kc - 1) / kc;
+      total += (long long)((t.M + bm - 1) / bm) * ((t.N + bn - 1) / bn) * std::max(1LL, stages[i]);
+    }
+    const long long units = (long long)std::max(1, c.n_sm) * per_sm;
+    const long long chunk = std::max<long long>(min_chunks, total / units);
+    for (size_t i = 0; i < tasks.size(); ++i) {
+      GemmTask& t = tasks[i];
       if (t.M <= 0 || t.N <= 0) continue;
       t.tiles_m = (t.M + bm - 1) / bm;
       int tn = (t.N + bn - 1) / bn;
-      // long K runs are shared by several CTAs (>= 8 K chunks each) that
-      // accumulate atomically into a zeroed output
       {
-        const int kc = fp64 ? 8 : tc_stage_k();
-        long long stages = 0;
-        for (int e = t.term_begin; e < t.term_end; ++e) stages += (terms[e].K + kc - 1) / kc;
-        t.splits = (int)std::min<long long>(64, std::max<long long>(1, stages / 8));
+        t.splits = (int)std::min<long long>(64, std::max<long long>(1, stages[i] / chunk));
         if (t.splits > 1 && !t.beta) {
           if (t.ldc != t.N) throw Error(TDMPS_ERR_INVALID_ARG, "split-K output must be contiguous");
           zero.push_back({t.C, (size_t)t.M * t.N * (t.tc ? sizeof(float2) : sizeof(double2))});
@@ -754,7 +773,8 @@ void run_qr(Context& c, FactWork& fw) {
   for (auto& t : fw.tasks) {
     if (t.m > QR_MAX_ROWS || t.n > QR_MAX_COLS)
       throw Error(TDMPS_ERR_INVALID_ARG, "QR block exceeds the supported size");
-    fl += 16.0 * t.m * t.n * t.n;
+    // algorithmic work: one classical Gram-Schmidt pass, 8 m n min(m, n)
+    fl += 8.0 * t.m * t.n * std::min(t.m, t.n);
   }
   const FactTask* d = c.stage(fw.tasks);
   cudaEvent_t ev;

@@ -21,16 +21,30 @@ struct KStat {
   double ms = 0.0, flops = 0.0, bytes = 0.0;
 };
 
+struct Context;
+
+// A worker of the instance batch: its own non-blocking stream and context
+// (staging ring, status words, MPO caches), used by one host thread at a time.
+struct Worker {
+  cudaStream_t st = nullptr;
+  std::unique_ptr<Context> c;
+  Worker(int precision, size_t ring_bytes);
+  ~Worker();
+};
+
 struct Context {
   cudaStream_t st = nullptr;
+  int device = 0;
   int precision = TDMPS_FP64;
   int n_two_site = 2, n_one_site = 2;
-  bool krylov_fp64 = false;   // Krylov inner products in FP64 regardless of precision
+  bool krylov_fp64 = true;    // Krylov inner products in FP64 regardless of precision
+  int n_sm = 0;               // streaming multiprocessors of the device
   std::string err;
   // staging ring for task lists
   char* h_ring = nullptr;
   char* d_ring = nullptr;
   size_t ring_cap = 0, ring_off = 0;
+  std::vector<DevPtr> oversize;   // task lists larger than the ring, until the next sync()
   // statistics
   bool stats = false;
   KStat kstat[TDMPS_KSTAT_COUNT];
@@ -42,7 +56,9 @@ struct Context {
   std::unique_ptr<MPOd> rdm;     // density-matrix MPO cache (by L)
   std::unique_ptr<std::vector<MPOd>> rdm_read;   // its per-bond readouts (by L)
 
-  explicit Context(cudaStream_t s, int prec);
+  std::vector<std::unique_ptr<Worker>> workers;   // instance-batch workers (lazy)
+
+  explicit Context(cudaStream_t s, int prec, size_t ring_bytes = (size_t)64 << 20);
   ~Context();
 
   // copy a host array into device memory valid until the stream passes it
@@ -160,6 +176,19 @@ bool apply_site_op(Context& c, const MPSd& in, int site, int spin, bool dagger, 
 // Eq. (green_time) at tau = 0, dt, ..., n_steps dt (method 0 Krylov, 1 RK4)
 void green_function(Context& c, const MPOd& H, const MPSd& psi0, int i, int j, double dt,
                     int n_steps, int method, int m, bool orth, const FitOpts& o, cplx* G);
+// Many independent time evolutions at once (batch.cpp): item k advances
+// *states[k] by n_steps[k] steps of dt[k] with its own MPO, D and eps;
+// method 0 Krylov (m, orth), 1 RK4.  status[k] receives 0 or the item's
+// error code (its state is then unchanged) and msgs[k] the message.
+struct BatchItem {
+  const MPOd* H;
+  MPSd* state;
+  double dt;
+  int n_steps, D;
+  double eps;
+};
+void evolve_batch(Context& c, const std::vector<BatchItem>& items, int method, int m, bool orth,
+                  int n_workers, int* status, std::vector<std::string>& msgs);
 // overlap with all blocks in a fixed device array (noalloc.cu)
 cplx overlap_noalloc(Context& c, const MPSd& bra, const MPSd& ket);
 

@@ -5,10 +5,28 @@
 
 #include <cmath>
 #include <cstdio>
+#include <mutex>
+#include <set>
+#include <tuple>
 
 #include "kernels.hpp"
 
 namespace tdmps {
+
+// Raise a kernel's dynamic shared-memory limit once per (device, kernel, size).
+// Thread-safe; a failure is left for the launch to report.
+void set_smem_limit(const void* func, int bytes) {
+  static std::mutex mu;
+  static std::set<std::tuple<int, const void*, int>> done;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return;
+  std::lock_guard<std::mutex> lk(mu);
+  auto key = std::make_tuple(dev, func, bytes);
+  if (done.count(key)) return;
+  if (cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) == cudaSuccess)
+    done.insert(key);
+}
+
 
 // ------------------------------------------------------------------ complex helpers
 
@@ -493,19 +511,20 @@ void launch_svd(const FactTask* d_tasks, int ntasks, int* d_status, cudaStream_t
   // static shared: perm (4 KB) + scalars
   const size_t cap = 227 * 1024 - 5 * 1024;
   size_t dyn = max_bytes < cap ? max_bytes : cap;
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_svd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cap);
-    attr = true;
-  }
+  set_smem_limit((const void*)k_svd, (int)cap);
   k_svd<<<ntasks, SVD_THREADS, dyn, st>>>(d_tasks, d_status, (int)dyn);
 }
 
 // ------------------------------------------------------------------ CGS2 QR
 
-// Classical Gram-Schmidt with one re-orthogonalisation on a column-major
-// m x n matrix.  Columns whose residual norm falls to <= 1e-12 times the
-// largest input column norm are dependent: they add no new direction.  The
+// Classical Gram-Schmidt with re-orthogonalisation on a column-major m x n
+// matrix.  The second projection pass runs when the first one removed more
+// than 1 - 1/sqrt(2) of the column's norm (the Daniel-Gragg-Kaufman-Stewart
+// criterion: otherwise one classical pass is already orthogonal to working
+// precision); it halves the FP64 work on well-conditioned blocks.  Columns
+// whose residual norm falls to <= 1e-12 times the largest input column norm
+// are dependent: they add no new direction (such a column always lost far
+// more than the criterion's share, so it always gets both passes).  The
 // independent directions are stored compactly in the first columns (at most
 // k = min(m, n)), the remaining of the first k columns are zero.  R (k x n,
 // column-major, leading dimension n) holds the coefficients, so that
@@ -549,7 +568,18 @@ __global__ void __launch_bounds__(QR_THREADS) k_qr(const FactTask* __restrict__ 
     for (int i = threadIdx.x; i < m; i += blockDim.x) v[i] = A[(size_t)j * m + i];
     __syncthreads();
     const int q = nq;
-    for (int pass = 0; pass < 2; ++pass) {
+    double norm_before = 0.0;
+    if (q > 0 && warp == 0) {
+      double s2 = 0.0;
+      for (int i = lane; i < m; i += 32) s2 += cabs2(v[i]);
+      s2 = warp_sum(s2);
+      if (lane == 0) vn = s2;
+    }
+    if (q > 0) {
+      __syncthreads();
+      norm_before = vn;
+    }
+    for (int pass = 0; pass < 2 && q > 0; ++pass) {
       for (int cc = warp; cc < q; cc += nwarp) {
         const double2* qc = A + (size_t)cc * m;
         double re = 0.0, im = 0.0;
@@ -572,6 +602,18 @@ __global__ void __launch_bounds__(QR_THREADS) k_qr(const FactTask* __restrict__ 
         *rr = cadd(*rr, coef[cc]);
       }
       __syncthreads();
+      if (pass == 0) {
+        if (warp == 0) {
+          double s2 = 0.0;
+          for (int i = lane; i < m; i += 32) s2 += cabs2(v[i]);
+          s2 = warp_sum(s2);
+          if (lane == 0) vn = s2;
+        }
+        __syncthreads();
+        const bool again = vn < 0.5 * norm_before;   // |v'|^2 < |v|^2 / 2
+        __syncthreads();
+        if (!again) break;
+      }
     }
     if (warp == 0) {
       double s2 = 0.0;
@@ -603,11 +645,7 @@ __global__ void __launch_bounds__(QR_THREADS) k_qr(const FactTask* __restrict__ 
 
 void launch_qr(const FactTask* d_tasks, int ntasks, cudaStream_t st) {
   if (ntasks <= 0) return;
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_qr, cudaFuncAttributeMaxDynamicSharedMemorySize, QR_SMEM);
-    attr = true;
-  }
+  set_smem_limit((const void*)k_qr, QR_SMEM);
   k_qr<<<ntasks, QR_THREADS, QR_SMEM, st>>>(d_tasks);
 }
 

@@ -98,6 +98,8 @@ void launch_zero_regions(const ZeroRegion* d_regions, int n, cudaStream_t st);
 // out (double2) = in (element type et), n elements
 void launch_to_double(const void* in, int et, double2* out, size_t n, cudaStream_t st);
 void launch_fill_one(void* p, int et, cudaStream_t st);
+// raise a kernel's dynamic shared-memory limit once per device (thread-safe)
+void set_smem_limit(const void* func, int bytes);
 void launch_copy(const CopyTask* d_tasks, int ntasks, int to_work, cudaStream_t st);
 void launch_scatter(const ScatterTask* d_tasks, int ntasks, cudaStream_t st);
 void launch_zero(double2* p, size_t n, cudaStream_t st);

@@ -396,19 +396,11 @@ void launch_gemm_tc(const GemmTask* d_tasks, const GemmTerm* d_terms, const int*
   if (ntiles <= 0) return;
   if (mode == 0) {
     const int smem = 2 * (TILE_A_BYTES + TILE_B_BYTES);
-    static bool attr = false;
-    if (!attr) {
-      cudaFuncSetAttribute(k_gemm_tc<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-      attr = true;
-    }
+    set_smem_limit((const void*)k_gemm_tc<0>, smem);
     k_gemm_tc<0><<<ntiles, TC_THREADS, smem, st>>>(d_tasks, d_terms, d_tile_task, d_err);
   } else {
     const int smem = 2 * 2 * (TILE_A_BYTES + TILE_B_BYTES);
-    static bool attr = false;
-    if (!attr) {
-      cudaFuncSetAttribute(k_gemm_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-      attr = true;
-    }
+    set_smem_limit((const void*)k_gemm_tc<1>, smem);
     k_gemm_tc<1><<<ntiles, TC_THREADS, smem, st>>>(d_tasks, d_terms, d_tile_task, d_err);
   }
 }
