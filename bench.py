@@ -170,6 +170,8 @@ def roofline(st, precision):
         tf32 = bf16 * (1100.0 / 2250.0)
         if precision == "tf32x3":
             peak, src = tf32 / 3.0, "measured sustained bf16 x nominal TF32/bf16 (1.1/2.25), /3 for split TF32"
+        elif precision == "bf16":
+            peak, src = bf16, "measured sustained bf16"
         else:
             peak, src = tf32, "measured sustained bf16 x nominal TF32/bf16 (1.1/2.25)"
         kern, bound, unit = "k_gemm_tc (tcgen05 grouped complex block GEMM)", "tensor", "TFLOP/s"
@@ -241,7 +243,7 @@ def run_batch(args, td, ctx, torch, local):
     line = {"metric": "instance RK4 steps/s, 64 uneven instances", "value": n * args.steps / (ms / 1e3),
             "unit": "instance-steps/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": {"fp64": "f64", "tf32": "tf32", "tf32x3": "tf32x3"}[args.precision],
+            "vs_baseline": None, "dtype": {"fp64": "f64", "tf32": "tf32", "tf32x3": "tf32x3", "bf16": "bf16"}[args.precision],
             "data": "synthetic",
             "config": {"workload": "64 instances, seeds 0..63, L in {8,10,12,14}, N = L, D in "
                                    "{32,64,128}, RK4 dt=0.01, schedule %d two-site + %d one-site "
@@ -262,7 +264,7 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--precision", default="tf32x3", choices=["fp64", "tf32", "tf32x3"])
+    ap.add_argument("--precision", default="tf32x3", choices=["fp64", "tf32", "tf32x3", "bf16"])
     ap.add_argument("--no-fp64-compare", action="store_true",
                     help="skip the FP64 run of the same steps (error and FP64 steps/s)")
     ap.add_argument("--no-cpu-baseline", action="store_true")

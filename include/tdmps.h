@@ -66,8 +66,8 @@ enum {
   TDMPS_FP64 = 0,   /* complex FP64 everywhere                               */
   TDMPS_TF32 = 1,   /* TF32 tensor-core products, FP32 accumulation          */
   TDMPS_TF32X3 = 2, /* split TF32 (hi*hi + hi*lo + lo*hi), FP32 accumulation */
-  TDMPS_BF16 = 3    /* reserved: BF16 tensor-core products (not in this build,
-                       INVALID_ARG)                                          */
+  TDMPS_BF16 = 3    /* BF16 tensor-core products (kind::f16), FP32
+                       accumulation; environments stored in FP32             */
 };
 
 /* ---------------------------------------------------------------- context */
@@ -99,6 +99,21 @@ int tdmps_set_schedule(tdmps_ctx_t ctx, int n_two_site, int n_one_site);
  * orthogonalisation then sees the TF32 rounding of N and H).  The matrices
  * are accumulated and processed in FP64 either way. */
 int tdmps_set_krylov_fp64(tdmps_ctx_t ctx, int on);
+
+/* ------------------------------------------------------- orbital order */
+
+/* Fiedler ordering of the orbitals (Sec. 3.2: the molecular orbitals are
+ * ordered by a Fiedler reduction of the bandwidth of the Hamiltonian
+ * matrix).  Graph weights W_ij = |h_ij| + |(ij|ji)| (symmetrised), Laplacian
+ * D - W, and the orbitals sorted by the eigenvector of its second smallest
+ * eigenvalue (ties by index; the eigenvector's sign is chosen so that its
+ * correlation with the input order is >= 0).  perm[k] = input orbital placed
+ * at position k; permute h and eri with it before tdmps_build_mpo.  Host
+ * only, no context.  A graph whose second eigenvalue is degenerate (for
+ * example a disconnected one) has no unique Fiedler vector; the result is
+ * then one valid ordering.  Errors: INVALID_ARG (L < 1 or > 64, NULL),
+ * NONFINITE. */
+int tdmps_fiedler_order(const double* h, const double* eri, int L, int* perm);
 
 /* ------------------------------------------------------------------- MPO */
 

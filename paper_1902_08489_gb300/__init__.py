@@ -82,6 +82,7 @@ _SIGS = {
     "tdmps_apply_site_op": (I, [P, P, I, I, I, ctypes.POINTER(P)]),
     "tdmps_green_function": (I, [P, P, P, I, I, D, I, I, I, I, I, D, P]),
     "tdmps_evolve_batch": (I, [P, I, P, P, P, P, P, P, I, I, I, I, P]),
+    "tdmps_fiedler_order": (I, [P, P, I, P]),
     "tdmps_stats_enable": (I, [P, I]),
     "tdmps_stats_reset": (I, [P]),
     "tdmps_stats_get": (I, [P, I, ctypes.POINTER(KStat)]),
@@ -393,3 +394,21 @@ def evolve_batch(ctx, mpos, states, dt, n_steps, D, eps=0.0, method="rk4", m=10,
     if raise_on_error:
         _check(rc, ctx)
     return status
+
+
+def fiedler_order(h, eri) -> np.ndarray:
+    """Fiedler ordering of the orbitals: perm[k] = orbital at position k."""
+    h = np.ascontiguousarray(h, dtype=np.float64)
+    eri = np.ascontiguousarray(eri, dtype=np.float64)
+    L = h.shape[0]
+    perm = np.zeros(L, dtype=np.int32)
+    rc = lib().tdmps_fiedler_order(_ptr(h), _ptr(eri), L, _ptr(perm))
+    if rc != 0:
+        raise TdmpsError(rc, (lib().tdmps_create_error() or b"").decode())
+    return perm.astype(np.int64)
+
+
+def permute_integrals(h, eri, perm):
+    """Integrals in the orbital order perm (perm[k] = old orbital at k)."""
+    p = np.asarray(perm)
+    return np.asarray(h)[np.ix_(p, p)], np.asarray(eri)[np.ix_(p, p, p, p)]

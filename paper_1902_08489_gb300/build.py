@@ -17,7 +17,7 @@ OUT = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT, "libtdmps.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["kernels.cu", "kernels_tc.cu", "noalloc.cu", "engine.cpp", "batch.cpp", "mpo_build.cpp",
-           "capi.cpp"]
+           "ordering.cpp", "capi.cpp"]
 
 
 def nvcc() -> str:

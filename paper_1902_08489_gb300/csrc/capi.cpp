@@ -70,9 +70,8 @@ extern "C" {
 
 int tdmps_create(tdmps_ctx_t* ctx, void* cuda_stream, int precision) {
   if (!ctx) { g_create_err = "ctx is NULL"; return TDMPS_ERR_INVALID_ARG; }
-  if (precision < TDMPS_FP64 || precision > TDMPS_TF32X3) {
-    g_create_err = precision == TDMPS_BF16 ? "BF16 contractions are not available in this build"
-                                           : "unknown precision";
+  if (precision < TDMPS_FP64 || precision > TDMPS_BF16) {
+    g_create_err = "unknown precision";
     return TDMPS_ERR_INVALID_ARG;
   }
   try {
@@ -102,9 +101,7 @@ const char* tdmps_create_error(void) { return g_create_err.c_str(); }
 int tdmps_set_precision(tdmps_ctx_t ctx, int precision) {
   if (!ctx) return TDMPS_ERR_INVALID_ARG;
   return guard(ctx, [&] {
-    need(precision >= TDMPS_FP64 && precision <= TDMPS_TF32X3,
-         precision == TDMPS_BF16 ? "BF16 contractions are not available in this build"
-                                 : "unknown precision");
+    need(precision >= TDMPS_FP64 && precision <= TDMPS_BF16, "unknown precision");
     ctx->c->precision = precision;
   });
 }
@@ -432,6 +429,19 @@ int tdmps_evolve_batch(tdmps_ctx_t ctx, int n, const tdmps_mpo_t* mpos, tdmps_mp
       }
   });
   return rc != TDMPS_OK ? rc : first;
+}
+
+int tdmps_fiedler_order(const double* h, const double* eri, int L, int* perm) {
+  try {
+    if (!h || !eri || !perm) return TDMPS_ERR_INVALID_ARG;
+    fiedler_order(h, eri, L, perm);
+    return TDMPS_OK;
+  } catch (const Error& e) {
+    g_create_err = e.what();
+    return e.code;
+  } catch (...) {
+    return TDMPS_ERR_INVALID_ARG;
+  }
 }
 
 int tdmps_stats_enable(tdmps_ctx_t ctx, int enable) {

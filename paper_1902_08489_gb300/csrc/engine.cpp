@@ -314,9 +314,57 @@ struct GemmBatch {
     flops += 8.0 * t.M * t.N * K;
     bytes += (t.ta ? 8.0 : 16.0) * t.M * K + (t.tb ? 8.0 : 16.0) * K * t.N;
   }
+  // C^T = op(B)^T op(A)^T: the operand modes of the transposed product
+  static int op_t(int op) {
+    switch (op) {
+      case OP_N: return OP_T;
+      case OP_T: return OP_N;
+      case OP_C: return OP_J;
+      default: return OP_C;
+    }
+  }
+  // FP64 tiles skip whole warps of rows past the block edge, so a task whose
+  // N is the short side runs transposed (rows <- the short side).
+  void orient_fp64() {
+    for (auto& t : tasks) {
+      if (t.M <= 0 || t.N <= 0 || t.N >= t.M || t.N >= 32) continue;
+      for (int e = t.term_begin; e < t.term_end; ++e) {
+        std::swap(terms[e].A, terms[e].B);
+        std::swap(terms[e].lda, terms[e].ldb);
+      }
+      const int oa = t.opA;
+      t.opA = op_t(t.opB);
+      t.opB = op_t(oa);
+      std::swap(t.ta, t.tb);
+      std::swap(t.M, t.N);
+      t.ct = 1;
+    }
+  }
+  // Tensor-core tiles are 128 rows (the MMA M) by up to 64 complex columns
+  // (the MMA N rounds to 8 complex), so a task with few rows and many
+  // columns runs transposed: its long side fills the 128 TMEM lanes.
+  void orient_tc() {
+    for (auto& t : tasks) {
+      if (t.M <= 0 || t.N <= 0 || t.M >= tc_tile_m() || t.N <= t.M) continue;
+      const long long pad_now = (long long)((t.M + 127) / 128) * 128 * ((t.N + 7) / 8) * 8;
+      const long long pad_t = (long long)((t.N + 127) / 128) * 128 * ((t.M + 7) / 8) * 8;
+      if (pad_t >= pad_now) continue;
+      for (int e = t.term_begin; e < t.term_end; ++e) {
+        std::swap(terms[e].A, terms[e].B);
+        std::swap(terms[e].lda, terms[e].ldb);
+      }
+      const int oa = t.opA;
+      t.opA = op_t(t.opB);
+      t.opB = op_t(oa);
+      std::swap(t.ta, t.tb);
+      std::swap(t.M, t.N);
+      t.ct = 1;
+    }
+  }
   void run() {
     const int bm = fp64 ? 32 : tc_tile_m();
     const int bn = fp64 ? 32 : tc_tile_n();
+    if (fp64) orient_fp64(); else orient_tc();
     std::vector<int> tile_task;
     std::vector<GemmTask> tk;
     std::vector<ZeroRegion> zero;
@@ -346,7 +394,8 @@ struct GemmBatch {
       {
         t.splits = (int)std::min<long long>(64, std::max<long long>(1, stages[i] / chunk));
         if (t.splits > 1 && !t.beta) {
-          if (t.ldc != t.N) throw Error(TDMPS_ERR_INVALID_ARG, "split-K output must be contiguous");
+          if (t.ldc != (t.ct ? t.M : t.N))
+            throw Error(TDMPS_ERR_INVALID_ARG, "split-K output must be contiguous");
           zero.push_back({t.C, (size_t)t.M * t.N * (t.tc ? sizeof(float2) : sizeof(double2))});
         }
       }
@@ -366,7 +415,8 @@ struct GemmBatch {
     if (fp64)
       launch_gemm(dt, (int)tk.size(), dm, dtt, (int)tile_task.size(), c.st);
     else
-      launch_gemm_tc(dt, dm, dtt, (int)tile_task.size(), c.precision == TDMPS_TF32X3 ? 1 : 0,
+      launch_gemm_tc(dt, dm, dtt, (int)tile_task.size(),
+                     c.precision == TDMPS_TF32X3 ? 1 : c.precision == TDMPS_BF16 ? 2 : 0,
                      c.tc_err(), c.st);
     c.kend(kind, ev, flops, bytes);
   }
@@ -779,7 +829,7 @@ void run_qr(Context& c, FactWork& fw) {
   const FactTask* d = c.stage(fw.tasks);
   cudaEvent_t ev;
   c.kbegin(TDMPS_KSTAT_QR, &ev);
-  launch_qr(d, (int)fw.tasks.size(), c.st);
+  launch_qr(d, (int)fw.tasks.size(), c.st, fw.tasks.data());
   c.kend(TDMPS_KSTAT_QR, ev, fl, 0.0);
 }
 

@@ -154,5 +154,7 @@ MPOd build_qc_mpo(const double* h, const double* eri, int L, double e0);
 MPOd build_identity_mpo(int L);
 MPOd build_rdm_mpo(int L);          // channels {I, c+_{i s}: i < k}; see rdm code
 void upload_mpo(MPOd& m, cudaStream_t st);
+// Fiedler ordering of the orbitals (ordering.cpp): perm[k] = orbital at position k
+void fiedler_order(const double* h, const double* eri, int L, int* perm);
 
 }  // namespace tdmps

@@ -1,6 +1,7 @@
 // FP64 device kernels of the tdmps library: grouped complex block GEMM, sparse
 // MPO-tensor application, block gather/scatter, one-sided Jacobi SVD, CGS2
 // QR, the truncation rule, and the small Krylov algebra.
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -81,6 +82,9 @@ __global__ void __launch_bounds__(256) k_gemm(const GemmTask* __restrict__ tasks
   const int m0 = (rest % t.tiles_m) * GT;
   const int n0 = (rest / t.tiles_m) * GT;
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  // rows past the block edge do no arithmetic (a warp covers 4 rows, so a
+  // short block leaves whole warps idle instead of multiplying zeros)
+  const bool rows_live = m0 + 2 * ty < t.M;
   double2 acc[2][2];
   for (int i = 0; i < 2; ++i)
     for (int j = 0; j < 2; ++j) acc[i][j] = make_double2(0.0, 0.0);
@@ -107,14 +111,28 @@ __global__ void __launch_bounds__(256) k_gemm(const GemmTask* __restrict__ tasks
         Bs[kk][j] = load_op((const double2*)g.B, g.ldb, t.opB, k0 + kk, n0 + j, g.K, t.N);
       }
       __syncthreads();
+      if (rows_live) {
+        if (k0 + GK <= g.K) {
 #pragma unroll
-      for (int k = 0; k < GK; ++k) {
-        double2 a0 = As[k][ty * 2], a1 = As[k][ty * 2 + 1];
-        double2 b0 = Bs[k][tx * 2], b1 = Bs[k][tx * 2 + 1];
-        acc[0][0] = cfma(a0, b0, acc[0][0]);
-        acc[0][1] = cfma(a0, b1, acc[0][1]);
-        acc[1][0] = cfma(a1, b0, acc[1][0]);
-        acc[1][1] = cfma(a1, b1, acc[1][1]);
+          for (int k = 0; k < GK; ++k) {
+            double2 a0 = As[k][ty * 2], a1 = As[k][ty * 2 + 1];
+            double2 b0 = Bs[k][tx * 2], b1 = Bs[k][tx * 2 + 1];
+            acc[0][0] = cfma(a0, b0, acc[0][0]);
+            acc[0][1] = cfma(a0, b1, acc[0][1]);
+            acc[1][0] = cfma(a1, b0, acc[1][0]);
+            acc[1][1] = cfma(a1, b1, acc[1][1]);
+          }
+        } else {   // ragged last chunk: only the valid K
+          const int kl = g.K - k0;
+          for (int k = 0; k < kl; ++k) {
+            double2 a0 = As[k][ty * 2], a1 = As[k][ty * 2 + 1];
+            double2 b0 = Bs[k][tx * 2], b1 = Bs[k][tx * 2 + 1];
+            acc[0][0] = cfma(a0, b0, acc[0][0]);
+            acc[0][1] = cfma(a0, b1, acc[0][1]);
+            acc[1][0] = cfma(a1, b0, acc[1][0]);
+            acc[1][1] = cfma(a1, b1, acc[1][1]);
+          }
+        }
       }
       __syncthreads();
     }
@@ -127,7 +145,7 @@ __global__ void __launch_bounds__(256) k_gemm(const GemmTask* __restrict__ tasks
     for (int j = 0; j < 2; ++j) {
       int r = m0 + ty * 2 + i, c = n0 + tx * 2 + j;
       if (r < t.M && c < t.N) {
-        double2* p = (double2*)t.C + (size_t)r * t.ldc + c;
+        double2* p = (double2*)t.C + (t.ct ? (size_t)c * t.ldc + r : (size_t)r * t.ldc + c);
         double2 v = cmul(alpha, acc[i][j]);
         if (t.splits > 1) {
           atomicAdd(&p->x, v.x);
@@ -179,13 +197,22 @@ __global__ void __launch_bounds__(256) k_wstage(const WTask* __restrict__ tasks,
                                                 const int* __restrict__ ent_w,
                                                 const double* __restrict__ ent_v) {
   using R = typename WAcc<T>::R;
-  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
-       idx += (int64_t)gridDim.x * blockDim.x) {
-    int lo = 0, hi = ntasks - 1;
+  // each CTA owns one contiguous range of the flat output index, so a
+  // thread finds its task once (binary search) and then only steps forward
+  const int64_t per = (total + gridDim.x - 1) / gridDim.x;
+  const int64_t beg = (int64_t)blockIdx.x * per;
+  const int64_t end = beg + per < total ? beg + per : total;
+  int lo = 0;
+  if (beg + threadIdx.x < end) {
+    int hi = ntasks - 1;
+    const int64_t first = beg + threadIdx.x;
     while (lo < hi) {
       int mid = (lo + hi + 1) >> 1;
-      if (tasks[mid].work_base <= idx) lo = mid; else hi = mid - 1;
+      if (tasks[mid].work_base <= first) lo = mid; else hi = mid - 1;
     }
+  }
+  for (int64_t idx = beg + threadIdx.x; idx < end; idx += blockDim.x) {
+    while (lo + 1 < ntasks && tasks[lo + 1].work_base <= idx) ++lo;
     const WTask& t = tasks[lo];
     int64_t loc = idx - t.work_base;
     int b = (int)(loc % t.cols);
@@ -530,8 +557,6 @@ void launch_svd(const FactTask* d_tasks, int ntasks, int* d_status, cudaStream_t
 // column-major, leading dimension n) holds the coefficients, so that
 // A = Q R.
 constexpr int QR_THREADS = 256;
-constexpr int QR_MAX_M = 4096;
-constexpr int QR_MAX_N = 2048;
 constexpr int QR_SMEM = 200 * 1024;   // matrix held in shared memory when it fits
 
 __global__ void __launch_bounds__(QR_THREADS) k_qr(const FactTask* __restrict__ tasks) {
@@ -643,8 +668,175 @@ __global__ void __launch_bounds__(QR_THREADS) k_qr(const FactTask* __restrict__ 
   }
 }
 
-void launch_qr(const FactTask* d_tasks, int ntasks, cudaStream_t st) {
+// The same Gram-Schmidt QR (dependency rule, conditional second pass)
+// with one sector spread over a cluster of QRC_CS CTAs: CTA `rank` holds
+// rows [rank*mc, rank*mc + mc) of the matrix in its shared memory, and every
+// inner product (projection coefficients, norms) is a partial sum per CTA
+// combined across the cluster through distributed shared memory.  Each CTA
+// writes its partial vector into a slot of every CTA, the cluster barrier
+// publishes them, and every CTA adds the slots in rank order -- so all CTAs
+// hold bit-identical sums and take identical branch decisions.  Slots are
+// double buffered: the barrier of reduction r also tells a CTA that every
+// CTA has read the buffer of reduction r - 1, which reduction r + 1 reuses.
+// A sector's FP64 work is divided by the cluster size, which is what limits
+// the single-CTA kernel on large sectors (one SM's FP64 pipe).
+constexpr int QRC_CS = 8;
+constexpr int QRC_THREADS = 256;
+
+__host__ __device__ inline int qrc_mc(int m) { return (m + QRC_CS - 1) / QRC_CS; }
+// complex elements of dynamic shared memory per CTA
+__host__ __device__ inline size_t qrc_elems(int m, int n) {
+  const size_t mc = qrc_mc(m);
+  return mc * n + mc + n + 2 * (size_t)QRC_CS * (n + 1) + 8;
+}
+
+__global__ void __launch_bounds__(QRC_THREADS) k_qr_cl(const FactTask* __restrict__ tasks) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cl = cg::this_cluster();
+  extern __shared__ double2 shc[];
+  const int rank = (int)cl.block_rank();
+  const FactTask t = tasks[blockIdx.x / QRC_CS];
+  const int m = t.m, n = t.n, kmax = m < n ? m : n;
+  const int mc = qrc_mc(m);
+  const int row0 = rank * mc;
+  const int ml = max(0, min(mc, m - row0));   // rows held here
+  const int SL = n + 1;                       // slot length
+  double2* A = shc;                           // [n][mc]
+  double2* v = A + (size_t)mc * n;            // [mc]
+  double2* coef = v + mc;                     // [n]
+  double2* slots = coef + n;                  // [2][CS][SL]
+  double2* scal = slots + 2 * (size_t)QRC_CS * SL;   // small scratch
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  int red = 0;
+  // all-reduce of len values (mine may alias out)
+  auto allreduce = [&](const double2* mine, int len, double2* out) {
+    const int buf = red & 1;
+    ++red;
+    for (int r = 0; r < QRC_CS; ++r) {
+      double2* dst = cl.map_shared_rank(slots, r) + ((size_t)buf * QRC_CS + rank) * SL;
+      for (int i = threadIdx.x; i < len; i += blockDim.x) dst[i] = mine[i];
+    }
+    cl.sync();
+    for (int i = threadIdx.x; i < len; i += blockDim.x) {
+      double2 acc = make_double2(0.0, 0.0);
+      for (int r = 0; r < QRC_CS; ++r) acc = cadd(acc, slots[((size_t)buf * QRC_CS + r) * SL + i]);
+      out[i] = acc;
+    }
+    __syncthreads();
+  };
+  // squared norm of v over all rows
+  auto vnorm2 = [&]() {
+    if (warp == 0) {
+      double s2 = 0.0;
+      for (int i = lane; i < ml; i += 32) s2 += cabs2(v[i]);
+      s2 = warp_sum(s2);
+      if (lane == 0) scal[0] = make_double2(s2, 0.0);
+    }
+    __syncthreads();
+    allreduce(scal, 1, scal + 1);
+    return scal[1].x;
+  };
+
+  for (int c = 0; c < n; ++c)
+    for (int i = threadIdx.x; i < ml; i += blockDim.x) A[(size_t)c * mc + i] = t.A[(size_t)c * m + row0 + i];
+  if (rank == 0)
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) t.V[e] = make_double2(0.0, 0.0);
+  // largest column norm
+  for (int c = warp; c < n; c += nwarp) {
+    double s2 = 0.0;
+    for (int i = lane; i < ml; i += 32) s2 += cabs2(A[(size_t)c * mc + i]);
+    s2 = warp_sum(s2);
+    if (lane == 0) coef[c] = make_double2(s2, 0.0);
+  }
+  __syncthreads();
+  allreduce(coef, n, coef);
+  double maxn = 0.0;
+  for (int c = 0; c < n; ++c) maxn = fmax(maxn, sqrt(coef[c].x));
+  __syncthreads();
+  const double tol = 1e-12 * maxn;
+  int nq = 0;
+  for (int j = 0; j < n; ++j) {
+    for (int i = threadIdx.x; i < ml; i += blockDim.x) v[i] = A[(size_t)j * mc + i];
+    __syncthreads();
+    const int q = nq;
+    double nrm2;
+    if (q == 0) {
+      nrm2 = vnorm2();
+    } else {
+      const double before = vnorm2();
+      nrm2 = 0.0;
+      for (int pass = 0; pass < 2; ++pass) {
+        for (int cc = warp; cc < q; cc += nwarp) {
+          const double2* qc = A + (size_t)cc * mc;
+          double re = 0.0, im = 0.0;
+          for (int i = lane; i < ml; i += 32) {
+            const double2 a = qc[i], b = v[i];
+            re += a.x * b.x + a.y * b.y;   // conj(q) * v
+            im += a.x * b.y - a.y * b.x;
+          }
+          re = warp_sum(re);
+          im = warp_sum(im);
+          if (lane == 0) coef[cc] = make_double2(re, im);
+        }
+        __syncthreads();
+        allreduce(coef, q, coef);
+        for (int i = threadIdx.x; i < ml; i += blockDim.x) {
+          double2 acc = v[i];
+          for (int cc = 0; cc < q; ++cc) acc = csub(acc, cmul(coef[cc], A[(size_t)cc * mc + i]));
+          v[i] = acc;
+        }
+        if (rank == 0)
+          for (int cc = threadIdx.x; cc < q; cc += blockDim.x) {
+            double2* rr = t.V + (size_t)j * n + cc;   // R[cc, j], leading dimension n
+            *rr = cadd(*rr, coef[cc]);
+          }
+        __syncthreads();
+        nrm2 = vnorm2();
+        if (pass == 0 && !(nrm2 < 0.5 * before)) break;   // one pass was enough
+      }
+    }
+    const double nrm = sqrt(nrm2);
+    if (nrm > tol && q < kmax) {
+      const double inv = 1.0 / nrm;
+      for (int i = threadIdx.x; i < ml; i += blockDim.x) A[(size_t)q * mc + i] = cscale(v[i], inv);
+      if (rank == 0 && threadIdx.x == 0) t.V[(size_t)j * n + q] = make_double2(nrm, 0.0);
+      nq = q + 1;
+    }
+    __syncthreads();
+  }
+  for (int c = 0; c < kmax; ++c)
+    for (int i = threadIdx.x; i < ml; i += blockDim.x)
+      t.A[(size_t)c * m + row0 + i] = c < nq ? A[(size_t)c * mc + i] : make_double2(0.0, 0.0);
+  // no CTA may leave while others can still write into its slots
+  cl.sync();
+}
+
+void launch_qr(const FactTask* d_tasks, int ntasks, cudaStream_t st, const FactTask* h_tasks) {
   if (ntasks <= 0) return;
+  // the cluster kernel pays off when some sector is large and all fit
+  size_t need = 0;
+  bool large = false;
+  for (int i = 0; h_tasks && i < ntasks; ++i) {
+    need = std::max(need, qrc_elems(h_tasks[i].m, h_tasks[i].n) * sizeof(double2));
+    if (h_tasks[i].n >= 16 && (long long)h_tasks[i].m * h_tasks[i].n >= 2048) large = true;
+  }
+  if (large && need <= (size_t)QR_SMEM) {
+    set_smem_limit((const void*)k_qr_cl, QR_SMEM);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(ntasks * QRC_CS));
+    cfg.blockDim = dim3(QRC_THREADS);
+    cfg.dynamicSmemBytes = need;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = QRC_CS;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, k_qr_cl, d_tasks);
+    return;
+  }
   set_smem_limit((const void*)k_qr, QR_SMEM);
   k_qr<<<ntasks, QR_THREADS, QR_SMEM, st>>>(d_tasks);
 }

@@ -33,7 +33,8 @@ struct GemmTask {
   int term_begin, term_end;
   int tiles_m, tile_base;
   int ta, tb, tc;        // element types of A, B, C: 0 double2, 1 float2 (tensor-core path)
-  int splits;            // tensor-core path: CTAs sharing the K range (atomic accumulation)
+  int splits;            // CTAs sharing the K range (atomic accumulation)
+  int ct;                // 1: the task computes C^T (M x N); element (r, c) goes to C[c][r]
 };
 
 // Sparse MPO-tensor application.  Output block Y[r][w][c] (rows r, W_out
@@ -106,7 +107,9 @@ void launch_zero(double2* p, size_t n, cudaStream_t st);
 // max_bytes: largest (m*n + n*n) * 16 of the tasks (shared-memory sizing)
 void launch_svd(const FactTask* d_tasks, int ntasks, int* d_status, cudaStream_t st,
                 size_t max_bytes);
-void launch_qr(const FactTask* d_tasks, int ntasks, cudaStream_t st);
+// h_tasks: the same tasks on the host (shapes decide between the one-CTA and
+// the cluster kernel)
+void launch_qr(const FactTask* d_tasks, int ntasks, cudaStream_t st, const FactTask* h_tasks);
 // dst[t].A (n x n) = src[t].V^H (the R factor of a QR), n = dst[t].n
 void launch_adjoint(const FactTask* d_src, const FactTask* d_dst, int n, cudaStream_t st);
 // truncation rule over nv singular values (grouped by sector, each sector

@@ -13,11 +13,14 @@
 // matrices) because the symmetry blocks are ragged and addressed through
 // arbitrary leading dimensions and operand modes; one elected thread issues
 // tcgen05.mma and commits to an mbarrier.  3xTF32 splits each operand into
-// a TF32 head and a TF32 tail and accumulates hi*hi + hi*lo + lo*hi.
+// a TF32 head and a TF32 tail and accumulates hi*hi + hi*lo + lo*hi.  The
+// BF16 mode rounds both operands to BF16 (kind::f16, FP32 accumulation).
 //
 // Every wait is bounded: a stuck barrier sets the error word, the CTA waits
 // (bounded) for its own MMAs, frees its TMEM and returns.
 #include <cuda_runtime.h>
+
+#include <cuda_bf16.h>
 
 #include <cstdint>
 
@@ -56,6 +59,34 @@ __device__ __forceinline__ uint64_t make_desc(uint32_t saddr) {
   const uint64_t lbo = 128, sbo = (TC_KR / 4) * 128;
   return (uint64_t)((saddr >> 4) & 0x3FFF) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
          ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | (1ull << 46);
+}
+
+// BF16 operands: element (r, k) of a rows x 16 tile, 2-byte elements
+__device__ __forceinline__ int canon_off16(int r, int k) {
+  return ((r >> 3) * 2 + (k >> 3)) * 128 + (r & 7) * 16 + (k & 7) * 2;
+}
+__device__ __forceinline__ uint64_t make_desc16(uint32_t saddr) {
+  const uint64_t lbo = 128, sbo = 2 * 128;
+  return (uint64_t)((saddr >> 4) & 0x3FFF) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | (1ull << 46);
+}
+// instruction descriptor: F32 accumulator, BF16 A and B (kind::f16), K-major
+__device__ __forceinline__ uint32_t make_idesc_bf16(int n_real) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n_real >> 3) << 17) |
+         ((uint32_t)(TC_BM >> 4) << 24);
+}
+__device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t da, uint64_t db, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n"
+      :
+      : "r"(tmem), "l"(da), "l"(db), "r"(idesc), "r"(accumulate));
+}
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+  __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+  return *(uint32_t*)&v;
 }
 
 // instruction descriptor: F32 accumulator, TF32 A and B, both K-major
@@ -158,13 +189,13 @@ __device__ __forceinline__ float2 load_el(const void* P, int t, int ld, int op, 
   return v;
 }
 
-template <int MODE>   // 0: TF32, 1: 3xTF32
-__global__ void __launch_bounds__(TC_THREADS) k_gemm_tc(const GemmTask* __restrict__ tasks,
+template <int MODE>   // 0: TF32, 1: 3xTF32, 2: BF16
+__global__ void __launch_bounds__(TC_THREADS, 3) k_gemm_tc(const GemmTask* __restrict__ tasks,
                                                         const GemmTerm* __restrict__ terms,
                                                         const int* __restrict__ tile_task,
                                                         int* err) {
   extern __shared__ __align__(1024) unsigned char sm[];
-  constexpr int NSPLIT = MODE == 0 ? 1 : 2;                 // operand tiles per stage (hi[, lo])
+  constexpr int NSPLIT = MODE == 1 ? 2 : 1;                 // operand tiles per stage (hi[, lo])
   constexpr int BUF_BYTES = NSPLIT * (TILE_A_BYTES + TILE_B_BYTES);
   __shared__ __align__(8) uint64_t mbar[2];
   __shared__ uint32_t tmem_base;
@@ -180,7 +211,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_gemm_tc(const GemmTask* __restri
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int ncols = min(TC_BNC, t.N - n0);
   const int nreal = ((2 * ncols + 15) / 16) * 16;   // MMA N: multiple of 16
-  const uint32_t idesc = make_idesc_tf32(nreal);
+  const uint32_t idesc = MODE == 2 ? make_idesc_bf16(nreal) : make_idesc_tf32(nreal);
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n"
@@ -218,6 +249,31 @@ __global__ void __launch_bounds__(TC_THREADS) k_gemm_tc(const GemmTask* __restri
 
   uint32_t uses[2] = {0u, 0u};
   bool ok = true;
+  // The global loads of stage s + 1 are issued right after the MMAs of stage
+  // s, into registers, so their latency overlaps the MMAs and the wait for
+  // the next shared-memory buffer.
+  const int ra_r = threadIdx.x & (TC_BM - 1);
+  const int ra_k = (threadIdx.x >> 7) * (TC_BKC / 2);
+  const int rb_n = threadIdx.x & (TC_BNC - 1);
+  const int rb_k = (threadIdx.x >> 6) * (TC_BKC / 4);
+  float2 ra[TC_BKC / 2], rb[TC_BKC / 4];
+  float2 sc = make_float2(1.f, 0.f);
+  auto load_stage = [&](int ee, int kk0) {
+    const GemmTerm g = terms[ee];
+    double2 scd = g.scale;
+    if (g.scale_ptr) {
+      const double2 p = *g.scale_ptr;
+      scd = make_double2(scd.x * p.x - scd.y * p.y, scd.x * p.y + scd.y * p.x);
+    }
+    sc = make_float2((float)scd.x, (float)scd.y);
+#pragma unroll
+    for (int j = 0; j < TC_BKC / 2; ++j)
+      ra[j] = load_el(g.A, t.ta, g.lda, t.opA, m0 + ra_r, kk0 + ra_k + j, t.M, g.K);
+#pragma unroll
+    for (int j = 0; j < TC_BKC / 4; ++j)
+      rb[j] = load_el(g.B, t.tb, g.ldb, t.opB, kk0 + rb_k + j, n0 + rb_n, g.K, t.N);
+  };
+  if (count > 0) load_stage(e, k0);
   for (int s = 0; s < count && ok; ++s) {
     const int b = s & 1;
     unsigned char* sA = sm + b * BUF_BYTES;
@@ -228,48 +284,42 @@ __global__ void __launch_bounds__(TC_THREADS) k_gemm_tc(const GemmTask* __restri
         abort_flag = 1;
       }
     }
-    const GemmTerm g = terms[e];
-    double2 scd = g.scale;
-    if (g.scale_ptr) {
-      const double2 p = *g.scale_ptr;
-      scd = make_double2(scd.x * p.x - scd.y * p.y, scd.x * p.y + scd.y * p.x);
-    }
-    const float2 sc = make_float2((float)scd.x, (float)scd.y);
-    // ---- stage A: 128 rows x 8 complex; thread -> row, 4 complex of K
-    {
-      const int r = threadIdx.x & (TC_BM - 1);
-      const int kq = (threadIdx.x >> 7) * (TC_BKC / 2);
+    // ---- A: 128 rows x 8 complex; thread -> row, 4 complex of K
 #pragma unroll
-      for (int j = 0; j < TC_BKC / 2; ++j) {
-        const int kk = kq + j;
-        float2 a0 = load_el(g.A, t.ta, g.lda, t.opA, m0 + r, k0 + kk, t.M, g.K);
-        float2 a = make_float2(sc.x * a0.x - sc.y * a0.y, sc.x * a0.y + sc.y * a0.x);
-        float2 hi = make_float2(to_tf32(a.x), to_tf32(a.y));
-        *(float2*)(sA + canon_off(r, 2 * kk)) = hi;
-        if (MODE == 1) {
-          float2 lo2 = make_float2(to_tf32(a.x - hi.x), to_tf32(a.y - hi.y));
-          *(float2*)(sA + TILE_A_BYTES + canon_off(r, 2 * kk)) = lo2;
-        }
+    for (int j = 0; j < TC_BKC / 2; ++j) {
+      const int kk = ra_k + j;
+      const float2 a0 = ra[j];
+      const float2 a = make_float2(sc.x * a0.x - sc.y * a0.y, sc.x * a0.y + sc.y * a0.x);
+      if (MODE == 2) {
+        *(uint32_t*)(sA + canon_off16(ra_r, 2 * kk)) = pack_bf16(a.x, a.y);
+        continue;
+      }
+      const float2 hi = make_float2(to_tf32(a.x), to_tf32(a.y));
+      *(float2*)(sA + canon_off(ra_r, 2 * kk)) = hi;
+      if (MODE == 1) {
+        const float2 lo2 = make_float2(to_tf32(a.x - hi.x), to_tf32(a.y - hi.y));
+        *(float2*)(sA + TILE_A_BYTES + canon_off(ra_r, 2 * kk)) = lo2;
       }
     }
-    // ---- stage B-tilde (K-major, rows = real N): thread -> column n, 2 complex of K
-    {
-      const int n = threadIdx.x & (TC_BNC - 1);
-      const int kq = (threadIdx.x >> 6) * (TC_BKC / 4);
+    // ---- B-tilde (K-major, rows = real N): thread -> column n, 2 complex of K
 #pragma unroll
-      for (int j = 0; j < TC_BKC / 4; ++j) {
-        const int kk = kq + j;
-        float2 bv = load_el(g.B, t.tb, g.ldb, t.opB, k0 + kk, n0 + n, g.K, t.N);
-        float2 hr = make_float2(to_tf32(bv.x), to_tf32(-bv.y));   // row 2n:   (br, -bi)
-        float2 hi2 = make_float2(to_tf32(bv.y), to_tf32(bv.x));   // row 2n+1: (bi,  br)
-        *(float2*)(sB + canon_off(2 * n, 2 * kk)) = hr;
-        *(float2*)(sB + canon_off(2 * n + 1, 2 * kk)) = hi2;
-        if (MODE == 1) {
-          float2 lr = make_float2(to_tf32(bv.x - hr.x), to_tf32(-bv.y - hr.y));
-          float2 li = make_float2(to_tf32(bv.y - hi2.x), to_tf32(bv.x - hi2.y));
-          *(float2*)(sB + TILE_B_BYTES + canon_off(2 * n, 2 * kk)) = lr;
-          *(float2*)(sB + TILE_B_BYTES + canon_off(2 * n + 1, 2 * kk)) = li;
-        }
+    for (int j = 0; j < TC_BKC / 4; ++j) {
+      const int kk = rb_k + j;
+      const float2 bv = rb[j];
+      if (MODE == 2) {
+        *(uint32_t*)(sB + canon_off16(2 * rb_n, 2 * kk)) = pack_bf16(bv.x, -bv.y);
+        *(uint32_t*)(sB + canon_off16(2 * rb_n + 1, 2 * kk)) = pack_bf16(bv.y, bv.x);
+        continue;
+      }
+      const float2 hr = make_float2(to_tf32(bv.x), to_tf32(-bv.y));   // row 2n:   (br, -bi)
+      const float2 hi2 = make_float2(to_tf32(bv.y), to_tf32(bv.x));   // row 2n+1: (bi,  br)
+      *(float2*)(sB + canon_off(2 * rb_n, 2 * kk)) = hr;
+      *(float2*)(sB + canon_off(2 * rb_n + 1, 2 * kk)) = hi2;
+      if (MODE == 1) {
+        const float2 lr = make_float2(to_tf32(bv.x - hr.x), to_tf32(-bv.y - hr.y));
+        const float2 li = make_float2(to_tf32(bv.y - hi2.x), to_tf32(bv.x - hi2.y));
+        *(float2*)(sB + TILE_B_BYTES + canon_off(2 * rb_n, 2 * kk)) = lr;
+        *(float2*)(sB + TILE_B_BYTES + canon_off(2 * rb_n + 1, 2 * kk)) = li;
       }
     }
     fence_async_smem();
@@ -278,6 +328,9 @@ __global__ void __launch_bounds__(TC_THREADS) k_gemm_tc(const GemmTask* __restri
     if (threadIdx.x == 0) {
       tc_fence_after();
       const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
+      if (MODE == 2) {   // one K = 16 step covers the stage
+        mma_bf16(tmem, make_desc16(a0), make_desc16(b0), idesc, s > 0 ? 1u : 0u);
+      } else
 #pragma unroll
       for (int q = 0; q < TC_KR / 8; ++q) {
         const uint32_t off = q * 256;   // two core matrices along K per k-step
@@ -292,6 +345,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_gemm_tc(const GemmTask* __restri
     uses[b] += 1;
     k0 += TC_BKC;
     while (e < t.term_end && k0 >= terms[e].K) { ++e; k0 = 0; }
+    if (s + 1 < count) load_stage(e, k0);
   }
   // the last commit covers every MMA issued before it
   uint32_t failed_bar = 0, failed_phase = 0;
@@ -323,9 +377,14 @@ __global__ void __launch_bounds__(TC_THREADS) k_gemm_tc(const GemmTask* __restri
     }
     const bool atomic = t.splits > 1;
     const int quad = warp & 3, chalf = warp >> 2;
-    const int r = m0 + quad * 32 + lane;
     const bool have = count > 0;
     const float fax = (float)alpha.x, fay = (float)alpha.y;
+    // Each warp moves its 32 x 16-complex chunk through a 4 KB shared-memory
+    // scratch (the operand buffers, free once the last MMA completed) so
+    // that the global writes run along rows: 16 lanes per 128-byte row.
+    // Slots are XOR-swizzled by row so neither side has bank conflicts.
+    float2* scr = (float2*)(sm + warp * 4096);
+    const int hrow = lane >> 4, jj = lane & 15;
     for (int c0 = 32 * chalf; c0 < 2 * ncols; c0 += 64) {
       float v[32];
       if (have) {
@@ -334,37 +393,43 @@ __global__ void __launch_bounds__(TC_THREADS) k_gemm_tc(const GemmTask* __restri
 #pragma unroll
         for (int i = 0; i < 32; ++i) v[i] = 0.f;
       }
-      if (r < t.M && (have || !atomic)) {
-        const int jn = min(16, ncols - c0 / 2);
-        const size_t o0 = (size_t)r * t.ldc + n0 + c0 / 2;
+#pragma unroll
+      for (int j = 0; j < 16; ++j) scr[lane * 16 + (j ^ (lane & 15))] = make_float2(v[2 * j], v[2 * j + 1]);
+      __syncwarp();
+      const int jn = min(16, ncols - c0 / 2);
+      // transposed tasks (C^T computed) write along C's rows = this tile's
+      // columns: lanes over the 32 tile rows, one tile column at a time
+      for (int it = 0; it < 16; ++it) {
+        int rl, jc;
+        if (t.ct) { rl = lane; jc = it; } else { rl = 2 * it + hrow; jc = jj; }
+        const int row = m0 + quad * 32 + rl;
+        const float2 x = scr[rl * 16 + (jc ^ (rl & 15))];
+        if (row >= t.M || jc >= jn || !(have || !atomic)) continue;
+        const size_t col = (size_t)n0 + c0 / 2 + jc;
+        const size_t o = t.ct ? col * t.ldc + row : (size_t)row * t.ldc + col;
         if (t.tc == 0) {
-          double2* C = (double2*)t.C + o0;
-          for (int j = 0; j < jn; ++j) {
-            const double re = v[2 * j], im = v[2 * j + 1];
-            double ore = alpha.x * re - alpha.y * im, oim = alpha.x * im + alpha.y * re;
-            if (atomic) {
-              atomicAdd(&C[j].x, ore);
-              atomicAdd(&C[j].y, oim);
-            } else {
-              if (t.beta) { ore += C[j].x; oim += C[j].y; }
-              C[j] = make_double2(ore, oim);
-            }
+          double2* C = (double2*)t.C + o;
+          double ore = alpha.x * x.x - alpha.y * x.y, oim = alpha.x * x.y + alpha.y * x.x;
+          if (atomic) {
+            atomicAdd(&C->x, ore);
+            atomicAdd(&C->y, oim);
+          } else {
+            if (t.beta) { ore += C->x; oim += C->y; }
+            *C = make_double2(ore, oim);
           }
         } else {
-          float2* C = (float2*)t.C + o0;
-          for (int j = 0; j < jn; ++j) {
-            const float re = v[2 * j], im = v[2 * j + 1];
-            float ore = fax * re - fay * im, oim = fax * im + fay * re;
-            if (atomic) {
-              atomicAdd(&C[j].x, ore);
-              atomicAdd(&C[j].y, oim);
-            } else {
-              if (t.beta) { ore += C[j].x; oim += C[j].y; }
-              C[j] = make_float2(ore, oim);
-            }
+          float2* C = (float2*)t.C + o;
+          float ore = fax * x.x - fay * x.y, oim = fax * x.y + fay * x.x;
+          if (atomic) {
+            atomicAdd(&C->x, ore);
+            atomicAdd(&C->y, oim);
+          } else {
+            if (t.beta) { ore += C->x; oim += C->y; }
+            *C = make_float2(ore, oim);
           }
         }
       }
+      __syncwarp();
     }
   } else if (pending) {
     // give this CTA's MMAs one more bounded chance to drain before the
@@ -394,7 +459,11 @@ __global__ void k_zero_regions(const ZeroRegion* __restrict__ r) {
 void launch_gemm_tc(const GemmTask* d_tasks, const GemmTerm* d_terms, const int* d_tile_task,
                     int ntiles, int mode, int* d_err, cudaStream_t st) {
   if (ntiles <= 0) return;
-  if (mode == 0) {
+  if (mode == 2) {
+    const int smem = 2 * (TILE_A_BYTES + TILE_B_BYTES);
+    set_smem_limit((const void*)k_gemm_tc<2>, smem);
+    k_gemm_tc<2><<<ntiles, TC_THREADS, smem, st>>>(d_tasks, d_terms, d_tile_task, d_err);
+  } else if (mode == 0) {
     const int smem = 2 * (TILE_A_BYTES + TILE_B_BYTES);
     set_smem_limit((const void*)k_gemm_tc<0>, smem);
     k_gemm_tc<0><<<ntiles, TC_THREADS, smem, st>>>(d_tasks, d_terms, d_tile_task, d_err);

@@ -3,7 +3,9 @@ accumulation, FP64 factorisations) against the FP64 GPU path and the oracle.
 
 Tolerances follow from the arithmetic: a TF32 product carries a relative
 rounding of 2^-11 per operand, so sums of K ~ 10^3 terms land near 1e-3
-relative; the split 3xTF32 product keeps ~21 mantissa bits, and FP32
+relative; a BF16 operand carries 2^-8 (about 4e-3 per product, chained over
+~2L environment updates: a few 1e-2); the split 3xTF32 product keeps ~21
+mantissa bits, and FP32
 accumulation plus FP32 storage of the environments (2^-24 per element,
 ~sqrt(K) growth per contraction, chained over ~2L environment updates) bound
 a fitted state at ~2e-5 relative.
@@ -17,7 +19,7 @@ from oracle import mps as om
 
 pytestmark = pytest.mark.gpu
 
-TOLS = {"tf32": 3e-3, "tf32x3": 2e-5}
+TOLS = {"tf32": 3e-3, "tf32x3": 2e-5, "bf16": 5e-2}
 
 
 @pytest.fixture(scope="module")
@@ -39,7 +41,7 @@ def _rel(a, b):
     return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
 
 
-@pytest.mark.parametrize("prec", ["tf32x3", "tf32"])
+@pytest.mark.parametrize("prec", ["tf32x3", "tf32", "bf16"])
 def test_small_apply_tensor_core_vs_oracle(td, prec):
     # the fit contractions run on the tensor cores; compare with the oracle
     L = 6
@@ -57,7 +59,7 @@ def test_small_apply_tensor_core_vs_oracle(td, prec):
     ctx.close()
 
 
-@pytest.mark.parametrize("prec", ["tf32x3", "tf32"])
+@pytest.mark.parametrize("prec", ["tf32x3", "tf32", "bf16"])
 def test_apply_h_mixed_vs_fp64(td, prec):
     L = 8
     I = synth.make_integrals(L, seed=0)

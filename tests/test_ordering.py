@@ -1,0 +1,61 @@
+"""Fiedler orbital ordering: the oracle against closed forms of path graphs,
+and the library's host routine (no GPU) against the oracle."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import ordering
+
+
+def _chain_integrals(L, order, seed):
+    """h and eri whose coupling graph is a path through the orbitals in
+    `order` (nearest-neighbour hopping and exchange only)."""
+    rng = np.random.default_rng(seed)
+    h = np.diag(rng.uniform(-2, -0.5, L))
+    eri = np.zeros((L, L, L, L))
+    for a, b in zip(order[:-1], order[1:]):
+        t = rng.uniform(0.5, 1.0)
+        h[a, b] = h[b, a] = -t
+        k = rng.uniform(0.05, 0.1)
+        eri[a, b, b, a] = eri[b, a, a, b] = k
+    return h, eri
+
+
+def test_path_graph_laplacian_closed_form():
+    # path graph P_L: lambda_2 = 2 - 2 cos(pi / L), Fiedler vector ~ cos(pi (k + 1/2) / L)
+    L = 9
+    W = np.zeros((L, L))
+    for k in range(L - 1):
+        W[k, k + 1] = W[k + 1, k] = 1.0
+    lam, V = np.linalg.eigh(ordering.laplacian(W))
+    assert abs(lam[1] - (2 - 2 * np.cos(np.pi / L))) < 1e-12
+    ref = np.cos(np.pi * (np.arange(L) + 0.5) / L)
+    f = V[:, 1]
+    assert abs(abs(np.dot(f, ref)) - np.linalg.norm(ref)) < 1e-12
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_oracle_recovers_a_hidden_chain(seed):
+    L = 10
+    order = np.random.default_rng(100 + seed).permutation(L)
+    h, eri = _chain_integrals(L, order, seed)
+    perm = ordering.fiedler_order(h, eri)
+    assert list(perm) == list(order) or list(perm) == list(order[::-1])
+
+
+def test_library_matches_oracle_on_host():
+    import paper_1902_08489_gb300 as td
+    try:
+        td.lib()
+    except td.TdmpsError:
+        pytest.skip("library not built")
+    for L, seed in [(8, 0), (12, 3), (16, 5)]:
+        I = synth.make_integrals(L, seed=seed)
+        assert list(td.fiedler_order(I.h, I.eri)) == list(ordering.fiedler_order(I.h, I.eri))
+    order = np.random.default_rng(7).permutation(11)
+    h, eri = _chain_integrals(11, order, 7)
+    assert list(td.fiedler_order(h, eri)) == list(ordering.fiedler_order(h, eri))
+    # the permuted integrals are those of the reordered orbitals
+    p = td.fiedler_order(h, eri)
+    h2, e2 = td.permute_integrals(h, eri, p)
+    assert h2[0, 1] == h[p[0], p[1]] and e2[0, 1, 1, 0] == eri[p[0], p[1], p[1], p[0]]
