@@ -262,6 +262,8 @@ void upload_mpo_tables(MPOd& m, Context& c) {
   m.rowptr = dev_alloc(std::max<size_t>(rowptr.size(), 1) * sizeof(int), c.st);
   m.ent_w = dev_alloc(std::max<size_t>(ent_w.size(), 1) * sizeof(int), c.st);
   m.ent_v = dev_alloc(std::max<size_t>(ent_v.size(), 1) * sizeof(double), c.st);
+  m.ent_vf = dev_alloc(std::max<size_t>(ent_v.size(), 1) * sizeof(float), c.st);
+  std::vector<float> ent_vf(ent_v.begin(), ent_v.end());
   if (!rowptr.empty())
     TD_CHECK_CUDA(cudaMemcpyAsync(m.rowptr->p, rowptr.data(), rowptr.size() * sizeof(int),
                                   cudaMemcpyHostToDevice, c.st));
@@ -269,6 +271,8 @@ void upload_mpo_tables(MPOd& m, Context& c) {
     TD_CHECK_CUDA(cudaMemcpyAsync(m.ent_w->p, ent_w.data(), ent_w.size() * sizeof(int),
                                   cudaMemcpyHostToDevice, c.st));
     TD_CHECK_CUDA(cudaMemcpyAsync(m.ent_v->p, ent_v.data(), ent_v.size() * sizeof(double),
+                                  cudaMemcpyHostToDevice, c.st));
+    TD_CHECK_CUDA(cudaMemcpyAsync(m.ent_vf->p, ent_vf.data(), ent_vf.size() * sizeof(float),
                                   cudaMemcpyHostToDevice, c.st));
   }
   // host vectors must outlive the async copies
@@ -436,7 +440,7 @@ struct WBatch {
     cudaEvent_t ev;
     c.kbegin(TDMPS_KSTAT_WSTAGE, &ev);
     launch_wstage(dt, (int)tasks.size(), work, (const int*)m.rowptr->p, (const int*)m.ent_w->p,
-                  (const double*)m.ent_v->p, et, c.st);
+                  (const double*)m.ent_v->p, (const float*)m.ent_vf->p, et, c.st);
     c.kend(TDMPS_KSTAT_WSTAGE, ev, flops, bytes);
   }
 };
@@ -474,6 +478,26 @@ static Env env_right_boundary(Context& c, const MPSd& bra, const MPSd& ket, cons
   return e;
 }
 
+// A site tensor as a GEMM operand: the FP64 blocks in FP64 mode, else an
+// FP32 copy made once per tensor (the tensor-core kernels then convert no
+// FP64 data per tile -- FP64 conversions run at the FP64 pipe's rate).
+static const void* site_operand(Context& c, const SiteT& s, int b, int& et) {
+  if (c.precision == TDMPS_FP64) {
+    et = 0;
+    return s.ptr(b);
+  }
+  if (!s.data32) {
+    s.data32 = dev_alloc(std::max<size_t>(s.size, 1) * sizeof(float2), c.st);
+    cudaEvent_t ev;
+    c.kbegin(TDMPS_KSTAT_OTHER, &ev);
+    launch_to_float((const double2*)s.data->p, (float2*)s.data32->p, s.size, c.st);
+    c.kend(TDMPS_KSTAT_OTHER, ev, 0.0, 24.0 * s.size);
+  }
+  et = 1;
+  return (const float2*)s.data32->p + s.blocks[b].off;
+}
+static int site_et(Context& c) { return c.precision == TDMPS_FP64 ? 0 : 1; }
+
 // ---- stage planners: each appends its work to a batch; callers run one
 // launch per stage for all terms of a fit or all pairs of a sandwich.
 
@@ -497,8 +521,10 @@ static Inter plan_lstage(Context& c, const Env& E, const SiteT& ket, const Bond&
   for (int x = 0; x < (int)X.blocks.size(); ++x) {
     const Inter::Blk& xb = X.blocks[x];
     const Inter::Blk& eb = E.t.blocks[src[x].first];
-    gb.task(X.ptr(x), X.et, xb.rows * xb.W, xb.cols, xb.cols, OP_N, E.t.et, OP_N, 0, false, 1.0);
-    gb.term(E.t.ptr(src[x].first), eb.cols, ket.ptr(src[x].second), xb.cols, eb.cols);
+    int bet;
+    const void* bp = site_operand(c, ket, src[x].second, bet);
+    gb.task(X.ptr(x), X.et, xb.rows * xb.W, xb.cols, xb.cols, OP_N, E.t.et, OP_N, bet, false, 1.0);
+    gb.term(E.t.ptr(src[x].first), eb.cols, bp, xb.cols, eb.cols);
   }
   return X;
 }
@@ -669,10 +695,12 @@ static Env plan_env_left(Context& c, const Inter& Y, const SiteT& bra, const Bon
   for (auto& kv : contrib) {
     const Inter::Blk& eb = e.t.blocks[id];
     int N = eb.W * eb.cols;
-    gb.task(e.t.ptr(id), e.t.et, eb.rows, N, N, OP_C, 0, OP_N, Y.et, false, 1.0);
+    gb.task(e.t.ptr(id), e.t.et, eb.rows, N, N, OP_C, site_et(c), OP_N, Y.et, false, 1.0);
     for (auto& tm : kv.second) {
       const SiteT::Blk& cb = bra.blocks[tm.bra];
-      gb.term(bra.ptr(tm.bra), cb.cols, Y.ptr(tm.y), N, cb.rows);
+      int aet;
+      const void* ap = site_operand(c, bra, tm.bra, aet);
+      gb.term(ap, cb.cols, Y.ptr(tm.y), N, cb.rows);
     }
     ++id;
   }
@@ -701,8 +729,10 @@ static Inter plan_r1(Context& c, const Env& R, const SiteT& A, const Bond& ket_l
   for (int z = 0; z < (int)Z.blocks.size(); ++z) {
     const Inter::Blk& zb = Z.blocks[z];
     const Inter::Blk& r = R.t.blocks[src[z].first];
-    gb.task(Z.ptr(z), Z.et, zb.rows * zb.W, zb.cols, zb.cols, OP_N, R.t.et, OP_T, 0, false, 1.0);
-    gb.term(R.t.ptr(src[z].first), r.cols, A.ptr(src[z].second), r.cols, r.cols);
+    int bet;
+    const void* bp = site_operand(c, A, src[z].second, bet);
+    gb.task(Z.ptr(z), Z.et, zb.rows * zb.W, zb.cols, zb.cols, OP_N, R.t.et, OP_T, bet, false, 1.0);
+    gb.term(R.t.ptr(src[z].first), r.cols, bp, r.cols, r.cols);
   }
   return Z;
 }
@@ -734,10 +764,12 @@ static Env plan_env_right(Context& c, const Inter& Zp, const SiteT& bra, const B
   for (auto& kv : contrib) {
     const Inter::Blk& eb = e.t.blocks[id];
     int N = eb.W * eb.cols;
-    gb.task(e.t.ptr(id), e.t.et, eb.rows, N, N, OP_J, 0, OP_N, Zp.et, false, 1.0);
+    gb.task(e.t.ptr(id), e.t.et, eb.rows, N, N, OP_J, site_et(c), OP_N, Zp.et, false, 1.0);
     for (auto& tm : kv.second) {
       const SiteT::Blk& cb = bra.blocks[tm.bra];
-      gb.term(bra.ptr(tm.bra), cb.cols, Zp.ptr(tm.z), N, cb.cols);
+      int aet;
+      const void* ap = site_operand(c, bra, tm.bra, aet);
+      gb.term(ap, cb.cols, Zp.ptr(tm.z), N, cb.cols);
     }
     ++id;
   }
@@ -840,7 +872,7 @@ void run_svd(Context& c, FactWork& fw) {
   c.kbegin(TDMPS_KSTAT_SVD, &ev);
   size_t mx = 0;
   for (auto& t : fw.tasks) mx = std::max(mx, (size_t)(t.m * t.n + t.n * t.n) * sizeof(double2));
-  launch_svd(d, (int)fw.tasks.size(), (int*)c.status->p, c.st, mx);
+  launch_svd(d, (int)fw.tasks.size(), (int*)c.status->p, c.st, mx, fw.tasks.data());
   double fl = 0.0;
   for (auto& t : fw.tasks) fl += 8.0 * 8.0 * t.m * t.n * t.n;
   c.kend(TDMPS_KSTAT_SVD, ev, fl, 0.0);
@@ -1446,6 +1478,7 @@ void normalize_center(Context& c, MPSd& m, double2* norm_out) {
   cudaEvent_t ev;
   c.kbegin(TDMPS_KSTAT_OTHER, &ev);
   launch_normalize((double2*)m.sites[0].data->p, m.sites[0].size, norm_out, c.st);
+  m.sites[0].data32.reset();
   c.kend(TDMPS_KSTAT_OTHER, ev, 0.0, 0.0);
 }
 

@@ -100,6 +100,9 @@ struct SiteT {
   std::vector<int> index;  // [r*4 + sig] -> block id or -1
   size_t size = 0;         // complex elements
   DevPtr data;             // double2
+  // float2 copy for the mixed-precision contractions, made on first use and
+  // dropped whenever `data` is written in place
+  mutable DevPtr data32;
   int block_of(int r, int sig) const { return index[(size_t)r * 4 + sig]; }
   double2* ptr(int b) const { return (double2*)data->p + blocks[b].off; }
 };
@@ -145,7 +148,7 @@ struct MPOd {
   // device tables
   std::vector<std::vector<WTable>> tab_left, tab_right;
   std::vector<std::map<std::array<int, 3>, int>> tab_left_idx, tab_right_idx;
-  DevPtr rowptr, ent_w, ent_v;                // int, int, double
+  DevPtr rowptr, ent_w, ent_v, ent_vf;        // int, int, double, float
   int64_t n_elem = 0;
 };
 

@@ -195,7 +195,7 @@ template <class T>
 __global__ void __launch_bounds__(256) k_wstage(const WTask* __restrict__ tasks, int ntasks,
                                                 int64_t total, const int* __restrict__ rowptr,
                                                 const int* __restrict__ ent_w,
-                                                const double* __restrict__ ent_v) {
+                                                const typename WAcc<T>::R* __restrict__ ent_v) {
   using R = typename WAcc<T>::R;
   // each CTA owns one contiguous range of the flat output index, so a
   // thread finds its task once (binary search) and then only steps forward
@@ -226,7 +226,7 @@ __global__ void __launch_bounds__(256) k_wstage(const WTask* __restrict__ tasks,
       const T* X = (const T*)t.X[s];
       int win = t.win[s];
       for (int e = rp[w]; e < rp[w + 1]; ++e) {
-        R v = (R)ent_v[e];
+        const R v = ent_v[e];
         T x = X[((size_t)a * win + ent_w[e]) * t.cols + b];
         ax = fma(v, (R)x.x, ax);
         ay = fma(v, (R)x.y, ay);
@@ -240,14 +240,15 @@ __global__ void __launch_bounds__(256) k_wstage(const WTask* __restrict__ tasks,
 }
 
 void launch_wstage(const WTask* d_tasks, int ntasks, int64_t total_work, const int* d_rowptr,
-                   const int* d_ent_w, const double* d_ent_v, int et, cudaStream_t st) {
+                   const int* d_ent_w, const double* d_ent_v, const float* d_ent_vf, int et,
+                   cudaStream_t st) {
   if (total_work <= 0) return;
   int64_t blocks = (total_work + 255) / 256;
   if (blocks > 152 * 64) blocks = 152 * 64;
   if (et == 0)
     k_wstage<double2><<<(int)blocks, 256, 0, st>>>(d_tasks, ntasks, total_work, d_rowptr, d_ent_w, d_ent_v);
   else
-    k_wstage<float2><<<(int)blocks, 256, 0, st>>>(d_tasks, ntasks, total_work, d_rowptr, d_ent_w, d_ent_v);
+    k_wstage<float2><<<(int)blocks, 256, 0, st>>>(d_tasks, ntasks, total_work, d_rowptr, d_ent_w, d_ent_vf);
 }
 
 template <class T>
@@ -263,6 +264,21 @@ void launch_to_double(const void* in, int et, double2* out, size_t n, cudaStream
   if (blocks > 152 * 32) blocks = 152 * 32;
   if (et == 0) k_to_double<double2><<<(unsigned)blocks, 256, 0, st>>>((const double2*)in, out, n);
   else k_to_double<float2><<<(unsigned)blocks, 256, 0, st>>>((const float2*)in, out, n);
+}
+
+__global__ void k_to_float(const double2* in, float2* out, size_t n) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * blockDim.x) {
+    const double2 v = in[i];
+    out[i] = make_float2((float)v.x, (float)v.y);
+  }
+}
+
+void launch_to_float(const double2* in, float2* out, size_t n, cudaStream_t st) {
+  if (n == 0) return;
+  size_t blocks = (n + 255) / 256;
+  if (blocks > 152 * 32) blocks = 152 * 32;
+  k_to_float<<<(unsigned)blocks, 256, 0, st>>>(in, out, n);
 }
 
 __global__ void k_fill_one(void* p, int et) {
@@ -532,9 +548,226 @@ __global__ void __launch_bounds__(SVD_THREADS) k_svd(const FactTask* __restrict_
   }
 }
 
+// The same one-sided Jacobi SVD with one matrix spread over a cluster of
+// SVDC_CS CTAs: CTA `rank` holds rows [rank*mc, rank*mc + mc) of A in shared
+// memory and rows [rank*nc, rank*nc + nc) of V in global memory.  Each round
+// of the round-robin ordering computes the partial inner products (|a_p|^2,
+// |a_q|^2, a_p^H a_q) of all its n/2 disjoint column pairs over the local
+// rows, sums them across the cluster in one reduction (slots in every CTA's
+// shared memory, rank-ordered sums, so every CTA takes the same rotation
+// decisions), and rotates its own rows.  One cluster barrier per round
+// instead of one SM doing all of the FP64 work.
+constexpr int SVDC_CS = 8;
+constexpr int SVDC_THREADS = 512;
+
+__host__ __device__ inline size_t svdc_elems(int m, int n) {
+  const size_t mc = (m + SVDC_CS - 1) / SVDC_CS;
+  const size_t np = (size_t)((n + 1) & ~1);
+  const size_t SL = np > (size_t)n ? np : (size_t)n;
+  return mc * n + SL + 2 * (size_t)SVDC_CS * SL + (size_t)n + 16;
+}
+
+__global__ void __launch_bounds__(SVDC_THREADS) k_svd_cl(const FactTask* __restrict__ tasks,
+                                                         int* status) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cl = cg::this_cluster();
+  extern __shared__ double2 shv[];
+  const int rank = (int)cl.block_rank();
+  const FactTask t = tasks[blockIdx.x / SVDC_CS];
+  const int m = t.m, n = t.n;
+  const int mc = (m + SVDC_CS - 1) / SVDC_CS, nc = (n + SVDC_CS - 1) / SVDC_CS;
+  const int row0 = rank * mc, ml = max(0, min(mc, m - row0));
+  const int vr0 = rank * nc, nl = max(0, min(nc, n - vr0));
+  const int np = (n + 1) & ~1;
+  const int SL = np > n ? np : n;
+  double2* A = shv;                          // [n][mc]
+  double2* part = A + (size_t)mc * n;        // [SL]: pair k -> (al, be), (gr, gi) at 2k, 2k+1
+  double2* slots = part + SL;                // [2][CS][SL]
+  double* sv = (double*)(slots + 2 * (size_t)SVDC_CS * SL);   // [n]
+  int* perm = (int*)(sv + n);                // [n]
+  __shared__ int rotated;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  int red = 0;
+  auto allreduce = [&](double2* buf, int len) {
+    const int b = red & 1;
+    ++red;
+    for (int r = 0; r < SVDC_CS; ++r) {
+      double2* dst = cl.map_shared_rank(slots, r) + ((size_t)b * SVDC_CS + rank) * SL;
+      for (int i = threadIdx.x; i < len; i += blockDim.x) dst[i] = buf[i];
+    }
+    cl.sync();
+    for (int i = threadIdx.x; i < len; i += blockDim.x) {
+      double2 acc = make_double2(0.0, 0.0);
+      for (int r = 0; r < SVDC_CS; ++r) acc = cadd(acc, slots[((size_t)b * SVDC_CS + r) * SL + i]);
+      buf[i] = acc;
+    }
+    __syncthreads();
+  };
+  for (int c = 0; c < n; ++c)
+    for (int i = threadIdx.x; i < ml; i += blockDim.x) A[(size_t)c * mc + i] = t.A[(size_t)c * m + row0 + i];
+  for (int c = 0; c < n; ++c)
+    for (int i = threadIdx.x; i < nl; i += blockDim.x)
+      t.V[(size_t)c * n + vr0 + i] = make_double2(vr0 + i == c ? 1.0 : 0.0, 0.0);
+  // Frobenius norm
+  {
+    if (warp == 0) {
+      double s2 = 0.0;
+      for (size_t e = lane; e < (size_t)ml * n; e += 32) {
+        const size_t c = e / ml, i = e % ml;
+        s2 += cabs2(A[c * mc + i]);
+      }
+      s2 = warp_sum(s2);
+      if (lane == 0) part[0] = make_double2(s2, 0.0);
+    }
+    __syncthreads();
+    allreduce(part, 1);
+  }
+  const double negl = 1e-26 * part[0].x;
+  const double tol = 2.2e-16 * fmax(16.0, (double)m);
+  __syncthreads();
+  int sweep = 0;
+  for (; sweep < SVD_MAX_SWEEPS; ++sweep) {
+    if (threadIdx.x == 0) rotated = 0;
+    __syncthreads();
+    for (int r = 0; r < np - 1; ++r) {
+      for (int k = warp; k < np / 2; k += nwarp) {
+        int pa = k, pb = np - 1 - k;
+        int p = pa == 0 ? 0 : ((pa - 1 + r) % (np - 1)) + 1;
+        int q = ((pb - 1 + r) % (np - 1)) + 1;
+        double al = 0.0, be = 0.0, gr = 0.0, gi = 0.0;
+        if (p < n && q < n) {
+          if (p > q) { int tmp = p; p = q; q = tmp; }
+          const double2* ap = A + (size_t)p * mc;
+          const double2* aq = A + (size_t)q * mc;
+          for (int i = lane; i < ml; i += 32) {
+            const double2 x = ap[i], y = aq[i];
+            al += cabs2(x);
+            be += cabs2(y);
+            gr += x.x * y.x + x.y * y.y;     // conj(x) * y
+            gi += x.x * y.y - x.y * y.x;
+          }
+          al = warp_sum(al); be = warp_sum(be); gr = warp_sum(gr); gi = warp_sum(gi);
+        }
+        if (lane == 0) {
+          part[2 * k] = make_double2(al, be);
+          part[2 * k + 1] = make_double2(gr, gi);
+        }
+      }
+      __syncthreads();
+      allreduce(part, np);
+      for (int k = warp; k < np / 2; k += nwarp) {
+        int pa = k, pb = np - 1 - k;
+        int p = pa == 0 ? 0 : ((pa - 1 + r) % (np - 1)) + 1;
+        int q = ((pb - 1 + r) % (np - 1)) + 1;
+        if (p >= n || q >= n) continue;
+        if (p > q) { int tmp = p; p = q; q = tmp; }
+        const double al = part[2 * k].x, be = part[2 * k].y;
+        const double gr = part[2 * k + 1].x, gi = part[2 * k + 1].y;
+        const double g = sqrt(gr * gr + gi * gi);
+        if (g == 0.0 || al <= negl || be <= negl || g <= tol * sqrt(al * be)) continue;
+        const double zeta = (be - al) / (2.0 * g);
+        const double tt = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+        const double c = 1.0 / sqrt(1.0 + tt * tt), s = c * tt;
+        const double2 ph = make_double2(gr / g, gi / g);   // e^{i phi}
+        const double2 sph = cscale(ph, s);                  // s e^{i phi}
+        const double2 sphc = cconj(sph);                    // s e^{-i phi}
+        double2* ap = A + (size_t)p * mc;
+        double2* aq = A + (size_t)q * mc;
+        for (int i = lane; i < ml; i += 32) {
+          const double2 x = ap[i], y = aq[i];
+          ap[i] = csub(cscale(x, c), cmul(sphc, y));
+          aq[i] = cadd(cmul(sph, x), cscale(y, c));
+        }
+        double2* vp = t.V + (size_t)p * n + vr0;
+        double2* vq = t.V + (size_t)q * n + vr0;
+        for (int i = lane; i < nl; i += 32) {
+          const double2 x = vp[i], y = vq[i];
+          vp[i] = csub(cscale(x, c), cmul(sphc, y));
+          vq[i] = cadd(cmul(sph, x), cscale(y, c));
+        }
+        if (lane == 0) rotated = 1;
+      }
+      __syncthreads();
+    }
+    const int any = rotated;   // identical in every CTA of the cluster
+    __syncthreads();
+    if (!any) break;
+  }
+  if (rank == 0 && threadIdx.x == 0 && sweep == SVD_MAX_SWEEPS) atomicExch(status, 1);
+  // singular values: column norms over all rows
+  for (int j = warp; j < n; j += nwarp) {
+    const double2* aj = A + (size_t)j * mc;
+    double s2 = 0.0;
+    for (int i = lane; i < ml; i += 32) s2 += cabs2(aj[i]);
+    s2 = warp_sum(s2);
+    if (lane == 0) part[j] = make_double2(s2, 0.0);
+  }
+  __syncthreads();
+  allreduce(part, n);
+  for (int j = threadIdx.x; j < n; j += blockDim.x) sv[j] = sqrt(part[j].x);
+  __syncthreads();
+  // descending order, ties: lower index first
+  for (int j = threadIdx.x; j < n; j += blockDim.x) {
+    const double sj = sv[j];
+    int rk = 0;
+    for (int k = 0; k < n; ++k) rk += (sv[k] > sj) || (sv[k] == sj && k < j);
+    perm[rk] = j;
+  }
+  __syncthreads();
+  for (int j = 0; j < n; ++j) {
+    const int pj = perm[j];
+    const double inv = sv[pj] > 0.0 ? 1.0 / sv[pj] : 0.0;
+    for (int i = threadIdx.x; i < ml; i += blockDim.x)
+      t.A[(size_t)j * m + row0 + i] = cscale(A[(size_t)pj * mc + i], inv);
+  }
+  if (rank == 0)
+    for (int j = threadIdx.x; j < n; j += blockDim.x) t.s[j] = sv[perm[j]];
+  // V columns permuted; each CTA owns its rows of V, staged through the A
+  // buffer (free now; the launcher requires m >= n, so nc <= mc)
+  __syncthreads();
+  for (int c = 0; c < n; ++c)
+    for (int i = threadIdx.x; i < nl; i += blockDim.x) A[(size_t)c * nc + i] = t.V[(size_t)c * n + vr0 + i];
+  __syncthreads();
+  for (int j = 0; j < n; ++j) {
+    const int pj = perm[j];
+    for (int i = threadIdx.x; i < nl; i += blockDim.x)
+      t.V[(size_t)j * n + vr0 + i] = A[(size_t)pj * nc + i];
+  }
+  // no CTA may leave while others can still write into its slots
+  cl.sync();
+}
+
 void launch_svd(const FactTask* d_tasks, int ntasks, int* d_status, cudaStream_t st,
-                size_t max_bytes) {
+                size_t max_bytes, const FactTask* h_tasks) {
   if (ntasks <= 0) return;
+  {
+    // the cluster kernel for square (or tall) matrices with a large one
+    const size_t cap_cl = 200 * 1024;
+    size_t need = 0;
+    bool large = false, shape_ok = h_tasks != nullptr;
+    for (int i = 0; h_tasks && i < ntasks; ++i) {
+      need = std::max(need, svdc_elems(h_tasks[i].m, h_tasks[i].n) * sizeof(double2));
+      if (h_tasks[i].m < h_tasks[i].n || h_tasks[i].n > 2048) shape_ok = false;
+      if (h_tasks[i].n >= 24) large = true;
+    }
+    if (shape_ok && large && need <= cap_cl) {
+      set_smem_limit((const void*)k_svd_cl, (int)cap_cl);
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3((unsigned)(ntasks * SVDC_CS));
+      cfg.blockDim = dim3(SVDC_THREADS);
+      cfg.dynamicSmemBytes = need;
+      cfg.stream = st;
+      cudaLaunchAttribute attr[1];
+      attr[0].id = cudaLaunchAttributeClusterDimension;
+      attr[0].val.clusterDim.x = SVDC_CS;
+      attr[0].val.clusterDim.y = 1;
+      attr[0].val.clusterDim.z = 1;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+      cudaLaunchKernelEx(&cfg, k_svd_cl, d_tasks, d_status);
+      return;
+    }
+  }
   // static shared: perm (4 KB) + scalars
   const size_t cap = 227 * 1024 - 5 * 1024;
   size_t dyn = max_bytes < cap ? max_bytes : cap;
@@ -763,9 +996,19 @@ __global__ void __launch_bounds__(QRC_THREADS) k_qr_cl(const FactTask* __restric
     if (q == 0) {
       nrm2 = vnorm2();
     } else {
-      const double before = vnorm2();
+      // The first pass reduces the coefficients and |v|^2 together, and when
+      // it removed less than half of |v|^2 the residual norm follows from
+      // Pythagoras, |v'|^2 = |v|^2 - sum |c|^2 (accurate to a few ulp in that
+      // regime) -- one cluster reduction per column instead of three.
+      double before = 0.0;
       nrm2 = 0.0;
       for (int pass = 0; pass < 2; ++pass) {
+        if (pass == 0 && warp == nwarp - 1) {
+          double s2 = 0.0;
+          for (int i = lane; i < ml; i += 32) s2 += cabs2(v[i]);
+          s2 = warp_sum(s2);
+          if (lane == 0) coef[q] = make_double2(s2, 0.0);
+        }
         for (int cc = warp; cc < q; cc += nwarp) {
           const double2* qc = A + (size_t)cc * mc;
           double re = 0.0, im = 0.0;
@@ -779,7 +1022,12 @@ __global__ void __launch_bounds__(QRC_THREADS) k_qr_cl(const FactTask* __restric
           if (lane == 0) coef[cc] = make_double2(re, im);
         }
         __syncthreads();
-        allreduce(coef, q, coef);
+        allreduce(coef, pass == 0 ? q + 1 : q, coef);
+        double proj = 0.0;
+        if (pass == 0) {
+          before = coef[q].x;
+          for (int cc = 0; cc < q; ++cc) proj += cabs2(coef[cc]);
+        }
         for (int i = threadIdx.x; i < ml; i += blockDim.x) {
           double2 acc = v[i];
           for (int cc = 0; cc < q; ++cc) acc = csub(acc, cmul(coef[cc], A[(size_t)cc * mc + i]));
@@ -791,8 +1039,15 @@ __global__ void __launch_bounds__(QRC_THREADS) k_qr_cl(const FactTask* __restric
             *rr = cadd(*rr, coef[cc]);
           }
         __syncthreads();
-        nrm2 = vnorm2();
-        if (pass == 0 && !(nrm2 < 0.5 * before)) break;   // one pass was enough
+        if (pass == 0) {
+          const double est = before - proj;
+          if (!(est < 0.5 * before)) {   // one pass was enough
+            nrm2 = est;
+            break;
+          }
+        } else {
+          nrm2 = vnorm2();
+        }
       }
     }
     const double nrm = sqrt(nrm2);

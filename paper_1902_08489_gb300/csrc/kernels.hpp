@@ -81,9 +81,11 @@ struct FactTask {
 
 void launch_gemm(const GemmTask* d_tasks, int ntasks, const GemmTerm* d_terms,
                  const int* d_tile_task, int ntiles, cudaStream_t st);
-// et: element type of X and Y (0 double2, 1 float2)
+// et: element type of X and Y (0 double2 with the FP64 values, 1 float2 with
+// the FP32 copy of the values)
 void launch_wstage(const WTask* d_tasks, int ntasks, int64_t total_work, const int* d_rowptr,
-                   const int* d_ent_w, const double* d_ent_v, int et, cudaStream_t st);
+                   const int* d_ent_w, const double* d_ent_v, const float* d_ent_vf, int et,
+                   cudaStream_t st);
 // tensor-core grouped GEMM (kernels_tc.cu); mode 0 TF32, 1 3xTF32; tiles of
 // tc_tile_m() rows x tc_tile_n() complex columns
 void launch_gemm_tc(const GemmTask* d_tasks, const GemmTerm* d_terms, const int* d_tile_task,
@@ -96,6 +98,8 @@ struct ZeroRegion {
   size_t bytes;   // multiple of 4
 };
 void launch_zero_regions(const ZeroRegion* d_regions, int n, cudaStream_t st);
+// out (float2) = in (double2), n elements
+void launch_to_float(const double2* in, float2* out, size_t n, cudaStream_t st);
 // out (double2) = in (element type et), n elements
 void launch_to_double(const void* in, int et, double2* out, size_t n, cudaStream_t st);
 void launch_fill_one(void* p, int et, cudaStream_t st);
@@ -105,8 +109,10 @@ void launch_copy(const CopyTask* d_tasks, int ntasks, int to_work, cudaStream_t 
 void launch_scatter(const ScatterTask* d_tasks, int ntasks, cudaStream_t st);
 void launch_zero(double2* p, size_t n, cudaStream_t st);
 // max_bytes: largest (m*n + n*n) * 16 of the tasks (shared-memory sizing)
+// h_tasks: the same tasks on the host (shapes decide between the one-CTA and
+// the cluster kernel)
 void launch_svd(const FactTask* d_tasks, int ntasks, int* d_status, cudaStream_t st,
-                size_t max_bytes);
+                size_t max_bytes, const FactTask* h_tasks);
 // h_tasks: the same tasks on the host (shapes decide between the one-CTA and
 // the cluster kernel)
 void launch_qr(const FactTask* d_tasks, int ntasks, cudaStream_t st, const FactTask* h_tasks);

@@ -200,6 +200,7 @@ __global__ void __launch_bounds__(TC_THREADS, 3) k_gemm_tc(const GemmTask* __res
   __shared__ __align__(8) uint64_t mbar[2];
   __shared__ uint32_t tmem_base;
   __shared__ int abort_flag;
+  __shared__ float2 alpha_sh;
 
   const int ti = tile_task[blockIdx.x];
   const GemmTask t = tasks[ti];
@@ -258,14 +259,20 @@ __global__ void __launch_bounds__(TC_THREADS, 3) k_gemm_tc(const GemmTask* __res
   const int rb_k = (threadIdx.x >> 6) * (TC_BKC / 4);
   float2 ra[TC_BKC / 2], rb[TC_BKC / 4];
   float2 sc = make_float2(1.f, 0.f);
+  // the term coefficient is formed in FP64 once per term, not per stage (the
+  // FP64 pipe is the scarce unit: every thread computes it)
+  int sc_term = -1;
   auto load_stage = [&](int ee, int kk0) {
     const GemmTerm g = terms[ee];
-    double2 scd = g.scale;
-    if (g.scale_ptr) {
-      const double2 p = *g.scale_ptr;
-      scd = make_double2(scd.x * p.x - scd.y * p.y, scd.x * p.y + scd.y * p.x);
+    if (ee != sc_term) {
+      double2 scd = g.scale;
+      if (g.scale_ptr) {
+        const double2 p = *g.scale_ptr;
+        scd = make_double2(scd.x * p.x - scd.y * p.y, scd.x * p.y + scd.y * p.x);
+      }
+      sc = make_float2((float)scd.x, (float)scd.y);
+      sc_term = ee;
     }
-    sc = make_float2((float)scd.x, (float)scd.y);
 #pragma unroll
     for (int j = 0; j < TC_BKC / 2; ++j)
       ra[j] = load_el(g.A, t.ta, g.lda, t.opA, m0 + ra_r, kk0 + ra_k + j, t.M, g.K);
@@ -357,6 +364,7 @@ __global__ void __launch_bounds__(TC_THREADS, 3) k_gemm_tc(const GemmTask* __res
     pending = true;
     if (ok && !mbar_wait(failed_bar, failed_phase)) {
       if (lane == 0) atomicExch(err, 2);
+      abort_flag = 1;   // the epilogue's TMEM loads are warp-collective: fail as a CTA
       ok = false;
     }
   }
@@ -364,7 +372,7 @@ __global__ void __launch_bounds__(TC_THREADS, 3) k_gemm_tc(const GemmTask* __res
   tc_fence_after();
   if (abort_flag) ok = false;
 
-  if (ok) {
+  if (threadIdx.x == 0) {   // alpha in FP64, once per CTA
     double2 alpha = t.alpha;
     if (t.alpha_ptr) {
       double2 p = *t.alpha_ptr;
@@ -375,10 +383,14 @@ __global__ void __launch_bounds__(TC_THREADS, 3) k_gemm_tc(const GemmTask* __res
       double d = q.x * q.x + q.y * q.y;
       alpha = make_double2((alpha.x * q.x + alpha.y * q.y) / d, (alpha.y * q.x - alpha.x * q.y) / d);
     }
+    alpha_sh = make_float2((float)alpha.x, (float)alpha.y);
+  }
+  __syncthreads();
+  if (ok) {
     const bool atomic = t.splits > 1;
     const int quad = warp & 3, chalf = warp >> 2;
     const bool have = count > 0;
-    const float fax = (float)alpha.x, fay = (float)alpha.y;
+    const float fax = alpha_sh.x, fay = alpha_sh.y;
     // Each warp moves its 32 x 16-complex chunk through a 4 KB shared-memory
     // scratch (the operand buffers, free once the last MMA completed) so
     // that the global writes run along rows: 16 lanes per 128-byte row.
@@ -409,7 +421,7 @@ __global__ void __launch_bounds__(TC_THREADS, 3) k_gemm_tc(const GemmTask* __res
         const size_t o = t.ct ? col * t.ldc + row : (size_t)row * t.ldc + col;
         if (t.tc == 0) {
           double2* C = (double2*)t.C + o;
-          double ore = alpha.x * x.x - alpha.y * x.y, oim = alpha.x * x.y + alpha.y * x.x;
+          double ore = (double)(fax * x.x - fay * x.y), oim = (double)(fax * x.y + fay * x.x);
           if (atomic) {
             atomicAdd(&C->x, ore);
             atomicAdd(&C->y, oim);
