@@ -277,6 +277,10 @@ def main():
                          "RK4 step of each of 64 uneven instances (L in {8..14}, "
                          "D in {32, 64, 128}) on worker streams")
     ap.add_argument("--workers", type=int, default=16, help="batch mode: worker streams")
+    ap.add_argument("--size", default=None,
+                    help="apply/krylov modes: L,N,D of another workload (e.g. 32,23,512 for "
+                         "the large active space: 64 Cholesky vectors and the localised "
+                         "orbital block); the default is the L=16 workload")
     ap.add_argument("--schedule", default=None, help="two-site,one-site sweeps per fit")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -302,7 +306,13 @@ def main():
     if args.schedule:
         sched = tuple(int(x) for x in args.schedule.split(","))
     ctx.set_schedule(*sched)
-    I = synth.make_integrals(L, seed=0)
+    global L, N_ELEC, TWO_SZ, D
+    big = False
+    if args.size:
+        L, N_ELEC, D = (int(x) for x in args.size.split(","))
+        TWO_SZ = N_ELEC % 2
+        big = L >= 24
+    I = synth.make_integrals(L, seed=0, n_chol=64 if big else 16, localised_block=big)
     mpo = td.build_mpo(ctx, I.h, I.eri, n_elec=N_ELEC)
     # replicas only: each rank evolves its own seeded state, no collective
     A, q = synth.random_mps(L, N_ELEC, TWO_SZ, D, seed=rank)
@@ -386,7 +396,8 @@ def main():
     # steps (m = 10, dt = 0.05, D = 256, eps = 1e-8; one two-site + one
     # one-site sweep per fit so the bonds can grow), FP64 vs this precision.
     traj = None
-    if args.precision != "fp64" and not args.no_traj_compare and args.mode == "krylov":
+    if (args.precision != "fp64" and not args.no_traj_compare and args.mode == "krylov"
+            and not args.size):
         occ = synth.hole_occupation(L, L, 7)
         obs = {}
         for p in ("fp64", args.precision):
@@ -436,11 +447,13 @@ def main():
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": {"fp64": "f64", "tf32": "tf32", "tf32x3": "tf32x3", "bf16": "bf16"}[args.precision],
         "data": "synthetic",
-        "config": {"workload": ("Krylov step, L=16 N=15 2Sz=1 D=256 m=10 dt=0.05 eps=1e-8, "
+        "config": {"workload": ("Krylov step, L=%d N=%d 2Sz=%d D=%d m=10 dt=0.05 eps=1e-8, "
                                 "fit schedule %d two-site + %d one-site sweeps, random seeded "
-                                "D=256 start" % sched) if args.mode == "krylov" else
-                               ("apply_H fit, L=16 N=15 2Sz=1 D=256, schedule %d two-site + "
-                                "%d one-site sweeps, random seeded D=256 state" % sched),
+                                "D=%d start" % (L, N_ELEC, TWO_SZ, D, sched[0], sched[1], D))
+                               if args.mode == "krylov" else
+                               ("apply_H fit, L=%d N=%d 2Sz=%d D=%d, schedule %d two-site + "
+                                "%d one-site sweeps, random seeded D=%d state"
+                                % (L, N_ELEC, TWO_SZ, D, sched[0], sched[1], D)),
                    "l2": "inputs larger than L2 (Krylov basis + environments, several GB)",
                    "parallelism": "replicas" if world > 1 else "single"},
         "steps_per_s": 1e3 * args.steps / ms,

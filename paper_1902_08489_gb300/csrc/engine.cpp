@@ -106,6 +106,7 @@ Context::~Context() {
   workers.clear();
   cudaStreamSynchronize(st);
   for (auto& p : pending) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
+  for (auto e : event_pool) cudaEventDestroy(e);
   ident.reset();
   rdm.reset();
   status.reset();
@@ -138,19 +139,31 @@ const void* Context::stage(const void* src, size_t bytes) {
   return out;
 }
 
+// timing events come from a pool: creating an event costs more host time
+// than recording it, and every launch of a timed region records two
+cudaEvent_t Context::take_event() {
+  if (!event_pool.empty()) {
+    cudaEvent_t e = event_pool.back();
+    event_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e;
+  TD_CHECK_CUDA(cudaEventCreate(&e));
+  return e;
+}
+
 void Context::kbegin(int kind, cudaEvent_t* a) {
   (void)kind;
   *a = nullptr;
   if (!stats) return;
-  TD_CHECK_CUDA(cudaEventCreate(a));
+  *a = take_event();
   TD_CHECK_CUDA(cudaEventRecord(*a, st));
 }
 
 void Context::kend(int kind, cudaEvent_t a, double flops, double bytes) {
   TD_CHECK_CUDA(cudaGetLastError());
   if (!stats) return;
-  cudaEvent_t b;
-  TD_CHECK_CUDA(cudaEventCreate(&b));
+  cudaEvent_t b = take_event();
   TD_CHECK_CUDA(cudaEventRecord(b, st));
   pending.push_back({kind, a, b});
   kstat[kind].launches += 1;
@@ -164,8 +177,8 @@ void Context::collect_stats() {
     float ms = 0.f;
     TD_CHECK_CUDA(cudaEventElapsedTime(&ms, p.a, p.b));
     kstat[p.kind].ms += ms;
-    cudaEventDestroy(p.a);
-    cudaEventDestroy(p.b);
+    event_pool.push_back(p.a);
+    event_pool.push_back(p.b);
   }
   pending.clear();
 }
@@ -409,9 +422,20 @@ struct GemmBatch {
       for (int q = 0; q < t.tiles_m * tn * t.splits; ++q) tile_task.push_back(id);
     }
     if (tile_task.empty()) return;
-    const GemmTask* dt = c.stage(tk);
-    const GemmTerm* dm = terms.empty() ? nullptr : c.stage(terms);
-    const int* dtt = c.stage(tile_task);
+    // tasks, terms and the tile map go to the device in one staged copy
+    auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    const size_t o_terms = al(tk.size() * sizeof(GemmTask));
+    const size_t o_tiles = o_terms + al(terms.size() * sizeof(GemmTerm));
+    const size_t pk_bytes = o_tiles + tile_task.size() * sizeof(int);
+    std::vector<char>& pk = c.pack;
+    pk.resize(pk_bytes);
+    std::memcpy(pk.data(), tk.data(), tk.size() * sizeof(GemmTask));
+    if (!terms.empty()) std::memcpy(pk.data() + o_terms, terms.data(), terms.size() * sizeof(GemmTerm));
+    std::memcpy(pk.data() + o_tiles, tile_task.data(), tile_task.size() * sizeof(int));
+    const char* base = (const char*)c.stage(pk.data(), pk_bytes);
+    const GemmTask* dt = (const GemmTask*)base;
+    const GemmTerm* dm = terms.empty() ? nullptr : (const GemmTerm*)(base + o_terms);
+    const int* dtt = (const int*)(base + o_tiles);
     cudaEvent_t ev;
     const int kind = fp64 ? TDMPS_KSTAT_GEMM_FP64 : TDMPS_KSTAT_GEMM;
     c.kbegin(kind, &ev);
@@ -1346,7 +1370,7 @@ MPSd fit(Context& c, const std::vector<FitTerm>& terms, const MPSd& guess, const
           for (auto& b : Y1[t].blocks) {
             int id = (int)E2[t].t.blocks.size();
             E2[t].t.blocks.push_back({b.rg * 4 + b.sig, -1, b.g, b.k, b.rows, b.W, b.cols, b.off});
-            E2[t].t.index[{b.rg * 4 + b.sig, -1, b.g, b.k}] = id;
+            E2[t].t.index[Inter::key(b.rg * 4 + b.sig, -1, b.g, b.k)] = id;
           }
         }
         GemmBatch g2(c);

@@ -5,6 +5,7 @@
 #include <complex>
 #include <functional>
 #include <map>
+#include <unordered_map>
 #include <vector>
 
 #include "internal.hpp"
@@ -50,6 +51,8 @@ struct Context {
   KStat kstat[TDMPS_KSTAT_COUNT];
   struct Pending { int kind; cudaEvent_t a, b; };
   std::vector<Pending> pending;
+  std::vector<cudaEvent_t> event_pool;   // recorded and read back events, reused
+  std::vector<char> pack;                // host packing buffer for staged task lists
   // scratch for device status words
   DevPtr status;   // int[16]: [0] SVD convergence, [4..5] Krylov, [8] tensor-core waits
   std::unique_ptr<MPOd> ident;   // identity MPO cache (by L)
@@ -67,6 +70,7 @@ struct Context {
     return v.empty() ? nullptr : (const T*)stage(v.data(), v.size() * sizeof(T));
   }
   // kernel timing bracket
+  cudaEvent_t take_event();
   void kbegin(int kind, cudaEvent_t* a);
   void kend(int kind, cudaEvent_t a, double flops, double bytes);
   void collect_stats();
@@ -90,19 +94,24 @@ struct Inter {
     size_t off;
   };
   std::vector<Blk> blocks;
-  std::map<std::array<int, 4>, int> index;
+  std::unordered_map<uint64_t, int> index;   // key(rg, sig, g, k) -> block id
   size_t size = 0;
   int et = 0;   // element type: 0 complex double, 1 complex float
   DevPtr data;
   size_t esz() const { return et ? sizeof(float2) : sizeof(double2); }
+  // sector, channel-group and local-state indices are small: 16 bits each
+  static uint64_t key(int rg, int sig, int g, int k) {
+    return ((uint64_t)(uint16_t)rg << 48) | ((uint64_t)(uint16_t)(sig + 1) << 32) |
+           ((uint64_t)(uint16_t)g << 16) | (uint64_t)(uint16_t)k;
+  }
   int find(int rg, int sig, int g, int k) const {
-    auto it = index.find({rg, sig, g, k});
+    auto it = index.find(key(rg, sig, g, k));
     return it == index.end() ? -1 : it->second;
   }
   int add(int rg, int sig, int g, int k, int rows, int W, int cols) {
     int id = (int)blocks.size();
     blocks.push_back({rg, sig, g, k, rows, W, cols, size});
-    index[{rg, sig, g, k}] = id;
+    index[key(rg, sig, g, k)] = id;
     size += (size_t)rows * W * cols;
     return id;
   }
