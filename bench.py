@@ -153,6 +153,20 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def replica_totals(ms, work, dist, device):
+    """Whole-job timing of independent replicas (one process per GPU, no
+    data-path collective): the slowest rank's timed region and the work of
+    all ranks.  dist is torch.distributed (or None for one process)."""
+    if dist is None:
+        return ms, work
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    w = torch.tensor([work], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(w, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(w.item())
+
+
 def roofline(st, precision):
     """Roofline entry of the kernel class with the largest live event time:
     achieved = its algorithmic work per launch / its average launch time."""
@@ -161,7 +175,8 @@ def roofline(st, precision):
     bf16 = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops", 1716.0))
     hbm = peaks.get("hbm_gbs", 6675.5)
     fp64_peak = bf16 * 1.25 / 2250.0
-    top = max(st, key=lambda k: st[k]["ms"])
+    dev = {k: v for k, v in st.items() if not k.startswith("host")}
+    top = max(dev, key=lambda k: dev[k]["ms"])
     ks = st[top]
     per_launch_s = ks["ms"] / max(1, ks["launches"]) / 1e3
     per_launch = lambda x: x / max(1, ks["launches"])
@@ -188,7 +203,7 @@ def roofline(st, precision):
         achieved = per_launch(ks["bytes"]) / per_launch_s / 1e9
     return {"kernel": kern, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
             "frac": achieved / peak, "traffic": None, "peak_source": src,
-            "share_of_timed_device_time": ks["ms"] / max(1e-9, sum(v["ms"] for v in st.values()))}
+            "share_of_timed_device_time": ks["ms"] / max(1e-9, sum(v["ms"] for v in dev.values()))}
 
 
 def batch_instances(n=64):
@@ -251,7 +266,7 @@ def run_batch(args, td, ctx, torch, local):
                        "workers": args.workers,
                        "l2": "inputs larger than L2 (64 states + environments)"},
             "tflops": flops / (ms / 1e3) / 1e12, "host_wall_s_per_step": wall / args.steps,
-            "gpu_launches": int(sum(v["launches"] for v in st.values())),
+            "gpu_launches": int(sum(v["launches"] for k, v in st.items() if not k.startswith("host"))),
             "kernel_stats": {k: {"launches": v["launches"], "ms_summed_over_streams": round(v["ms"], 3),
                                  "gflop": round(v["flops"] / 1e9, 3)} for k, v in st.items()},
             "clocks": clk.summary()}
@@ -351,12 +366,9 @@ def main():
     ms = ev0.elapsed_time(ev1)
     st = ctx.stats()
     ctx.stats_enable(False)
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
     flops = st["gemm"]["flops"] + st["gemm_fp64"]["flops"] + st["wstage"]["flops"]
-    value = world * flops / (ms / 1e3) / 1e12
+    ms, flops_all = replica_totals(ms, flops, dist, "cuda")
+    value = flops_all / (ms / 1e3) / 1e12
     g_mixed = td.one_rdm(ctx, state)
     e_mixed = td.expectation(ctx, mpo, state, state).real / td.overlap(ctx, state, state).real
 
@@ -435,7 +447,8 @@ def main():
             s2.free()
         torch.cuda.synchronize()
         te = time.perf_counter() - t0
-        e2e = {"value": world * flops / te / 1e12,
+        te, _ = replica_totals(te, 0.0, dist, "cuda")
+        e2e = {"value": flops_all / te / 1e12,
                "unit": "TFLOP/s", "h2d_bytes_per_step": h2d_bytes,
                "d2h_bytes_per_step": int(g.nbytes)}
 
@@ -459,7 +472,7 @@ def main():
         "steps_per_s": 1e3 * args.steps / ms,
         "vs_fp64": fp64_cmp,
         "vs_fp64_trajectory": traj,
-        "gpu_launches": int(sum(v["launches"] for v in st.values())),
+        "gpu_launches": int(sum(v["launches"] for k, v in st.items() if not k.startswith("host"))),
         "kernel_stats": {k: {"launches": v["launches"], "ms": round(v["ms"], 3),
                              "gflop": round(v["flops"] / 1e9, 3), "gb": round(v["bytes"] / 1e9, 3)}
                          for k, v in st.items()},

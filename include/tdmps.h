@@ -313,7 +313,13 @@ enum {
   TDMPS_KSTAT_OTHER = 4,
   TDMPS_KSTAT_GEMM_FP64 = 5, /* FP64 block contractions (FP64 mode, inner products,
                                 observables, gauge moves)                          */
-  TDMPS_KSTAT_COUNT = 6
+  TDMPS_KSTAT_HOST_PLAN = 6,   /* host wall time between consecutive launches inside
+                                  one API call (planning, allocation, staging); no
+                                  flops/bytes; launches = number of intervals      */
+  TDMPS_KSTAT_HOST_LAUNCH = 7, /* host wall time inside the launch calls themselves */
+  TDMPS_KSTAT_HOST_SYNC = 8,   /* host wall time blocked in stream synchronisations
+                                  (part of HOST_PLAN when it falls between launches) */
+  TDMPS_KSTAT_COUNT = 9
 };
 typedef struct {
   int64_t launches;

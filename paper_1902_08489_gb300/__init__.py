@@ -23,7 +23,9 @@ HEADER = os.path.join(os.path.dirname(_HERE), "include", "tdmps.h")
 
 FP64, TF32, TF32X3, BF16 = 0, 1, 2, 3
 PRECISION = {"fp64": FP64, "tf32": TF32, "tf32x3": TF32X3, "bf16": BF16}
-KSTAT = {"gemm": 0, "wstage": 1, "qr": 2, "svd": 3, "other": 4, "gemm_fp64": 5}
+KSTAT = {"gemm": 0, "wstage": 1, "qr": 2, "svd": 3, "other": 4, "gemm_fp64": 5,
+         "host_plan": 6, "host_launch": 7, "host_sync": 8}
+DEVICE_KSTAT = ("gemm", "wstage", "qr", "svd", "other", "gemm_fp64")
 ERRORS = {-1: "INVALID_ARG", -2: "SECTOR", -3: "KRYLOV_SINGULAR", -4: "NONFINITE",
           -5: "CUDA", -6: "OOM", -7: "ZERO_STATE", -8: "NUMERIC"}
 

@@ -27,6 +27,7 @@ thread_local std::string g_create_err;
 template <class F>
 int guard(tdmps_ctx_t ctx, F&& f) {
   try {
+    if (ctx) ctx->c->api_enter();
     f();
     if (ctx) ctx->c->err.clear();
     return TDMPS_OK;

@@ -121,14 +121,14 @@ const void* Context::stage(const void* src, size_t bytes) {
     // oversize: dedicated buffer released after the stream passes it
     DevPtr b = dev_alloc(need, st);
     TD_CHECK_CUDA(cudaMemcpyAsync(b->p, src, bytes, cudaMemcpyHostToDevice, st));
-    TD_CHECK_CUDA(cudaStreamSynchronize(st));
+    wait_stream();
     // its stream-ordered free is enqueued when the last holder lets go, so
     // keeping it here until the context's next synchronisation is enough
     oversize.push_back(b);
     return b->p;
   }
   if (ring_off + need > ring_cap) {
-    TD_CHECK_CUDA(cudaStreamSynchronize(st));
+    wait_stream();
     ring_off = 0;
   }
   std::memcpy(h_ring + ring_off, src, bytes);
@@ -156,6 +156,12 @@ void Context::kbegin(int kind, cudaEvent_t* a) {
   (void)kind;
   *a = nullptr;
   if (!stats) return;
+  const auto now = std::chrono::steady_clock::now();
+  if (host_mark_valid) {
+    kstat[TDMPS_KSTAT_HOST_PLAN].launches += 1;
+    kstat[TDMPS_KSTAT_HOST_PLAN].ms += std::chrono::duration<double, std::milli>(now - host_mark).count();
+  }
+  launch_start = now;
   *a = take_event();
   TD_CHECK_CUDA(cudaEventRecord(*a, st));
 }
@@ -169,6 +175,11 @@ void Context::kend(int kind, cudaEvent_t a, double flops, double bytes) {
   kstat[kind].launches += 1;
   kstat[kind].flops += flops;
   kstat[kind].bytes += bytes;
+  host_mark = std::chrono::steady_clock::now();
+  host_mark_valid = true;
+  kstat[TDMPS_KSTAT_HOST_LAUNCH].launches += 1;
+  kstat[TDMPS_KSTAT_HOST_LAUNCH].ms +=
+      std::chrono::duration<double, std::milli>(host_mark - launch_start).count();
 }
 
 void Context::collect_stats() {
@@ -183,8 +194,20 @@ void Context::collect_stats() {
   pending.clear();
 }
 
-void Context::sync() {
+void Context::wait_stream() {
+  if (!stats) {
+    TD_CHECK_CUDA(cudaStreamSynchronize(st));
+    return;
+  }
+  const auto t0 = std::chrono::steady_clock::now();
   TD_CHECK_CUDA(cudaStreamSynchronize(st));
+  kstat[TDMPS_KSTAT_HOST_SYNC].launches += 1;
+  kstat[TDMPS_KSTAT_HOST_SYNC].ms +=
+      std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+}
+
+void Context::sync() {
+  wait_stream();
   oversize.clear();
   check_device_errors();
 }
@@ -226,6 +249,8 @@ void upload_mpo_tables(MPOd& m, Context& c) {
   m.tab_right.assign(m.L, {});
   m.tab_left_idx.assign(m.L, {});
   m.tab_right_idx.assign(m.L, {});
+  m.tab_left_flat.assign(m.L, {});
+  m.tab_right_flat.assign(m.L, {});
   for (int i = 0; i < m.L; ++i) {
     const MPOBond& bi = m.bonds[i];
     const MPOBond& bo = m.bonds[i + 1];
@@ -271,6 +296,13 @@ void upload_mpo_tables(MPOd& m, Context& c) {
       m.tab_right_idx[i][kv.first] = (int)m.tab_right[i].size();
       m.tab_right[i].push_back(t);
     }
+    const int ngo = (int)bo.gq.size(), ngi = (int)bi.gq.size();
+    m.tab_left_flat[i].assign((size_t)16 * ngo, -1);
+    m.tab_right_flat[i].assign((size_t)16 * ngi, -1);
+    for (auto& kv : m.tab_left_idx[i])
+      m.tab_left_flat[i][(size_t)(kv.first[0] * 4 + kv.first[1]) * ngo + kv.first[2]] = kv.second;
+    for (auto& kv : m.tab_right_idx[i])
+      m.tab_right_flat[i][(size_t)(kv.first[0] * 4 + kv.first[1]) * ngi + kv.first[2]] = kv.second;
   }
   m.rowptr = dev_alloc(std::max<size_t>(rowptr.size(), 1) * sizeof(int), c.st);
   m.ent_w = dev_alloc(std::max<size_t>(ent_w.size(), 1) * sizeof(int), c.st);
@@ -289,7 +321,7 @@ void upload_mpo_tables(MPOd& m, Context& c) {
                                   cudaMemcpyHostToDevice, c.st));
   }
   // host vectors must outlive the async copies
-  TD_CHECK_CUDA(cudaStreamSynchronize(c.st));
+  c.wait_stream();
 }
 
 // ------------------------------------------------------------------ batches
@@ -556,9 +588,9 @@ static Inter plan_lstage(Context& c, const Env& E, const SiteT& ket, const Bond&
 // Sparse MPO-tensor stage, either direction.
 //   left:  Y[rg][s][w_out][b'] = sum_{s', w_in} W[w_in, w_out, s, s'] X[rg][w_in][s'][b']
 //   right: Y[rb][s][w_in][a']  = sum_{s', w_out} W[w_in, w_out, s, s'] X[rb][w_out][s'][a']
-static Inter plan_wstage(Context& c, const Inter& X, const MPOd& m, int site, bool left,
+static Inter plan_wstage(Context& c, Inter&& X, const MPOd& m, int site, bool left,
                          WBatch& wb) {
-  if (m.identity) return X;
+  if (m.identity) return std::move(X);   // no copy of the block index
   if (wb.mpo && wb.mpo != &m) throw Error(TDMPS_ERR_INVALID_ARG, "mixed MPOs in one W batch");
   wb.mpo = &m;
   wb.et = X.et;
@@ -566,41 +598,47 @@ static Inter plan_wstage(Context& c, const Inter& X, const MPOd& m, int site, bo
   const MPOBond& bo = m.bonds[site + 1];
   const MPOBond& bx = left ? bi : bo;   // channels of the input
   const MPOBond& by = left ? bo : bi;   // channels of the output
-  std::map<std::pair<int, int>, std::array<int, 4>> groups;
-  for (int x = 0; x < (int)X.blocks.size(); ++x) {
-    auto key = std::make_pair(X.blocks[x].rg, X.blocks[x].k);
-    auto it = groups.find(key);
-    if (it == groups.end()) it = groups.emplace(key, std::array<int, 4>{-1, -1, -1, -1}).first;
-    it->second[X.blocks[x].sig] = x;
+  // X blocks grouped by (row group, column sector), in that order; a flat
+  // table replaces an ordered map (this runs for every launch)
+  int nrg = 0, nk = 0;
+  for (const auto& b : X.blocks) {
+    nrg = std::max(nrg, b.rg + 1);
+    nk = std::max(nk, b.k + 1);
   }
+  std::vector<std::array<int, 4>> groups((size_t)nrg * nk, std::array<int, 4>{-1, -1, -1, -1});
+  for (int x = 0; x < (int)X.blocks.size(); ++x)
+    groups[(size_t)X.blocks[x].rg * nk + X.blocks[x].k][X.blocks[x].sig] = x;
+  const std::vector<int>& flat = left ? m.tab_left_flat[site] : m.tab_right_flat[site];
+  const int ngy = (int)by.gq.size();
   Inter Y;
   struct P { int xs[4]; int tabs[4]; };
   std::vector<P> pend;
-  for (auto& kv : groups) {
+  for (size_t gi = 0; gi < groups.size(); ++gi) {
+    const std::array<int, 4>& grp = groups[gi];
+    if (grp[0] < 0 && grp[1] < 0 && grp[2] < 0 && grp[3] < 0) continue;
+    const int rg = (int)(gi / nk), kk = (int)(gi % nk);
     for (int s = 0; s < 4; ++s) {
       P p;
       int gy = -1, first = -1;
       for (int sp = 0; sp < 4; ++sp) {
         p.xs[sp] = -1;
         p.tabs[sp] = -1;
-        int x = kv.second[sp];
+        int x = grp[sp];
         if (x < 0) continue;
         // charge of the output channel group
         QN qy = left ? bx.gq[X.blocks[x].g] + SITE_Q[s] - SITE_Q[sp]
                      : bx.gq[X.blocks[x].g] - SITE_Q[s] + SITE_Q[sp];
         int g = by.find(qy);
         if (g < 0) continue;
-        const auto& idx = left ? m.tab_left_idx[site] : m.tab_right_idx[site];
-        auto it = idx.find({s, sp, g});
-        if (it == idx.end()) continue;
+        const int tab = flat[(size_t)(s * 4 + sp) * ngy + g];
+        if (tab < 0) continue;
         gy = g;
         p.xs[sp] = x;
-        p.tabs[sp] = it->second;
+        p.tabs[sp] = tab;
         if (first < 0) first = x;
       }
       if (first < 0) continue;
-      Y.add(kv.first.first, s, gy, kv.first.second, X.blocks[first].rows, by.gsize[gy],
-            X.blocks[first].cols);
+      Y.add(rg, s, gy, kk, X.blocks[first].rows, by.gsize[gy], X.blocks[first].cols);
       pend.push_back(p);
     }
   }
@@ -642,20 +680,34 @@ struct LocalTerm {
 };
 
 // out[r][s][b] = sum_t coef_t sum_{w', b'} Y_t[r][s][w'][b'] R_t[b][w'][b']
+// Environment blocks of one local term grouped by row group (CSR over rg).
+struct ByRow {
+  std::vector<int> start, list;
+  void build(const Inter& E) {
+    int n = 0;
+    for (const auto& b : E.blocks) n = std::max(n, b.rg + 1);
+    start.assign((size_t)n + 1, 0);
+    list.resize(E.blocks.size());
+    for (const auto& b : E.blocks) start[(size_t)b.rg + 1]++;
+    for (size_t i = 1; i < start.size(); ++i) start[i] += start[i - 1];
+    std::vector<int> fill(start.begin(), start.end() - 1);
+    for (int b = 0; b < (int)E.blocks.size(); ++b) list[fill[E.blocks[b].rg]++] = b;
+  }
+  int lo(int rg) const { return rg + 1 < (int)start.size() ? start[rg] : 0; }
+  int hi(int rg) const { return rg + 1 < (int)start.size() ? start[rg + 1] : 0; }
+};
+
 static void plan_rstage(const std::vector<LocalTerm>& ts, SiteT& out, GemmBatch& gb) {
-  std::vector<std::map<int, std::vector<int>>> rby(ts.size());
-  for (size_t t = 0; t < ts.size(); ++t)
-    for (int b = 0; b < (int)ts[t].E->t.blocks.size(); ++b)
-      rby[t][ts[t].E->t.blocks[b].rg].push_back(b);
+  std::vector<ByRow> rby(ts.size());
+  for (size_t t = 0; t < ts.size(); ++t) rby[t].build(ts[t].E->t);
   for (int o = 0; o < (int)out.blocks.size(); ++o) {
     const SiteT::Blk& ob = out.blocks[o];
     gb.task(out.ptr(o), 0, ob.rows, ob.cols, ob.cols, OP_N, ts[0].Y->et, OP_T, ts[0].E->t.et,
             false, 1.0);
     for (size_t t = 0; t < ts.size(); ++t) {
-      auto it = rby[t].find(ob.sb);
-      if (it == rby[t].end()) continue;
       const Inter& R = ts[t].E->t;
-      for (int rb : it->second) {
+      for (int q = rby[t].lo(ob.sb); q < rby[t].hi(ob.sb); ++q) {
+        const int rb = rby[t].list[q];
         const Inter::Blk& r = R.blocks[rb];
         int y = ts[t].Y->find(ob.r, ob.sig, r.g, r.k);
         if (y < 0) continue;
@@ -668,19 +720,16 @@ static void plan_rstage(const std::vector<LocalTerm>& ts, SiteT& out, GemmBatch&
 
 // out[a][s][b] = sum_t coef_t sum_{w, a'} L_t[a][w][a'] Zp_t[b][s][w][a']
 static void plan_lcontract(const std::vector<LocalTerm>& ts, SiteT& out, GemmBatch& gb) {
-  std::vector<std::map<int, std::vector<int>>> lby(ts.size());
-  for (size_t t = 0; t < ts.size(); ++t)
-    for (int b = 0; b < (int)ts[t].E->t.blocks.size(); ++b)
-      lby[t][ts[t].E->t.blocks[b].rg].push_back(b);
+  std::vector<ByRow> lby(ts.size());
+  for (size_t t = 0; t < ts.size(); ++t) lby[t].build(ts[t].E->t);
   for (int o = 0; o < (int)out.blocks.size(); ++o) {
     const SiteT::Blk& ob = out.blocks[o];
     gb.task(out.ptr(o), 0, ob.rows, ob.cols, ob.cols, OP_N, ts[0].E->t.et, OP_T, ts[0].Y->et,
             false, 1.0);
     for (size_t t = 0; t < ts.size(); ++t) {
-      auto it = lby[t].find(ob.r);
-      if (it == lby[t].end()) continue;
       const Inter& Lt = ts[t].E->t;
-      for (int lb : it->second) {
+      for (int q = lby[t].lo(ob.r); q < lby[t].hi(ob.r); ++q) {
+        const int lb = lby[t].list[q];
         const Inter::Blk& l = Lt.blocks[lb];
         int z = ts[t].Y->find(ob.sb, ob.sig, l.g, l.k);
         if (z < 0) continue;
@@ -698,33 +747,67 @@ static Env plan_env_left(Context& c, const Inter& Y, const SiteT& bra, const Bon
   e.rows = RowGroups::from_bond(bra_right);
   e.mb = &mb;
   e.ket_copy = ket_right;
-  std::map<std::pair<int, int>, std::vector<int>> ybys;
-  for (int y = 0; y < (int)Y.blocks.size(); ++y)
-    ybys[{Y.blocks[y].rg, Y.blocks[y].sig}].push_back(y);
-  struct T { int bra, y; };
-  std::map<std::array<int, 2>, std::vector<T>> contrib;   // (sb, g') -> terms
-  for (int b = 0; b < (int)bra.blocks.size(); ++b) {
-    const SiteT::Blk& cb = bra.blocks[b];
-    auto it = ybys.find({cb.r, cb.sig});
-    if (it == ybys.end()) continue;
-    for (int y : it->second) contrib[{cb.sb, Y.blocks[y].g}].push_back({b, y});
+  // Y blocks by (row group, sigma), then the terms of every output block
+  // (bra right sector, channel group) grouped in (sector, group) order --
+  // counting sorts over flat index ranges instead of ordered maps
+  int nrg = 0, ng = 0;
+  for (const auto& y : Y.blocks) {
+    nrg = std::max(nrg, y.rg + 1);
+    ng = std::max(ng, y.g + 1);
   }
-  for (auto& kv : contrib) {
-    const Inter::Blk& y0 = Y.blocks[kv.second[0].y];
-    e.t.add(kv.first[0], -1, kv.first[1], y0.k, bra_right.d[kv.first[0]], y0.W, y0.cols);
+  std::vector<int> ystart((size_t)nrg * 4 + 1, 0), ylist(Y.blocks.size());
+  for (const auto& y : Y.blocks) ystart[(size_t)y.rg * 4 + y.sig + 1]++;
+  for (size_t i = 1; i < ystart.size(); ++i) ystart[i] += ystart[i - 1];
+  {
+    std::vector<int> fill(ystart.begin(), ystart.end() - 1);
+    for (int y = 0; y < (int)Y.blocks.size(); ++y) ylist[fill[(size_t)Y.blocks[y].rg * 4 + Y.blocks[y].sig]++] = y;
+  }
+  struct T { int bra, y; };
+  const size_t nkey = (size_t)bra_right.nsec() * ng;
+  std::vector<int> cstart(nkey + 1, 0);
+  auto ys_of = [&](const SiteT::Blk& cb, int& lo, int& hi) {
+    lo = hi = 0;
+    if (cb.r >= nrg) return;
+    lo = ystart[(size_t)cb.r * 4 + cb.sig];
+    hi = ystart[(size_t)cb.r * 4 + cb.sig + 1];
+  };
+  for (const auto& cb : bra.blocks) {
+    int lo, hi;
+    ys_of(cb, lo, hi);
+    for (int q = lo; q < hi; ++q) cstart[(size_t)cb.sb * ng + Y.blocks[ylist[q]].g + 1]++;
+  }
+  for (size_t i = 1; i < cstart.size(); ++i) cstart[i] += cstart[i - 1];
+  std::vector<T> terms(cstart[nkey]);
+  {
+    std::vector<int> fill(cstart.begin(), cstart.end() - 1);
+    for (int b = 0; b < (int)bra.blocks.size(); ++b) {
+      int lo, hi;
+      ys_of(bra.blocks[b], lo, hi);
+      for (int q = lo; q < hi; ++q) {
+        const int y = ylist[q];
+        terms[fill[(size_t)bra.blocks[b].sb * ng + Y.blocks[y].g]++] = {b, y};
+      }
+    }
+  }
+  for (size_t key = 0; key < nkey; ++key) {
+    if (cstart[key] == cstart[key + 1]) continue;
+    const Inter::Blk& y0 = Y.blocks[terms[cstart[key]].y];
+    const int sb = (int)(key / ng), g = (int)(key % ng);
+    e.t.add(sb, -1, g, y0.k, bra_right.d[sb], y0.W, y0.cols);
   }
   e.t.et = Y.et;
   e.t.alloc(c.st, false);
   int id = 0;
-  for (auto& kv : contrib) {
+  for (size_t key = 0; key < nkey; ++key) {
+    if (cstart[key] == cstart[key + 1]) continue;
     const Inter::Blk& eb = e.t.blocks[id];
     int N = eb.W * eb.cols;
     gb.task(e.t.ptr(id), e.t.et, eb.rows, N, N, OP_C, site_et(c), OP_N, Y.et, false, 1.0);
-    for (auto& tm : kv.second) {
-      const SiteT::Blk& cb = bra.blocks[tm.bra];
+    for (int q = cstart[key]; q < cstart[key + 1]; ++q) {
+      const SiteT::Blk& cb = bra.blocks[terms[q].bra];
       int aet;
-      const void* ap = site_operand(c, bra, tm.bra, aet);
-      gb.term(ap, cb.cols, Y.ptr(tm.y), N, cb.rows);
+      const void* ap = site_operand(c, bra, terms[q].bra, aet);
+      gb.term(ap, cb.cols, Y.ptr(terms[q].y), N, cb.rows);
     }
     ++id;
   }
@@ -734,18 +817,21 @@ static Env plan_env_left(Context& c, const Inter& Y, const SiteT& bra, const Bon
 // Z[rb][w'][s'][a'] = sum_b' R[rb][w'][b'] A[a'][s'][b']
 static Inter plan_r1(Context& c, const Env& R, const SiteT& A, const Bond& ket_left,
                      GemmBatch& gb) {
-  std::map<std::pair<int, int>, int> kby;   // (right sector, sigma) -> ket block
-  for (int b = 0; b < (int)A.blocks.size(); ++b) kby[{A.blocks[b].sb, A.blocks[b].sig}] = b;
+  int nsb = 0;   // (right sector, sigma) -> ket block, flat
+  for (const auto& b : A.blocks) nsb = std::max(nsb, b.sb + 1);
+  std::vector<int> kby((size_t)nsb * 4, -1);
+  for (int b = 0; b < (int)A.blocks.size(); ++b) kby[(size_t)A.blocks[b].sb * 4 + A.blocks[b].sig] = b;
   Inter Z;
   std::vector<std::pair<int, int>> src;
   for (int rb = 0; rb < (int)R.t.blocks.size(); ++rb) {
     const Inter::Blk& r = R.t.blocks[rb];
+    if (r.k >= nsb) continue;
     for (int s = 0; s < 4; ++s) {
-      auto it = kby.find({r.k, s});
-      if (it == kby.end()) continue;
-      const SiteT::Blk& ab = A.blocks[it->second];
+      const int kb = kby[(size_t)r.k * 4 + s];
+      if (kb < 0) continue;
+      const SiteT::Blk& ab = A.blocks[kb];
       Z.add(r.rg, s, r.g, ab.r, r.rows, r.W, ket_left.d[ab.r]);
-      src.push_back({rb, it->second});
+      src.push_back({rb, kb});
     }
   }
   Z.et = R.t.et;
@@ -764,36 +850,70 @@ static Inter plan_r1(Context& c, const Env& R, const SiteT& A, const Bond& ket_l
 // R_new[a][w][a'] = sum_{s, b} conj(C[a][s][b]) Zp[b][s][w][a']
 static Env plan_env_right(Context& c, const Inter& Zp, const SiteT& bra, const Bond& bra_left,
                           const MPOBond& mb, const Bond& ket_left, GemmBatch& gb) {
-  std::map<std::pair<int, int>, std::vector<int>> zby;
-  for (int z = 0; z < (int)Zp.blocks.size(); ++z) zby[{Zp.blocks[z].rg, Zp.blocks[z].sig}].push_back(z);
+  // Z' blocks by (row group = right sector, sigma); terms of every output
+  // block (bra left sector, channel group) in (sector, group) order
+  int nrg = 0, ng = 0;
+  for (const auto& z : Zp.blocks) {
+    nrg = std::max(nrg, z.rg + 1);
+    ng = std::max(ng, z.g + 1);
+  }
+  std::vector<int> zstart((size_t)nrg * 4 + 1, 0), zlist(Zp.blocks.size());
+  for (const auto& z : Zp.blocks) zstart[(size_t)z.rg * 4 + z.sig + 1]++;
+  for (size_t i = 1; i < zstart.size(); ++i) zstart[i] += zstart[i - 1];
+  {
+    std::vector<int> fill(zstart.begin(), zstart.end() - 1);
+    for (int z = 0; z < (int)Zp.blocks.size(); ++z) zlist[fill[(size_t)Zp.blocks[z].rg * 4 + Zp.blocks[z].sig]++] = z;
+  }
   struct T { int bra, z; };
-  std::map<std::array<int, 2>, std::vector<T>> contrib;
-  for (int b = 0; b < (int)bra.blocks.size(); ++b) {
-    const SiteT::Blk& cb = bra.blocks[b];
-    auto it = zby.find({cb.sb, cb.sig});
-    if (it == zby.end()) continue;
-    for (int z : it->second) contrib[{cb.r, Zp.blocks[z].g}].push_back({b, z});
+  const size_t nkey = (size_t)bra_left.nsec() * ng;
+  std::vector<int> cstart(nkey + 1, 0);
+  auto zs_of = [&](const SiteT::Blk& cb, int& lo, int& hi) {
+    lo = hi = 0;
+    if (cb.sb >= nrg) return;
+    lo = zstart[(size_t)cb.sb * 4 + cb.sig];
+    hi = zstart[(size_t)cb.sb * 4 + cb.sig + 1];
+  };
+  for (const auto& cb : bra.blocks) {
+    int lo, hi;
+    zs_of(cb, lo, hi);
+    for (int q = lo; q < hi; ++q) cstart[(size_t)cb.r * ng + Zp.blocks[zlist[q]].g + 1]++;
+  }
+  for (size_t i = 1; i < cstart.size(); ++i) cstart[i] += cstart[i - 1];
+  std::vector<T> terms(cstart[nkey]);
+  {
+    std::vector<int> fill(cstart.begin(), cstart.end() - 1);
+    for (int b = 0; b < (int)bra.blocks.size(); ++b) {
+      int lo, hi;
+      zs_of(bra.blocks[b], lo, hi);
+      for (int q = lo; q < hi; ++q) {
+        const int z = zlist[q];
+        terms[fill[(size_t)bra.blocks[b].r * ng + Zp.blocks[z].g]++] = {b, z};
+      }
+    }
   }
   Env e;
   e.rows = RowGroups::from_bond(bra_left);
   e.mb = &mb;
   e.ket_copy = ket_left;
-  for (auto& kv : contrib) {
-    const Inter::Blk& z0 = Zp.blocks[kv.second[0].z];
-    e.t.add(kv.first[0], -1, kv.first[1], z0.k, bra_left.d[kv.first[0]], z0.W, z0.cols);
+  for (size_t key = 0; key < nkey; ++key) {
+    if (cstart[key] == cstart[key + 1]) continue;
+    const Inter::Blk& z0 = Zp.blocks[terms[cstart[key]].z];
+    const int r = (int)(key / ng), g = (int)(key % ng);
+    e.t.add(r, -1, g, z0.k, bra_left.d[r], z0.W, z0.cols);
   }
   e.t.et = Zp.et;
   e.t.alloc(c.st, false);
   int id = 0;
-  for (auto& kv : contrib) {
+  for (size_t key = 0; key < nkey; ++key) {
+    if (cstart[key] == cstart[key + 1]) continue;
     const Inter::Blk& eb = e.t.blocks[id];
     int N = eb.W * eb.cols;
     gb.task(e.t.ptr(id), e.t.et, eb.rows, N, N, OP_J, site_et(c), OP_N, Zp.et, false, 1.0);
-    for (auto& tm : kv.second) {
-      const SiteT::Blk& cb = bra.blocks[tm.bra];
+    for (int q = cstart[key]; q < cstart[key + 1]; ++q) {
+      const SiteT::Blk& cb = bra.blocks[terms[q].bra];
       int aet;
-      const void* ap = site_operand(c, bra, tm.bra, aet);
-      gb.term(ap, cb.cols, Zp.ptr(tm.z), N, cb.cols);
+      const void* ap = site_operand(c, bra, terms[q].bra, aet);
+      gb.term(ap, cb.cols, Zp.ptr(terms[q].z), N, cb.cols);
     }
     ++id;
   }
@@ -807,7 +927,7 @@ static Env env_update_left(Context& c, const Env& E, const SiteT& bra, const Bon
   Inter X = plan_lstage(c, E, ket.sites[site], ket.bonds[site + 1], g1);
   g1.run();
   WBatch wb;
-  Inter Y = plan_wstage(c, X, m, site, true, wb);
+  Inter Y = plan_wstage(c, std::move(X), m, site, true, wb);
   wb.run(c);
   GemmBatch g2(c);
   Env e = plan_env_left(c, Y, bra, bra_right, m.bonds[site + 1], ket.bonds[site + 1], g2);
@@ -821,7 +941,7 @@ static Env env_update_right(Context& c, const Env& R, const SiteT& bra, const Bo
   Inter Z = plan_r1(c, R, ket.sites[site], ket.bonds[site], g1);
   g1.run();
   WBatch wb;
-  Inter Zp = plan_wstage(c, Z, m, site, false, wb);
+  Inter Zp = plan_wstage(c, std::move(Z), m, site, false, wb);
   wb.run(c);
   GemmBatch g2(c);
   Env e = plan_env_right(c, Zp, bra, bra_left, m.bonds[site], ket.bonds[site], g2);
@@ -1242,16 +1362,16 @@ void check_same_space(const MPSd& a, const MPSd& b) {
 
 // MPO stage for all terms: one launch per distinct (non-identity) MPO
 std::vector<Inter> wstage_all(Context& c, const std::vector<TermState>& ts,
-                              const std::vector<Inter>& X, int site, bool left) {
+                              std::vector<Inter>&& X, int site, bool left) {
   std::vector<Inter> Y(ts.size());
   std::vector<WBatch> batches;
   std::vector<const MPOd*> mpos;
   for (size_t t = 0; t < ts.size(); ++t) {
-    if (ts[t].mpo->identity) { Y[t] = X[t]; continue; }
+    if (ts[t].mpo->identity) { Y[t] = std::move(X[t]); continue; }
     size_t b = 0;
     while (b < mpos.size() && mpos[b] != ts[t].mpo) ++b;
     if (b == mpos.size()) { mpos.push_back(ts[t].mpo); batches.emplace_back(); }
-    Y[t] = plan_wstage(c, X[t], *ts[t].mpo, site, left, batches[b]);
+    Y[t] = plan_wstage(c, std::move(X[t]), *ts[t].mpo, site, left, batches[b]);
   }
   for (auto& wb : batches) wb.run(c);
   return Y;
@@ -1267,7 +1387,7 @@ void right_env_step(Context& c, std::vector<TermState>& ts, const MPSd& C, int i
     for (size_t t = 0; t < ts.size(); ++t)
       Z[t] = plan_r1(c, ts[t].RE[i + 1], ts[t].ket->sites[i], ts[t].ket->bonds[i], g1);
     g1.run();
-    Zp = wstage_all(c, ts, Z, i, false);
+    Zp = wstage_all(c, ts, std::move(Z), i, false);
     zp = &Zp;
   }
   GemmBatch g3(c);
@@ -1293,7 +1413,7 @@ std::vector<Inter> left_stages(Context& c, std::vector<TermState>& ts, int i) {
   for (size_t t = 0; t < ts.size(); ++t)
     X[t] = plan_lstage(c, ts[t].LE[i], ts[t].ket->sites[i], ts[t].ket->bonds[i + 1], g1);
   g1.run();
-  return wstage_all(c, ts, X, i, true);
+  return wstage_all(c, ts, std::move(X), i, true);
 }
 
 // Zp_t = W_i^right (R_t[i+1] A_t[i]^T) for all terms
@@ -1303,7 +1423,7 @@ std::vector<Inter> right_stages(Context& c, std::vector<TermState>& ts, int i) {
   for (size_t t = 0; t < ts.size(); ++t)
     Z[t] = plan_r1(c, ts[t].RE[i + 1], ts[t].ket->sites[i], ts[t].ket->bonds[i], g1);
   g1.run();
-  return wstage_all(c, ts, Z, i, false);
+  return wstage_all(c, ts, std::move(Z), i, false);
 }
 
 }  // namespace
@@ -1378,7 +1498,7 @@ MPSd fit(Context& c, const std::vector<FitTerm>& terms, const MPSd& guess, const
         for (size_t t = 0; t < ts.size(); ++t)
           X2[t] = plan_lstage(c, E2[t], ts[t].ket->sites[i + 1], ts[t].ket->bonds[i + 2], g2);
         g2.run();
-        std::vector<Inter> Y2 = wstage_all(c, ts, X2, i + 1, true);
+        std::vector<Inter> Y2 = wstage_all(c, ts, std::move(X2), i + 1, true);
         SiteT Th = make_site(fr, C.bonds[i + 2], c.st, false);
         GemmBatch g3(c);
         plan_rstage(local_terms(Y2, i + 2, true), Th, g3);
@@ -1464,7 +1584,7 @@ void sandwich_batch(Context& c, const MPOd* mpo,
     g1.run();
     WBatch wb;
     std::vector<Inter> Y(pairs.size());
-    for (size_t p = 0; p < pairs.size(); ++p) Y[p] = plan_wstage(c, X[p], m, i, true, wb);
+    for (size_t p = 0; p < pairs.size(); ++p) Y[p] = plan_wstage(c, std::move(X[p]), m, i, true, wb);
     wb.run(c);
     GemmBatch g2(c);
     for (size_t p = 0; p < pairs.size(); ++p)
@@ -1709,7 +1829,7 @@ static void rdm_upper(Context& c, const MPSd& bra, const MPSd& ket, double2* out
     Inter X = plan_lstage(c, E, ket.sites[j], ket.bonds[j + 1], g1);
     g1.run();
     WBatch wb;
-    Inter Y = plan_wstage(c, X, R[j], 0, true, wb);
+    Inter Y = plan_wstage(c, std::move(X), R[j], 0, true, wb);
     wb.run(c);
     GemmBatch g2(c);
     Env Eo = plan_env_left(c, Y, bra.sites[j], bra.bonds[j + 1], R[j].bonds[1], ket.bonds[j + 1], g2);

@@ -2,6 +2,7 @@
 // contraction planners and the algorithms of the paper built on them.
 #pragma once
 
+#include <chrono>
 #include <complex>
 #include <functional>
 #include <map>
@@ -70,11 +71,16 @@ struct Context {
     return v.empty() ? nullptr : (const T*)stage(v.data(), v.size() * sizeof(T));
   }
   // kernel timing bracket
+  // host timing: the end of the previous launch call inside the current API call
+  std::chrono::steady_clock::time_point host_mark, launch_start;
+  bool host_mark_valid = false;
+  void api_enter() { host_mark_valid = false; }
   cudaEvent_t take_event();
   void kbegin(int kind, cudaEvent_t* a);
   void kend(int kind, cudaEvent_t a, double flops, double bytes);
   void collect_stats();
   void sync();
+  void wait_stream();   // cudaStreamSynchronize(st), timed into HOST_SYNC
   void check_device_errors();
   const MPOd& identity_mpo(int L);
   int et() const { return precision == TDMPS_FP64 ? 0 : 1; }

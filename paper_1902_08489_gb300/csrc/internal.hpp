@@ -148,6 +148,8 @@ struct MPOd {
   // device tables
   std::vector<std::vector<WTable>> tab_left, tab_right;
   std::vector<std::map<std::array<int, 3>, int>> tab_left_idx, tab_right_idx;
+  // the same lookups as flat arrays: [(sig*4 + sigp) * ngroups + g] -> table or -1
+  std::vector<std::vector<int>> tab_left_flat, tab_right_flat;
   DevPtr rowptr, ent_w, ent_v, ent_vf;        // int, int, double, float
   int64_t n_elem = 0;
 };
