@@ -54,7 +54,7 @@ void evolve_batch(Context& c, const std::vector<BatchItem>& items, int method, i
   if (n_workers <= 0) n_workers = 8;
   n_workers = std::min(n_workers, n);
   while ((int)c.workers.size() < n_workers)
-    c.workers.push_back(std::make_unique<Worker>(c.precision, (size_t)16 << 20));
+    c.workers.push_back(std::make_unique<Worker>(c.precision, (size_t)32 << 20));
   for (int w = 0; w < n_workers; ++w) {
     Context& wc = *c.workers[w]->c;
     wc.precision = c.precision;

@@ -93,7 +93,10 @@ void Inter::alloc(cudaStream_t st, bool zero) {
 // ------------------------------------------------------------------ context
 
 Context::Context(cudaStream_t s, int prec, size_t ring_bytes) : st(s), precision(prec) {
-  ring_cap = ring_bytes;
+  seg_cap = ((ring_bytes / RING_SEGS) + 255) & ~(size_t)255;
+  ring_cap = seg_cap * RING_SEGS;
+  for (int k = 0; k < RING_SEGS; ++k)
+    TD_CHECK_CUDA(cudaEventCreateWithFlags(&seg_ev[k], cudaEventDisableTiming));
   TD_CHECK_CUDA(cudaGetDevice(&device));
   TD_CHECK_CUDA(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, device));
   TD_CHECK_CUDA(cudaMallocHost((void**)&h_ring, ring_cap));
@@ -113,11 +116,13 @@ Context::~Context() {
   cudaStreamSynchronize(st);
   if (h_ring) cudaFreeHost(h_ring);
   if (d_ring) cudaFree(d_ring);
+  for (int k = 0; k < RING_SEGS; ++k)
+    if (seg_ev[k]) cudaEventDestroy(seg_ev[k]);
 }
 
 const void* Context::stage(const void* src, size_t bytes) {
   size_t need = (bytes + 255) & ~(size_t)255;
-  if (need > ring_cap) {
+  if (need > seg_cap) {
     // oversize: dedicated buffer released after the stream passes it
     DevPtr b = dev_alloc(need, st);
     TD_CHECK_CUDA(cudaMemcpyAsync(b->p, src, bytes, cudaMemcpyHostToDevice, st));
@@ -127,9 +132,14 @@ const void* Context::stage(const void* src, size_t bytes) {
     oversize.push_back(b);
     return b->p;
   }
-  if (ring_off + need > ring_cap) {
-    wait_stream();
-    ring_off = 0;
+  if (ring_off - (size_t)cur_seg * seg_cap + need > seg_cap) {
+    // leave the current segment (all its consumers are enqueued by now)
+    TD_CHECK_CUDA(cudaEventRecord(seg_ev[cur_seg], st));
+    seg_live[cur_seg] = true;
+    const int next = (cur_seg + 1) % RING_SEGS;
+    if (seg_live[next]) wait_event(seg_ev[next]);
+    cur_seg = next;
+    ring_off = (size_t)next * seg_cap;
   }
   std::memcpy(h_ring + ring_off, src, bytes);
   TD_CHECK_CUDA(cudaMemcpyAsync(d_ring + ring_off, h_ring + ring_off, bytes,
@@ -201,6 +211,18 @@ void Context::wait_stream() {
   }
   const auto t0 = std::chrono::steady_clock::now();
   TD_CHECK_CUDA(cudaStreamSynchronize(st));
+  kstat[TDMPS_KSTAT_HOST_SYNC].launches += 1;
+  kstat[TDMPS_KSTAT_HOST_SYNC].ms +=
+      std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+}
+
+void Context::wait_event(cudaEvent_t e) {
+  if (!stats) {
+    TD_CHECK_CUDA(cudaEventSynchronize(e));
+    return;
+  }
+  const auto t0 = std::chrono::steady_clock::now();
+  TD_CHECK_CUDA(cudaEventSynchronize(e));
   kstat[TDMPS_KSTAT_HOST_SYNC].launches += 1;
   kstat[TDMPS_KSTAT_HOST_SYNC].ms +=
       std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
@@ -457,12 +479,14 @@ struct GemmBatch {
     // tasks, terms and the tile map go to the device in one staged copy
     auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
     const size_t o_terms = al(tk.size() * sizeof(GemmTask));
-    const size_t o_tiles = o_terms + al(terms.size() * sizeof(GemmTerm));
+    const size_t o_zero = o_terms + al(terms.size() * sizeof(GemmTerm));
+    const size_t o_tiles = o_zero + al(zero.size() * sizeof(ZeroRegion));
     const size_t pk_bytes = o_tiles + tile_task.size() * sizeof(int);
     std::vector<char>& pk = c.pack;
     pk.resize(pk_bytes);
     std::memcpy(pk.data(), tk.data(), tk.size() * sizeof(GemmTask));
     if (!terms.empty()) std::memcpy(pk.data() + o_terms, terms.data(), terms.size() * sizeof(GemmTerm));
+    if (!zero.empty()) std::memcpy(pk.data() + o_zero, zero.data(), zero.size() * sizeof(ZeroRegion));
     std::memcpy(pk.data() + o_tiles, tile_task.data(), tile_task.size() * sizeof(int));
     const char* base = (const char*)c.stage(pk.data(), pk_bytes);
     const GemmTask* dt = (const GemmTask*)base;
@@ -471,7 +495,7 @@ struct GemmBatch {
     cudaEvent_t ev;
     const int kind = fp64 ? TDMPS_KSTAT_GEMM_FP64 : TDMPS_KSTAT_GEMM;
     c.kbegin(kind, &ev);
-    if (!zero.empty()) launch_zero_regions(c.stage(zero), (int)zero.size(), c.st);
+    if (!zero.empty()) launch_zero_regions((const ZeroRegion*)(base + o_zero), (int)zero.size(), c.st);
     if (fp64)
       launch_gemm(dt, (int)tk.size(), dm, dtt, (int)tile_task.size(), c.st);
     else
@@ -1239,9 +1263,10 @@ static SplitResult svd_split(Context& c, const SiteT& Th, const RowGroups& rows,
   for (auto& sh : shapes) sq.push_back({sh.second, sh.second});
   FactWork fj = fact_alloc(c, sq);
   {
-    const FactTask* ds = c.stage(fw.tasks);
-    const FactTask* dd = c.stage(fj.tasks);
-    launch_adjoint(ds, dd, (int)fw.tasks.size(), c.st);
+    std::vector<FactTask> both(fw.tasks);
+    both.insert(both.end(), fj.tasks.begin(), fj.tasks.end());
+    const FactTask* ds = c.stage(both);
+    launch_adjoint(ds, ds + fw.tasks.size(), (int)fw.tasks.size(), c.st);
   }
   run_svd(c, fj);
   // U = Q J  (column-major m x n), computed as U^T = J^T Q^T in row-major terms

@@ -43,9 +43,18 @@ struct Context {
   int n_sm = 0;               // streaming multiprocessors of the device
   std::string err;
   // staging ring for task lists
+  // The staging ring is split into RING_SEGS segments.  Every staged array's
+  // consumer is enqueued before the next stage() call, so when stage() leaves
+  // a segment, an event recorded there marks the point after which the GPU no
+  // longer reads it; re-entering that segment waits only for that event,
+  // never for the whole stream, so the GPU keeps the work queued behind it.
+  static constexpr int RING_SEGS = 8;
   char* h_ring = nullptr;
   char* d_ring = nullptr;
-  size_t ring_cap = 0, ring_off = 0;
+  size_t ring_cap = 0, ring_off = 0, seg_cap = 0;
+  int cur_seg = 0;
+  cudaEvent_t seg_ev[RING_SEGS] = {};
+  bool seg_live[RING_SEGS] = {};
   std::vector<DevPtr> oversize;   // task lists larger than the ring, until the next sync()
   // statistics
   bool stats = false;
@@ -62,7 +71,7 @@ struct Context {
 
   std::vector<std::unique_ptr<Worker>> workers;   // instance-batch workers (lazy)
 
-  explicit Context(cudaStream_t s, int prec, size_t ring_bytes = (size_t)64 << 20);
+  explicit Context(cudaStream_t s, int prec, size_t ring_bytes = (size_t)512 << 20);
   ~Context();
 
   // copy a host array into device memory valid until the stream passes it
@@ -81,6 +90,7 @@ struct Context {
   void collect_stats();
   void sync();
   void wait_stream();   // cudaStreamSynchronize(st), timed into HOST_SYNC
+  void wait_event(cudaEvent_t e);   // cudaEventSynchronize, timed into HOST_SYNC
   void check_device_errors();
   const MPOd& identity_mpo(int L);
   int et() const { return precision == TDMPS_FP64 ? 0 : 1; }

@@ -11,6 +11,7 @@
 // is not acceptable.
 #include <cuda_runtime.h>
 
+#include <cstring>
 #include <mutex>
 #include <vector>
 
@@ -46,10 +47,11 @@ double2* scratch_for_current_device() {
   return g_scratch_ptr[dev];
 }
 
-// copy a task list through the pre-allocated ring; never allocates
+// copy a task list through the pre-allocated ring; never allocates (a list
+// larger than one ring segment would need a dedicated buffer: rejected)
 const void* stage_ring(Context& c, const void* src, size_t bytes) {
   size_t need = (bytes + 255) & ~(size_t)255;
-  if (need > c.ring_cap) throw Error(TDMPS_ERR_INVALID_ARG, "task list exceeds the staging ring");
+  if (need > c.seg_cap) throw Error(TDMPS_ERR_INVALID_ARG, "task list exceeds the staging ring");
   return c.stage(src, bytes);
 }
 
@@ -164,10 +166,19 @@ cplx overlap_noalloc(Context& c, const MPSd& bra, const MPSd& ket) {
         for (int q = 0; q < g.tiles_m * tn; ++q) tile_task.push_back(id);
       }
       if (tile_task.empty()) continue;
-      const GemmTask* dt = (const GemmTask*)stage_ring(c, tk.data(), tk.size() * sizeof(GemmTask));
-      const GemmTerm* dm =
-          (const GemmTerm*)stage_ring(c, terms.data(), terms.size() * sizeof(GemmTerm));
-      const int* dtt = (const int*)stage_ring(c, tile_task.data(), tile_task.size() * sizeof(int));
+      // one staged copy per launch (the ring reuses a segment once the
+      // launches that read it are enqueued)
+      const size_t o_terms = (tk.size() * sizeof(GemmTask) + 255) & ~(size_t)255;
+      const size_t o_tiles = o_terms + ((terms.size() * sizeof(GemmTerm) + 255) & ~(size_t)255);
+      std::vector<char>& pk = c.pack;
+      pk.resize(o_tiles + tile_task.size() * sizeof(int));
+      std::memcpy(pk.data(), tk.data(), tk.size() * sizeof(GemmTask));
+      std::memcpy(pk.data() + o_terms, terms.data(), terms.size() * sizeof(GemmTerm));
+      std::memcpy(pk.data() + o_tiles, tile_task.data(), tile_task.size() * sizeof(int));
+      const char* base = (const char*)stage_ring(c, pk.data(), pk.size());
+      const GemmTask* dt = (const GemmTask*)base;
+      const GemmTerm* dm = (const GemmTerm*)(base + o_terms);
+      const int* dtt = (const int*)(base + o_tiles);
       launch_gemm(dt, (int)tk.size(), dm, dtt, (int)tile_task.size(), c.st);
       TD_CHECK_CUDA(cudaGetLastError());
     }
