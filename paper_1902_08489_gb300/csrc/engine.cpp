@@ -687,6 +687,7 @@ static Inter plan_wstage(Context& c, Inter&& X, const MPOd& m, int site, bool le
       wb.bytes += (double)X.esz() * X.blocks[x].rows * X.blocks[x].W * X.blocks[x].cols;
     }
     int64_t n = (int64_t)yb.rows * yb.W * yb.cols;
+    if (n >= ((int64_t)1 << 31)) throw Error(TDMPS_ERR_INVALID_ARG, "MPO-stage block too large");
     wb.work += n;
     wb.bytes += (double)Y.esz() * n;
     wb.flops += 4.0 * n;   // at least one real x complex MAC per output
