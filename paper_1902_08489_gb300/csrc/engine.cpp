@@ -380,7 +380,8 @@ struct GemmBatch {
             const double2* scale_ptr = nullptr) {
     if (K <= 0) return;
     GemmTask& t = tasks.back();
-    terms.push_back({A, B, K, lda, ldb, 0, make_double2(scale.real(), scale.imag()), scale_ptr});
+    terms.push_back({A, B, K, lda, ldb, 0, make_double2(scale.real(), scale.imag()), scale_ptr,
+                     make_float2((float)scale.real(), (float)scale.imag())});
     t.term_end = (int)terms.size();
     flops += 8.0 * t.M * t.N * K;
     bytes += (t.ta ? 8.0 : 16.0) * t.M * K + (t.tb ? 8.0 : 16.0) * K * t.N;

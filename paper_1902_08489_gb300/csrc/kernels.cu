@@ -211,22 +211,14 @@ __global__ void __launch_bounds__(256) k_wstage(const WTask* __restrict__ tasks,
       if (tasks[mid].work_base <= first) lo = mid; else hi = mid - 1;
     }
   }
-  // the task is copied into registers only when the thread moves to a new
-  // one, and the element index is split with 32-bit arithmetic (a task holds
-  // fewer than 2^31 outputs; 64-bit division is a long instruction sequence)
-  int cur = -1;
-  WTask t;
   for (int64_t idx = beg + threadIdx.x; idx < end; idx += blockDim.x) {
     while (lo + 1 < ntasks && tasks[lo + 1].work_base <= idx) ++lo;
-    if (lo != cur) {
-      t = tasks[lo];
-      cur = lo;
-    }
-    const int loc = (int)(idx - t.work_base);
-    const int b = loc % t.cols;
-    const int rw = loc / t.cols;
-    const int w = rw % t.wout;
-    const int a = rw / t.wout;
+    const WTask& t = tasks[lo];
+    int64_t loc = idx - t.work_base;
+    int b = (int)(loc % t.cols);
+    int64_t rw = loc / t.cols;
+    int w = (int)(rw % t.wout);
+    int a = (int)(rw / t.wout);
     R ax = 0, ay = 0;
     for (int s = 0; s < 4; ++s) {
       if (t.csr[s] < 0) continue;

@@ -19,6 +19,7 @@ struct GemmTerm {
   int K, lda, ldb, pad;
   double2 scale;
   const double2* scale_ptr;
+  float2 fscale;   // scale rounded to FP32 on the host (tensor-core path, scale_ptr null)
 };
 
 // C (M x N, ldc) = alpha * sum_terms op(A) op(B) + beta * C;
