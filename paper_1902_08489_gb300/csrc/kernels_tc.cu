@@ -84,24 +84,6 @@ __device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t da, uint64_t db
       :
       : "r"(tmem), "l"(da), "l"(db), "r"(idesc), "r"(accumulate));
 }
-// FP32 -> FP64 (exact) from the IEEE-754 encodings on the integer pipe: same
-// sign, exponent rebiased by 1023 - 127, mantissa shifted into the top bits.
-// The FP64 pipe, which a conversion instruction would use, is the scarce unit
-// on this part; zeros, infinities and NaNs map bit for bit, and the rare
-// subnormal input takes the hardware conversion.
-__device__ __forceinline__ double f32_to_f64(float f) {
-  const uint32_t u = __float_as_uint(f);
-  const uint32_t e = (u >> 23) & 0xffu, m = u & 0x7fffffu;
-  uint64_t out = (uint64_t)(u >> 31) << 63;
-  if (e == 0u) {
-    if (m == 0u) return __longlong_as_double((long long)out);
-    return (double)f;
-  }
-  const uint64_t e64 = e == 0xffu ? 0x7ffull : (uint64_t)(e + 896u);
-  out |= (e64 << 52) | ((uint64_t)m << 29);
-  return __longlong_as_double((long long)out);
-}
-
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
   __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
   return *(uint32_t*)&v;
@@ -441,7 +423,7 @@ __global__ void __launch_bounds__(TC_THREADS, 3) k_gemm_tc(const GemmTask* __res
         const size_t o = t.ct ? col * t.ldc + row : (size_t)row * t.ldc + col;
         if (t.tc == 0) {
           double2* C = (double2*)t.C + o;
-          double ore = f32_to_f64(fax * x.x - fay * x.y), oim = f32_to_f64(fax * x.y + fay * x.x);
+          double ore = (double)(fax * x.x - fay * x.y), oim = (double)(fax * x.y + fay * x.x);
           if (atomic) {
             atomicAdd(&C->x, ore);
             atomicAdd(&C->y, oim);
