@@ -214,11 +214,14 @@ __global__ void __launch_bounds__(256) k_wstage(const WTask* __restrict__ tasks,
   for (int64_t idx = beg + threadIdx.x; idx < end; idx += blockDim.x) {
     while (lo + 1 < ntasks && tasks[lo + 1].work_base <= idx) ++lo;
     const WTask& t = tasks[lo];
-    int64_t loc = idx - t.work_base;
-    int b = (int)(loc % t.cols);
-    int64_t rw = loc / t.cols;
-    int w = (int)(rw % t.wout);
-    int a = (int)(rw / t.wout);
+    // 32-bit index split (a task holds fewer than 2^31 outputs): 64-bit
+    // division is a long instruction sequence and this stage is issue-bound
+    const int loc = (int)(idx - t.work_base);
+    const int cols = t.cols, wout = t.wout;
+    const int rw = loc / cols;
+    const int b = loc - rw * cols;
+    const int a = rw / wout;
+    const int w = rw - a * wout;
     R ax = 0, ay = 0;
     for (int s = 0; s < 4; ++s) {
       if (t.csr[s] < 0) continue;
