@@ -125,3 +125,26 @@ def test_krylov_trajectory_mixed_observables(td):
     assert np.abs(out["fp64"][1] - out["tf32x3"][1]).max() < 3e-5
     # FP64 Krylov conserves the energy up to the truncation (eps = 1e-10 weight)
     assert np.ptp(out["fp64"][1]) < 1e-8
+
+
+def test_full_size_krylov_step_mixed_vs_fp64_physical(td):
+    # The benchmark's Krylov step at full size (L = 16, D = 256, m = 10,
+    # dt = 0.05, eps = 1e-8) on the physical beta-hole state, one two-site +
+    # one one-site sweep per fit: split 3xTF32 against FP64 on the GPU.  The
+    # energy stays within 1e-6 (the accuracy target of the mixed mode); the
+    # 1-RDM within the FP32 class of the products (~1e-5 per step).
+    L = 16
+    I = synth.make_integrals(L, seed=0)
+    occ = synth.hole_occupation(L, 16, 7)
+    res = {}
+    for p in ("fp64", "tf32x3"):
+        ctx = td.Context(p)
+        ctx.set_schedule(1, 1)
+        mpo = td.build_mpo(ctx, I.h, I.eri, n_elec=15)
+        psi = td.mps_from_determinant(ctx, occ)
+        td.krylov_step(ctx, mpo, psi, 0.05, 10, True, 256, 1e-8)
+        e = td.expectation(ctx, mpo, psi, psi).real / td.overlap(ctx, psi, psi).real
+        res[p] = (td.one_rdm(ctx, psi), e)
+        ctx.close()
+    assert abs(res["fp64"][1] - res["tf32x3"][1]) < 1e-6
+    assert np.abs(res["fp64"][0] - res["tf32x3"][0]).max() < 2e-5
