@@ -13,6 +13,8 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <exception>
+#include <thread>
 
 #include "engine.hpp"
 
@@ -106,6 +108,7 @@ Context::Context(cudaStream_t s, int prec, size_t ring_bytes) : st(s), precision
 }
 
 Context::~Context() {
+  aux.reset();
   workers.clear();
   cudaStreamSynchronize(st);
   for (auto& p : pending) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
@@ -1749,21 +1752,69 @@ MPSd krylov_step(Context& c, const MPOd& H, const MPSd& psi, double dt, int m, b
     sandwich_batch(c, nullptr, pn, on, c.krylov_fp64);
     sandwich_batch(c, &H, ph, oh, c.krylov_fp64);
   };
+  // The inner products of a Gram-Schmidt step depend on phi_0..phi_k only,
+  // not on the fit of H phi_k that precedes their use; with FP64 inner
+  // products they run on a helper context (its own stream, staging ring and
+  // caches) driven by a second host thread, while this thread plans and
+  // launches the fit.  The fit keeps the tensor cores and the QR busy, the
+  // inner products the FP64 pipe; events order both streams around the
+  // hand-over.  (In other precisions the two would share the FP32 copies of
+  // the site tensors, so they run one after the other.)
+  const bool concurrent = orth && c.krylov_fp64 && c.overlap_inner && m > 2;
+  Context* hc = nullptr;
+  struct Events {
+    cudaEvent_t in = nullptr, out = nullptr;
+    ~Events() {
+      if (in) cudaEventDestroy(in);
+      if (out) cudaEventDestroy(out);
+    }
+  } ev;
+  if (concurrent) {
+    if (!c.aux) c.aux = std::make_unique<Worker>(TDMPS_FP64, (size_t)32 << 20);
+    hc = c.aux->c.get();
+    hc->precision = c.precision;
+    hc->stats = c.stats;
+    TD_CHECK_CUDA(cudaEventCreateWithFlags(&ev.in, cudaEventDisableTiming));
+    TD_CHECK_CUDA(cudaEventCreateWithFlags(&ev.out, cudaEventDisableTiming));
+  }
   for (int k = 0; k + 1 < m; ++k) {
-    MPSd u = fit(c, {{&phi[k], &H, 1.0}}, phi[k], o);
     if (orth) {
-      // Eq. (kry_orth): c_j = <phi_j|H|phi_k> / <phi_j|phi_j>
-      std::vector<std::pair<int, int>> want;
-      for (int j = 0; j <= k; ++j) want.push_back({j, k});
-      for (int j = 0; j <= k; ++j) want.push_back({j, j});
-      {
-        // H sandwiches (j, k) and overlaps (j, j) in two batched sweeps
-        std::vector<std::pair<const MPSd*, const MPSd*>> pn, ph;
-        std::vector<double2*> on, oh;
-        for (int j = 0; j <= k; ++j) {
-          if (!haveH[j * m + k]) { ph.push_back({&phi[j], &phi[k]}); oh.push_back(Hd + j * m + k); haveH[j * m + k] = 1; }
-          if (!haveN[j * m + j]) { pn.push_back({&phi[j], &phi[j]}); on.push_back(Nd + j * m + j); haveN[j * m + j] = 1; }
+      // Eq. (kry_orth): c_j = <phi_j|H|phi_k> / <phi_j|phi_j>; the overlaps
+      // <phi_j|phi_k> of the Krylov matrix N are formed here too
+      std::vector<std::pair<const MPSd*, const MPSd*>> pn, ph;
+      std::vector<double2*> on, oh;
+      for (int j = 0; j <= k; ++j) {
+        if (!haveH[j * m + k]) { ph.push_back({&phi[j], &phi[k]}); oh.push_back(Hd + j * m + k); haveH[j * m + k] = 1; }
+        if (!haveN[j * m + k]) { pn.push_back({&phi[j], &phi[k]}); on.push_back(Nd + j * m + k); haveN[j * m + k] = 1; }
+      }
+      MPSd u;
+      if (concurrent) {
+        TD_CHECK_CUDA(cudaEventRecord(ev.in, c.st));
+        TD_CHECK_CUDA(cudaStreamWaitEvent(hc->st, ev.in, 0));
+        std::exception_ptr err;
+        const int dev = c.device;
+        std::thread th([&, dev] {
+          try {
+            TD_CHECK_CUDA(cudaSetDevice(dev));
+            hc->api_enter();
+            sandwich_batch(*hc, &H, ph, oh, true);
+            sandwich_batch(*hc, nullptr, pn, on, true);
+          } catch (...) {
+            err = std::current_exception();
+          }
+        });
+        try {
+          u = fit(c, {{&phi[k], &H, 1.0}}, phi[k], o);
+        } catch (...) {
+          th.join();
+          throw;
         }
+        th.join();
+        if (err) std::rethrow_exception(err);
+        TD_CHECK_CUDA(cudaEventRecord(ev.out, hc->st));
+        TD_CHECK_CUDA(cudaStreamWaitEvent(c.st, ev.out, 0));
+      } else {
+        u = fit(c, {{&phi[k], &H, 1.0}}, phi[k], o);
         sandwich_batch(c, &H, ph, oh, c.krylov_fp64);
         sandwich_batch(c, nullptr, pn, on, c.krylov_fp64);
       }
@@ -1778,8 +1829,23 @@ MPSd krylov_step(Context& c, const MPOd& H, const MPSd& psi, double dt, int m, b
       normalize_center(c, v, nullptr);
       phi.push_back(std::move(v));
     } else {
+      MPSd u = fit(c, {{&phi[k], &H, 1.0}}, phi[k], o);
       normalize_center(c, u, nullptr);
       phi.push_back(std::move(u));
+    }
+  }
+  if (hc && c.stats) {   // the helper's timings and work count as this context's
+    hc->collect_stats();
+    for (int q = 0; q < TDMPS_KSTAT_COUNT; ++q) {
+      if (q == TDMPS_KSTAT_HOST_PLAN || q == TDMPS_KSTAT_HOST_LAUNCH) {
+        hc->kstat[q] = KStat();   // host time of the helper thread overlaps this thread's
+        continue;
+      }
+      c.kstat[q].launches += hc->kstat[q].launches;
+      c.kstat[q].ms += hc->kstat[q].ms;
+      c.kstat[q].flops += hc->kstat[q].flops;
+      c.kstat[q].bytes += hc->kstat[q].bytes;
+      hc->kstat[q] = KStat();
     }
   }
   std::vector<std::pair<int, int>> rest;

@@ -70,6 +70,8 @@ struct Context {
   std::unique_ptr<std::vector<MPOd>> rdm_read;   // its per-bond readouts (by L)
 
   std::vector<std::unique_ptr<Worker>> workers;   // instance-batch workers (lazy)
+  std::unique_ptr<Worker> aux;    // helper for the concurrent Krylov inner products (lazy)
+  bool overlap_inner = true;      // run those inner products beside the fits
 
   explicit Context(cudaStream_t s, int prec, size_t ring_bytes = (size_t)512 << 20);
   ~Context();
