@@ -73,7 +73,7 @@ struct Context {
   std::unique_ptr<Worker> aux;    // helper for the concurrent Krylov inner products (lazy)
   bool overlap_inner = true;      // run those inner products beside the fits
 
-  explicit Context(cudaStream_t s, int prec, size_t ring_bytes = (size_t)512 << 20);
+  explicit Context(cudaStream_t s, int prec, size_t ring_bytes = (size_t)256 << 20);
   ~Context();
 
   // copy a host array into device memory valid until the stream passes it

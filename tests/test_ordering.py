@@ -59,3 +59,23 @@ def test_library_matches_oracle_on_host():
     p = td.fiedler_order(h, eri)
     h2, e2 = td.permute_integrals(h, eri, p)
     assert h2[0, 1] == h[p[0], p[1]] and e2[0, 1, 1, 0] == eri[p[0], p[1], p[1], p[0]]
+
+
+def test_library_rejects_bad_input_on_host():
+    import paper_1902_08489_gb300 as td
+    try:
+        td.lib()
+    except td.TdmpsError:
+        pytest.skip("library not built")
+    I = synth.make_integrals(5, seed=9)
+    h = I.h.copy()
+    h[1, 2] = np.nan
+    with pytest.raises(td.TdmpsError) as e:
+        td.fiedler_order(h, I.eri)
+    assert e.value.name == "NONFINITE"
+    # L = 65 is rejected before the integral arrays are read
+    with pytest.raises(td.TdmpsError) as e:
+        td.fiedler_order(np.zeros((65, 65)), np.zeros(1))
+    assert e.value.name == "INVALID_ARG"
+    # one and two orbitals have a single ordering
+    assert list(td.fiedler_order(I.h[:2, :2], I.eri[:2, :2, :2, :2])) == [0, 1]
