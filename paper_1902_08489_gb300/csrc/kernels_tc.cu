@@ -293,9 +293,15 @@ __global__ void __launch_bounds__(TC_THREADS, 3) k_gemm_tc(const GemmTask* __res
         abort_flag = 1;
       }
     }
+    // Rows past M and columns past N are zero in every stage: each of the
+    // two buffers receives those zeros in its first stage and keeps them, so
+    // later stages skip them (whole warps when the block is short -- the
+    // local-matvec outputs fill only a fraction of a 128 x 64 tile).
+    const bool a_stage = s < 2 || m0 + ra_r < t.M;
+    const bool b_stage = s < 2 || n0 + rb_n < t.N;
     // ---- A: 128 rows x 8 complex; thread -> row, 4 complex of K
 #pragma unroll
-    for (int j = 0; j < TC_BKC / 2; ++j) {
+    for (int j = 0; j < TC_BKC / 2 && a_stage; ++j) {
       const int kk = ra_k + j;
       const float2 a0 = ra[j];
       const float2 a = make_float2(sc.x * a0.x - sc.y * a0.y, sc.x * a0.y + sc.y * a0.x);
@@ -312,7 +318,7 @@ __global__ void __launch_bounds__(TC_THREADS, 3) k_gemm_tc(const GemmTask* __res
     }
     // ---- B-tilde (K-major, rows = real N): thread -> column n, 2 complex of K
 #pragma unroll
-    for (int j = 0; j < TC_BKC / 4; ++j) {
+    for (int j = 0; j < TC_BKC / 4 && b_stage; ++j) {
       const int kk = rb_k + j;
       const float2 bv = rb[j];
       if (MODE == 2) {
