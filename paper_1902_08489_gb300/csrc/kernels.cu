@@ -1,5 +1,5 @@
 // FP64 device kernels of the tdmps library: grouped complex block GEMM, sparse
-// MPO-tensor application, block gather/scatter, one-sided Jacobi SVD, CGS2
+// MPO-tensor application, block gather/scatter, one-sided Jacobi SVD, Gram-Schmidt
 // QR, the truncation rule, and the small Krylov algebra.
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
@@ -778,7 +778,7 @@ void launch_svd(const FactTask* d_tasks, int ntasks, int* d_status, cudaStream_t
   k_svd<<<ntasks, SVD_THREADS, dyn, st>>>(d_tasks, d_status, (int)dyn);
 }
 
-// ------------------------------------------------------------------ CGS2 QR
+// ------------------------------------------------------------------ Gram-Schmidt QR
 
 // Classical Gram-Schmidt with re-orthogonalisation on a column-major m x n
 // matrix.  The second projection pass runs when the first one removed more

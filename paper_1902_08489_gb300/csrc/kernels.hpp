@@ -61,7 +61,7 @@ struct CopyTask {
   double2 scale;
 };
 
-// One-sided Jacobi SVD / CGS2 QR on column-major matrices in global memory.
+// One-sided Jacobi SVD / Gram-Schmidt QR on column-major matrices in global memory.
 // blk(i, j) = src(r0 + i, c0 + j)            (conj_t = 0, src column-major, lds)
 // blk(i, j) = conj(src(r0 + j, c0 + i))      (conj_t = 1)
 // times s[j] (scale_dim = 1) or s[i] (scale_dim = 2)
