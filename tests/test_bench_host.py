@@ -1,0 +1,43 @@
+"""Host logic of the benchmark: the roofline entry of the dominant kernel
+class and the uneven-instance recipe (no GPU)."""
+import bench
+
+
+def _st(**ms):
+    base = {k: {"launches": 0, "ms": 0.0, "flops": 0.0, "bytes": 0.0}
+            for k in ("gemm", "wstage", "qr", "svd", "other", "gemm_fp64",
+                      "host_plan", "host_launch", "host_sync")}
+    for k, (launches, t, fl, by) in ms.items():
+        base[k] = {"launches": launches, "ms": t, "flops": fl, "bytes": by}
+    return base
+
+
+def test_roofline_picks_the_largest_device_class_and_ignores_host_time():
+    st = _st(gemm_fp64=(10, 100.0, 50e9, 1e9), gemm=(100, 60.0, 1e12, 1e9),
+             host_plan=(1000, 5000.0, 0.0, 0.0))
+    r = bench.roofline(st, "tf32x3")
+    assert r["kernel"].startswith("k_gemm (FP64")
+    assert r["bound"] == "alu" and r["unit"] == "TFLOP/s"
+    # 50 GFLOP in 100 ms = 0.5 TFLOP/s over the FP64 peak (bf16 x 1.25/2250)
+    assert abs(r["achieved"] - 0.5) < 1e-12
+    assert abs(r["frac"] - r["achieved"] / r["peak"]) < 1e-15
+    assert abs(r["share_of_timed_device_time"] - 100.0 / 160.0) < 1e-12
+
+
+def test_roofline_tensor_and_memory_classes():
+    r = bench.roofline(_st(gemm=(4, 40.0, 4e12, 1e9)), "tf32x3")
+    assert r["bound"] == "tensor"
+    tf32 = r["peak"] * 3.0
+    r1 = bench.roofline(_st(gemm=(4, 40.0, 4e12, 1e9)), "tf32")
+    assert abs(r1["peak"] - tf32) < 1e-9
+    r2 = bench.roofline(_st(wstage=(2, 10.0, 1e9, 20e9)), "tf32x3")
+    assert r2["bound"] == "hbm" and r2["unit"] == "GB/s"
+    assert abs(r2["achieved"] - 2000.0) < 1e-9   # 20 GB in 10 ms
+
+
+def test_batch_instances_recipe():
+    inst = bench.batch_instances()
+    assert len(inst) == 64 and [s for s, _, _ in inst] == list(range(64))
+    assert {L for _, L, _ in inst} <= {8, 10, 12, 14}
+    assert {D for _, _, D in inst} <= {32, 64, 128}
+    assert inst == bench.batch_instances()   # seeded
