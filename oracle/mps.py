@@ -205,6 +205,42 @@ def overlap(bra: MPS, ket: MPS) -> complex:
     return complex(E[0, 0])
 
 
+def _sector_dims(labels: np.ndarray) -> dict:
+    dims: dict = {}
+    for q in map(tuple, labels.tolist()):
+        dims[q] = dims.get(q, 0) + 1
+    return dims
+
+
+def overlap_flops(bra: MPS, ket: MPS) -> int:
+    """Algorithmic real FLOPs of <bra|ket> by the transfer recursion of
+    Section 2.1, E_{i+1} = sum_sigma B^sigma^dagger (E_i A^sigma), on the
+    U(1) x U(1) blocks (a site tensor maps the left sector q to q + q(sigma);
+    every other block is zero).  For each sector q that carries a non-zero
+    block of E_i and each sigma whose q' = q + q(sigma) is a sector of both
+    right bonds:
+        E_i A^sigma            8 |bra_i(q)| |ket_i(q)| |ket_{i+1}(q')|
+        B^sigma^dagger (E A)   8 |bra_{i+1}(q')| |bra_i(q)| |ket_{i+1}(q')|
+    (a complex multiply-add is 8 real FLOPs).  Products that no later step
+    uses (q' missing from the bra) are not algorithmic work."""
+    live = {(0, 0)}          # the left boundary sector
+    total = 0
+    for i in range(bra.L):
+        bl, kl = _sector_dims(bra.labels[i]), _sector_dims(ket.labels[i])
+        br, kr = _sector_dims(bra.labels[i + 1]), _sector_dims(ket.labels[i + 1])
+        nxt = set()
+        for q in live:
+            if q not in bl or q not in kl:
+                continue
+            for c in SITE_Q:
+                qp = (q[0] + int(c[0]), q[1] + int(c[1]))
+                if qp in br and qp in kr:
+                    total += 8 * bl[q] * kl[q] * kr[qp] + 8 * br[qp] * bl[q] * kr[qp]
+                    nxt.add(qp)
+        live = nxt
+    return total
+
+
 def norm(mps: MPS) -> float:
     return float(np.sqrt(max(overlap(mps, mps).real, 0.0)))
 
