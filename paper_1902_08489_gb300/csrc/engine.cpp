@@ -294,12 +294,14 @@ void upload_mpo_tables(MPOd& m, Context& c) {
         if (bi.ch_group[e->win] != gin) throw Error(TDMPS_ERR_SECTOR, "MPO charge inconsistency");
         perrow[bo.ch_local[e->wout]].push_back({bi.ch_local[e->win], e->v});
       }
-      WTable t{kv.first[0], kv.first[1], gout, gin, rows, (int)rowptr.size()};
+      WTable t{kv.first[0], kv.first[1], gout, gin, rows, (int)rowptr.size(), 0};
+      const int first = (int)ent_w.size();
       for (int r = 0; r < rows; ++r) {
         rowptr.push_back((int)ent_w.size());
         for (auto& pv : perrow[r]) { ent_w.push_back(pv.first); ent_v.push_back(pv.second); }
       }
       rowptr.push_back((int)ent_w.size());
+      t.nnz = (int)ent_w.size() - first;
       m.tab_left_idx[i][kv.first] = (int)m.tab_left[i].size();
       m.tab_left[i].push_back(t);
     }
@@ -312,12 +314,14 @@ void upload_mpo_tables(MPOd& m, Context& c) {
         if (bo.ch_group[e->wout] != gout) throw Error(TDMPS_ERR_SECTOR, "MPO charge inconsistency");
         perrow[bi.ch_local[e->win]].push_back({bo.ch_local[e->wout], e->v});
       }
-      WTable t{kv.first[0], kv.first[1], gout, gin, rows, (int)rowptr.size()};
+      WTable t{kv.first[0], kv.first[1], gout, gin, rows, (int)rowptr.size(), 0};
+      const int first = (int)ent_w.size();
       for (int r = 0; r < rows; ++r) {
         rowptr.push_back((int)ent_w.size());
         for (auto& pv : perrow[r]) { ent_w.push_back(pv.first); ent_v.push_back(pv.second); }
       }
       rowptr.push_back((int)ent_w.size());
+      t.nnz = (int)ent_w.size() - first;
       m.tab_right_idx[i][kv.first] = (int)m.tab_right[i].size();
       m.tab_right[i].push_back(t);
     }
@@ -586,8 +590,10 @@ static int site_et(Context& c) { return c.precision == TDMPS_FP64 ? 0 : 1; }
 // launch per stage for all terms of a fit or all pairs of a sandwich.
 
 // X[rg][w][s'][b'] = E[rg][w][k] A[k][s'][b']
+// With `bra` given (an identity-MPO sandwich, where X[rg][s] meets only the
+// bra block (rg, s)), blocks that no bra block consumes are not computed.
 static Inter plan_lstage(Context& c, const Env& E, const SiteT& ket, const Bond& ket_right,
-                         GemmBatch& gb) {
+                         GemmBatch& gb, const SiteT* bra = nullptr) {
   Inter X;
   std::vector<std::pair<int, int>> src;   // (env block, ket block) per X block
   for (int b = 0; b < (int)E.t.blocks.size(); ++b) {
@@ -595,6 +601,8 @@ static Inter plan_lstage(Context& c, const Env& E, const SiteT& ket, const Bond&
     for (int s = 0; s < 4; ++s) {
       int kb = ket.block_of(eb.k, s);
       if (kb < 0) continue;
+      if (bra && ((size_t)eb.rg * 4 + s >= bra->index.size() || bra->block_of(eb.rg, s) < 0))
+        continue;
       int sb = ket.blocks[kb].sb;
       X.add(eb.rg, s, eb.g, sb, eb.rows, eb.W, ket_right.d[sb]);
       src.push_back({b, kb});
@@ -681,6 +689,7 @@ static Inter plan_wstage(Context& c, Inter&& X, const MPOd& m, int site, bool le
     t.cols = yb.cols;
     t.beta = 0;
     t.work_base = wb.work;
+    int64_t nnz = 0;
     for (int sp = 0; sp < 4; ++sp) {
       int x = pend[y].xs[sp];
       if (x < 0) { t.X[sp] = nullptr; t.win[sp] = 0; t.csr[sp] = -1; continue; }
@@ -688,13 +697,15 @@ static Inter plan_wstage(Context& c, Inter&& X, const MPOd& m, int site, bool le
       t.win[sp] = X.blocks[x].W;
       const WTable& tb = (left ? m.tab_left[site] : m.tab_right[site])[pend[y].tabs[sp]];
       t.csr[sp] = tb.rowptr_off;
+      nnz += tb.nnz;
       wb.bytes += (double)X.esz() * X.blocks[x].rows * X.blocks[x].W * X.blocks[x].cols;
     }
     int64_t n = (int64_t)yb.rows * yb.W * yb.cols;
     if (n >= ((int64_t)1 << 31)) throw Error(TDMPS_ERR_INVALID_ARG, "MPO-stage block too large");
     wb.work += n;
     wb.bytes += (double)Y.esz() * n;
-    wb.flops += 4.0 * n;   // at least one real x complex MAC per output
+    // one real x complex multiply-add per non-zero W entry, row and column
+    wb.flops += 4.0 * (double)nnz * yb.rows * yb.cols;
     wb.tasks.push_back(t);
   }
   return Y;
@@ -1610,7 +1621,8 @@ void sandwich_batch(Context& c, const MPOd* mpo,
     GemmBatch g1(c);
     std::vector<Inter> X(pairs.size());
     for (size_t p = 0; p < pairs.size(); ++p)
-      X[p] = plan_lstage(c, E[p], pairs[p].second->sites[i], pairs[p].second->bonds[i + 1], g1);
+      X[p] = plan_lstage(c, E[p], pairs[p].second->sites[i], pairs[p].second->bonds[i + 1], g1,
+                         m.identity ? &pairs[p].first->sites[i] : nullptr);
     g1.run();
     WBatch wb;
     std::vector<Inter> Y(pairs.size());

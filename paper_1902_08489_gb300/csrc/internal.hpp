@@ -138,6 +138,7 @@ struct WTable {
   int sig, sigp, g_out, g_in;
   int rows;         // rows of the CSR (W_gout for left, W_gin for right)
   int rowptr_off;   // offset into rowptr array
+  int nnz;          // non-zero entries of the table
 };
 
 struct MPOd {
