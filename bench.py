@@ -300,6 +300,10 @@ def main():
                          "the large active space: 64 Cholesky vectors and the localised "
                          "orbital block); the default is the L=16 workload")
     ap.add_argument("--schedule", default=None, help="two-site,one-site sweeps per fit")
+    ap.add_argument("--serial-inner", action="store_true",
+                    help="run the Krylov inner products after each fit on the context "
+                         "stream instead of beside it on a helper thread (for profilers "
+                         "that serialise kernels across threads)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -318,6 +322,8 @@ def main():
         dist.init_process_group("nccl")
 
     ctx = td.Context(args.precision)
+    if args.serial_inner:
+        ctx.set_concurrent_inner(False)
     if args.mode == "batch":
         return run_batch(args, td, ctx, torch, local)
     sched = SCHEDULE if args.mode == "krylov" else (0, 1)
@@ -473,6 +479,7 @@ def main():
                                 "%d one-site sweeps, random seeded D=%d state"
                                 % (L, N_ELEC, TWO_SZ, D, sched[0], sched[1], D)),
                    "l2": "inputs larger than L2 (Krylov basis + environments, several GB)",
+                   "inner_products": "serial" if args.serial_inner else "concurrent",
                    "parallelism": "replicas" if world > 1 else "single"},
         "steps_per_s": 1e3 * args.steps / ms,
         "vs_fp64": fp64_cmp,

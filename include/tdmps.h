@@ -100,6 +100,17 @@ int tdmps_set_schedule(tdmps_ctx_t ctx, int n_two_site, int n_one_site);
  * are accumulated and processed in FP64 either way. */
 int tdmps_set_krylov_fp64(tdmps_ctx_t ctx, int on);
 
+/* Scheduling of the FP64 Krylov inner products of an orthogonal-basis step
+ * (Eq. kry_orth).  Those of Gram-Schmidt step k depend on phi_0..phi_k only.
+ * With on != 0 (the default) they run on a helper stream driven by a
+ * second host thread, concurrently with the fit of H phi_k. With on == 0
+ * they run after that fit, in order, on the context stream.  Both give the
+ * same values up to the summation order of split-K accumulation.  The
+ * serial order is for tools that serialise kernels across threads, such as
+ * profilers.  It applies when the inner products are FP64
+ * (tdmps_set_krylov_fp64) and m > 2.  Errors: INVALID_ARG for a NULL ctx. */
+int tdmps_set_concurrent_inner(tdmps_ctx_t ctx, int on);
+
 /* ------------------------------------------------------- orbital order */
 
 /* Fiedler ordering of the orbitals (Sec. 3.2: the molecular orbitals are

@@ -59,6 +59,7 @@ _SIGS = {
     "tdmps_set_precision": (I, [P, I]),
     "tdmps_set_schedule": (I, [P, I, I]),
     "tdmps_set_krylov_fp64": (I, [P, I]),
+    "tdmps_set_concurrent_inner": (I, [P, I]),
     "tdmps_build_mpo": (I, [P, P, P, I, I, D, ctypes.POINTER(P)]),
     "tdmps_mpo_info": (I, [P, P, ctypes.POINTER(I64)]),
     "tdmps_mpo_elements": (I, [P, I, ctypes.POINTER(I64), P, P, P, P, P]),
@@ -163,6 +164,9 @@ class Context:
 
     def set_krylov_fp64(self, on: bool = True):
         _check(lib().tdmps_set_krylov_fp64(self.h, 1 if on else 0), self)
+
+    def set_concurrent_inner(self, on: bool = True):
+        _check(lib().tdmps_set_concurrent_inner(self.h, 1 if on else 0), self)
 
     # statistics
     def stats_enable(self, on=True):

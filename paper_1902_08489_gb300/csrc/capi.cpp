@@ -122,6 +122,12 @@ int tdmps_set_krylov_fp64(tdmps_ctx_t ctx, int on) {
   return TDMPS_OK;
 }
 
+int tdmps_set_concurrent_inner(tdmps_ctx_t ctx, int on) {
+  if (!ctx) return TDMPS_ERR_INVALID_ARG;
+  ctx->c->overlap_inner = on != 0;
+  return TDMPS_OK;
+}
+
 int tdmps_build_mpo(tdmps_ctx_t ctx, const double* h, const double* eri, int L, int n_elec,
                     double e0, tdmps_mpo_t* out) {
   return guard(ctx, [&] {

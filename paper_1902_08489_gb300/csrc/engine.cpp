@@ -589,11 +589,32 @@ static int site_et(Context& c) { return c.precision == TDMPS_FP64 ? 0 : 1; }
 // ---- stage planners: each appends its work to a batch; callers run one
 // launch per stage for all terms of a fit or all pairs of a sandwich.
 
+// Does the bra site have the block (row group rg, local state s)?
+static bool bra_has(const SiteT& bra, int rg, int s) {
+  return (size_t)rg * 4 + s < bra.index.size() && bra.block_of(rg, s) >= 0;
+}
+
 // X[rg][w][s'][b'] = E[rg][w][k] A[k][s'][b']
-// With `bra` given (an identity-MPO sandwich, where X[rg][s] meets only the
-// bra block (rg, s)), blocks that no bra block consumes are not computed.
+// In a sandwich (`bra` given, left-to-right), X[rg][g][s'] reaches the bra
+// only through the MPO-stage outputs Y[rg][s] whose tables connect s' to s
+// and for which the bra has the block (rg, s); X blocks with no such
+// consumer are not computed.  With the identity MPO that is s = s'.
 static Inter plan_lstage(Context& c, const Env& E, const SiteT& ket, const Bond& ket_right,
-                         GemmBatch& gb, const SiteT* bra = nullptr) {
+                         GemmBatch& gb, const SiteT* bra = nullptr, const MPOd* m = nullptr,
+                         int site = 0) {
+  auto consumed = [&](const Inter::Blk& eb, int sp) {
+    if (!m || m->identity) return bra_has(*bra, eb.rg, sp);
+    const MPOBond& bi = m->bonds[site];
+    const MPOBond& bo = m->bonds[site + 1];
+    const std::vector<int>& flat = m->tab_left_flat[site];
+    const int ngy = (int)bo.gq.size();
+    for (int s = 0; s < 4; ++s) {
+      if (!bra_has(*bra, eb.rg, s)) continue;
+      const int g = bo.find(bi.gq[eb.g] + SITE_Q[s] - SITE_Q[sp]);
+      if (g >= 0 && flat[(size_t)(s * 4 + sp) * ngy + g] >= 0) return true;
+    }
+    return false;
+  };
   Inter X;
   std::vector<std::pair<int, int>> src;   // (env block, ket block) per X block
   for (int b = 0; b < (int)E.t.blocks.size(); ++b) {
@@ -601,8 +622,7 @@ static Inter plan_lstage(Context& c, const Env& E, const SiteT& ket, const Bond&
     for (int s = 0; s < 4; ++s) {
       int kb = ket.block_of(eb.k, s);
       if (kb < 0) continue;
-      if (bra && ((size_t)eb.rg * 4 + s >= bra->index.size() || bra->block_of(eb.rg, s) < 0))
-        continue;
+      if (bra && !consumed(eb, s)) continue;
       int sb = ket.blocks[kb].sb;
       X.add(eb.rg, s, eb.g, sb, eb.rows, eb.W, ket_right.d[sb]);
       src.push_back({b, kb});
@@ -624,9 +644,12 @@ static Inter plan_lstage(Context& c, const Env& E, const SiteT& ket, const Bond&
 // Sparse MPO-tensor stage, either direction.
 //   left:  Y[rg][s][w_out][b'] = sum_{s', w_in} W[w_in, w_out, s, s'] X[rg][w_in][s'][b']
 //   right: Y[rb][s][w_in][a']  = sum_{s', w_out} W[w_in, w_out, s, s'] X[rb][w_out][s'][a']
+// With `bra` given (a left-to-right sandwich), outputs Y[rg][s] for which the
+// bra has no block (rg, s) are not computed: no environment term uses them.
 static Inter plan_wstage(Context& c, Inter&& X, const MPOd& m, int site, bool left,
-                         WBatch& wb) {
+                         WBatch& wb, const SiteT* bra = nullptr) {
   if (m.identity) return std::move(X);   // no copy of the block index
+  if (bra && !left) throw Error(TDMPS_ERR_INVALID_ARG, "bra filter is left-to-right only");
   if (wb.mpo && wb.mpo != &m) throw Error(TDMPS_ERR_INVALID_ARG, "mixed MPOs in one W batch");
   wb.mpo = &m;
   wb.et = X.et;
@@ -654,6 +677,7 @@ static Inter plan_wstage(Context& c, Inter&& X, const MPOd& m, int site, bool le
     if (grp[0] < 0 && grp[1] < 0 && grp[2] < 0 && grp[3] < 0) continue;
     const int rg = (int)(gi / nk), kk = (int)(gi % nk);
     for (int s = 0; s < 4; ++s) {
+      if (bra && !bra_has(*bra, rg, s)) continue;
       P p;
       int gy = -1, first = -1;
       for (int sp = 0; sp < 4; ++sp) {
@@ -964,10 +988,10 @@ static Env plan_env_right(Context& c, const Inter& Zp, const SiteT& bra, const B
 static Env env_update_left(Context& c, const Env& E, const SiteT& bra, const Bond& bra_right,
                            const MPSd& ket, int site, const MPOd& m) {
   GemmBatch g1(c);
-  Inter X = plan_lstage(c, E, ket.sites[site], ket.bonds[site + 1], g1);
+  Inter X = plan_lstage(c, E, ket.sites[site], ket.bonds[site + 1], g1, &bra, &m, site);
   g1.run();
   WBatch wb;
-  Inter Y = plan_wstage(c, std::move(X), m, site, true, wb);
+  Inter Y = plan_wstage(c, std::move(X), m, site, true, wb, &bra);
   wb.run(c);
   GemmBatch g2(c);
   Env e = plan_env_left(c, Y, bra, bra_right, m.bonds[site + 1], ket.bonds[site + 1], g2);
@@ -1622,11 +1646,12 @@ void sandwich_batch(Context& c, const MPOd* mpo,
     std::vector<Inter> X(pairs.size());
     for (size_t p = 0; p < pairs.size(); ++p)
       X[p] = plan_lstage(c, E[p], pairs[p].second->sites[i], pairs[p].second->bonds[i + 1], g1,
-                         m.identity ? &pairs[p].first->sites[i] : nullptr);
+                         &pairs[p].first->sites[i], &m, i);
     g1.run();
     WBatch wb;
     std::vector<Inter> Y(pairs.size());
-    for (size_t p = 0; p < pairs.size(); ++p) Y[p] = plan_wstage(c, std::move(X[p]), m, i, true, wb);
+    for (size_t p = 0; p < pairs.size(); ++p)
+      Y[p] = plan_wstage(c, std::move(X[p]), m, i, true, wb, &pairs[p].first->sites[i]);
     wb.run(c);
     GemmBatch g2(c);
     for (size_t p = 0; p < pairs.size(); ++p)

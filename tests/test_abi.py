@@ -40,6 +40,9 @@ def test_invalid_arguments_are_rejected_without_gpu(built):
     with pytest.raises(td.TdmpsError) as e:
         td.build_mpo(None, h, eri)
     assert e.value.name == "NONFINITE"
+    # context setters reject a NULL context
+    assert td.ERRORS[built.tdmps_set_concurrent_inner(None, 0)] == "INVALID_ARG"
+    assert td.ERRORS[built.tdmps_set_krylov_fp64(None, 1)] == "INVALID_ARG"
 
 
 def _dense_mpo(mpo, L):

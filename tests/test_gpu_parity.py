@@ -232,6 +232,28 @@ def test_krylov_step_matches_oracle(td, ctx):
             assert abs(td.overlap(ctx, psi, psi) - 1.0) < 1e-10
 
 
+def test_krylov_step_serial_inner_products_match_oracle(td, ctx):
+    """The truncated step above with the inner products run after each fit on
+    the context stream (tdmps_set_concurrent_inner(ctx, 0)) instead of beside
+    it on the helper thread."""
+    L = 6
+    I, sys_ = _system(L, 5, 1, 7)
+    mpo = td.build_mpo(ctx, I.h, I.eri, n_elec=5)
+    A, q = synth.random_mps(L, 5, 1, 12, seed=12)
+    oa = om.from_arrays(A, q)
+    oa = om.scale(oa, 1.0 / om.norm(oa))
+    ctx.set_schedule(1, 2)
+    ctx.set_concurrent_inner(False)
+    try:
+        psi = td.mps_import(ctx, oa.tensors, oa.labels)
+        td.krylov_step(ctx, mpo, psi, 0.05, 5, True, 10, 0.0)
+    finally:
+        ctx.set_concurrent_inner(True)
+    ref, *_ = om.krylov_step(sys_, oa.copy(), 0.05, 5,
+                             om.Schedule(D=10, n_two_site=1, n_one_site=2))
+    assert _rel(sys_.vec(_to_oracle(psi)), sys_.vec(ref)) < 1e-9
+
+
 def test_one_rdm_matches_oracle(td, ctx):
     L = 6
     I, sys_ = _system(L, 5, 1, 8)
