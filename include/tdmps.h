@@ -85,8 +85,8 @@ const char* tdmps_last_error(tdmps_ctx_t ctx);
 const char* tdmps_create_error(void);
 int tdmps_set_precision(tdmps_ctx_t ctx, int precision);
 
-/* Sweep schedule of every variational fit (paper Sec. 2.2.1, "Operations on
- * MPS", Eq. add_min; "after ~10 sweeps"): n_two_site two-site sweeps (each a
+/* Sweep schedule of every variational fit (Sec. 2.2.1, Eq. add_min; the
+ * paper converges its fits in about ten sweeps): n_two_site two-site sweeps (each a
  * left-to-right and a right-to-left half sweep, truncated SVD of every
  * two-site tensor) followed by n_one_site one-site sweeps (QR / LQ gauge
  * moves, bond dimensions fixed).  Defaults: 2 and 2.  Errors: INVALID_ARG if
@@ -113,8 +113,8 @@ int tdmps_set_concurrent_inner(tdmps_ctx_t ctx, int on);
 
 /* ------------------------------------------------------- orbital order */
 
-/* Fiedler ordering of the orbitals (Sec. 3.2: the molecular orbitals are
- * ordered by a Fiedler reduction of the bandwidth of the Hamiltonian
+/* Fiedler ordering of the orbitals (Sec. 3.2 sorts the molecular orbitals
+ * along a Fiedler vector, which narrows the band of the Hamiltonian
  * matrix).  Graph weights W_ij = |h_ij| + |(ij|ji)| (symmetrised), Laplacian
  * D - W, and the orbitals sorted by the eigenvector of its second smallest
  * eigenvalue (ties by index; the eigenvector's sign is chosen so that its

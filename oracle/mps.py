@@ -31,7 +31,7 @@ Fixed schedule (the paper leaves it open; the same schedule runs on the GPU):
 The initial guess is the input MPS for H|A> and the first term's MPS for sums,
 a deterministic stand-in for the paper's random initial MPS.
 
-Truncation rule (Section 2.1, "D largest singular values"): singular values
+Truncation rule (Section 2.1 keeps the D largest singular values): singular values
 of all sectors of a bond are sorted in descending order (ties: sector label
 ascending, then index); values <= 1e-12 * max are dropped; at most D are kept
 and, of those, the fewest whose discarded weight sum(s^2) stays <= eps *

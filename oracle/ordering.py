@@ -1,7 +1,7 @@
 """Fiedler ordering of the orbitals (TEST INFRASTRUCTURE ONLY).
 
-Sec. 3.2: the molecular orbitals of the MPS calculations are ordered by a
-Fiedler reduction of the bandwidth of the Hamiltonian matrix (spectral
+Sec. 3.2 sorts the molecular orbitals of the MPS calculations along a
+Fiedler vector, which narrows the band of the Hamiltonian matrix (spectral
 ordering).  The orbitals are vertices of a graph with weights
 W_ij = |h_ij| + |(ij|ji)| (i != j, symmetrised); the eigenvector of the
 Laplacian D - W with the second smallest eigenvalue orders them.  Sign of

@@ -1,8 +1,8 @@
 // Fiedler ordering of the orbitals (host).
 //
-// The paper orders the molecular orbitals of its MPS calculations by a
-// Fiedler reduction of the bandwidth of the Hamiltonian matrix (Sec. 3.2,
-// citing the spectral ordering of orbitals for DMRG): orbitals are vertices
+// Sec. 3.2 sorts the molecular orbitals of the MPS calculations along a
+// Fiedler vector, which narrows the band of the Hamiltonian matrix (the
+// spectral ordering of orbitals known from DMRG): orbitals are vertices
 // of a weighted graph, the eigenvector of the graph Laplacian with the
 // second smallest eigenvalue (the Fiedler vector) embeds them on a line,
 // and sorting by it places strongly coupled orbitals next to each other --
