@@ -129,12 +129,50 @@ def cpu_baseline(seconds=20.0):
             "ms_per_fit": 1e3 * dt / n}
 
 
+def fit_schedule(args):
+    """Sweeps per fit: (two-site, one-site)."""
+    if args.schedule:
+        return tuple(int(x) for x in args.schedule.split(","))
+    return SCHEDULE if args.mode == "krylov" else (0, 1)
+
+
+def workload_size(args):
+    """(L, N, 2Sz, D) of the krylov / apply workloads."""
+    if args.size:
+        Ls, Ns, Ds = (int(x) for x in args.size.split(","))
+        return Ls, Ns, Ns % 2, Ds
+    return L, N_ELEC, TWO_SZ, D
+
+
+def workload_config(args, sched, size, world):
+    """The `config` of the krylov / apply bench line (both arms)."""
+    Ls, Ns, Ss, Ds = size
+    if args.mode == "krylov":
+        w = ("Krylov step, L=%d N=%d 2Sz=%d D=%d m=10 dt=0.05 eps=1e-8, fit schedule %d "
+             "two-site + %d one-site sweeps, random seeded D=%d start"
+             % (Ls, Ns, Ss, Ds, sched[0], sched[1], Ds))
+    else:
+        w = ("apply_H fit, L=%d N=%d 2Sz=%d D=%d, schedule %d two-site + %d one-site sweeps, "
+             "random seeded D=%d state" % (Ls, Ns, Ss, Ds, sched[0], sched[1], Ds))
+    return {"workload": w,
+            "l2": "inputs larger than L2 (Krylov basis + environments, several GB)",
+            "inner_products": "serial" if args.serial_inner else "concurrent",
+            "parallelism": "replicas" if world > 1 else "single"}
+
+
 def run_reference(args):
+    """The oracle on the host cores, on the native arm's config: each step is a
+    bounded sample (fitted H applications of a system the oracle can hold,
+    described in cpu_baseline.sample); each warm-up step is one untimed fit."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
+    if args.mode == "batch":
+        print(json.dumps({"impl": "reference",
+                          "unavailable": "the oracle arm covers the krylov and apply modes"}))
+        return
     for _ in range(args.warmup):
-        pass
+        cpu_baseline(seconds=0.0)
     t0 = time.perf_counter()
     vals = []
     for _ in range(args.steps):
@@ -147,7 +185,8 @@ def run_reference(args):
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * dt / max(1, args.steps), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "oracle sample: apply_H L=8 N=7 D=64 (stands in for L=16 D=256)"},
+            "config": workload_config(args, fit_schedule(args), workload_size(args),
+                                      int(os.environ.get("WORLD_SIZE", "1"))),
             "cpu_baseline": cb,
             "e2e": {"value": v, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
@@ -326,16 +365,11 @@ def main():
         ctx.set_concurrent_inner(False)
     if args.mode == "batch":
         return run_batch(args, td, ctx, torch, local)
-    sched = SCHEDULE if args.mode == "krylov" else (0, 1)
-    if args.schedule:
-        sched = tuple(int(x) for x in args.schedule.split(","))
+    sched = fit_schedule(args)
     ctx.set_schedule(*sched)
     global L, N_ELEC, TWO_SZ, D
-    big = False
-    if args.size:
-        L, N_ELEC, D = (int(x) for x in args.size.split(","))
-        TWO_SZ = N_ELEC % 2
-        big = L >= 24
+    L, N_ELEC, TWO_SZ, D = workload_size(args)
+    big = L >= 24
     I = synth.make_integrals(L, seed=0, n_chol=64 if big else 16, localised_block=big)
     mpo = td.build_mpo(ctx, I.h, I.eri, n_elec=N_ELEC)
     # replicas only: each rank evolves its own seeded state, no collective
@@ -471,16 +505,7 @@ def main():
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": {"fp64": "f64", "tf32": "tf32", "tf32x3": "tf32x3", "bf16": "bf16"}[args.precision],
         "data": "synthetic",
-        "config": {"workload": ("Krylov step, L=%d N=%d 2Sz=%d D=%d m=10 dt=0.05 eps=1e-8, "
-                                "fit schedule %d two-site + %d one-site sweeps, random seeded "
-                                "D=%d start" % (L, N_ELEC, TWO_SZ, D, sched[0], sched[1], D))
-                               if args.mode == "krylov" else
-                               ("apply_H fit, L=%d N=%d 2Sz=%d D=%d, schedule %d two-site + "
-                                "%d one-site sweeps, random seeded D=%d state"
-                                % (L, N_ELEC, TWO_SZ, D, sched[0], sched[1], D)),
-                   "l2": "inputs larger than L2 (Krylov basis + environments, several GB)",
-                   "inner_products": "serial" if args.serial_inner else "concurrent",
-                   "parallelism": "replicas" if world > 1 else "single"},
+        "config": workload_config(args, sched, (L, N_ELEC, TWO_SZ, D), world),
         "steps_per_s": 1e3 * args.steps / ms,
         "vs_fp64": fp64_cmp,
         "vs_fp64_trajectory": traj,

@@ -41,3 +41,21 @@ def test_batch_instances_recipe():
     assert {L for _, L, _ in inst} <= {8, 10, 12, 14}
     assert {D for _, _, D in inst} <= {32, 64, 128}
     assert inst == bench.batch_instances()   # seeded
+
+
+def test_both_arms_describe_the_same_workload():
+    """The native line and the oracle (reference) line build `config` with
+    the same helper from the same arguments."""
+    from types import SimpleNamespace
+    a = SimpleNamespace(mode="krylov", schedule=None, size=None, serial_inner=False)
+    sched = bench.fit_schedule(a)
+    assert sched == bench.SCHEDULE
+    cfg = bench.workload_config(a, sched, bench.workload_size(a), 1)
+    assert "L=16 N=15 2Sz=1 D=256" in cfg["workload"]
+    assert "0 two-site + 2 one-site" in cfg["workload"]
+    assert cfg["parallelism"] == "single" and cfg["inner_products"] == "concurrent"
+    b = SimpleNamespace(mode="apply", schedule="1,1", size="32,23,512", serial_inner=True)
+    assert bench.workload_size(b) == (32, 23, 1, 512)
+    cfg = bench.workload_config(b, bench.fit_schedule(b), bench.workload_size(b), 2)
+    assert cfg["workload"].startswith("apply_H fit, L=32 N=23 2Sz=1 D=512, schedule 1 two-site")
+    assert cfg["parallelism"] == "replicas" and cfg["inner_products"] == "serial"
