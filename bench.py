@@ -129,6 +129,15 @@ def cpu_baseline(seconds=20.0):
             "ms_per_fit": 1e3 * dt / n}
 
 
+def dipole(gammas):
+    """Synthetic dipole of each 1-RDM in a stack (..., L, L): mu = sum_i x_i
+    Re gamma_ii with orbital coordinate x_i = i (there are no dipole
+    integrals; charge density per orbital = gamma_ii, Sec. 3.2)."""
+    g = np.asarray(gammas)
+    occ = np.real(np.diagonal(g, axis1=-2, axis2=-1))
+    return occ @ np.arange(g.shape[-1], dtype=np.float64)
+
+
 def fit_schedule(args):
     """Sweeps per fit: (two-site, one-site)."""
     if args.schedule:
@@ -477,6 +486,7 @@ def main():
         traj = {"workload": "beta-hole determinant, L=16 N=15, 2 Krylov steps, schedule 1+1",
                 "max_abs_err_one_rdm": float(np.abs(gm - g64).max()),
                 "max_abs_err_energy": float(np.abs(em - e64).max()),
+                "max_abs_err_dipole": float(np.abs(dipole(gm) - dipole(g64)).max()),
                 "s_per_step_fp64": t64 / 2, "s_per_step": tm / 2, "max_bond": int(bm)}
 
     # end-to-end through the public API with host buffers: import the state

@@ -59,3 +59,13 @@ def test_both_arms_describe_the_same_workload():
     cfg = bench.workload_config(b, bench.fit_schedule(b), bench.workload_size(b), 2)
     assert cfg["workload"].startswith("apply_H fit, L=32 N=23 2Sz=1 D=512, schedule 1 two-site")
     assert cfg["parallelism"] == "replicas" and cfg["inner_products"] == "serial"
+
+
+def test_synthetic_dipole():
+    """mu = sum_i i * gamma_ii: a determinant's 1-RDM gives the sum of the
+    occupied orbital indices weighted by occupation; stacks work per matrix."""
+    import numpy as np
+    g = np.diag([2.0, 2.0, 1.0, 0.0]).astype(complex)
+    assert bench.dipole(g) == 0 * 2 + 1 * 2 + 2 * 1
+    g2 = np.stack([g, np.diag([0.0, 1.0, 2.0, 2.0]).astype(complex) + 0.3j])
+    assert np.allclose(bench.dipole(g2), [4.0, 1 + 4 + 6])
