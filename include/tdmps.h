@@ -152,6 +152,9 @@ int tdmps_mpo_info(tdmps_mpo_t mpo, int* bond_dims, int64_t* n_elements);
  * number is returned.  No GPU is needed. */
 int tdmps_mpo_elements(tdmps_mpo_t mpo, int site, int64_t* count, int* win, int* wout, int* sig,
                        int* sigp, double* v);
+/* Releases the MPO handle, its host tables and its device tables (freed in
+ * stream order on the stream that uploaded them).  NULL is a no-op; always
+ * returns 0. */
 int tdmps_mpo_free(tdmps_mpo_t mpo);
 
 /* ------------------------------------------------------------------- MPS */
@@ -173,8 +176,15 @@ int tdmps_mps_import(tdmps_ctx_t ctx, int L, const int* bond_dims, const int* la
  * call again with labels (sum D_k pairs) and tensors[i] of D_i*4*D_{i+1}. */
 int tdmps_mps_export(tdmps_ctx_t ctx, tdmps_mps_t mps, int* bond_dims, int* labels,
                      tdmps_complex* const* tensors);
+/* Length, total charge (N, 2S_z) and the largest bond dimension (sum over
+ * the sectors of a bond, maximised over bonds).  Host only, no stream work;
+ * any output pointer may be NULL.  Errors: INVALID_ARG for a NULL handle. */
 int tdmps_mps_info(tdmps_mps_t mps, int* L, int* n_elec, int* two_sz, int* max_bond);
+/* Deep copy of `in` (device to device on the context stream); *out is a new
+ * handle owned by the caller.  Errors: INVALID_ARG, CUDA, OOM. */
 int tdmps_mps_copy(tdmps_ctx_t ctx, tdmps_mps_t in, tdmps_mps_t* out);
+/* Releases the MPS handle and its device memory (freed in stream order on
+ * the stream it was allocated on).  NULL is a no-op; always returns 0. */
 int tdmps_mps_free(tdmps_mps_t mps);
 
 /* ---------------------------------------------------------- operations */
@@ -338,8 +348,17 @@ typedef struct {
   double flops;     /* algorithmic real FLOPs                */
   double bytes;     /* algorithmic bytes read + written      */
 } tdmps_kstat;
+/* Turns the recording on (enable != 0) or off.  Pending records are first
+ * folded into the totals, which synchronises the context stream.  Recording
+ * is off by default, and no events are recorded while it is off.
+ * Errors: INVALID_ARG for a NULL ctx, CUDA. */
 int tdmps_stats_enable(tdmps_ctx_t ctx, int enable);
+/* Zeroes every class after folding in what is pending (synchronises the
+ * context stream).  Errors: INVALID_ARG for a NULL ctx, CUDA. */
 int tdmps_stats_reset(tdmps_ctx_t ctx);
+/* Totals of class `kind` (0 <= kind < TDMPS_KSTAT_COUNT) since the last
+ * reset.  Reading the event times synchronises the context stream.
+ * Errors: INVALID_ARG for a NULL ctx or out, or a kind out of range. */
 int tdmps_stats_get(tdmps_ctx_t ctx, int kind, tdmps_kstat* out);
 
 #ifdef __cplusplus
