@@ -37,6 +37,14 @@ ascending, then index); values <= 1e-12 * max are dropped; at most D are kept
 and, of those, the fewest whose discarded weight sum(s^2) stays <= eps *
 sum(s^2); a cut inside a cluster of values within 1e-10 * max of each other
 moves down to the cluster edge.
+
+Pins (tests/test_oracle_mps.py, test_oracle_observables.py,
+test_oracle_flops.py): untruncated fits and integrators equal the full-CI
+results, compression of two sites equals the library SVD, and the truncated
+fit lowers its residual at every local solve.  Parity unpinned: whether a
+truncated fit (D below the exact bond dimension) reaches the best truncated
+state.  No closed form fixes that state, so the GPU is compared with this
+oracle on the same schedule instead.
 """
 from __future__ import annotations
 
