@@ -69,3 +69,30 @@ def test_synthetic_dipole():
     assert bench.dipole(g) == 0 * 2 + 1 * 2 + 2 * 1
     g2 = np.stack([g, np.diag([0.0, 1.0, 2.0, 2.0]).astype(complex) + 0.3j])
     assert np.allclose(bench.dipole(g2), [4.0, 1 + 4 + 6])
+
+
+def test_reference_arm_json_line():
+    """`bench.py --impl reference` prints one JSON line with the contract's
+    keys, the native arm's metric and config, and an e2e entry without
+    host-device traffic (about 20 s of oracle work on the host cores)."""
+    import json
+    import subprocess
+    import sys
+    from types import SimpleNamespace
+    out = subprocess.run([sys.executable, bench.__file__, "--impl", "reference", "--steps", "1",
+                          "--warmup", "1"], capture_output=True, text=True, timeout=300)
+    assert out.returncode == 0, out.stderr[-2000:]
+    line = json.loads(out.stdout.strip().splitlines()[-1])
+    for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
+              "higher_is_better", "scaling", "vs_baseline", "dtype", "data", "config",
+              "cpu_baseline", "e2e"):
+        assert k in line, k
+    assert line["impl"] == "reference" and line["metric"] == bench.METRIC
+    assert line["value"] > 0 and line["unit"] == "TFLOP/s" and line["steps"] == 1
+    a = SimpleNamespace(mode="krylov", schedule=None, size=None, serial_inner=False)
+    assert line["config"] == bench.workload_config(a, bench.fit_schedule(a),
+                                                   bench.workload_size(a), 1)
+    cb = line["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == line["value"]
+    assert line["e2e"] == {"value": line["value"], "unit": "TFLOP/s",
+                           "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
