@@ -97,7 +97,10 @@ def cpu_baseline(seconds=20.0):
     """The oracle as it stands on the host cores: fitted H applications of the
     same kind (dense-projection fit, same sweep schedule) on a bounded sample,
     the L = 8, N = 7 system (the oracle holds 4^L-long vectors, so L = 16 is
-    out of its reach).  FLOPs are the oracle's own complex arithmetic."""
+    out of its reach).  FLOPs are the oracle's own complex arithmetic.
+    `cores` is the thread count the BLAS may use (OMP_NUM_THREADS, else the
+    host's CPUs); `avg_busy_threads` is process CPU time / wall time over the
+    sample, the threads actually kept busy."""
     import synth
     from oracle import mps as om
     Ls, Ds = 8, 64
@@ -113,6 +116,8 @@ def cpu_baseline(seconds=20.0):
         for i in range(Ls):
             flops_fit += 8.0 * (4 ** Ls) * (dims[i] + dims[i + 1])
     flops_H = 2.0 * len(sysb.dets) ** 2
+    import resource
+    r0 = resource.getrusage(resource.RUSAGE_SELF)
     t0 = time.perf_counter()
     n = 0
     while True:
@@ -121,9 +126,12 @@ def cpu_baseline(seconds=20.0):
         if time.perf_counter() - t0 > seconds:
             break
     dt = time.perf_counter() - t0
+    r1 = resource.getrusage(resource.RUSAGE_SELF)
+    cpu_s = (r1.ru_utime - r0.ru_utime) + (r1.ru_stime - r0.ru_stime)
     threads = os.environ.get("OMP_NUM_THREADS") or str(os.cpu_count())
     return {"value": n * (flops_fit + flops_H) / dt / 1e12, "unit": "TFLOP/s",
             "cores": int(threads), "kind": "oracle",
+            "avg_busy_threads": round(cpu_s / dt, 2),
             "sample": "%d dense-projection apply_H fits, L=8 N=7 D=64, one-site x2 "
                       "(L=16 needs 4^16-long vectors)" % n,
             "ms_per_fit": 1e3 * dt / n}

@@ -94,5 +94,6 @@ def test_reference_arm_json_line():
                                                    bench.workload_size(a), 1)
     cb = line["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == line["value"]
+    assert 0.0 < cb["avg_busy_threads"] <= cb["cores"] + 0.5
     assert line["e2e"] == {"value": line["value"], "unit": "TFLOP/s",
                            "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
