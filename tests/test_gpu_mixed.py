@@ -143,8 +143,16 @@ def test_full_size_krylov_step_mixed_vs_fp64_physical(td):
         mpo = td.build_mpo(ctx, I.h, I.eri, n_elec=15)
         psi = td.mps_from_determinant(ctx, occ)
         td.krylov_step(ctx, mpo, psi, 0.05, 10, True, 256, 1e-8)
-        e = td.expectation(ctx, mpo, psi, psi).real / td.overlap(ctx, psi, psi).real
-        res[p] = (td.one_rdm(ctx, psi), e)
+        nrm = td.overlap(ctx, psi, psi).real
+        e = td.expectation(ctx, mpo, psi, psi).real / nrm
+        g = td.one_rdm(ctx, psi)
+        res[p] = (g, e)
         ctx.close()
+        # properties of any 15-electron state, at full size: the particle
+        # number is exact (one block-sparse sector), and the occupations of a
+        # spatial orbital (eigenvalues of the spin-summed 1-RDM) lie in [0, 2]
+        assert abs(np.trace(g).real / nrm - 15.0) < 1e-9
+        lam = np.linalg.eigvalsh(g / nrm)
+        assert lam.min() > -1e-9 and lam.max() < 2.0 + 1e-9
     assert abs(res["fp64"][1] - res["tf32x3"][1]) < 1e-6
     assert np.abs(res["fp64"][0] - res["tf32x3"][0]).max() < 2e-5
