@@ -130,6 +130,75 @@ def test_green_function_noninteracting_closed_form():
         assert abs(G[0] + 1j) < 1e-13
 
 
+@pytest.mark.parametrize("t,U", [(1.0, 4.0), (0.3, 1.7), (2.0, 0.5), (1.0, 0.0)])
+def test_green_function_hubbard_dimer_lehmann_closed_form(t, U):
+    """Interacting pin (textbook Hubbard dimer: hopping -t, on-site U, two
+    electrons in the singlet ground state, E0 = (U - sqrt(U^2 + 16 t^2))/2).
+    The ground state is C |covalent> + I |ionic> with I / C = r = |E0| / (2t).
+    Removing an electron leaves one electron, whose states are the bonding
+    (energy -t) and antibonding (+t) orbitals, reached with the Lehmann weights
+    w_b = (1 + r)^2 / (2 (1 + r^2)) and w_a = (1 - r)^2 / (2 (1 + r^2))
+    (w_b + w_a = 1 = the occupation of one site).  So
+        G_11(tau) = -i (w_b e^{-i t tau} + w_a e^{+i t tau}),
+        G_12(tau) = -i (w_b e^{-i t tau} - w_a e^{+i t tau}) / (w_b - w_a):
+    the antibonding orbital changes sign between the sites, and any sign
+    convention multiplies numerator and normalisation alike."""
+    h = np.array([[0.0, -t], [-t, 0.0]])
+    eri = np.zeros((2, 2, 2, 2))
+    eri[0, 0, 0, 0] = eri[1, 1, 1, 1] = U
+    dets = fci.basis(2, 1, 1)
+    w, V = np.linalg.eigh(fci.hamiltonian(h, eri, dets))
+    E0 = 0.5 * (U - np.sqrt(U * U + 16 * t * t))
+    assert abs(w[0] - E0) < 1e-13 and w[1] - w[0] > 1e-6
+    psi0 = V[:, 0].astype(complex)
+    r = abs(E0) / (2 * t)
+    wb = (1 + r) ** 2 / (2 * (1 + r * r))
+    wa = (1 - r) ** 2 / (2 * (1 + r * r))
+    taus = np.array([0.0, 0.4, 1.3, 2.9])
+    G11 = fci.green_function(h, eri, psi0, dets, 2, 0, 0, taus)
+    assert np.allclose(G11, -1j * (wb * np.exp(-1j * t * taus) + wa * np.exp(1j * t * taus)),
+                       atol=1e-12)
+    G12 = fci.green_function(h, eri, psi0, dets, 2, 0, 1, taus)
+    assert np.allclose(G12, -1j * (wb * np.exp(-1j * t * taus) - wa * np.exp(1j * t * taus))
+                       / (wb - wa), atol=1e-12)
+
+
+def test_green_function_equals_kronecker_fock_space():
+    """Eq. (green_time) on the whole Fock space with Kronecker-product
+    Jordan-Wigner operators and scipy's matrix exponential, for a random
+    complex state with unequal spin counts (so neither the i <-> j exchange
+    nor the two spins are related by a symmetry)."""
+    L = 3
+    I = synth.make_integrals(L, seed=21, n_chol=3)
+    dets = fci.basis(L, 2, 1)
+    psi0 = _rand_sector_vector(dets, 22)
+    a = spin_orbital_ops(L)
+    ad = [x.T for x in a]
+    H = np.zeros((4 ** L, 4 ** L))
+    for i in range(L):
+        for j in range(L):
+            for s in range(2):
+                H += I.h[i, j] * ad[2 * i + s] @ a[2 * j + s]
+    for i in range(L):
+        for j in range(L):
+            for k in range(L):
+                for l in range(L):
+                    for s in range(2):
+                        for u in range(2):
+                            H += 0.5 * I.eri[i, j, k, l] * (ad[2 * i + s] @ ad[2 * k + u]
+                                                           @ a[2 * l + u] @ a[2 * j + s])
+    v = np.zeros(4 ** L, dtype=complex)
+    v[dets.astype(np.int64)] = psi0        # a determinant mask is its Kronecker index
+    taus = np.array([0.0, 0.35, 1.2])
+    for i, j in [(0, 2), (2, 0), (1, 1), (2, 1)]:
+        den = sum(np.vdot(a[2 * i + s] @ v, a[2 * j + s] @ v) for s in range(2))
+        ref = np.array([-1j * sum(np.vdot(a[2 * i + s] @ v,
+                                          scipy.linalg.expm(1j * H * t) @ (a[2 * j + s] @ v))
+                                  for s in range(2)) / den for t in taus])
+        G = fci.green_function(I.h, I.eri, psi0, dets, L, i, j, taus)
+        assert np.allclose(G, ref, atol=1e-11)
+
+
 def test_mps_green_function_matches_full_ci():
     L = 4
     I = synth.make_integrals(L, seed=13, n_chol=3)
