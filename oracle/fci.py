@@ -311,12 +311,13 @@ def krylov_coefficients(N: np.ndarray, Hk: np.ndarray, dt: float):
 
 
 def krylov_step(H: np.ndarray, psi: np.ndarray, dt: float, m: int,
-                orthogonal: bool = True) -> np.ndarray:
+                orthogonal: bool = True, return_basis: bool = False):
     """One Krylov step with m basis vectors (phi_0 = psi).
 
     orthogonal=True: Eq. (kry_orth), full Gram-Schmidt against all previous
     vectors; orthogonal=False: Eq. (kry_non), phi_{k+1} = H phi_k normalised.
-    Then Eq. (krylov_evo) with the measured overlap matrix N.
+    Then Eq. (krylov_evo) with the measured overlap matrix N.  Returns the new
+    vector, and with return_basis=True also the basis (columns phi_0..phi_{m-1}).
     """
     phis = [psi.astype(np.complex128)]
     for k in range(m - 1):
@@ -331,4 +332,4 @@ def krylov_step(H: np.ndarray, psi: np.ndarray, dt: float, m: int,
     N = P.conj().T @ P
     Hk = P.conj().T @ (H @ P)
     c, _ = krylov_coefficients(N, Hk, dt)
-    return P @ c
+    return (P @ c, P) if return_basis else P @ c

@@ -131,12 +131,13 @@ def test_hermitian_and_slater_condon_diagonal():
 def test_h_on_determinant_matches_dense_columns():
     I = synth.make_integrals(6, seed=2)
     dets = fci.basis(6, 3, 2)
-    H = fci.hamiltonian(I.h, I.eri, dets)
-    for col in (0, 17, 101):
-        m, c = fci.h_on_determinant(I.h, I.eri, int(dets[col]))
-        full = np.zeros(len(dets))
-        full[np.searchsorted(dets, m)] = c
-        assert np.allclose(full, H[:, col], atol=1e-13)
+    for e0 in (0.0, 0.37):
+        H = fci.hamiltonian(I.h, I.eri, dets, e0)
+        for col in (0, 17, 101):
+            m, c = fci.h_on_determinant(I.h, I.eri, int(dets[col]), e0)
+            full = np.zeros(len(dets))
+            full[np.searchsorted(dets, m)] = c
+            assert np.allclose(full, H[:, col], atol=1e-13)
 
 
 def test_one_rdm_of_determinant_and_trace():
@@ -219,9 +220,16 @@ def test_krylov_orthogonal_and_plain_bases_agree():
     H = fci.hamiltonian(I.h, I.eri, dets)
     rng = np.random.default_rng(3)
     psi = rng.standard_normal(len(dets)) + 1j * rng.standard_normal(len(dets))
-    a = fci.krylov_step(H, psi, 0.05, 4, orthogonal=True)
-    b = fci.krylov_step(H, psi, 0.05, 4, orthogonal=False)
+    a, P = fci.krylov_step(H, psi, 0.05, 4, orthogonal=True, return_basis=True)
+    b, Q = fci.krylov_step(H, psi, 0.05, 4, orthogonal=False, return_basis=True)
     assert np.allclose(a, b, atol=1e-10)
+    # Eq. (kry_orth) makes the basis orthogonal, and phi_1.. are normalised
+    # (phi_0 = psi keeps its norm); Eq. (kry_non) is not orthogonal
+    G = P.conj().T @ P
+    assert np.allclose(G - np.diag(np.diag(G)), 0.0, atol=1e-12)
+    assert np.allclose(np.diag(G)[1:], 1.0, atol=1e-12)
+    G2 = Q.conj().T @ Q
+    assert np.abs(G2 - np.diag(np.diag(G2))).max() > 1e-3
 
 
 def test_krylov_coefficients_match_expm_and_scaling_invariance():
@@ -233,13 +241,16 @@ def test_krylov_coefficients_match_expm_and_scaling_invariance():
     assert dropped == 0
     assert np.allclose(c, scipy.linalg.expm(-0.3j * Hk)[:, 0], atol=1e-13)
     # non-orthogonal basis P = Q S: coefficients transform with S^-1
-    S = np.triu(rng.standard_normal((m, m))) + 3 * np.eye(m)
-    S[0, :] = 0
-    S[0, 0] = 1.0       # phi_0 unchanged
+    S = np.triu(rng.standard_normal((m, m)) + 1j * rng.standard_normal((m, m))) + 3 * np.eye(m)
+    S[0, 0] = 1.0       # column 0 = e_0: phi_0 unchanged; the later vectors keep
+    #                     complex phi_0 components, so N[:, 0] is complex
     N = S.conj().T @ S
+    assert np.abs(N[1:, 0].imag).max() > 1e-2
     H2 = S.conj().T @ Hk @ S
     c2, _ = fci.krylov_coefficients(N, H2, 0.3)
     assert np.allclose(S @ c2, c, atol=1e-12)
+    # the definition of Eq. (krylov_evo) for a regular N
+    assert np.allclose(c2, scipy.linalg.expm(-0.3j * np.linalg.solve(N, H2))[:, 0], atol=1e-11)
 
 
 def test_krylov_error_decreases_with_time_step():

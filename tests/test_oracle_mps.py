@@ -86,11 +86,12 @@ def test_truncation_rule_eps_D_and_clusters():
     assert kept == {(0, 0): 2, (1, 1): 1, (1, -1): 0}
 
 
-@pytest.mark.parametrize("n_two", [3])
-def test_untruncated_apply_h_is_exact(n_two):
+@pytest.mark.parametrize("n_two,n_one", [(3, 1), (4, 0)])
+def test_untruncated_apply_h_is_exact(n_two, n_one):
+    # (4, 0): two-site sweeps alone (their projections decide the result)
     sys_ = _system(6, 6, 0, seed=5)
     psi = om.from_determinant([3, 3, 0, 0, 1, 2])
-    sch = om.Schedule(D=500, eps=0.0, n_two_site=n_two, n_one_site=1)
+    sch = om.Schedule(D=500, eps=0.0, n_two_site=n_two, n_one_site=n_one)
     c = om.apply_H(sys_, psi, 0.7 - 0.2j, sch)
     ref = (0.7 - 0.2j) * (sys_.H @ sys_.vec(psi))
     assert np.linalg.norm(sys_.vec(c) - ref) < 1e-12 * np.linalg.norm(ref)
@@ -104,6 +105,9 @@ def test_untruncated_integrators_equal_full_ci_integrators():
     p = om.rk4_step(sys_, psi, 0.03, sch)
     assert np.linalg.norm(sys_.vec(p) - fci.rk4_step(sys_.H, v, 0.03)) < 1e-11
     k, c, N, Hk = om.krylov_step(sys_, p, 0.05, 5, sch)
+    # Eq. (kry_orth): the fitted, normalised basis is orthonormal when nothing
+    # is truncated (p is complex, so a conjugated coefficient would show)
+    assert np.allclose(N, np.eye(5), atol=1e-10)
     ref = fci.krylov_step(sys_.H, sys_.vec(p), 0.05, 5)
     assert np.linalg.norm(sys_.vec(k) - ref) < 1e-10
     assert abs(om.norm(k) - om.norm(p)) < 1e-12
