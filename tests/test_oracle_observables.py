@@ -211,3 +211,20 @@ def test_mps_green_function_matches_full_ci():
     G = om.green_function(systems, psi0, 1, 2, dt, n, 6, sch)
     ref = fci.green_function(I.h, I.eri, U[:, 0], dets, L, 1, 2, dt * np.arange(n + 1))
     assert np.allclose(G, ref, atol=1e-9)
+    # RK4 variant: untruncated, it equals the same backward steps taken by the
+    # vector RK4 (time step -dt) on the ionised full-CI vectors
+    G4 = om.green_function(systems, psi0, 1, 2, dt, n, 6, sch, method="rk4")
+    num = np.zeros(n + 1, dtype=complex)
+    den = 0.0
+    for s, (na, nb) in ((0, (1, 2)), (1, (2, 1))):
+        dm = fci.basis(L, na, nb)
+        Hm = fci.hamiltonian(I.h, I.eri, dm)
+        chi_i = fci.apply_to_vector(U[:, 0], dets, dm, 2 * 1 + s, False)
+        chi = fci.apply_to_vector(U[:, 0], dets, dm, 2 * 2 + s, False)
+        den += np.vdot(chi_i, chi)
+        num[0] += np.vdot(chi_i, chi)
+        for k in range(n):
+            chi = fci.rk4_step(Hm, chi, -dt)
+            num[k + 1] += np.vdot(chi_i, chi)
+    assert np.allclose(G4, -1j * num / den, atol=1e-9)
+    assert np.abs(G4 - ref).max() > 1e-9    # RK4 is not the exact propagation

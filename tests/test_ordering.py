@@ -43,6 +43,31 @@ def test_oracle_recovers_a_hidden_chain(seed):
     assert list(perm) == list(order) or list(perm) == list(order[::-1])
 
 
+def test_chain_in_exchange_integrals_only_and_forward_sign():
+    """Reading of the graph weights: hopping plus exchange (ij|ji).  The
+    chain lives only in the exchange integrals, and every Coulomb (ii|jj) is
+    the same, so a Coulomb-weighted graph would carry no order.  A chain given
+    in input order comes back unreversed: the sign of the Fiedler vector makes
+    its correlation with the input order positive."""
+    L = 8
+    rng = np.random.default_rng(7)
+    order = rng.permutation(L)
+    for chain, forward in ((order, False), (np.arange(L), True)):
+        h = np.diag(rng.uniform(-2, -0.5, L))
+        eri = np.zeros((L, L, L, L))
+        for i in range(L):
+            for j in range(L):
+                eri[i, i, j, j] = 0.4
+        for a, b in zip(chain[:-1], chain[1:]):
+            k = rng.uniform(0.05, 0.1)
+            eri[a, b, b, a] = eri[b, a, a, b] = k
+        perm = list(ordering.fiedler_order(h, eri))
+        if forward:
+            assert perm == list(range(L))
+        else:
+            assert perm == list(chain) or perm == list(chain[::-1])
+
+
 def test_library_matches_oracle_on_host():
     import paper_1902_08489_gb300 as td
     try:
