@@ -128,6 +128,26 @@ def test_full_size_overlap(td, ctx):
     assert abs(td.overlap(ctx, b, a) - ref) < TOL * max(1.0, abs(ref))
 
 
+def test_full_size_apply_h_projection_property(td, ctx):
+    # L = 16, D = 256, the benchmark's apply_H (one one-site sweep) in FP64.
+    # The fit ends with the local solve at site 0, which is the projection of
+    # the target alpha H|psi> on the orthonormal bases of the other sites
+    # (Eq. add_min in the mixed-canonical gauge).  So <C|C> = <C|alpha H|psi>
+    # at any size; the oracle pins the same identity on small systems.
+    L, N, S = 16, 15, 1
+    I = synth.make_integrals(L, seed=0)
+    mpo = td.build_mpo(ctx, I.h, I.eri, n_elec=N)
+    A, q = synth.random_mps(L, N, S, 256, seed=3)
+    psi = td.mps_import(ctx, A, q)
+    ctx.set_schedule(0, 1)
+    alpha = 0.4 - 0.9j
+    c = td.apply_H(ctx, mpo, psi, alpha, 256, 0.0)
+    cc = td.overlap(ctx, c, c)
+    ct = alpha * td.expectation(ctx, mpo, c, psi)
+    assert abs(cc.imag) < 1e-12 * abs(cc)
+    assert abs(cc - ct) < 1e-9 * abs(cc), (cc, ct)
+
+
 # ---------------------------------------------------------------- fits
 
 @pytest.mark.parametrize("n2,n1,D", [(3, 1, 500), (1, 2, 12), (0, 3, 64)])
