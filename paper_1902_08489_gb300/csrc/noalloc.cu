@@ -119,7 +119,7 @@ cplx overlap_noalloc(Context& c, const MPSd& bra, const MPSd& ket) {
       tasks.push_back(t);
     };
     auto add_term = [&](const double2* Ap, int lda, const double2* Bp, int ldb, int K) {
-      terms.push_back({Ap, Bp, K, lda, ldb, 0, one, nullptr});
+      terms.push_back({Ap, Bp, K, lda, ldb, 0, one, nullptr, make_float2(1.f, 0.f)});
       tasks.back().term_end = (int)terms.size();
     };
     // X = E A
