@@ -149,7 +149,10 @@ int tdmps_mpo_info(tdmps_mpo_t mpo, int* bond_dims, int64_t* n_elements);
  * matrix element <sig|W[w_in, w_out]|sigp> = v[e] between channel w_in of
  * bond `site` and channel w_out of bond site+1.  *count is the capacity on
  * entry and the number of elements on return; with win == NULL only the
- * number is returned.  No GPU is needed. */
+ * number is returned.  No GPU is needed.  Errors: INVALID_ARG for a NULL
+ * mpo or count, a site out of range, a NULL wout/sig/sigp/v when win is
+ * given, or a capacity below the element count (*count then holds the
+ * count needed). */
 int tdmps_mpo_elements(tdmps_mpo_t mpo, int site, int64_t* count, int* win, int* wout, int* sig,
                        int* sigp, double* v);
 /* Releases the MPO handle, its host tables and its device tables (freed in

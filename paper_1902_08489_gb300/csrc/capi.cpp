@@ -160,7 +160,11 @@ int tdmps_mpo_elements(tdmps_mpo_t mpo, int site, int64_t* count, int* win, int*
   if (!mpo || site < 0 || site >= mpo->m.L || !count) return TDMPS_ERR_INVALID_ARG;
   const auto& W = mpo->m.W[site];
   if (win) {
-    if (*count < (int64_t)W.size()) return TDMPS_ERR_INVALID_ARG;
+    if (!wout || !sig || !sigp || !v) return TDMPS_ERR_INVALID_ARG;
+    if (*count < (int64_t)W.size()) {
+      *count = (int64_t)W.size();
+      return TDMPS_ERR_INVALID_ARG;
+    }
     for (size_t e = 0; e < W.size(); ++e) {
       win[e] = W[e].win;
       wout[e] = W[e].wout;

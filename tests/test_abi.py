@@ -40,6 +40,29 @@ def test_invalid_arguments_are_rejected_without_gpu(built):
     with pytest.raises(td.TdmpsError) as e:
         td.build_mpo(None, h, eri)
     assert e.value.name == "NONFINITE"
+    # host-only calls: NULL handles, sites out of range, short buffers
+    import ctypes
+    assert td.ERRORS[built.tdmps_mps_info(None, None, None, None, None)] == "INVALID_ARG"
+    assert td.ERRORS[built.tdmps_mpo_info(None, None, None)] == "INVALID_ARG"
+    mpo = td.build_mpo(None, np.diag([-1.0, -0.5]), np.zeros((2, 2, 2, 2)), n_elec=2)
+    n = ctypes.c_int64(0)
+    for site in (-1, 2):
+        assert td.ERRORS[built.tdmps_mpo_elements(mpo.h, site, ctypes.byref(n), None, None, None,
+                                                  None, None)] == "INVALID_ARG"
+    assert built.tdmps_mpo_elements(mpo.h, 0, ctypes.byref(n), None, None, None, None, None) == 0
+    need = n.value
+    assert need > 0
+    buf = [np.zeros(need, dtype=np.int32) for _ in range(4)]
+    vals = np.zeros(need)
+    ptrs = [b.ctypes.data_as(ctypes.c_void_p) for b in buf]
+    assert td.ERRORS[built.tdmps_mpo_elements(mpo.h, 0, ctypes.byref(n), ptrs[0], None, ptrs[2],
+                                              ptrs[3], vals.ctypes.data_as(ctypes.c_void_p))] \
+        == "INVALID_ARG"
+    short = ctypes.c_int64(need - 1)
+    assert td.ERRORS[built.tdmps_mpo_elements(mpo.h, 0, ctypes.byref(short), *ptrs,
+                                              vals.ctypes.data_as(ctypes.c_void_p))] == "INVALID_ARG"
+    assert short.value == need
+    mpo.free()
     # context setters reject a NULL context
     assert td.ERRORS[built.tdmps_set_concurrent_inner(None, 0)] == "INVALID_ARG"
     assert td.ERRORS[built.tdmps_set_krylov_fp64(None, 1)] == "INVALID_ARG"
