@@ -22,7 +22,9 @@
  *   message of the last error of a context is returned by tdmps_last_error.
  *   There is no CPU fallback: when a CUDA call fails the entry point returns
  *   TDMPS_ERR_CUDA.  A handle whose call failed stays valid and unchanged
- *   unless stated otherwise.
+ *   unless stated otherwise.  A NaN or Inf scalar argument (alpha, dt)
+ *   returns TDMPS_ERR_NONFINITE, and a NULL handle or an out-of-range size
+ *   TDMPS_ERR_INVALID_ARG, both before any work is enqueued.
  * - Complex numbers are passed as tdmps_complex {re, im} (layout of C99
  *   double complex).
  */

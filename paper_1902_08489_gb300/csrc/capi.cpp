@@ -47,6 +47,11 @@ void need(bool cond, const char* msg) {
   if (!cond) throw Error(TDMPS_ERR_INVALID_ARG, msg);
 }
 
+// A scalar input that must be finite (NaN or Inf -> TDMPS_ERR_NONFINITE).
+void need_finite(double x, const char* msg) {
+  if (!std::isfinite(x)) throw Error(TDMPS_ERR_NONFINITE, msg);
+}
+
 void ensure_uploaded(tdmps_ctx_t ctx, tdmps_mpo_t mpo) {
   if (!mpo->uploaded) {
     upload_mpo_tables(mpo->m, *ctx->c);
@@ -247,6 +252,8 @@ int tdmps_apply_H(tdmps_ctx_t ctx, tdmps_mpo_t mpo, tdmps_mps_t in, tdmps_comple
   return guard(ctx, [&] {
     need(mpo && in && out, "NULL argument");
     need(mpo->m.L == in->m.L, "MPO and MPS lengths differ");
+    need_finite(alpha.re, "alpha must be finite");
+    need_finite(alpha.im, "alpha must be finite");
     ensure_uploaded(ctx, mpo);
     FitOpts o = opts(ctx, D, eps);
     if (n_sweeps > 0) o.n_one_site = n_sweeps;
@@ -326,6 +333,7 @@ int tdmps_rk4_step(tdmps_ctx_t ctx, tdmps_mpo_t mpo, tdmps_mps_t inout, double d
   return guard(ctx, [&] {
     need(mpo && inout, "NULL argument");
     need(mpo->m.L == inout->m.L, "MPO and MPS lengths differ");
+    need_finite(dt, "dt must be finite");
     ensure_uploaded(ctx, mpo);
     FitOpts o = opts(ctx, D, eps);
     MPSd r = rk4_step(*ctx->c, mpo->m, inout->m, dt, o);
@@ -339,6 +347,7 @@ int tdmps_krylov_step(tdmps_ctx_t ctx, tdmps_mpo_t mpo, tdmps_mps_t inout, doubl
   return guard(ctx, [&] {
     need(mpo && inout, "NULL argument");
     need(mpo->m.L == inout->m.L, "MPO and MPS lengths differ");
+    need_finite(dt, "dt must be finite");
     ensure_uploaded(ctx, mpo);
     FitOpts o = opts(ctx, D, eps);
     MPSd r = krylov_step(*ctx->c, mpo->m, inout->m, dt, m, orthogonal != 0, o);
@@ -397,7 +406,7 @@ int tdmps_green_function(tdmps_ctx_t ctx, tdmps_mpo_t mpo, tdmps_mps_t psi0, int
     need(mpo && psi0 && G, "NULL argument");
     need(mpo->m.L == psi0->m.L, "MPO and MPS lengths differ");
     need(i >= 0 && i < psi0->m.L && j >= 0 && j < psi0->m.L, "orbital index out of range");
-    need(std::isfinite(dt), "dt must be finite");
+    need_finite(dt, "dt must be finite");
     if (method == 0) need(m >= 2 && m <= 16, "Krylov dimension must be in [2, 16]");
     ensure_uploaded(ctx, mpo);
     std::vector<cplx> g((size_t)std::max(n_steps, 0) + 1);
@@ -423,7 +432,7 @@ int tdmps_evolve_batch(tdmps_ctx_t ctx, int n, const tdmps_mpo_t* mpos, tdmps_mp
       need(mpos[k] && states[k], "NULL MPO or state in the batch");
       need(mpos[k]->m.L == states[k]->m.L, "MPO and MPS lengths differ");
       need(n_steps[k] >= 0, "n_steps must be >= 0");
-      need(std::isfinite(dt[k]), "dt must be finite");
+      need_finite(dt[k], "dt must be finite");
       opts(ctx, D[k], eps[k]);   // argument checks
       for (int q = 0; q < k; ++q) need(states[q] != states[k], "a state appears twice in the batch");
       ensure_uploaded(ctx, mpos[k]);

@@ -149,6 +149,13 @@ def test_argument_errors(td, ctx):
         with pytest.raises(td.TdmpsError) as e:
             bad()
         assert e.value.name == "INVALID_ARG"
+    # non-finite scalar inputs are rejected on the host before any launch
+    for bad in (lambda: td.apply_H(ctx, mpo, psi, complex(float("nan"), 0.0), 8, 0.0),
+                lambda: td.rk4_step(ctx, mpo, psi, float("inf"), 8),
+                lambda: td.krylov_step(ctx, mpo, psi, float("nan"), 4, True, 8)):
+        with pytest.raises(td.TdmpsError) as e:
+            bad()
+        assert e.value.name == "NONFINITE"
     other = td.mps_from_determinant(ctx, [3, 1, 0, 0])
     with pytest.raises(td.TdmpsError) as e:
         td.overlap(ctx, psi, other)
