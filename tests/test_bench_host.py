@@ -97,3 +97,101 @@ def test_reference_arm_json_line():
     assert 0.0 < cb["avg_busy_threads"] <= cb["cores"] + 0.5
     assert line["e2e"] == {"value": line["value"], "unit": "TFLOP/s",
                            "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+
+
+def test_native_arm_json_assembly_with_a_stand_in_library(monkeypatch, capsys):
+    """Runs bench.main() on the CPU with a stand-in for the library and for
+    torch.cuda (test double only: every number it prints is meaningless).  It
+    checks the control flow and the JSON line of the native arm in the krylov,
+    apply and serial-inner-product modes, so that a Python-level mistake there
+    shows up without a GPU.  The real library is exercised by the GPU tests."""
+    import json
+    import sys
+    import time
+    import types
+    import numpy as np
+    import torch
+
+    class Ev:
+        def __init__(self, enable_timing=False):
+            self.t = None
+
+        def record(self, stream=None):
+            self.t = time.perf_counter()
+
+        def elapsed_time(self, other):
+            return 1e3 * (other.t - self.t) + 1e-3
+
+    for name, fn in (("Event", Ev), ("synchronize", lambda *a, **k: None),
+                     ("set_device", lambda *a, **k: None),
+                     ("current_stream", lambda *a, **k: object())):
+        monkeypatch.setattr(torch.cuda, name, fn)
+    classes = ["gemm", "wstage", "qr", "svd", "other", "gemm_fp64", "host_plan", "host_launch",
+               "host_sync"]
+    seen = []
+
+    class MPS:
+        def __init__(self, L=16):
+            self.L = L
+
+        def info(self):
+            return {"L": self.L, "n_elec": 15, "two_sz": 1, "max_bond": 256}
+
+        def free(self):
+            pass
+
+    class Ctx:
+        def __init__(self, prec):
+            self.prec = prec
+
+        def set_precision(self, p):
+            self.prec = p
+
+        def set_schedule(self, a, b):
+            pass
+
+        def set_concurrent_inner(self, on):
+            seen.append(on)
+
+        def stats_enable(self, on=True):
+            pass
+
+        def stats_reset(self):
+            pass
+
+        def stats(self):
+            return {k: dict(launches=10, ms=5.0 * (i + 1), flops=1e10 * (i + 1), bytes=1e8)
+                    for i, k in enumerate(classes)}
+
+    lib = types.ModuleType("paper_1902_08489_gb300")
+    lib.Context = Ctx
+    lib.build_mpo = lambda ctx, h, eri, L=None, n_elec=0, e0=0.0: object()
+    lib.mps_import = lambda ctx, A, q: MPS(len(A))
+    lib.mps_from_determinant = lambda ctx, occ: MPS(len(occ))
+    lib.overlap = lambda ctx, a, b: 1.0 + 0j
+    lib.expectation = lambda ctx, mpo, a, b: -20.6 + 0j
+    lib.one_rdm = lambda ctx, m: np.eye(m.L, dtype=complex) * (15.0 / m.L)
+    lib.krylov_step = lambda *a, **k: None
+    lib.apply_H = lambda *a, **k: MPS()
+    monkeypatch.setitem(sys.modules, "paper_1902_08489_gb300", lib)
+    monkeypatch.delenv("WORLD_SIZE", raising=False)
+    for argv, mode in ((["--steps", "2", "--warmup", "3"], "krylov"),
+                       (["--mode", "apply", "--steps", "2", "--warmup", "3"], "apply"),
+                       (["--steps", "1", "--warmup", "3", "--serial-inner", "--no-traj-compare",
+                         "--no-fp64-compare", "--no-e2e"], "serial")):
+        monkeypatch.setattr(sys, "argv", ["bench.py", "--no-cpu-baseline", *argv])
+        bench.main()
+        line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+        for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
+                  "higher_is_better", "scaling", "vs_baseline", "dtype", "data", "config",
+                  "roofline", "clocks", "e2e", "gpu_launches"):
+            assert k in line, (mode, k)
+        assert line["metric"] == bench.METRIC and line["gpu_launches"] > 0
+        assert line["config"]["inner_products"] == ("serial" if mode == "serial" else "concurrent")
+        if mode == "krylov":
+            traj = line["vs_fp64_trajectory"]
+            assert traj["max_abs_err_dipole"] == 0.0 and line["vs_fp64"] is not None
+            assert line["e2e"]["h2d_bytes_per_step"] > 0
+        else:
+            assert line["vs_fp64_trajectory"] is None
+    assert seen == [False]
