@@ -70,6 +70,25 @@ def test_hubbard_dimer_closed_form():
         assert np.allclose(w, ref, atol=1e-13)
 
 
+def test_one_electron_rabi_oscillation():
+    # Two orbitals (h = [[e1, -t], [-t, e2]]), one up electron started in
+    # orbital 0: orbital 1 holds it with the textbook Rabi probability
+    # (4 t^2 / W^2) sin^2(W tau / 2), W = sqrt((e1 - e2)^2 + 4 t^2).
+    for e1, e2, t in [(0.0, 0.0, 1.0), (-0.3, 0.5, 0.7)]:
+        h = np.array([[e1, -t], [-t, e2]])
+        eri = np.zeros((2, 2, 2, 2))
+        eri[0, 0, 1, 1] = eri[1, 1, 0, 0] = 0.4     # no second electron: no effect
+        dets = fci.basis(2, 1, 0)
+        H = fci.hamiltonian(h, eri, dets)
+        psi = np.zeros(len(dets), dtype=complex)
+        psi[np.searchsorted(dets, np.uint64(fci.occupation_mask([1, 0])))] = 1.0
+        W = np.sqrt((e1 - e2) ** 2 + 4 * t * t)
+        for tau in (0.0, 0.37, 1.9):
+            g = fci.one_rdm(fci.exact_evolve(H, psi, tau), dets, 2)
+            assert abs(g[1, 1].real - 4 * t * t / W ** 2 * np.sin(W * tau / 2) ** 2) < 1e-13
+            assert abs(np.trace(g).real - 1.0) < 1e-13
+
+
 @pytest.mark.parametrize("L,na,nb", [(4, 2, 1), (5, 2, 2), (3, 3, 1)])
 def test_noninteracting_spectrum_is_sum_of_orbital_energies(L, na, nb):
     I = _random_integrals(L, 3)
