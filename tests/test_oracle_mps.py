@@ -84,6 +84,13 @@ def test_truncation_rule_eps_D_and_clusters():
     assert kept == {(0, 0): 1, (1, 1): 0, (1, -1): 0}
     kept, _, _ = om.truncation_rule(s, D=3, eps=0.0)
     assert kept == {(0, 0): 2, (1, 1): 1, (1, -1): 0}
+    # a degenerate cluster at the very top is kept whole even beyond D (there
+    # is no cluster edge below the cut); spin symmetry makes such clusters
+    # span sectors
+    top = {(1, 1): np.array([1.0]), (1, -1): np.array([1.0 - 1e-13]), (2, 0): np.array([0.3])}
+    kept, disc, tot = om.truncation_rule(top, D=1, eps=0.0)
+    assert kept == {(1, 1): 1, (1, -1): 1, (2, 0): 0}
+    assert abs(disc - 0.09) < 1e-12
 
 
 @pytest.mark.parametrize("n_two,n_one", [(3, 1), (4, 0)])
