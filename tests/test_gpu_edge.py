@@ -160,3 +160,23 @@ def test_argument_errors(td, ctx):
     with pytest.raises(td.TdmpsError) as e:
         td.overlap(ctx, psi, other)
     assert e.value.name == "SECTOR"
+
+
+def test_compress_keeps_a_degenerate_top_cluster_whole(td, ctx):
+    # Two orbitals, one up and one down electron in an equal-weight
+    # superposition of |up, down> and |down, up>: the middle bond has two
+    # one-dimensional sectors, (1, 1) and (1, -1), with equal singular values.
+    # Compressing to D = 1 would cut inside that top cluster, so the rule
+    # keeps both (like the oracle), the state is unchanged, nothing is
+    # discarded.
+    dets = fci.basis(2, 1, 1)
+    v = np.zeros(len(dets), dtype=complex)
+    for occ, amp in (([1, 2], 1 / np.sqrt(2)), ([2, 1], -1 / np.sqrt(2))):
+        v[np.searchsorted(dets, np.uint64(fci.occupation_mask(occ)))] = amp
+    m = om.from_fock(om.sector_to_fock(v, dets, 2), 2)
+    psi = td.mps_import(ctx, m.tensors, m.labels)
+    disc = td.compress(ctx, psi, 1, 0.0)
+    ref, rdisc = om.compress(m, 1, 0.0)
+    assert om.from_arrays(*psi.export()).bond_dims == ref.bond_dims == [1, 2, 1]
+    assert abs(disc) < 1e-12 and abs(rdisc) < 1e-12
+    assert abs(abs(td.overlap(ctx, td.mps_import(ctx, m.tensors, m.labels), psi)) - 1.0) < 1e-12
