@@ -59,12 +59,6 @@ def occupation_mask(occ) -> int:
     return m
 
 
-def mask_counts(mask: int, L: int) -> tuple[int, int]:
-    na = sum((mask >> (2 * i)) & 1 for i in range(L))
-    nb = sum((mask >> (2 * i + 1)) & 1 for i in range(L))
-    return na, nb
-
-
 def _popcount(x: np.ndarray) -> np.ndarray:
     return np.bitwise_count(x).astype(np.int64)
 
