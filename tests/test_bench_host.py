@@ -192,6 +192,7 @@ def test_native_arm_json_assembly_with_a_stand_in_library(monkeypatch, capsys):
             traj = line["vs_fp64_trajectory"]
             assert traj["max_abs_err_dipole"] == 0.0 and line["vs_fp64"] is not None
             assert line["e2e"]["h2d_bytes_per_step"] > 0
+            assert line["e2e"]["pinned_inputs"] is False      # no driver here
         else:
             assert line["vs_fp64_trajectory"] is None
     assert seen == [False]
