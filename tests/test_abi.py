@@ -119,3 +119,20 @@ def test_mpo_bond_dimension_is_quadratic_in_the_smaller_side(built):
         m = min(k, L - k)
         assert dims[k] <= 2 + 4 * L + 8 * m * m + 8 * m, (k, dims[k])
     assert dims[L // 2] <= 600
+
+
+def test_binding_constants_match_the_header():
+    """The Python binding's precision codes, error codes and statistics
+    classes equal the enums of include/tdmps.h."""
+    import re
+    src = open(os.path.join(os.path.dirname(td.__file__), "..", "include", "tdmps.h")).read()
+    enum = {m.group(1): int(m.group(2))
+            for m in re.finditer(r"\bTDMPS_([A-Z0-9_]+)\s*=\s*(-?\d+)", src)}
+    for name, code in td.PRECISION.items():
+        assert enum[name.upper()] == code
+    for code, name in td.ERRORS.items():
+        assert enum["ERR_" + name] == code
+    assert {k for k in enum if k.startswith("ERR_")} == {"ERR_" + n for n in td.ERRORS.values()}
+    for name, k in td.KSTAT.items():
+        assert enum["KSTAT_" + name.upper()] == k
+    assert enum["KSTAT_COUNT"] == len(td.KSTAT)
