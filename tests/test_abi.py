@@ -136,3 +136,44 @@ def test_binding_constants_match_the_header():
     for name, k in td.KSTAT.items():
         assert enum["KSTAT_" + name.upper()] == k
     assert enum["KSTAT_COUNT"] == len(td.KSTAT)
+
+
+def test_binding_signatures_match_the_header_prototypes():
+    """Every entry point of include/tdmps.h has a ctypes signature in the
+    binding with the same number of arguments and the same kind of each
+    (pointer or handle, int, int64, double, complex by value)."""
+    import ctypes
+    import re
+    src = open(os.path.join(os.path.dirname(td.__file__), "..", "include", "tdmps.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    protos = {m.group(2): (m.group(1), m.group(3)) for m in re.finditer(
+        r"^\s*(int|const char\*)\s+(tdmps_\w+)\(([^;]*?)\);", src, re.M | re.S)}
+    assert set(protos) == set(td.header_symbols())
+
+    def kind_c(p):
+        p = " ".join(p.split())
+        if "*" in p or re.search(r"\btdmps_(ctx|mpo|mps)_t\b", p):
+            return "ptr"
+        if re.search(r"\btdmps_complex\b", p):
+            return "complex"
+        if "int64_t" in p:
+            return "int64"
+        if re.search(r"\bdouble\b", p):
+            return "double"
+        if re.search(r"\bint\b", p):
+            return "int"
+        raise AssertionError(p)
+
+    def kind_py(t):
+        if t is ctypes.c_void_p or t is ctypes.c_char_p or hasattr(t, "_type_") and \
+                issubclass(t, ctypes._Pointer):
+            return "ptr"
+        return {ctypes.c_int: "int", ctypes.c_int64: "int64", ctypes.c_double: "double",
+                td.Complex: "complex"}[t]
+
+    for name, (ret, params) in protos.items():
+        assert name in td._SIGS, name
+        restype, argtypes = td._SIGS[name]
+        assert restype is (ctypes.c_int if ret == "int" else ctypes.c_char_p), name
+        plist = [p for p in params.split(",") if p.strip() and p.strip() != "void"]
+        assert [kind_c(p) for p in plist] == [kind_py(t) for t in argtypes], name
