@@ -177,3 +177,23 @@ def test_binding_signatures_match_the_header_prototypes():
         assert restype is (ctypes.c_int if ret == "int" else ctypes.c_char_p), name
         plist = [p for p in params.split(",") if p.strip() and p.strip() != "void"]
         assert [kind_c(p) for p in plist] == [kind_py(t) for t in argtypes], name
+
+
+def test_binding_structs_match_the_header():
+    """tdmps_complex and tdmps_kstat: same fields, order and types as the
+    ctypes mirrors Complex and KStat."""
+    import ctypes
+    import re
+    src = open(os.path.join(os.path.dirname(td.__file__), "..", "include", "tdmps.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    ctype = {"double": ctypes.c_double, "int64_t": ctypes.c_int64, "int": ctypes.c_int}
+    for cname, mirror in (("tdmps_complex", td.Complex), ("tdmps_kstat", td.KStat)):
+        body = re.search(r"typedef struct \{([^}]*)\}\s*%s;" % cname, src).group(1)
+        fields = []
+        for decl in body.split(";"):
+            decl = decl.strip()
+            if not decl:
+                continue
+            typ, names = decl.split(None, 1)
+            fields += [(n.strip(), ctype[typ]) for n in names.split(",")]
+        assert fields == list(mirror._fields_), cname
