@@ -75,16 +75,25 @@ enum {
 /* ---------------------------------------------------------------- context */
 
 /* Create a context on the current CUDA device.  cuda_stream: a cudaStream_t
- * (NULL = the legacy default stream).  precision: TDMPS_FP64, TDMPS_TF32 or
- * TDMPS_TF32X3 (TF32 modes keep environments and intermediates in complex
- * FP32 and run the block contractions on the tcgen05 tensor cores).
- * Errors: INVALID_ARG (bad precision, ctx == NULL), CUDA. */
+ * (NULL = the legacy default stream).  precision: TDMPS_FP64, TDMPS_TF32,
+ * TDMPS_TF32X3 or TDMPS_BF16 (the mixed modes keep environments and
+ * intermediates in complex FP32 and run the block contractions on the
+ * tcgen05 tensor cores).  The context allocates its staging ring (pinned
+ * host and device memory) here.  Errors: INVALID_ARG (bad precision,
+ * ctx == NULL; message in tdmps_create_error), CUDA, OOM. */
 int tdmps_create(tdmps_ctx_t* ctx, void* cuda_stream, int precision);
+/* Waits for the context stream, then releases the context: its staging
+ * ring, caches and helper streams.  MPO and MPS handles made with it can
+ * then only be freed; their memory is freed in stream order on the CUDA
+ * stream the context was created on, which must still exist at that point.
+ * Errors: INVALID_ARG for a NULL ctx. */
 int tdmps_destroy(tdmps_ctx_t ctx);
 /* Message of the last failed call on ctx ("" if none).  Owned by ctx. */
 const char* tdmps_last_error(tdmps_ctx_t ctx);
 /* Message of the last failed tdmps_create on this thread. */
 const char* tdmps_create_error(void);
+/* Precision of the following calls (TDMPS_FP64, _TF32, _TF32X3, _BF16).
+ * Errors: INVALID_ARG for a NULL ctx or an unknown precision. */
 int tdmps_set_precision(tdmps_ctx_t ctx, int precision);
 
 /* Sweep schedule of every variational fit (Sec. 2.2.1, Eq. add_min; the
