@@ -4,7 +4,7 @@ Matrix Product States").
 
 TEST INFRASTRUCTURE ONLY.  Nothing in the product path may import, call, link
 or execute anything in this package; only the test-suite, the smoke check and
-the benchmark's CPU-baseline leg use it.  It shares no code with the CUDA
+the benchmark's CPU-baseline and reference (``--impl reference``) legs use it.  It shares no code with the CUDA
 implementation; the two meet only in the seeded input generators (``synth``).
 
 * ``oracle.fci`` -- full configuration interaction in the occupation-number

@@ -22,6 +22,14 @@ Conventions
   normalised after construction; exp(-i dt N^-1 H) e_0 is evaluated by
   canonical orthogonalisation of N (eigenvalues of N below 1e-12 * max are
   discarded), which equals the plain formula whenever N is regular.
+
+Pins (tests/test_oracle_fci.py, test_oracle_observables.py): the Hubbard-dimer
+spectrum and Lehmann Green's function, the one-electron Rabi oscillation,
+non-interacting spectra and dynamics, an independent Kronecker-product
+Jordan-Wigner build of H, of the density matrices and of the Green's function,
+[H, S^2] = 0, Slater-Condon diagonals, RK4 = fourth-order Taylor, Krylov exact
+on the full space and norm- and energy-conserving below it.  No function here
+is parity unpinned.
 """
 from __future__ import annotations
 

@@ -7,6 +7,11 @@ W_ij = |h_ij| + |(ij|ji)| (i != j, symmetrised); the eigenvector of the
 Laplacian D - W with the second smallest eigenvalue orders them.  Sign of
 that eigenvector: its correlation with the input order is made >= 0; ties
 keep the input order.
+
+Pins (tests/test_ordering.py): the path-graph Laplacian's closed-form second
+eigenvalue and Fiedler vector; chains hidden by a permutation, in the hopping
+or only in the exchange integrals, are recovered; a chain in input order comes
+back unreversed.
 """
 from __future__ import annotations
 
