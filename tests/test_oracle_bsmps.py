@@ -1,0 +1,205 @@
+"""Pins for oracle C (block-sparse MPS with the Hamiltonian as an MPO) against
+oracle A (full CI), oracle B (dense-projection MPS fits) and exact identities.
+
+The MPO is pinned by contracting it to a matrix and comparing with the full-CI
+Hamiltonian on the whole Fock space, with integrals that have no index
+symmetry (so a transposed index or a dropped spin sum shows), and with a
+constant e0.  The fit machinery is pinned by running the same schedules as
+oracle B, which projects the exact target vector, and comparing the states.
+"""
+import numpy as np
+import pytest
+
+import synth
+from oracle import bsmps as ob
+from oracle import fci
+from oracle import mps as om
+
+
+def _fock_masks(L):
+    """All 4^L determinant masks, listed in Fock index order of oracle.mps."""
+    masks = np.arange(4 ** L, dtype=np.uint64)
+    order = np.argsort(om.fock_index(masks, L))
+    return masks[order]
+
+
+@pytest.mark.parametrize("L", [1, 2, 3, 4])
+def test_mpo_matrix_equals_full_ci_on_fock_space(L):
+    rng = np.random.default_rng(100 + L)
+    h = rng.standard_normal((L, L))                 # no symmetry on purpose
+    eri = rng.standard_normal((L, L, L, L))
+    e0 = 0.37
+    M = ob.mpo_to_matrix(ob.hamiltonian_mpo(h, eri, e0))
+    dets = _fock_masks(L)
+    srt = np.argsort(dets)
+    Hs = fci.hamiltonian(h, eri, dets[srt], e0)     # rows/cols in sorted-mask order
+    inv = np.empty_like(srt)
+    inv[srt] = np.arange(len(srt))
+    H = Hs[np.ix_(inv, inv)]
+    assert np.max(np.abs(M - H)) < 1e-12
+
+
+def test_mpo_bond_dimension_and_boundaries():
+    I = synth.make_integrals(8, seed=0)
+    mpo = ob.hamiltonian_mpo(I.h, I.eri)
+    dims = mpo.bond_dims()
+    assert dims[0] == 1 and dims[-1] == 1
+    # complementary-operator count: start and done, 4L single operators,
+    # O(8 min(k, L-k)^2) pairs on the smaller side (k spatial orbitals left)
+    for k, d in enumerate(dims[1:-1], start=1):
+        m = min(k, 8 - k)
+        assert d <= 2 + 4 * 8 + 8 * m * m + 8 * m
+    # bond 1 exactly: start, done, 4 single operators and 6 non-vanishing
+    # pairs of site 0 (two-against-two splits are named on the left in the
+    # left half), and the 28 single operators of sites 1..7 that close the
+    # three-operator left parts
+    assert dims[1] == 2 + 4 + 6 + 28
+    # every channel charge is a difference of two site charges summed
+    for qs in mpo.charges:
+        for q in qs:
+            assert abs(q[0]) <= 2 and abs(q[1]) <= 2
+
+
+def _sector_system(L, n_elec, two_sz, seed):
+    I = synth.make_integrals(L, seed=seed)
+    na, nb = (n_elec + two_sz) // 2, (n_elec - two_sz) // 2
+    return I, om.System.build(I.h, I.eri, na, nb)
+
+
+def test_sandwich_and_overlap_equal_contracted_vectors():
+    L = 6
+    I, sys_ = _sector_system(L, 5, 1, 0)
+    mpo = ob.hamiltonian_mpo(I.h, I.eri)
+    A, qa = synth.random_mps(L, 5, 1, 20, seed=1)
+    B, qb = synth.random_mps(L, 5, 1, 14, seed=2)
+    a, b = ob.from_dense(A, qa), ob.from_dense(B, qb)
+    va, vb = sys_.vec(om.from_arrays(A, qa)), sys_.vec(om.from_arrays(B, qb))
+    ref = np.vdot(vb, sys_.H @ va)
+    assert abs(ob.sandwich(mpo, b, a) - ref) < 1e-11 * abs(ref)
+    ref2 = np.vdot(vb, va)
+    assert abs(ob.overlap(b, a) - ref2) < 1e-12 * np.linalg.norm(va) * np.linalg.norm(vb)
+
+
+def test_overlap_flop_count_equals_transfer_count():
+    A, qa = synth.random_mps(8, 7, 1, 40, seed=3)
+    B, qb = synth.random_mps(8, 7, 1, 25, seed=4)
+    fl = ob.Flops()
+    ob.overlap(ob.from_dense(B, qb), ob.from_dense(A, qa), fl)
+    assert fl.total == om.overlap_flops(om.from_arrays(B, qb), om.from_arrays(A, qa))
+
+
+def test_dense_roundtrip_and_coefficients():
+    A, q = synth.random_mps(6, 6, 0, 16, seed=5)
+    m = ob.from_dense(A, q)
+    t, lab = ob.to_dense(m)
+    v1 = om.to_fock(om.from_arrays(A, q))
+    v2 = om.to_fock(om.from_arrays(t, lab))
+    assert np.max(np.abs(v1 - v2)) < 1e-14
+    rng = np.random.default_rng(0)
+    dets = fci.basis(6, 3, 3)
+    occs = []
+    for msk in rng.choice(dets, 6):
+        occs.append([((int(msk) >> (2 * i)) & 1) + 2 * ((int(msk) >> (2 * i + 1)) & 1)
+                     for i in range(6)])
+    ref = [om.coefficient(om.from_arrays(A, q), o) for o in occs]
+    assert np.max(np.abs(ob.coefficients(m, occs) - ref)) < 1e-13
+
+
+def _fid(u, v):
+    return abs(np.vdot(u, v)) / (np.linalg.norm(u) * np.linalg.norm(v))
+
+
+@pytest.mark.parametrize("sched,D", [((1, 2), 200), ((1, 2), 12), ((0, 2), 30)])
+def test_apply_H_equals_projection_oracle(sched, D):
+    L = 6
+    I, sys_ = _sector_system(L, 5, 1, 1)
+    mpo = ob.hamiltonian_mpo(I.h, I.eri)
+    A, q = synth.random_mps(L, 5, 1, 30, seed=6)
+    alpha = 0.3 - 0.7j
+    ref = om.apply_H(sys_, om.from_arrays(A, q), alpha,
+                     om.Schedule(D, 0.0, sched[0], sched[1]))
+    got = ob.apply_H(mpo, ob.from_dense(A, q), alpha, ob.Schedule(D, 0.0, sched[0], sched[1]))
+    vr = sys_.vec(ref)
+    vg = sys_.vec(om.from_arrays(*ob.to_dense(got)))
+    assert np.linalg.norm(vg - vr) < 1e-10 * np.linalg.norm(vr)
+    assert got.bond_dims() == ref.bond_dims
+    if D >= 200:   # untruncated: the exact alpha H |psi>
+        exact = alpha * (sys_.H @ sys_.vec(om.from_arrays(A, q)))
+        assert np.linalg.norm(vg - exact) < 1e-10 * np.linalg.norm(exact)
+
+
+def test_sum_fit_equals_projection_oracle_truncated():
+    L = 6
+    _, sys_ = _sector_system(L, 6, 0, 2)
+    A, qa = synth.random_mps(L, 6, 0, 20, seed=7)
+    B, qb = synth.random_mps(L, 6, 0, 20, seed=8)
+    terms_o = [(1.0, om.from_arrays(A, qa)), (0.4 - 0.2j, om.from_arrays(B, qb))]
+    terms_b = [(1.0, ob.from_dense(A, qa)), (0.4 - 0.2j, ob.from_dense(B, qb))]
+    for D, eps in ((10, 0.0), (40, 1e-6), (64, 0.0)):
+        ref = om.sum_fit(sys_, terms_o, om.Schedule(D, eps, 1, 1))
+        got = ob.sum_fit(terms_b, ob.Schedule(D, eps, 1, 1))
+        vr = sys_.vec(ref)
+        vg = sys_.vec(om.from_arrays(*ob.to_dense(got)))
+        assert np.linalg.norm(vg - vr) < 1e-10 * np.linalg.norm(vr)
+
+
+def test_rk4_and_krylov_steps_equal_projection_oracle_and_full_ci():
+    L = 6
+    I, sys_ = _sector_system(L, 5, 1, 3)
+    mpo = ob.hamiltonian_mpo(I.h, I.eri)
+    occ = synth.hole_occupation(L, 6, 2)
+    sch_o, sch_b = om.Schedule(200, 0.0, 3, 1), ob.Schedule(200, 0.0, 3, 1)
+    psi_o, psi_b = om.from_determinant(occ), ob.from_determinant(occ)
+    v0 = sys_.vec(psi_o)
+    r = ob.rk4_step(mpo, psi_b, 0.05, sch_b)
+    vr = sys_.vec(om.from_arrays(*ob.to_dense(r)))
+    assert np.linalg.norm(vr - fci.rk4_step(sys_.H, v0, 0.05)) < 1e-10
+    assert np.linalg.norm(vr - sys_.vec(om.rk4_step(sys_, psi_o, 0.05, sch_o))) < 1e-10
+    k, c, N, Hk = ob.krylov_step(mpo, psi_b, 0.1, 4, sch_b)
+    vk = sys_.vec(om.from_arrays(*ob.to_dense(k)))
+    ko, co, No, Hko = om.krylov_step(sys_, psi_o, 0.1, 4, sch_o)
+    assert np.linalg.norm(vk - fci.krylov_step(sys_.H, v0, 0.1, 4)) < 1e-10
+    assert np.linalg.norm(vk - sys_.vec(ko)) < 1e-10
+    assert np.max(np.abs(N - No)) < 1e-11 and np.max(np.abs(Hk - Hko)) < 1e-11
+    # the plain (non-orthogonal) basis of Eq. kry_non
+    kn, _, _, _ = ob.krylov_step(mpo, psi_b, 0.1, 4, sch_b, orthogonal=False)
+    kno, _, _, _ = om.krylov_step(sys_, psi_o, 0.1, 4, sch_o, orthogonal=False)
+    assert np.linalg.norm(sys_.vec(om.from_arrays(*ob.to_dense(kn))) - sys_.vec(kno)) < 1e-10
+
+
+def test_truncated_krylov_step_equals_projection_oracle():
+    L = 6
+    I, sys_ = _sector_system(L, 5, 1, 4)
+    mpo = ob.hamiltonian_mpo(I.h, I.eri)
+    A, q = synth.random_mps(L, 5, 1, 24, seed=9)
+    sch_o, sch_b = om.Schedule(16, 1e-10, 1, 1), ob.Schedule(16, 1e-10, 1, 1)
+    ko = om.krylov_step(sys_, om.from_arrays(A, q), 0.05, 3, sch_o)[0]
+    kb = ob.krylov_step(mpo, ob.from_dense(A, q), 0.05, 3, sch_b)[0]
+    vo, vb = sys_.vec(ko), sys_.vec(om.from_arrays(*ob.to_dense(kb)))
+    assert np.linalg.norm(vb - vo) < 1e-9 * np.linalg.norm(vo)
+
+
+def test_one_rdm_equals_full_ci():
+    L = 6
+    I, sys_ = _sector_system(L, 5, 1, 5)
+    A, q = synth.random_mps(L, 5, 1, 20, seed=10)
+    g = ob.one_rdm(ob.from_dense(A, q))
+    ref = fci.one_rdm(sys_.vec(om.from_arrays(A, q)), sys_.dets, L)
+    assert np.max(np.abs(g - ref)) < 1e-12 * np.max(np.abs(ref))
+    # a determinant has its occupations on the diagonal and nothing else
+    occ = [3, 1, 0, 2, 3, 0]
+    gd = ob.one_rdm(ob.from_determinant(occ))
+    assert np.max(np.abs(gd - np.diag([2, 1, 0, 1, 2, 0]))) < 1e-15
+
+
+def test_energy_of_determinant_is_slater_condon():
+    L = 8
+    I = synth.make_integrals(L, seed=11)
+    mpo = ob.hamiltonian_mpo(I.h, I.eri, 0.25)
+    occ = synth.hole_occupation(L, 8, 3)
+    d = ob.from_determinant(occ)
+    e = ob.sandwich(mpo, d, d)
+    dets = fci.basis(L, 4, 3)
+    H = fci.hamiltonian(I.h, I.eri, dets, 0.25)
+    col = np.searchsorted(dets, np.uint64(fci.occupation_mask(occ)))
+    assert abs(e - H[col, col]) < 1e-12
