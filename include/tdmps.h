@@ -231,8 +231,10 @@ int tdmps_overlap(tdmps_ctx_t ctx, tdmps_mps_t bra, tdmps_mps_t ket, tdmps_compl
  * before any stream capture.  Task lists go through the staging ring that
  * tdmps_create allocated.  All calls on a device share the array and each
  * overwrites it, so calls that overlap on the GPU (several contexts or
- * streams at once) race.  A pair whose environments do not fit returns
- * TDMPS_ERR_INVALID_ARG before any work is enqueued on the GPU. */
+ * streams at once) race.  A pair whose environments do not fit, or whose
+ * task list for one launch exceeds a segment of the staging ring, returns
+ * TDMPS_ERR_INVALID_ARG before any work is enqueued on the GPU; so does a
+ * context whose device is not the current device. */
 #define TDMPS_NOALLOC_SCRATCH_BYTES (16u << 20)
 int tdmps_overlap_noalloc(tdmps_ctx_t ctx, tdmps_mps_t bra, tdmps_mps_t ket, tdmps_complex* out);
 

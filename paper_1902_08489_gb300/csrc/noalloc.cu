@@ -29,12 +29,15 @@ static __device__ __align__(256) double2 g_overlap_scratch[kScratchElems];
 std::mutex g_mu;
 double2* g_scratch_ptr[128] = {nullptr};
 
-// Device address of the scratch array for the current device.  The first
-// call on a device resolves it with cudaGetSymbolAddress (the host-side name
-// of a __device__ array is not a device address).
-double2* scratch_for_current_device() {
+// Device address of the scratch array on the context's device, which must be
+// the current device.  The first call on a device resolves it with
+// cudaGetSymbolAddress (the host-side name of a __device__ array is not a
+// device address).
+double2* scratch_for_device(const Context& c) {
   int dev = 0;
   TD_CHECK_CUDA(cudaGetDevice(&dev));
+  if (dev != c.device)
+    throw Error(TDMPS_ERR_INVALID_ARG, "the context's device is not the current device");
   if (dev < 0 || dev >= 128) throw Error(TDMPS_ERR_INVALID_ARG, "device index out of range");
   std::lock_guard<std::mutex> lk(g_mu);
   if (!g_scratch_ptr[dev]) {
@@ -47,13 +50,9 @@ double2* scratch_for_current_device() {
   return g_scratch_ptr[dev];
 }
 
-// copy a task list through the pre-allocated ring; never allocates (a list
-// larger than one ring segment would need a dedicated buffer: rejected)
-const void* stage_ring(Context& c, const void* src, size_t bytes) {
-  size_t need = (bytes + 255) & ~(size_t)255;
-  if (need > c.seg_cap) throw Error(TDMPS_ERR_INVALID_ARG, "task list exceeds the staging ring");
-  return c.stage(src, bytes);
-}
+// bytes a task list takes in the pre-allocated staging ring; a list larger
+// than one ring segment would need a dedicated buffer and is rejected
+size_t ring_bytes(size_t bytes) { return (bytes + 255) & ~(size_t)255; }
 
 struct Blocks {   // per-sector dense blocks of one environment E[b][b']
   std::vector<size_t> off;   // element offset per bra sector (SIZE_MAX if absent)
@@ -65,9 +64,8 @@ struct Blocks {   // per-sector dense blocks of one environment E[b][b']
 cplx overlap_noalloc(Context& c, const MPSd& bra, const MPSd& ket) {
   if (bra.L != ket.L) throw Error(TDMPS_ERR_INVALID_ARG, "MPS lengths differ");
   if (bra.tot != ket.tot) throw Error(TDMPS_ERR_SECTOR, "MPS quantum numbers (N, 2Sz) differ");
-  double2* base = scratch_for_current_device();
+  double2* base = scratch_for_device(c);
   const int L = bra.L;
-  // ping-pong environments and one intermediate region; sizes checked per site
   auto env_layout = [&](int k, Blocks& b) {
     b.off.assign(bra.bonds[k].nsec(), SIZE_MAX);
     b.size = 0;
@@ -78,6 +76,11 @@ cplx overlap_noalloc(Context& c, const MPSd& bra, const MPSd& ket) {
       b.size += (size_t)bra.bonds[k].d[s] * ket.bonds[k].d[sk];
     }
   };
+  // Plan every launch on the host first: the scratch layout of each site and
+  // the packed task lists.  A pair that does not fit is rejected here, before
+  // anything is enqueued on the GPU.
+  struct Launch { std::vector<char> pack; size_t o_terms, o_tiles; int ntask, ntile; };
+  std::vector<Launch> plan;
   Blocks cur, nxt;
   env_layout(0, cur);
   if (cur.size != 1) throw Error(TDMPS_ERR_SECTOR, "left boundary bond must be one-dimensional");
@@ -85,9 +88,8 @@ cplx overlap_noalloc(Context& c, const MPSd& bra, const MPSd& ket) {
   // the intermediate sits between them
   bool cur_front = true;
   double2* Ecur = base;
+  double2* Efirst = base;
   const double2 one = make_double2(1.0, 0.0);
-  TD_CHECK_CUDA(cudaMemcpyAsync(Ecur, stage_ring(c, &one, sizeof(one)), sizeof(double2),
-                                cudaMemcpyDeviceToDevice, c.st));
   for (int i = 0; i < L; ++i) {
     const SiteT& A = ket.sites[i];
     const SiteT& B = bra.sites[i];
@@ -166,30 +168,39 @@ cplx overlap_noalloc(Context& c, const MPSd& bra, const MPSd& ket) {
         for (int q = 0; q < g.tiles_m * tn; ++q) tile_task.push_back(id);
       }
       if (tile_task.empty()) continue;
-      // one staged copy per launch (the ring reuses a segment once the
-      // launches that read it are enqueued)
-      const size_t o_terms = (tk.size() * sizeof(GemmTask) + 255) & ~(size_t)255;
-      const size_t o_tiles = o_terms + ((terms.size() * sizeof(GemmTerm) + 255) & ~(size_t)255);
-      std::vector<char>& pk = c.pack;
-      pk.resize(o_tiles + tile_task.size() * sizeof(int));
-      std::memcpy(pk.data(), tk.data(), tk.size() * sizeof(GemmTask));
-      std::memcpy(pk.data() + o_terms, terms.data(), terms.size() * sizeof(GemmTerm));
-      std::memcpy(pk.data() + o_tiles, tile_task.data(), tile_task.size() * sizeof(int));
-      const char* base = (const char*)stage_ring(c, pk.data(), pk.size());
-      const GemmTask* dt = (const GemmTask*)base;
-      const GemmTerm* dm = (const GemmTerm*)(base + o_terms);
-      const int* dtt = (const int*)(base + o_tiles);
-      launch_gemm(dt, (int)tk.size(), dm, dtt, (int)tile_task.size(), c.st);
-      TD_CHECK_CUDA(cudaGetLastError());
+      Launch ln;
+      ln.o_terms = ring_bytes(tk.size() * sizeof(GemmTask));
+      ln.o_tiles = ln.o_terms + ring_bytes(terms.size() * sizeof(GemmTerm));
+      ln.pack.resize(ln.o_tiles + tile_task.size() * sizeof(int));
+      std::memcpy(ln.pack.data(), tk.data(), tk.size() * sizeof(GemmTask));
+      std::memcpy(ln.pack.data() + ln.o_terms, terms.data(), terms.size() * sizeof(GemmTerm));
+      std::memcpy(ln.pack.data() + ln.o_tiles, tile_task.data(), tile_task.size() * sizeof(int));
+      // a list larger than one ring segment would need a dedicated buffer
+      if (ring_bytes(ln.pack.size()) > c.seg_cap)
+        throw Error(TDMPS_ERR_INVALID_ARG, "task list exceeds the staging ring");
+      ln.ntask = (int)tk.size();
+      ln.ntile = (int)tile_task.size();
+      plan.push_back(std::move(ln));
     }
     Ecur = Enext;
     cur_front = !cur_front;
     cur = nxt;
   }
+  // Enqueue: the unit left boundary, then every launch, each with one staged
+  // copy (the ring reuses a segment once the launches that read it are
+  // enqueued).
+  TD_CHECK_CUDA(cudaMemcpyAsync(Efirst, c.stage(&one, sizeof(one)), sizeof(double2),
+                                cudaMemcpyDeviceToDevice, c.st));
+  for (const Launch& ln : plan) {
+    const char* p = (const char*)c.stage(ln.pack.data(), ln.pack.size());
+    launch_gemm((const GemmTask*)p, ln.ntask, (const GemmTerm*)(p + ln.o_terms),
+                (const int*)(p + ln.o_tiles), ln.ntile, c.st);
+    TD_CHECK_CUDA(cudaGetLastError());
+  }
   double2 h = make_double2(0.0, 0.0);
   if (cur.size == 1)
     TD_CHECK_CUDA(cudaMemcpyAsync(&h, Ecur, sizeof(double2), cudaMemcpyDeviceToHost, c.st));
-  TD_CHECK_CUDA(cudaStreamSynchronize(c.st));
+  c.sync();
   return cplx(h.x, h.y);
 }
 
