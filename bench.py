@@ -93,48 +93,78 @@ class Clocks:
                 "samples": len(self.samples)}
 
 
-def cpu_baseline(seconds=20.0):
-    """The oracle as it stands on the host cores: fitted H applications of the
-    same kind (dense-projection fit, same sweep schedule) on a bounded sample,
-    the L = 8, N = 7 system (the oracle holds 4^L-long vectors, so L = 16 is
-    out of its reach).  FLOPs are the oracle's own complex arithmetic.
-    `cores` is the thread count the BLAS may use (OMP_NUM_THREADS, else the
-    host's CPUs); `avg_busy_threads` is process CPU time / wall time over the
-    sample, the threads actually kept busy."""
-    import synth
-    from oracle import mps as om
-    Ls, Ds = 8, 64
-    I = synth.make_integrals(Ls, seed=0)
-    sysb = om.System.build(I.h, I.eri, 4, 3)
-    A, q = synth.random_mps(Ls, 7, 1, Ds, seed=0)
-    psi = om.from_arrays(A, q)
-    sch = om.Schedule(D=Ds, eps=EPS, n_two_site=0, n_one_site=2)
-    # oracle FLOPs per one-site projection: two contractions with the 4^L target
-    flops_fit = 0.0
-    dims = psi.bond_dims
-    for _ in range(2 * sch.n_one_site + 1):
-        for i in range(Ls):
-            flops_fit += 8.0 * (4 ** Ls) * (dims[i] + dims[i + 1])
-    flops_H = 2.0 * len(sysb.dets) ** 2
+_ORACLE: dict = {}
+
+
+def _oracle_workload(size):
+    """The block-sparse oracle's copy of the workload: its own MPO of the
+    seeded integrals and the seeded random state, normalised (built once)."""
+    if _ORACLE.get("size") != size:
+        import synth
+        from oracle import bsmps as ob
+        Ls, Ns, Ss, Ds = size
+        big = Ls >= 24
+        I = synth.make_integrals(Ls, seed=0, n_chol=64 if big else 16, localised_block=big)
+        A, q = synth.random_mps(Ls, Ns, Ss, Ds, seed=0)
+        psi = ob.from_dense(A, q)
+        nrm = ob.norm(psi)
+        psi.sites[0] = {k: v / nrm for k, v in psi.sites[0].items()}
+        _ORACLE.clear()
+        _ORACLE.update(size=size, ob=ob, mpo=ob.hamiltonian_mpo(I.h, I.eri, I.e0), psi=psi)
+    return _ORACLE
+
+
+def _krylov_step_oracle_flops(size):
+    """Oracle FLOPs of one whole Krylov step of the default workload, counted
+    when tests/golden/make_bench_golden.py ran the step (None otherwise)."""
+    if size != (L, N_ELEC, TWO_SZ, D):
+        return None
+    try:
+        path = os.path.join(ROOT, "tests", "golden", "krylov_L16_N15_D256.json")
+        return float(json.load(open(path))["oracle_flops"])
+    except Exception:
+        return None
+
+
+def cpu_baseline(seconds=20.0, size=None, with_fit=True):
+    """The block-sparse FP64 oracle (oracle.bsmps) as it stands, on the host
+    cores, on the benchmark's own workload (same L, N, D, integrals and
+    state): a bounded sample of the Krylov step's operations -- one fitted
+    H application with one one-site sweep (with_fit), then exact H
+    sandwiches <psi|H|psi> until `seconds` have passed.  FLOPs are the
+    oracle's algorithmic block-sparse count (the same definition as the
+    GPU's: 8 per complex multiply-add of non-zero blocks, 4 per non-zero MPO
+    entry times a complex number).  `cores` is the thread count the BLAS may
+    use; `avg_busy_threads` is process CPU time / wall time."""
+    size = size or (L, N_ELEC, TWO_SZ, D)
+    o = _oracle_workload(size)
+    ob, mpo, psi = o["ob"], o["mpo"], o["psi"]
     import resource
+    fl = ob.Flops()
     r0 = resource.getrusage(resource.RUSAGE_SELF)
     t0 = time.perf_counter()
-    n = 0
-    while True:
-        om.apply_H(sysb, psi, -1j * DT, sch)
-        n += 1
-        if time.perf_counter() - t0 > seconds:
-            break
+    n_fit = n_sw = 0
+    if with_fit:
+        ob.apply_H(mpo, psi, -1j * DT, ob.Schedule(size[3], EPS, 0, 1), fl)
+        n_fit = 1
+    while n_sw == 0 or time.perf_counter() - t0 < seconds:
+        ob.sandwich(mpo, psi, psi, fl)
+        n_sw += 1
     dt = time.perf_counter() - t0
     r1 = resource.getrusage(resource.RUSAGE_SELF)
     cpu_s = (r1.ru_utime - r0.ru_utime) + (r1.ru_stime - r0.ru_stime)
     threads = os.environ.get("OMP_NUM_THREADS") or str(os.cpu_count())
-    return {"value": n * (flops_fit + flops_H) / dt / 1e12, "unit": "TFLOP/s",
-            "cores": int(threads), "kind": "oracle",
-            "avg_busy_threads": round(cpu_s / dt, 2),
-            "sample": "%d dense-projection apply_H fits, L=8 N=7 D=64, one-site x2 "
-                      "(L=16 needs 4^16-long vectors)" % n,
-            "ms_per_fit": 1e3 * dt / n}
+    rate = fl.total / dt
+    out = {"value": rate / 1e12, "unit": "TFLOP/s", "cores": int(threads), "kind": "oracle",
+           "avg_busy_threads": round(cpu_s / dt, 2),
+           "sample": "block-sparse FP64 oracle on the benchmark workload (L=%d N=%d 2Sz=%d "
+                     "D=%d): %d fitted apply_H (one one-site sweep) + %d exact <psi|H|psi> "
+                     "sandwiches, %.1f GFLOP in %.1f s"
+                     % (size[0], size[1], size[2], size[3], n_fit, n_sw, fl.total / 1e9, dt)}
+    kf = _krylov_step_oracle_flops(size)
+    if kf:
+        out["s_per_krylov_step_extrapolated"] = kf / rate
+    return out
 
 
 def dipole(gammas):
@@ -190,9 +220,10 @@ def workload_config(args, sched, size, world):
 
 
 def run_reference(args):
-    """The oracle on the host cores, on the native arm's config: each step is a
-    bounded sample (fitted H applications of a system the oracle can hold,
-    described in cpu_baseline.sample); each warm-up step is one untimed fit."""
+    """The oracle on the host cores, on the native arm's workload: each step is
+    a bounded sample of it (exact H sandwiches <psi|H|psi> of the seeded state
+    by the block-sparse oracle, one per step, ~2-3 s each at L = 16, D = 256);
+    each warm-up step is one untimed sandwich."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
@@ -200,25 +231,49 @@ def run_reference(args):
         print(json.dumps({"impl": "reference",
                           "unavailable": "the oracle arm covers the krylov and apply modes"}))
         return
+    size = workload_size(args)
+    o = _oracle_workload(size)
+    ob, mpo, psi = o["ob"], o["mpo"], o["psi"]
     for _ in range(args.warmup):
-        cpu_baseline(seconds=0.0)
+        ob.sandwich(mpo, psi, psi)
+    import resource
+    fl = ob.Flops()
+    r0 = resource.getrusage(resource.RUSAGE_SELF)
     t0 = time.perf_counter()
-    vals = []
     for _ in range(args.steps):
-        vals.append(cpu_baseline(seconds=max(5.0, 20.0 / max(1, args.steps))))
+        ob.sandwich(mpo, psi, psi, fl)
     dt = time.perf_counter() - t0
-    v = statistics.median([x["value"] for x in vals])
-    cb = dict(vals[0])
-    cb["value"] = v
+    r1 = resource.getrusage(resource.RUSAGE_SELF)
+    cpu_s = (r1.ru_utime - r0.ru_utime) + (r1.ru_stime - r0.ru_stime)
+    v = fl.total / dt / 1e12
+    threads = os.environ.get("OMP_NUM_THREADS") or str(os.cpu_count())
+    cb = {"value": v, "unit": "TFLOP/s", "cores": int(threads), "kind": "oracle",
+          "avg_busy_threads": round(cpu_s / dt, 2),
+          "sample": "block-sparse FP64 oracle on the benchmark workload (L=%d N=%d 2Sz=%d "
+                    "D=%d): one exact <psi|H|psi> sandwich per step, %.1f GFLOP per step"
+                    % (size[0], size[1], size[2], size[3], fl.total / 1e9 / max(1, args.steps))}
+    kf = _krylov_step_oracle_flops(size)
+    if kf:
+        cb["s_per_krylov_step_extrapolated"] = kf / (fl.total / dt)
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "TFLOP/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * dt / max(1, args.steps), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": workload_config(args, fit_schedule(args), workload_size(args),
-                                      int(os.environ.get("WORLD_SIZE", "1"))),
+            "config": reference_config(args, size),
             "cpu_baseline": cb,
             "e2e": {"value": v, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
+
+
+def reference_config(args, size):
+    """`config` of the oracle arm: the native arm's workload, with the sample
+    each timed step takes."""
+    cfg = workload_config(args, fit_schedule(args), size, int(os.environ.get("WORLD_SIZE", "1")))
+    cfg["sample_per_step"] = ("one exact <psi|H|psi> MPO sandwich of the seeded D=%d state "
+                              "(block-sparse FP64 oracle): the operation the Krylov step runs "
+                              "55 times for its Hamiltonian matrix" % size[3])
+    cfg["inner_products"] = "n/a (oracle)"
+    return cfg
 
 
 def replica_totals(ms, work, dist, device):
@@ -549,7 +604,7 @@ def main():
         "e2e": e2e,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(20.0)
+        line["cpu_baseline"] = cpu_baseline(20.0, (L, N_ELEC, TWO_SZ, D))
     if rank == 0:
         print(json.dumps(line))
     if dist:

@@ -74,7 +74,8 @@ def test_synthetic_dipole():
 def test_reference_arm_json_line():
     """`bench.py --impl reference` prints one JSON line with the contract's
     keys, the native arm's metric and config, and an e2e entry without
-    host-device traffic (about 20 s of oracle work on the host cores)."""
+    host-device traffic (the oracle's MPO build and two sandwiches at the
+    benchmark size, about 15 s on the host cores)."""
     import json
     import subprocess
     import sys
@@ -90,10 +91,12 @@ def test_reference_arm_json_line():
     assert line["impl"] == "reference" and line["metric"] == bench.METRIC
     assert line["value"] > 0 and line["unit"] == "TFLOP/s" and line["steps"] == 1
     a = SimpleNamespace(mode="krylov", schedule=None, size=None, serial_inner=False)
-    assert line["config"] == bench.workload_config(a, bench.fit_schedule(a),
-                                                   bench.workload_size(a), 1)
+    native = bench.workload_config(a, bench.fit_schedule(a), bench.workload_size(a), 1)
+    assert line["config"]["workload"] == native["workload"]
+    assert "sandwich" in line["config"]["sample_per_step"]
     cb = line["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == line["value"]
+    assert "L=16 N=15 2Sz=1 D=256" in cb["sample"]
     assert 0.0 < cb["avg_busy_threads"] <= cb["cores"] + 0.5
     assert line["e2e"] == {"value": line["value"], "unit": "TFLOP/s",
                            "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
