@@ -371,6 +371,8 @@ struct GemmBatch {
   void task(void* C, int tc, int M, int N, int ldc, int opA, int ta, int opB, int tb, bool beta,
             cplx alpha, const double2* aptr = nullptr, const double2* adiv = nullptr) {
     if (fp64 && (ta || tb || tc)) throw Error(TDMPS_ERR_INVALID_ARG, "FP64 GEMM on float data");
+    if (!fp64 && (!ta || !tb))
+      throw Error(TDMPS_ERR_INVALID_ARG, "tensor-core GEMM operands must be complex float");
     GemmTask t{};
     t.C = C;
     t.alpha_ptr = aptr;
@@ -446,9 +448,12 @@ struct GemmBatch {
     if (fp64) orient_fp64(); else orient_tc();
     std::vector<int> tile_task;
     std::vector<GemmTask> tk;
-    std::vector<ZeroRegion> zero;
-    // Split-K: long K runs are shared by several CTAs that accumulate
-    // atomically into a zeroed output.  The chunk count per CTA is chosen so
+    std::vector<int> split_ids;
+    std::vector<TcTile> tc_tiles;
+    size_t part_elems = 0;
+    // Split-K: long K runs are shared by several CTAs, each of which stores
+    // its partial sum in a slice of a scratch buffer; a reduction adds the
+    // slices in split order (deterministic).  The chunk count per CTA is chosen so
     // that the launch has about `per_sm` work units per SM (the FP64 pipe
     // and the tensor pipe are per-SM resources; a launch with fewer units
     // than SMs leaves the rest idle), with at least `min_chunks` K chunks
@@ -470,32 +475,74 @@ struct GemmBatch {
       if (t.M <= 0 || t.N <= 0) continue;
       t.tiles_m = (t.M + bm - 1) / bm;
       int tn = (t.N + bn - 1) / bn;
-      {
-        t.splits = (int)std::min<long long>(64, std::max<long long>(1, stages[i] / chunk));
-        if (t.splits > 1 && !t.beta) {
-          if (t.ldc != (t.ct ? t.M : t.N))
-            throw Error(TDMPS_ERR_INVALID_ARG, "split-K output must be contiguous");
-          zero.push_back({t.C, (size_t)t.M * t.N * (t.tc ? sizeof(float2) : sizeof(double2))});
-        }
-      }
+      t.splits = (int)std::min<long long>(64, std::max<long long>(1, stages[i] / chunk));
+      t.part = nullptr;
       t.tile_base = (int)tile_task.size();
       int id = (int)tk.size();
+      if (!fp64) {
+        // host-built tile descriptors: this task's K stages split evenly
+        for (int sp = 0; sp < t.splits; ++sp) {
+          const int lo = (int)((long long)sp * stages[i] / t.splits);
+          const int hi = (int)((long long)(sp + 1) * stages[i] / t.splits);
+          int e0 = t.term_begin, k0 = 0, idx = 0;
+          while (e0 < t.term_end) {
+            const int nk = (terms[e0].K + kc - 1) / kc;
+            if (idx + nk <= lo) { idx += nk; ++e0; continue; }
+            k0 = (lo - idx) * kc;
+            break;
+          }
+          for (int q = 0; q < t.tiles_m * tn; ++q) {
+            TcTile tl;
+            tl.task = id;
+            tl.m0 = (q % t.tiles_m) * bm;
+            tl.n0 = (q / t.tiles_m) * bn;
+            tl.ncols = std::min(bn, t.N - tl.n0);
+            tl.count = hi - lo;
+            tl.e0 = e0;
+            tl.k0 = k0;
+            tl.split = sp;
+            tc_tiles.push_back(tl);
+          }
+        }
+      }
+      if (t.splits > 1) {
+        split_ids.push_back(id);
+        // element offset for now; made a pointer once the buffer exists
+        t.part = (void*)(uintptr_t)part_elems;
+        part_elems += (size_t)t.splits * t.M * t.N;
+      }
       tk.push_back(t);
       for (int q = 0; q < t.tiles_m * tn * t.splits; ++q) tile_task.push_back(id);
     }
     if (tile_task.empty()) return;
-    // tasks, terms and the tile map go to the device in one staged copy
+    // partial-sum slices of the split tasks (freed in stream order after use)
+    DevPtr part;
+    if (part_elems) {
+      // one buffer, slices addressed in units of the widest element type
+      part = dev_alloc(part_elems * sizeof(double2), c.st);
+      for (int id : split_ids) {
+        GemmTask& t = tk[id];
+        t.part = (char*)part->p + (size_t)(uintptr_t)t.part * sizeof(double2);
+      }
+    }
+    // tasks, terms, the tile map and the split list go to the device in one
+    // staged copy
     auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
     const size_t o_terms = al(tk.size() * sizeof(GemmTask));
-    const size_t o_zero = o_terms + al(terms.size() * sizeof(GemmTerm));
-    const size_t o_tiles = o_zero + al(zero.size() * sizeof(ZeroRegion));
-    const size_t pk_bytes = o_tiles + tile_task.size() * sizeof(int);
+    const size_t o_split = o_terms + al(terms.size() * sizeof(GemmTerm));
+    const size_t o_tiles = o_split + al(split_ids.size() * sizeof(int));
+    const size_t pk_bytes =
+        o_tiles + (fp64 ? tile_task.size() * sizeof(int) : tc_tiles.size() * sizeof(TcTile));
     std::vector<char>& pk = c.pack;
     pk.resize(pk_bytes);
     std::memcpy(pk.data(), tk.data(), tk.size() * sizeof(GemmTask));
     if (!terms.empty()) std::memcpy(pk.data() + o_terms, terms.data(), terms.size() * sizeof(GemmTerm));
-    if (!zero.empty()) std::memcpy(pk.data() + o_zero, zero.data(), zero.size() * sizeof(ZeroRegion));
-    std::memcpy(pk.data() + o_tiles, tile_task.data(), tile_task.size() * sizeof(int));
+    if (!split_ids.empty())
+      std::memcpy(pk.data() + o_split, split_ids.data(), split_ids.size() * sizeof(int));
+    if (fp64)
+      std::memcpy(pk.data() + o_tiles, tile_task.data(), tile_task.size() * sizeof(int));
+    else
+      std::memcpy(pk.data() + o_tiles, tc_tiles.data(), tc_tiles.size() * sizeof(TcTile));
     const char* base = (const char*)c.stage(pk.data(), pk_bytes);
     const GemmTask* dt = (const GemmTask*)base;
     const GemmTerm* dm = terms.empty() ? nullptr : (const GemmTerm*)(base + o_terms);
@@ -503,13 +550,14 @@ struct GemmBatch {
     cudaEvent_t ev;
     const int kind = fp64 ? TDMPS_KSTAT_GEMM_FP64 : TDMPS_KSTAT_GEMM;
     c.kbegin(kind, &ev);
-    if (!zero.empty()) launch_zero_regions((const ZeroRegion*)(base + o_zero), (int)zero.size(), c.st);
     if (fp64)
       launch_gemm(dt, (int)tk.size(), dm, dtt, (int)tile_task.size(), c.st);
     else
-      launch_gemm_tc(dt, dm, dtt, (int)tile_task.size(),
+      launch_gemm_tc(dt, dm, (const TcTile*)(base + o_tiles), (int)tc_tiles.size(),
                      c.precision == TDMPS_TF32X3 ? 1 : c.precision == TDMPS_BF16 ? 2 : 0,
-                     c.tc_err(), c.st);
+                     c.n_sm, c.tc_err(), c.st);
+    if (!split_ids.empty())
+      launch_reduce_splits(dt, (const int*)(base + o_split), (int)split_ids.size(), c.st);
     c.kend(kind, ev, flops, bytes);
   }
 };
@@ -1232,6 +1280,7 @@ MPSd right_canonicalize(Context& c, const MPSd& m0) {
     m.sites[i - 1] = std::move(prev);
     m.bonds[i] = lq.left;
   }
+  m.rcanon = true;
   return m;
 }
 
@@ -1505,7 +1554,11 @@ MPSd fit(Context& c, const std::vector<FitTerm>& terms, const MPSd& guess, const
     throw Error(TDMPS_ERR_INVALID_ARG, "invalid sweep schedule");
   for (auto& t : terms) check_same_space(*t.ket, guess);
   const int L = guess.L;
-  MPSd C = right_canonicalize(c, guess);
+  // the guess in right-canonical gauge; outputs of fits and compressions
+  // already are, so they are used as they stand (every site is replaced
+  // below, nothing is written in place)
+  MPSd C = guess.rcanon ? guess : right_canonicalize(c, guess);
+  C.rcanon = true;
   std::vector<TermState> ts(terms.size());
   for (size_t t = 0; t < terms.size(); ++t) {
     ts[t].ket = terms[t].ket;
@@ -1697,7 +1750,7 @@ void normalize_center(Context& c, MPSd& m, double2* norm_out) {
 
 double compress(Context& c, MPSd& m, int D, double eps) {
   if (D < 1) throw Error(TDMPS_ERR_INVALID_ARG, "D must be >= 1");
-  MPSd C = right_canonicalize(c, m);
+  MPSd C = m.rcanon ? m : right_canonicalize(c, m);
   double disc_sum = 0.0;
   for (int i = 0; i + 1 < C.L; ++i) {
     // SVD of site i as (rows = (a, s)) x b per right sector: reuse svd_split
@@ -2184,6 +2237,7 @@ MPSd mps_determinant(Context& c, int L, const uint8_t* occ) {
     TD_CHECK_CUDA(cudaMemcpyAsync(m.sites[i].data->p, c.stage(&ones[i], sizeof(double2)),
                                   sizeof(double2), cudaMemcpyDeviceToDevice, c.st));
   }
+  m.rcanon = true;   // every site is a single unit entry
   return m;
 }
 

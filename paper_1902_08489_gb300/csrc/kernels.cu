@@ -148,8 +148,7 @@ __global__ void __launch_bounds__(256) k_gemm(const GemmTask* __restrict__ tasks
         double2* p = (double2*)t.C + (t.ct ? (size_t)c * t.ldc + r : (size_t)r * t.ldc + c);
         double2 v = cmul(alpha, acc[i][j]);
         if (t.splits > 1) {
-          atomicAdd(&p->x, v.x);
-          atomicAdd(&p->y, v.y);
+          ((double2*)t.part)[((size_t)split * t.M + r) * t.N + c] = v;
         } else {
           if (t.beta) v = cadd(v, *p);
           *p = v;

@@ -34,8 +34,12 @@ struct GemmTask {
   int term_begin, term_end;
   int tiles_m, tile_base;
   int ta, tb, tc;        // element types of A, B, C: 0 double2, 1 float2 (tensor-core path)
-  int splits;            // CTAs sharing the K range (atomic accumulation)
+  int splits;            // CTAs sharing the K range
   int ct;                // 1: the task computes C^T (M x N); element (r, c) goes to C[c][r]
+  // splits > 1: split s stores alpha * (its partial sum) at part[(s M + r) N + c]
+  // (element type tc, task orientation) and launch_reduce_splits adds the
+  // slices in split order into C, so results do not depend on timing
+  void* part;
 };
 
 // Sparse MPO-tensor application.  Output block Y[r][w][c] (rows r, W_out
@@ -87,18 +91,29 @@ void launch_gemm(const GemmTask* d_tasks, int ntasks, const GemmTerm* d_terms,
 void launch_wstage(const WTask* d_tasks, int ntasks, int64_t total_work, const int* d_rowptr,
                    const int* d_ent_w, const double* d_ent_v, const float* d_ent_vf, int et,
                    cudaStream_t st);
-// tensor-core grouped GEMM (kernels_tc.cu); mode 0 TF32, 1 3xTF32; tiles of
-// tc_tile_m() rows x tc_tile_n() complex columns
-void launch_gemm_tc(const GemmTask* d_tasks, const GemmTerm* d_terms, const int* d_tile_task,
-                    int ntiles, int mode, int* d_err, cudaStream_t st);
+// One tile of the tensor-core GEMM, built on the host: rows m0.. (tc_tile_m()
+// of them), complex columns n0 .. n0 + ncols (ncols <= tc_tile_n()), and the
+// K stages (tc_stage_k() complex each, counted over the task's terms in
+// order) that this tile's split owns: `count` of them, the first in term e0
+// at complex offset k0.
+struct TcTile {
+  int task;
+  int m0, n0, ncols;
+  int count, e0, k0;
+  int split;
+};
+// tensor-core grouped GEMM (kernels_tc.cu); mode 0 TF32, 1 3xTF32, 2 BF16;
+// operands complex float, C complex double (tc = 0) or float (tc = 1);
+// persistent: min(ntiles, n_sm) CTAs walk the tile list
+void launch_gemm_tc(const GemmTask* d_tasks, const GemmTerm* d_terms, const TcTile* d_tiles,
+                    int ntiles, int mode, int n_sm, int* d_err, cudaStream_t st);
+int tc_smem_bytes(int mode);
 int tc_tile_m();
 int tc_tile_n();
 int tc_stage_k();   // complex K per staged tile
-struct ZeroRegion {
-  void* p;
-  size_t bytes;   // multiple of 4
-};
-void launch_zero_regions(const ZeroRegion* d_regions, int n, cudaStream_t st);
+// C of each listed split task = sum over s in order of its part slices
+// (+ C when beta); d_ids: indices into d_tasks
+void launch_reduce_splits(const GemmTask* d_tasks, const int* d_ids, int n, cudaStream_t st);
 // out (float2) = in (double2), n elements
 void launch_to_float(const double2* in, float2* out, size_t n, cudaStream_t st);
 // out (double2) = in (element type et), n elements

@@ -7,20 +7,40 @@
 //     [ br  bi ]
 //     [ -bi br ]   per complex entry,
 // the real product is the complex product with re/im interleaved along N,
-// i.e. exactly the storage of C.  Each CTA computes a 128 x N' real tile
-// (N' <= 128, 64 complex columns) in TMEM; operands are staged by the CTA's
-// threads in the canonical K-major no-swizzle layout (8-row x 16-byte core
-// matrices) because the symmetry blocks are ragged and addressed through
-// arbitrary leading dimensions and operand modes; one elected thread issues
-// tcgen05.mma and commits to an mbarrier.  3xTF32 splits each operand into
-// a TF32 head and a TF32 tail and accumulates hi*hi + hi*lo + lo*hi.  The
-// BF16 mode rounds both operands to BF16 (kind::f16, FP32 accumulation).
+// i.e. exactly the storage of C.  A tile is 128 rows (the TMEM lanes) by up
+// to 64 complex columns (128 real accumulator columns), K in stages of 8
+// complex.  Split TF32 (3xTF32) splits each operand into a TF32 head and a
+// TF32 tail and accumulates hi*hi + hi*lo + lo*hi; BF16 rounds both operands
+// to BF16 (kind::f16, FP32 accumulation).
 //
-// Every wait is bounded: a stuck barrier sets the error word, the CTA waits
-// (bounded) for its own MMAs, frees its TMEM and returns.
+// The kernel is persistent (one CTA per SM walking a host-built tile list)
+// and warp-specialised:
+//   warps 0..7   producers.  The symmetry blocks are ragged and addressed
+//                through arbitrary leading dimensions and operand modes, so
+//                every element of a stage is fetched on its own: cp.async
+//                copies the raw complex-float operands of a stage into a
+//                ring of TC_NR raw slots (zero-filled past K) TC_NR - 1
+//                stages ahead of use; a thread later reads back the elements
+//                it fetched, applies the term coefficient and conjugation,
+//                splits them into TF32 (or BF16) pieces with integer
+//                operations and stores them in the canonical K-major
+//                no-swizzle layout of a ring of TC_NS MMA stages
+//                (full[s] / empty[s] mbarriers);
+//   warp 12      issues tcgen05.mma for every stage into one of two TMEM
+//                accumulators (acc_full[a] / acc_empty[a]) and commits;
+//   warps 8..11  epilogue: drain an accumulator with tcgen05.ld (warp w
+//                reads TMEM lanes 32 (w - 8) ..), scale by alpha and store
+//                (split-K tasks store their slice of the partial buffer),
+//                while the MMAs of the next tile run into the other
+//                accumulator.
+// FP64 work (device coefficients) is done by one lane per warp; the operand
+// path issues no FP64 or conversion instruction (on this part the FP64 pipe,
+// which also executes conversions, is the narrow one).
+//
+// Every wait is bounded: a timeout sets the error word and a CTA-wide abort
+// flag, after which every role stops waiting and leaves, the MMA warp waits
+// (bounded) for its issued MMAs, and the TMEM columns are released.
 #include <cuda_runtime.h>
-
-#include <cuda_bf16.h>
 
 #include <cstdint>
 
@@ -34,20 +54,33 @@ constexpr int TC_BM = 128;        // rows per tile (TMEM lanes)
 constexpr int TC_BNC = 64;        // complex columns per tile
 constexpr int TC_BKC = 8;         // complex K per stage
 constexpr int TC_KR = 2 * TC_BKC; // real K per stage (16 tf32 = 2 MMA k-steps)
-constexpr int TC_NR = 2 * TC_BNC; // real N per tile
-constexpr int TC_THREADS = 256;
-constexpr int TC_TMEM_COLS = 128;
+constexpr int TC_NREAL = 2 * TC_BNC;
 constexpr uint32_t TC_SPIN_LIMIT = 1u << 22;
 
+constexpr int TC_NS = 4;          // MMA stages in the ring
+constexpr int TC_NR = 5;          // raw operand slots (prefetch depth + 1)
+constexpr int TC_PROD_WARPS = 8;
+constexpr int TC_PROD = TC_PROD_WARPS * 32;
+constexpr int TC_EPI_WARP0 = 8;
+constexpr int TC_MMA_WARP = 12;
+constexpr int TC_THREADS = 13 * 32;
+constexpr int TC_ACC_COLS = 128;  // real columns per accumulator
+constexpr int TC_TMEM_ALLOC = 2 * TC_ACC_COLS;
+
+// per producer thread and stage: 4 complex of A (one row) and 2 of B (one column)
+constexpr int TC_AEL = TC_BM * TC_BKC / TC_PROD;    // 4
+constexpr int TC_BEL = TC_BNC * TC_BKC / TC_PROD;   // 2
+constexpr int RAW_BYTES = (TC_AEL + TC_BEL) * TC_PROD * 8;   // 12 KB per raw slot
+
 // bytes of one staged operand tile (rows x 16 tf32)
-constexpr int TILE_A_BYTES = TC_BM * TC_KR * 4;   // 8 KB
-constexpr int TILE_B_BYTES = TC_NR * TC_KR * 4;   // 8 KB
+constexpr int TILE_A_BYTES = TC_BM * TC_KR * 4;       // 8 KB
+constexpr int TILE_B_BYTES = TC_NREAL * TC_KR * 4;    // 8 KB
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
 }
 
-// canonical K-major, no-swizzle layout: element (r, k) of a rows x 32 tile
+// canonical K-major, no-swizzle layout: element (r, k) of a rows x 16 tf32 tile
 __device__ __forceinline__ int canon_off(int r, int k) {
   return ((r >> 3) * (TC_KR / 4) + (k >> 2)) * 128 + (r & 7) * 16 + (k & 3) * 4;
 }
@@ -75,6 +108,12 @@ __device__ __forceinline__ uint32_t make_idesc_bf16(int n_real) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n_real >> 3) << 17) |
          ((uint32_t)(TC_BM >> 4) << 24);
 }
+// instruction descriptor: F32 accumulator, TF32 A and B, both K-major
+__device__ __forceinline__ uint32_t make_idesc_tf32(int n_real) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n_real >> 3) << 17) |
+         ((uint32_t)(TC_BM >> 4) << 24);
+}
+
 __device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t da, uint64_t db, uint32_t idesc,
                                          uint32_t accumulate) {
   asm volatile(
@@ -84,17 +123,6 @@ __device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t da, uint64_t db
       :
       : "r"(tmem), "l"(da), "l"(db), "r"(idesc), "r"(accumulate));
 }
-__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
-  __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
-  return *(uint32_t*)&v;
-}
-
-// instruction descriptor: F32 accumulator, TF32 A and B, both K-major
-__device__ __forceinline__ uint32_t make_idesc_tf32(int n_real) {
-  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n_real >> 3) << 17) |
-         ((uint32_t)(TC_BM >> 4) << 24);
-}
-
 __device__ __forceinline__ void mma_tf32(uint32_t tmem, uint64_t da, uint64_t db, uint32_t idesc,
                                          uint32_t accumulate) {
   asm volatile(
@@ -104,31 +132,38 @@ __device__ __forceinline__ void mma_tf32(uint32_t tmem, uint64_t da, uint64_t db
       :
       : "r"(tmem), "l"(da), "l"(db), "r"(idesc), "r"(accumulate));
 }
-
 __device__ __forceinline__ void mma_commit(uint32_t mbar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n"
                :
                : "r"(mbar)
                : "memory");
 }
-
 __device__ __forceinline__ void mbar_init(uint32_t mbar, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" : : "r"(mbar), "r"(count) : "memory");
 }
-
-// bounded wait on an mbarrier phase; returns false on timeout
-__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t phase) {
+__device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" : : "r"(mbar) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint32_t mbar, uint32_t phase) {
+  uint32_t done;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(done)
+      : "r"(mbar), "r"(phase)
+      : "memory");
+  return done != 0;
+}
+// bounded wait that also gives up once another role aborted
+__device__ __forceinline__ bool wait_or_abort(uint32_t mbar, uint32_t phase,
+                                              volatile int* abort_flag, int* err) {
   for (uint32_t it = 0; it < TC_SPIN_LIMIT; ++it) {
-    uint32_t done;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}\n"
-        : "=r"(done)
-        : "r"(mbar), "r"(phase)
-        : "memory");
-    if (done) return true;
+    if (mbar_try(mbar, phase)) return true;
+    if ((it & 255u) == 255u && *abort_flag) return false;
   }
+  atomicExch(err, 2);
+  *abort_flag = 1;
   return false;
 }
 
@@ -142,10 +177,35 @@ __device__ __forceinline__ void tc_fence_before() {
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
 }
 
-__device__ __forceinline__ float to_tf32(float x) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;\n" : "=r"(r) : "f"(x));
-  return __uint_as_float(r);
+// 8-byte asynchronous copy global -> shared; src_bytes = 0 fills zeros
+__device__ __forceinline__ void cp_async8(uint32_t dst, const void* src, uint32_t src_bytes) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n"
+               :
+               : "r"(dst), "l"(src), "r"(src_bytes)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" : : "n"(N) : "memory");
+}
+
+// TF32 head of x, rounded to nearest (ties away from zero) on the integer
+// ALU: the tensor pipe reads the top 19 bits of a 32-bit operand, so adding
+// half a unit of the 13 dropped bits to the magnitude and clearing them is
+// the rounding; the tail x - head is exact in FP32 and the pipe truncates it.
+__device__ __forceinline__ float tf32_head(float x) {
+  return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
+}
+// BF16 bits of x rounded to nearest even (finite x)
+__device__ __forceinline__ uint32_t bf16_bits(float x) {
+  const uint32_t u = __float_as_uint(x);
+  return (u + 0x7FFFu + ((u >> 16) & 1u)) >> 16;
+}
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+  return bf16_bits(lo) | (bf16_bits(hi) << 16);
 }
 
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
@@ -166,337 +226,439 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// element (r, c) of op(P) (R x C), P of element type t (0 double2, 1 float2)
-__device__ __forceinline__ float2 load_el(const void* P, int t, int ld, int op, int r, int c, int R,
-                                          int C) {
-  if (r >= R || c >= C) return make_float2(0.f, 0.f);
-  size_t idx;
-  bool conj = false;
-  switch (op) {
-    case OP_N: idx = (size_t)r * ld + c; break;
-    case OP_T: idx = (size_t)c * ld + r; break;
-    case OP_C: idx = (size_t)c * ld + r; conj = true; break;
-    default: idx = (size_t)r * ld + c; conj = true; break;
-  }
-  float2 v;
-  if (t == 0) {
-    double2 d = ((const double2*)P)[idx];
-    v = make_float2((float)d.x, (float)d.y);
-  } else {
-    v = ((const float2*)P)[idx];
-  }
-  if (conj) v.y = -v.y;
-  return v;
+// address of element (r, c) of op(P), P complex float with leading dimension ld
+__device__ __forceinline__ const float2* el_addr(const void* P, int ld, int op, int r, int c) {
+  const size_t idx = (op == OP_N || op == OP_J) ? (size_t)r * ld + c : (size_t)c * ld + r;
+  return (const float2*)P + idx;
 }
+__device__ __forceinline__ bool op_conj(int op) { return op == OP_C || op == OP_J; }
+
+// One K stage of one tile, as a producer thread walks them
+struct Item {
+  int tile, s, e, k0;   // tile index, stage within the tile, term, complex K offset
+};
+// What the conversion of an issued stage needs (one per raw slot)
+struct Pend {
+  int valid, arow, bcol, conj_a, conj_b;
+  float2 sc;
+};
 
 template <int MODE>   // 0: TF32, 1: 3xTF32, 2: BF16
-__global__ void __launch_bounds__(TC_THREADS, 3) k_gemm_tc(const GemmTask* __restrict__ tasks,
-                                                        const GemmTerm* __restrict__ terms,
-                                                        const int* __restrict__ tile_task,
-                                                        int* err) {
+__global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_tc(const GemmTask* __restrict__ tasks,
+                                                         const GemmTerm* __restrict__ terms,
+                                                         const TcTile* __restrict__ tiles,
+                                                         int ntiles, int* err) {
   extern __shared__ __align__(1024) unsigned char sm[];
-  constexpr int NSPLIT = MODE == 1 ? 2 : 1;                 // operand tiles per stage (hi[, lo])
-  constexpr int BUF_BYTES = NSPLIT * (TILE_A_BYTES + TILE_B_BYTES);
-  __shared__ __align__(8) uint64_t mbar[2];
+  constexpr int NSPLIT = MODE == 1 ? 2 : 1;   // operand tiles per stage (hi[, lo])
+  constexpr int A_BYTES = MODE == 2 ? TILE_A_BYTES / 2 : TILE_A_BYTES;
+  constexpr int B_BYTES = MODE == 2 ? TILE_B_BYTES / 2 : TILE_B_BYTES;
+  constexpr int STAGE_BYTES = NSPLIT * (A_BYTES + B_BYTES);
+  unsigned char* raw = sm + TC_NS * STAGE_BYTES;
+  __shared__ __align__(8) uint64_t full[TC_NS], empty[TC_NS], acc_full[2], acc_empty[2];
   __shared__ uint32_t tmem_base;
-  __shared__ int abort_flag;
-  __shared__ float2 alpha_sh;
+  __shared__ volatile int abort_flag;
 
-  const int ti = tile_task[blockIdx.x];
-  const GemmTask t = tasks[ti];
-  const int local = blockIdx.x - t.tile_base;
-  const int split = local % t.splits;
-  const int rest = local / t.splits;
-  const int m0 = (rest % t.tiles_m) * TC_BM;
-  const int n0 = (rest / t.tiles_m) * TC_BNC;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int ncols = min(TC_BNC, t.N - n0);
-  const int nreal = ((2 * ncols + 15) / 16) * 16;   // MMA N: multiple of 16
-  const uint32_t idesc = MODE == 2 ? make_idesc_bf16(nreal) : make_idesc_tf32(nreal);
-
-  if (warp == 0) {
+  if (warp == TC_MMA_WARP) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n"
                  :
-                 : "r"(smem_u32(&tmem_base)), "r"(TC_TMEM_COLS)
+                 : "r"(smem_u32(&tmem_base)), "r"(TC_TMEM_ALLOC)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
   }
   if (threadIdx.x == 0) {
-    mbar_init(smem_u32(&mbar[0]), 1);
-    mbar_init(smem_u32(&mbar[1]), 1);
+    for (int s = 0; s < TC_NS; ++s) {
+      mbar_init(smem_u32(&full[s]), TC_PROD);
+      mbar_init(smem_u32(&empty[s]), 1);
+    }
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(smem_u32(&acc_full[a]), 1);
+      mbar_init(smem_u32(&acc_empty[a]), 128);
+    }
     abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = tmem_base;
 
-  // stages of this task: (term, k0) pairs of TC_BKC complex, this split's share
-  int S = 0;
-  for (int e = t.term_begin; e < t.term_end; ++e) S += (terms[e].K + TC_BKC - 1) / TC_BKC;
-  const int lo = (int)((long long)split * S / t.splits);
-  const int hi = (int)((long long)(split + 1) * S / t.splits);
-  int e = t.term_begin, k0 = 0;
-  {
-    int idx = 0;
-    while (e < t.term_end) {
-      const int nk = (terms[e].K + TC_BKC - 1) / TC_BKC;
-      if (idx + nk <= lo) { idx += nk; ++e; continue; }
-      k0 = (lo - idx) * TC_BKC;
-      break;
-    }
-  }
-  const int count = hi - lo;
-
-  uint32_t uses[2] = {0u, 0u};
-  bool ok = true;
-  // The global loads of stage s + 1 are issued right after the MMAs of stage
-  // s, into registers, so their latency overlaps the MMAs and the wait for
-  // the next shared-memory buffer.
-  const int ra_r = threadIdx.x & (TC_BM - 1);
-  const int ra_k = (threadIdx.x >> 7) * (TC_BKC / 2);
-  const int rb_n = threadIdx.x & (TC_BNC - 1);
-  const int rb_k = (threadIdx.x >> 6) * (TC_BKC / 4);
-  float2 ra[TC_BKC / 2], rb[TC_BKC / 4];
-  float2 sc = make_float2(1.f, 0.f);
-  // the term coefficient is formed in FP64 once per term, not per stage (the
-  // FP64 pipe is the scarce unit: every thread computes it)
-  int sc_term = -1;
-  auto load_stage = [&](int ee, int kk0) {
-    const GemmTerm g = terms[ee];
-    if (ee != sc_term) {
-      if (g.scale_ptr) {   // a coefficient that lives on the device: form it in FP64
-        const double2 p = *g.scale_ptr;
-        const double2 scd = make_double2(g.scale.x * p.x - g.scale.y * p.y,
-                                         g.scale.x * p.y + g.scale.y * p.x);
-        sc = make_float2((float)scd.x, (float)scd.y);
-      } else {             // FP32 copy made on the host: no FP64 instruction here
-        sc = g.fscale;
-      }
-      sc_term = ee;
-    }
-#pragma unroll
-    for (int j = 0; j < TC_BKC / 2; ++j)
-      ra[j] = load_el(g.A, t.ta, g.lda, t.opA, m0 + ra_r, kk0 + ra_k + j, t.M, g.K);
-#pragma unroll
-    for (int j = 0; j < TC_BKC / 4; ++j)
-      rb[j] = load_el(g.B, t.tb, g.ldb, t.opB, kk0 + rb_k + j, n0 + rb_n, g.K, t.N);
-  };
-  if (count > 0) load_stage(e, k0);
-  for (int s = 0; s < count && ok; ++s) {
-    const int b = s & 1;
-    unsigned char* sA = sm + b * BUF_BYTES;
-    unsigned char* sB = sA + NSPLIT * TILE_A_BYTES;
-    if (uses[b] > 0) {   // the MMAs that last read this buffer must be done
-      if (!mbar_wait(smem_u32(&mbar[b]), (uses[b] - 1) & 1u)) {
-        if (lane == 0) atomicExch(err, 2);
-        abort_flag = 1;
-      }
-    }
-    // Rows past M and columns past N are zero in every stage: each of the
-    // two buffers receives those zeros in its first stage and keeps them, so
-    // later stages skip them (whole warps when the block is short -- the
-    // local-matvec outputs fill only a fraction of a 128 x 64 tile).
-    const bool a_stage = s < 2 || m0 + ra_r < t.M;
-    const bool b_stage = s < 2 || n0 + rb_n < t.N;
-    // ---- A: 128 rows x 8 complex; thread -> row, 4 complex of K
-#pragma unroll
-    for (int j = 0; j < TC_BKC / 2 && a_stage; ++j) {
-      const int kk = ra_k + j;
-      const float2 a0 = ra[j];
-      const float2 a = make_float2(sc.x * a0.x - sc.y * a0.y, sc.x * a0.y + sc.y * a0.x);
-      if (MODE == 2) {
-        *(uint32_t*)(sA + canon_off16(ra_r, 2 * kk)) = pack_bf16(a.x, a.y);
-        continue;
-      }
-      const float2 hi = make_float2(to_tf32(a.x), to_tf32(a.y));
-      *(float2*)(sA + canon_off(ra_r, 2 * kk)) = hi;
-      if (MODE == 1) {
-        const float2 lo2 = make_float2(to_tf32(a.x - hi.x), to_tf32(a.y - hi.y));
-        *(float2*)(sA + TILE_A_BYTES + canon_off(ra_r, 2 * kk)) = lo2;
-      }
-    }
-    // ---- B-tilde (K-major, rows = real N): thread -> column n, 2 complex of K
-#pragma unroll
-    for (int j = 0; j < TC_BKC / 4 && b_stage; ++j) {
-      const int kk = rb_k + j;
-      const float2 bv = rb[j];
-      if (MODE == 2) {
-        *(uint32_t*)(sB + canon_off16(2 * rb_n, 2 * kk)) = pack_bf16(bv.x, -bv.y);
-        *(uint32_t*)(sB + canon_off16(2 * rb_n + 1, 2 * kk)) = pack_bf16(bv.y, bv.x);
-        continue;
-      }
-      const float2 hr = make_float2(to_tf32(bv.x), to_tf32(-bv.y));   // row 2n:   (br, -bi)
-      const float2 hi2 = make_float2(to_tf32(bv.y), to_tf32(bv.x));   // row 2n+1: (bi,  br)
-      *(float2*)(sB + canon_off(2 * rb_n, 2 * kk)) = hr;
-      *(float2*)(sB + canon_off(2 * rb_n + 1, 2 * kk)) = hi2;
-      if (MODE == 1) {
-        const float2 lr = make_float2(to_tf32(bv.x - hr.x), to_tf32(-bv.y - hr.y));
-        const float2 li = make_float2(to_tf32(bv.y - hi2.x), to_tf32(bv.x - hi2.y));
-        *(float2*)(sB + TILE_B_BYTES + canon_off(2 * rb_n, 2 * kk)) = lr;
-        *(float2*)(sB + TILE_B_BYTES + canon_off(2 * rb_n + 1, 2 * kk)) = li;
-      }
-    }
-    fence_async_smem();
-    __syncthreads();
-    if (abort_flag) { ok = false; break; }
-    if (threadIdx.x == 0) {
-      tc_fence_after();
-      const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
-      if (MODE == 2) {   // one K = 16 step covers the stage
-        mma_bf16(tmem, make_desc16(a0), make_desc16(b0), idesc, s > 0 ? 1u : 0u);
-      } else
-#pragma unroll
-      for (int q = 0; q < TC_KR / 8; ++q) {
-        const uint32_t off = q * 256;   // two core matrices along K per k-step
-        mma_tf32(tmem, make_desc(a0 + off), make_desc(b0 + off), idesc, (s > 0 || q > 0) ? 1u : 0u);
-        if (MODE == 1) {
-          mma_tf32(tmem, make_desc(a0 + off), make_desc(b0 + TILE_B_BYTES + off), idesc, 1u);
-          mma_tf32(tmem, make_desc(a0 + TILE_A_BYTES + off), make_desc(b0 + off), idesc, 1u);
+  if (warp < TC_PROD_WARPS) {
+    // ------------------------------------------------------------ producers
+    const int p = threadIdx.x;
+    const int ra_r = p & (TC_BM - 1);            // A: row of this thread
+    const int ra_k = (p >> 7) * TC_AEL;          //    first complex K of its 4
+    const int rb_n = p & (TC_BNC - 1);           // B: column of this thread
+    const int rb_k = (p >> 6) * TC_BEL;          //    first complex K of its 2
+    // the stage being issued, with its tile's and term's fields kept in
+    // registers while they stay the same (they are reloaded on a change only)
+    Item cur{(int)blockIdx.x, 0, 0, 0};
+    TcTile tl{};
+    int tM = 0, topA = 0, topB = 0, tend = 0;
+    const void* gA = nullptr;
+    const void* gB = nullptr;
+    int gK = 0, glda = 0, gldb = 0;
+    float2 gsc = make_float2(1.f, 0.f);
+    auto load_term = [&]() {
+      const GemmTerm& g = terms[cur.e];
+      gA = g.A;
+      gB = g.B;
+      gK = g.K;
+      glda = g.lda;
+      gldb = g.ldb;
+      gsc = g.fscale;
+      if (g.scale_ptr) {   // a device coefficient: formed in FP64 by one lane
+        float sx = 0.f, sy = 0.f;
+        if (lane == 0) {
+          const double2 q = *g.scale_ptr;
+          sx = (float)(g.scale.x * q.x - g.scale.y * q.y);
+          sy = (float)(g.scale.x * q.y + g.scale.y * q.x);
         }
+        gsc = make_float2(__shfl_sync(0xffffffffu, sx, 0), __shfl_sync(0xffffffffu, sy, 0));
       }
-      mma_commit(smem_u32(&mbar[b]));
-    }
-    uses[b] += 1;
-    k0 += TC_BKC;
-    while (e < t.term_end && k0 >= terms[e].K) { ++e; k0 = 0; }
-    if (s + 1 < count) load_stage(e, k0);
-  }
-  // the last commit covers every MMA issued before it
-  uint32_t failed_bar = 0, failed_phase = 0;
-  bool pending = false;
-  if (count > 0) {
-    const int b = (count - 1) & 1;
-    failed_bar = smem_u32(&mbar[b]);
-    failed_phase = (uses[b] - 1) & 1u;
-    pending = true;
-    if (ok && !mbar_wait(failed_bar, failed_phase)) {
-      if (lane == 0) atomicExch(err, 2);
-      abort_flag = 1;   // the epilogue's TMEM loads are warp-collective: fail as a CTA
-      ok = false;
-    }
-  }
-  __syncthreads();
-  tc_fence_after();
-  if (abort_flag) ok = false;
-
-  if (threadIdx.x == 0) {   // alpha in FP64, once per CTA
-    double2 alpha = t.alpha;
-    if (t.alpha_ptr) {
-      double2 p = *t.alpha_ptr;
-      alpha = make_double2(alpha.x * p.x - alpha.y * p.y, alpha.x * p.y + alpha.y * p.x);
-    }
-    if (t.alpha_div) {
-      double2 q = *t.alpha_div;
-      double d = q.x * q.x + q.y * q.y;
-      alpha = make_double2((alpha.x * q.x + alpha.y * q.y) / d, (alpha.y * q.x - alpha.x * q.y) / d);
-    }
-    alpha_sh = make_float2((float)alpha.x, (float)alpha.y);
-  }
-  __syncthreads();
-  if (ok) {
-    const bool atomic = t.splits > 1;
-    const int quad = warp & 3, chalf = warp >> 2;
-    const bool have = count > 0;
-    const float fax = alpha_sh.x, fay = alpha_sh.y;
-    // Each warp moves its 32 x 16-complex chunk through a 4 KB shared-memory
-    // scratch (the operand buffers, free once the last MMA completed) so
-    // that the global writes run along rows: 16 lanes per 128-byte row.
-    // Slots are XOR-swizzled by row so neither side has bank conflicts.
-    float2* scr = (float2*)(sm + warp * 4096);
-    const int hrow = lane >> 4, jj = lane & 15;
-    for (int c0 = 32 * chalf; c0 < 2 * ncols; c0 += 64) {
-      float v[32];
-      if (have) {
-        tmem_ld32(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)c0, v);
-      } else {
+    };
+    auto first = [&]() {   // the first stage of the next tile that has K stages
+      while (cur.tile < ntiles && tiles[cur.tile].count <= 0) cur.tile += gridDim.x;
+      if (cur.tile >= ntiles) return;
+      tl = tiles[cur.tile];
+      const GemmTask& t = tasks[tl.task];
+      tM = t.M;
+      topA = t.opA;
+      topB = t.opB;
+      tend = t.term_end;
+      cur.s = 0;
+      cur.e = tl.e0;
+      cur.k0 = tl.k0;
+      load_term();
+    };
+    first();
+    // issue the copies of `cur` into raw slot r and step `cur` forward
+    auto issue = [&](Pend& pd, int r) {
+      pd.valid = cur.tile < ntiles;
+      if (pd.valid) {
+        pd.arow = tl.m0 + ra_r < tM;
+        pd.bcol = rb_n < tl.ncols;
+        pd.conj_a = op_conj(topA);
+        pd.conj_b = op_conj(topB);
+        pd.sc = gsc;
+        const uint32_t base = smem_u32(raw + r * RAW_BYTES);
+        if (pd.arow) {
 #pragma unroll
-        for (int i = 0; i < 32; ++i) v[i] = 0.f;
-      }
-#pragma unroll
-      for (int j = 0; j < 16; ++j) scr[lane * 16 + (j ^ (lane & 15))] = make_float2(v[2 * j], v[2 * j + 1]);
-      __syncwarp();
-      const int jn = min(16, ncols - c0 / 2);
-      // transposed tasks (C^T computed) write along C's rows = this tile's
-      // columns: lanes over the 32 tile rows, one tile column at a time
-      for (int it = 0; it < 16; ++it) {
-        int rl, jc;
-        if (t.ct) { rl = lane; jc = it; } else { rl = 2 * it + hrow; jc = jj; }
-        const int row = m0 + quad * 32 + rl;
-        const float2 x = scr[rl * 16 + (jc ^ (rl & 15))];
-        if (row >= t.M || jc >= jn || !(have || !atomic)) continue;
-        const size_t col = (size_t)n0 + c0 / 2 + jc;
-        const size_t o = t.ct ? col * t.ldc + row : (size_t)row * t.ldc + col;
-        if (t.tc == 0) {
-          double2* C = (double2*)t.C + o;
-          double ore = (double)(fax * x.x - fay * x.y), oim = (double)(fax * x.y + fay * x.x);
-          if (atomic) {
-            atomicAdd(&C->x, ore);
-            atomicAdd(&C->y, oim);
-          } else {
-            if (t.beta) { ore += C->x; oim += C->y; }
-            *C = make_double2(ore, oim);
+          for (int j = 0; j < TC_AEL; ++j) {
+            const int k = cur.k0 + ra_k + j;
+            const bool in = k < gK;
+            const void* src = in ? (const void*)el_addr(gA, glda, topA, tl.m0 + ra_r, k) : gA;
+            cp_async8(base + (j * TC_PROD + p) * 8, src, in ? 8u : 0u);
           }
+        }
+        if (pd.bcol) {
+#pragma unroll
+          for (int j = 0; j < TC_BEL; ++j) {
+            const int k = cur.k0 + rb_k + j;
+            const bool in = k < gK;
+            const void* src = in ? (const void*)el_addr(gB, gldb, topB, k, tl.n0 + rb_n) : gB;
+            cp_async8(base + ((TC_AEL + j) * TC_PROD + p) * 8, src, in ? 8u : 0u);
+          }
+        }
+        // next stage
+        if (++cur.s >= tl.count) {
+          cur.tile += gridDim.x;
+          first();
         } else {
-          float2* C = (float2*)t.C + o;
-          float ore = fax * x.x - fay * x.y, oim = fax * x.y + fay * x.x;
-          if (atomic) {
-            atomicAdd(&C->x, ore);
-            atomicAdd(&C->y, oim);
-          } else {
-            if (t.beta) { ore += C->x; oim += C->y; }
-            *C = make_float2(ore, oim);
+          cur.k0 += TC_BKC;
+          if (cur.k0 >= gK) {
+            do { ++cur.e; } while (cur.e < tend && terms[cur.e].K <= 0);
+            cur.k0 = 0;
+            if (cur.e < tend) load_term();
           }
         }
       }
-      __syncwarp();
+      cp_async_commit();
+    };
+    uint32_t g = 0;   // stages converted so far (MMA ring position)
+    // convert the oldest issued stage (raw slot r) into the MMA ring
+    auto convert = [&](const Pend& pd, int r) -> bool {
+      cp_async_wait<TC_NR - 1>();
+      if (!pd.valid) return false;
+      const int slot = g % TC_NS;
+      const uint32_t use = g / TC_NS;
+      if (!wait_or_abort(smem_u32(&empty[slot]), (use & 1u) ^ 1u, &abort_flag, err)) return false;
+      unsigned char* sA = sm + slot * STAGE_BYTES;
+      unsigned char* sB = sA + NSPLIT * A_BYTES;
+      const float2* rw = (const float2*)(raw + r * RAW_BYTES);
+      // A: 128 rows x 8 complex; rows past M are left as they are (they only
+      // reach accumulator rows that are never stored)
+      if (pd.arow) {
+#pragma unroll
+        for (int j = 0; j < TC_AEL; ++j) {
+          const int kk = ra_k + j;
+          float2 a0 = rw[j * TC_PROD + p];
+          if (pd.conj_a) a0.y = -a0.y;
+          const float2 a = make_float2(pd.sc.x * a0.x - pd.sc.y * a0.y,
+                                       pd.sc.x * a0.y + pd.sc.y * a0.x);
+          if (MODE == 2) {
+            *(uint32_t*)(sA + canon_off16(ra_r, 2 * kk)) = pack_bf16(a.x, a.y);
+            continue;
+          }
+          const float2 hi = make_float2(tf32_head(a.x), tf32_head(a.y));
+          *(float2*)(sA + canon_off(ra_r, 2 * kk)) = hi;
+          if (MODE == 1)
+            *(float2*)(sA + A_BYTES + canon_off(ra_r, 2 * kk)) = make_float2(a.x - hi.x, a.y - hi.y);
+        }
+      }
+      // B-tilde (K-major, rows = real N): column n -> rows 2n (br, -bi), 2n+1 (bi, br)
+      if (pd.bcol) {
+#pragma unroll
+        for (int j = 0; j < TC_BEL; ++j) {
+          const int kk = rb_k + j;
+          float2 bv = rw[(TC_AEL + j) * TC_PROD + p];
+          if (pd.conj_b) bv.y = -bv.y;
+          if (MODE == 2) {
+            *(uint32_t*)(sB + canon_off16(2 * rb_n, 2 * kk)) = pack_bf16(bv.x, -bv.y);
+            *(uint32_t*)(sB + canon_off16(2 * rb_n + 1, 2 * kk)) = pack_bf16(bv.y, bv.x);
+            continue;
+          }
+          const float2 r0 = make_float2(bv.x, -bv.y), r1 = make_float2(bv.y, bv.x);
+          const float2 h0 = make_float2(tf32_head(r0.x), tf32_head(r0.y));
+          const float2 h1 = make_float2(tf32_head(r1.x), tf32_head(r1.y));
+          *(float2*)(sB + canon_off(2 * rb_n, 2 * kk)) = h0;
+          *(float2*)(sB + canon_off(2 * rb_n + 1, 2 * kk)) = h1;
+          if (MODE == 1) {
+            *(float2*)(sB + B_BYTES + canon_off(2 * rb_n, 2 * kk)) =
+                make_float2(r0.x - h0.x, r0.y - h0.y);
+            *(float2*)(sB + B_BYTES + canon_off(2 * rb_n + 1, 2 * kk)) =
+                make_float2(r1.x - h1.x, r1.y - h1.y);
+          }
+        }
+      }
+      fence_async_smem();
+      mbar_arrive(smem_u32(&full[slot]));
+      ++g;
+      return true;
+    };
+    // TC_NR raw slots rotated through registers (the unrolled loop keeps
+    // every index a constant): issue TC_NR - 1 stages ahead, then alternate
+    // issue / convert
+    Pend q[TC_NR];
+#pragma unroll
+    for (int j = 0; j < TC_NR - 1; ++j) issue(q[j], j);
+    bool go = true;
+    while (go) {
+#pragma unroll
+      for (int j = 0; j < TC_NR; ++j) {
+        if (go) {
+          issue(q[(j + TC_NR - 1) % TC_NR], (j + TC_NR - 1) % TC_NR);
+          if (abort_flag || !convert(q[j], j)) go = false;
+        }
+      }
     }
-  } else if (pending) {
-    // give this CTA's MMAs one more bounded chance to drain before the
-    // accumulator columns are released
-    mbar_wait(failed_bar, failed_phase);
+    cp_async_wait<0>();
+  } else if (warp == TC_MMA_WARP) {
+    // ------------------------------------------------------------ MMA issuer
+    uint32_t g = 0, v = 0;   // stages consumed, accumulator uses
+    bool issued = false;
+    uint32_t last_bar = 0, last_phase = 0;
+    for (int tile = blockIdx.x; tile < ntiles && !abort_flag; tile += gridDim.x) {
+      const TcTile tl = tiles[tile];
+      if (tl.count <= 0) continue;
+      const int acc = v & 1;
+      const uint32_t vuse = v >> 1;
+      if (!wait_or_abort(smem_u32(&acc_empty[acc]), (vuse & 1u) ^ 1u, &abort_flag, err)) break;
+      tc_fence_after();
+      const int nreal = ((2 * tl.ncols + 15) / 16) * 16;
+      const uint32_t idesc = MODE == 2 ? make_idesc_bf16(nreal) : make_idesc_tf32(nreal);
+      const uint32_t dacc = tmem + (uint32_t)(acc * TC_ACC_COLS);
+      bool ok = true;
+      for (int s = 0; s < tl.count; ++s, ++g) {
+        const int slot = g % TC_NS;
+        const uint32_t use = g / TC_NS;
+        if (!wait_or_abort(smem_u32(&full[slot]), use & 1u, &abort_flag, err)) { ok = false; break; }
+        tc_fence_after();
+        if (lane == 0) {
+          const uint32_t a0 = smem_u32(sm + slot * STAGE_BYTES);
+          const uint32_t b0 = a0 + NSPLIT * A_BYTES;
+          if (MODE == 2) {
+            mma_bf16(dacc, make_desc16(a0), make_desc16(b0), idesc, s > 0 ? 1u : 0u);
+          } else {
+#pragma unroll
+            for (int q = 0; q < TC_KR / 8; ++q) {
+              const uint32_t off = q * 256;
+              mma_tf32(dacc, make_desc(a0 + off), make_desc(b0 + off), idesc,
+                       (s > 0 || q > 0) ? 1u : 0u);
+              if (MODE == 1) {
+                mma_tf32(dacc, make_desc(a0 + off), make_desc(b0 + B_BYTES + off), idesc, 1u);
+                mma_tf32(dacc, make_desc(a0 + A_BYTES + off), make_desc(b0 + off), idesc, 1u);
+              }
+            }
+          }
+          mma_commit(smem_u32(&empty[slot]));
+        }
+        __syncwarp();
+        issued = true;
+        last_bar = smem_u32(&empty[slot]);
+        last_phase = use & 1u;
+      }
+      if (!ok) break;
+      if (lane == 0) mma_commit(smem_u32(&acc_full[acc]));
+      __syncwarp();
+      ++v;
+    }
+    // no MMA of this CTA may still run when the columns are released
+    if (issued && abort_flag)
+      for (uint32_t it = 0; it < TC_SPIN_LIMIT && !mbar_try(last_bar, last_phase); ++it) {
+      }
+  } else {
+    // ------------------------------------------------------------ epilogue
+    const int ew = warp - TC_EPI_WARP0;      // TMEM lanes 32 ew .. 32 ew + 31
+    uint32_t v = 0;
+    for (int tile = blockIdx.x; tile < ntiles && !abort_flag; tile += gridDim.x) {
+      const TcTile tl = tiles[tile];
+      const GemmTask& t = tasks[tl.task];
+      const bool split = t.splits > 1;
+      const bool have = tl.count > 0;
+      // alpha in FP64 (device scalars) by one lane, shared by the warp
+      float ax = 0.f, ay = 0.f;
+      if (lane == 0) {
+        double2 alpha = t.alpha;
+        if (t.alpha_ptr) {
+          const double2 q = *t.alpha_ptr;
+          alpha = make_double2(alpha.x * q.x - alpha.y * q.y, alpha.x * q.y + alpha.y * q.x);
+        }
+        if (t.alpha_div) {
+          const double2 q = *t.alpha_div;
+          const double d = q.x * q.x + q.y * q.y;
+          alpha = make_double2((alpha.x * q.x + alpha.y * q.y) / d,
+                               (alpha.y * q.x - alpha.x * q.y) / d);
+        }
+        ax = (float)alpha.x;
+        ay = (float)alpha.y;
+      }
+      const float fax = __shfl_sync(0xffffffffu, ax, 0), fay = __shfl_sync(0xffffffffu, ay, 0);
+      const int acc = v & 1;
+      const uint32_t vuse = v >> 1;
+      if (have) {
+        if (!wait_or_abort(smem_u32(&acc_full[acc]), vuse & 1u, &abort_flag, err)) break;
+        tc_fence_after();
+      }
+      const int row = tl.m0 + 32 * ew + lane;
+      const int nchunk = (2 * tl.ncols + 31) / 32;
+      for (int c = 0; c < nchunk; ++c) {
+        float vv[32];
+        if (have) {
+          tmem_ld32(tmem + (uint32_t)(acc * TC_ACC_COLS) + ((uint32_t)(32 * ew) << 16) +
+                        (uint32_t)(32 * c),
+                    vv);
+        } else {
+#pragma unroll
+          for (int i = 0; i < 32; ++i) vv[i] = 0.f;
+        }
+        if (have && c == nchunk - 1) {
+          tc_fence_before();
+          mbar_arrive(smem_u32(&acc_empty[acc]));
+        }
+        if (row >= t.M) continue;
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const int col = tl.n0 + 16 * c + j;
+          if (col >= tl.n0 + tl.ncols) break;
+          const float xr = vv[2 * j], xi = vv[2 * j + 1];
+          const float ore = fax * xr - fay * xi, oim = fax * xi + fay * xr;
+          if (split) {   // this split's slice; launch_reduce_splits adds them in order
+            const size_t o = ((size_t)tl.split * t.M + row) * t.N + col;
+            if (t.tc == 0) ((double2*)t.part)[o] = make_double2((double)ore, (double)oim);
+            else ((float2*)t.part)[o] = make_float2(ore, oim);
+            continue;
+          }
+          const size_t o = t.ct ? (size_t)col * t.ldc + row : (size_t)row * t.ldc + col;
+          if (t.tc == 0) {
+            double2* C = (double2*)t.C + o;
+            double2 out = make_double2((double)ore, (double)oim);
+            if (t.beta) { out.x += C->x; out.y += C->y; }
+            *C = out;
+          } else {
+            float2* C = (float2*)t.C + o;
+            float2 out = make_float2(ore, oim);
+            if (t.beta) { out.x += C->x; out.y += C->y; }
+            *C = out;
+          }
+        }
+      }
+      if (have) ++v;
+    }
   }
   tc_fence_before();
   __syncthreads();
-  if (warp == 0) {
+  if (warp == TC_MMA_WARP) {
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n"
                  :
-                 : "r"(tmem), "r"(TC_TMEM_COLS)
+                 : "r"(tmem), "r"(TC_TMEM_ALLOC)
                  : "memory");
   }
 }
 
-// zero a list of (pointer, bytes) regions (outputs of split-K tasks)
-__global__ void k_zero_regions(const ZeroRegion* __restrict__ r) {
-  const ZeroRegion z = r[blockIdx.x];
-  uint32_t* p = (uint32_t*)z.p;
-  const size_t n = z.bytes / 4;
-  for (size_t i = threadIdx.x; i < n; i += blockDim.x) p[i] = 0u;
+// C of a split task = sum of its part slices in split order (+ C when beta):
+// one CTA per task, the same summation order on every run
+__global__ void k_reduce_splits(const GemmTask* __restrict__ tasks, const int* __restrict__ ids) {
+  const GemmTask& t = tasks[ids[blockIdx.x]];
+  const size_t mn = (size_t)t.M * t.N;
+  for (size_t i = threadIdx.x; i < mn; i += blockDim.x) {
+    const int r = (int)(i / t.N), c = (int)(i % t.N);
+    const size_t o = t.ct ? (size_t)c * t.ldc + r : (size_t)r * t.ldc + c;
+    if (t.tc == 0) {
+      const double2* P = (const double2*)t.part;
+      double2 s = P[i];
+      for (int q = 1; q < t.splits; ++q) {
+        const double2 x = P[q * mn + i];
+        s.x += x.x;
+        s.y += x.y;
+      }
+      double2* C = (double2*)t.C + o;
+      if (t.beta) { s.x += C->x; s.y += C->y; }
+      *C = s;
+    } else {
+      const float2* P = (const float2*)t.part;
+      float2 s = P[i];
+      for (int q = 1; q < t.splits; ++q) {
+        const float2 x = P[q * mn + i];
+        s.x += x.x;
+        s.y += x.y;
+      }
+      float2* C = (float2*)t.C + o;
+      if (t.beta) { s.x += C->x; s.y += C->y; }
+      *C = s;
+    }
+  }
 }
 
 }  // namespace
 
-void launch_gemm_tc(const GemmTask* d_tasks, const GemmTerm* d_terms, const int* d_tile_task,
-                    int ntiles, int mode, int* d_err, cudaStream_t st) {
+int tc_smem_bytes(int mode) {
+  const int stage = mode == 1 ? 2 * (TILE_A_BYTES + TILE_B_BYTES)
+                              : mode == 2 ? (TILE_A_BYTES + TILE_B_BYTES) / 2
+                                          : TILE_A_BYTES + TILE_B_BYTES;
+  return TC_NS * stage + TC_NR * RAW_BYTES;
+}
+
+void launch_gemm_tc(const GemmTask* d_tasks, const GemmTerm* d_terms, const TcTile* d_tiles,
+                    int ntiles, int mode, int n_sm, int* d_err, cudaStream_t st) {
   if (ntiles <= 0) return;
+  const int grid = ntiles < n_sm ? ntiles : n_sm;
+  const int smem = tc_smem_bytes(mode);
   if (mode == 2) {
-    const int smem = 2 * (TILE_A_BYTES + TILE_B_BYTES);
     set_smem_limit((const void*)k_gemm_tc<2>, smem);
-    k_gemm_tc<2><<<ntiles, TC_THREADS, smem, st>>>(d_tasks, d_terms, d_tile_task, d_err);
+    k_gemm_tc<2><<<grid, TC_THREADS, smem, st>>>(d_tasks, d_terms, d_tiles, ntiles, d_err);
   } else if (mode == 0) {
-    const int smem = 2 * (TILE_A_BYTES + TILE_B_BYTES);
     set_smem_limit((const void*)k_gemm_tc<0>, smem);
-    k_gemm_tc<0><<<ntiles, TC_THREADS, smem, st>>>(d_tasks, d_terms, d_tile_task, d_err);
+    k_gemm_tc<0><<<grid, TC_THREADS, smem, st>>>(d_tasks, d_terms, d_tiles, ntiles, d_err);
   } else {
-    const int smem = 2 * 2 * (TILE_A_BYTES + TILE_B_BYTES);
     set_smem_limit((const void*)k_gemm_tc<1>, smem);
-    k_gemm_tc<1><<<ntiles, TC_THREADS, smem, st>>>(d_tasks, d_terms, d_tile_task, d_err);
+    k_gemm_tc<1><<<grid, TC_THREADS, smem, st>>>(d_tasks, d_terms, d_tiles, ntiles, d_err);
   }
 }
 
-void launch_zero_regions(const ZeroRegion* d_regions, int n, cudaStream_t st) {
+void launch_reduce_splits(const GemmTask* d_tasks, const int* d_ids, int n, cudaStream_t st) {
   if (n <= 0) return;
-  k_zero_regions<<<n, 256, 0, st>>>(d_regions);
+  k_reduce_splits<<<n, 256, 0, st>>>(d_tasks, d_ids);
 }
 
 int tc_stage_k() { return TC_BKC; }
