@@ -113,6 +113,10 @@ struct MPSd {
   QN tot;
   std::vector<Bond> bonds;    // L+1
   std::vector<SiteT> sites;   // L, left index = plain row groups of bonds[i]
+  // sites 1..L-1 are right-canonical (sum_s A^s A^s+ = 1 on their left bond):
+  // set by the routines that produce that gauge (fits, compression,
+  // right_canonicalize, determinants), cleared by anything else
+  bool rcanon = false;
 };
 
 // ------------------------------------------------------------------ MPO
