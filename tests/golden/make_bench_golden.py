@@ -3,16 +3,17 @@
 Workload (Sec. 2.2.3 with the fit of Sec. 2.2.1): L = 16 orbitals, 15
 electrons (2S_z = +1), the seeded synthetic integrals (seed 0), the seeded
 random MPS of bond dimension D = 256 (seed 0) as psi_0, one orthogonal Krylov
-step with m = 10 basis vectors, dt = 0.05 a.u., D = 256, eps = 1e-8, every fit
-0 two-site + 2 one-site sweeps.
+step with m = 10 basis vectors (the benchmark's step; also m = 4), dt = 0.05
+a.u., D = 256, eps = 1e-8, every fit 0 two-site + 2 one-site sweeps.
 
 Only ``oracle`` (the block-sparse MPO/MPS oracle) and ``synth`` run here; no
 value comes from the CUDA library.  Run from the repository root:
 
-    python tests/golden/make_bench_golden.py
+    python tests/golden/make_bench_golden.py [m]
 
 It takes several minutes on a few CPU cores and writes
-tests/golden/krylov_L16_N15_D256.json.
+tests/golden/krylov_L16_N15_D256.json (m = 10) or
+tests/golden/krylov_L16_N15_D256_m<m>.json.
 """
 from __future__ import annotations
 
@@ -30,7 +31,7 @@ import synth  # noqa: E402
 from oracle import bsmps as ob  # noqa: E402
 
 L, N_ELEC, TWO_SZ, D, EPS = 16, 15, 1, 256, 1e-8
-DT, M = 0.05, 10
+DT = 0.05
 SCHEDULE = (0, 2)
 N_SAMPLES = 64
 
@@ -59,7 +60,7 @@ def cplx(a):
     return [a.real.tolist(), a.imag.tolist()]
 
 
-def main():
+def main(M=10):
     t0 = time.time()
     I = synth.make_integrals(L, seed=0)
     mpo = ob.hamiltonian_mpo(I.h, I.eri, I.e0)
@@ -86,11 +87,12 @@ def main():
         "oracle_flops": fl.total,
         "oracle_seconds": time.time() - t0,
     }
-    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "krylov_L16_N15_D256.json")
+    name = "krylov_L16_N15_D256.json" if M == 10 else "krylov_L16_N15_D256_m%d.json" % M
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), name)
     with open(path, "w") as f:
         json.dump(out, f)
     print("wrote %s (%.0f s)" % (path, time.time() - t0))
 
 
 if __name__ == "__main__":
-    main()
+    main(int(sys.argv[1]) if len(sys.argv) > 1 else 10)
