@@ -365,11 +365,107 @@ struct GemmBatch {
   bool fp64;
   std::vector<GemmTask> tasks;
   std::vector<GemmTerm> terms;
+  std::vector<GemmSeg> segs;
+  std::vector<SegOps> segops;
   double flops = 0.0, bytes = 0.0;
+  // a segmented task of an FP64 batch, expanded into one plain task per
+  // segment once its terms are known (the FP64 kernel has no segments)
+  struct PendSeg {
+    bool live = false;
+    GemmSeg s;
+    int other, tc, opA, ta, opB, tb;
+    bool beta;
+    cplx alpha;
+    struct T { const void* shared; int ld; SegOps so; int K; cplx scale; const double2* sp; };
+    std::vector<T> terms;
+  } pend;
   explicit GemmBatch(Context& ctx, bool force_fp64 = false)
       : c(ctx), fp64(force_fp64 || ctx.precision == TDMPS_FP64) {}
+  // A task whose rows (dim 0) or columns (dim 1) are n output blocks of the
+  // given sizes (GemmSeg); `other` is the extent of the other dimension.
+  void task_seg(int dim, int n, void* const* Cs, const int* ldcs, const int* sizes, int other,
+                int tc, int opA, int ta, int opB, int tb, bool beta, cplx alpha) {
+    flush();
+    if (n < 1 || n > 4) throw Error(TDMPS_ERR_INVALID_ARG, "a GEMM task holds 1 to 4 segments");
+    GemmSeg s{};
+    s.dim = dim;
+    s.n = n;
+    for (int i = 0; i < n; ++i) {
+      s.off[i + 1] = s.off[i] + sizes[i];
+      s.C[i] = Cs[i];
+      s.ldc[i] = ldcs[i];
+    }
+    for (int i = n; i < 4; ++i) s.off[i + 1] = s.off[i];
+    if (fp64) {
+      pend.live = true;
+      pend.s = s;
+      pend.other = other; pend.tc = tc; pend.opA = opA; pend.ta = ta; pend.opB = opB; pend.tb = tb;
+      pend.beta = beta; pend.alpha = alpha;
+      pend.terms.clear();
+      return;
+    }
+    const int total = s.off[n];
+    task(Cs[0], tc, dim == 0 ? total : other, dim == 0 ? other : total, ldcs[0], opA, ta, opB, tb,
+         beta, alpha);
+    tasks.back().seg1 = (int)segs.size() + 1;
+    segs.push_back(s);
+  }
+  // One term of the current segmented task: the shared operand (B for row
+  // segments, A for column segments) and one block per segment (null: none).
+  void term_seg(const void* shared, int ld_shared, const void* const* segp, const int* segld,
+                int K, cplx scale = 1.0, const double2* scale_ptr = nullptr) {
+    if (K <= 0) return;
+    SegOps so{};
+    const void* any = nullptr;
+    const GemmSeg& s = pend.live ? pend.s : segs[tasks.back().seg1 - 1];
+    for (int i = 0; i < s.n; ++i) {
+      so.p[i] = segp[i];
+      so.ld[i] = segld[i];
+      if (segp[i] && !any) any = segp[i];
+    }
+    if (!any) return;
+    if (pend.live) {
+      pend.terms.push_back({shared, ld_shared, so, K, scale, scale_ptr});
+      return;
+    }
+    GemmTask& t = tasks.back();
+    GemmTerm g{};
+    if (s.dim == 0) { g.A = any; g.B = shared; g.ldb = ld_shared; }
+    else { g.A = shared; g.lda = ld_shared; g.B = any; }
+    g.K = K;
+    g.pad = (int)segops.size();
+    g.scale = make_double2(scale.real(), scale.imag());
+    g.scale_ptr = scale_ptr;
+    g.fscale = make_float2((float)scale.real(), (float)scale.imag());
+    segops.push_back(so);
+    terms.push_back(g);
+    t.term_end = (int)terms.size();
+    const int other = s.dim == 0 ? t.N : t.M;
+    double live = 0.0;
+    for (int i = 0; i < s.n; ++i)
+      if (segp[i]) live += s.off[i + 1] - s.off[i];
+    flops += 8.0 * live * other * K;
+    bytes += 8.0 * (live * K + (double)other * K);
+  }
+  void flush() {
+    if (!pend.live) return;
+    pend.live = false;
+    const GemmSeg& s = pend.s;
+    for (int i = 0; i < s.n; ++i) {
+      const int sz = s.off[i + 1] - s.off[i];
+      if (sz <= 0) continue;
+      task(s.C[i], pend.tc, s.dim == 0 ? sz : pend.other, s.dim == 0 ? pend.other : sz, s.ldc[i],
+           pend.opA, pend.ta, pend.opB, pend.tb, pend.beta, pend.alpha);
+      for (const auto& tm : pend.terms) {
+        if (!tm.so.p[i]) continue;
+        if (s.dim == 0) term(tm.so.p[i], tm.so.ld[i], tm.shared, tm.ld, tm.K, tm.scale, tm.sp);
+        else term(tm.shared, tm.ld, tm.so.p[i], tm.so.ld[i], tm.K, tm.scale, tm.sp);
+      }
+    }
+  }
   void task(void* C, int tc, int M, int N, int ldc, int opA, int ta, int opB, int tb, bool beta,
             cplx alpha, const double2* aptr = nullptr, const double2* adiv = nullptr) {
+    flush();
     if (fp64 && (ta || tb || tc)) throw Error(TDMPS_ERR_INVALID_ARG, "FP64 GEMM on float data");
     if (!fp64 && (!ta || !tb))
       throw Error(TDMPS_ERR_INVALID_ARG, "tensor-core GEMM operands must be complex float");
@@ -426,7 +522,7 @@ struct GemmBatch {
   // columns runs transposed: its long side fills the 128 TMEM lanes.
   void orient_tc() {
     for (auto& t : tasks) {
-      if (t.M <= 0 || t.N <= 0 || t.M >= tc_tile_m() || t.N <= t.M) continue;
+      if (t.seg1 || t.M <= 0 || t.N <= 0 || t.M >= tc_tile_m() || t.N <= t.M) continue;
       const long long pad_now = (long long)((t.M + 127) / 128) * 128 * ((t.N + 7) / 8) * 8;
       const long long pad_t = (long long)((t.N + 127) / 128) * 128 * ((t.M + 7) / 8) * 8;
       if (pad_t >= pad_now) continue;
@@ -443,6 +539,7 @@ struct GemmBatch {
     }
   }
   void run() {
+    flush();
     const int bm = fp64 ? 32 : tc_tile_m();
     const int bn = fp64 ? 32 : tc_tile_n();
     if (fp64) orient_fp64(); else orient_tc();
@@ -530,7 +627,9 @@ struct GemmBatch {
     auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
     const size_t o_terms = al(tk.size() * sizeof(GemmTask));
     const size_t o_split = o_terms + al(terms.size() * sizeof(GemmTerm));
-    const size_t o_tiles = o_split + al(split_ids.size() * sizeof(int));
+    const size_t o_segs = o_split + al(split_ids.size() * sizeof(int));
+    const size_t o_segops = o_segs + al(segs.size() * sizeof(GemmSeg));
+    const size_t o_tiles = o_segops + al(segops.size() * sizeof(SegOps));
     const size_t pk_bytes =
         o_tiles + (fp64 ? tile_task.size() * sizeof(int) : tc_tiles.size() * sizeof(TcTile));
     std::vector<char>& pk = c.pack;
@@ -539,6 +638,9 @@ struct GemmBatch {
     if (!terms.empty()) std::memcpy(pk.data() + o_terms, terms.data(), terms.size() * sizeof(GemmTerm));
     if (!split_ids.empty())
       std::memcpy(pk.data() + o_split, split_ids.data(), split_ids.size() * sizeof(int));
+    if (!segs.empty()) std::memcpy(pk.data() + o_segs, segs.data(), segs.size() * sizeof(GemmSeg));
+    if (!segops.empty())
+      std::memcpy(pk.data() + o_segops, segops.data(), segops.size() * sizeof(SegOps));
     if (fp64)
       std::memcpy(pk.data() + o_tiles, tile_task.data(), tile_task.size() * sizeof(int));
     else
@@ -553,11 +655,13 @@ struct GemmBatch {
     if (fp64)
       launch_gemm(dt, (int)tk.size(), dm, dtt, (int)tile_task.size(), c.st);
     else
-      launch_gemm_tc(dt, dm, (const TcTile*)(base + o_tiles), (int)tc_tiles.size(),
+      launch_gemm_tc(dt, dm, (const TcTile*)(base + o_tiles), (const GemmSeg*)(base + o_segs),
+                     (const SegOps*)(base + o_segops), (int)tc_tiles.size(),
                      c.precision == TDMPS_TF32X3 ? 1 : c.precision == TDMPS_BF16 ? 2 : 0,
                      c.n_sm, c.tc_err(), c.st);
     if (!split_ids.empty())
-      launch_reduce_splits(dt, (const int*)(base + o_split), (int)split_ids.size(), c.st);
+      launch_reduce_splits(dt, (const GemmSeg*)(base + o_segs), (const int*)(base + o_split),
+                           (int)split_ids.size(), c.st);
     c.kend(kind, ev, flops, bytes);
   }
 };
@@ -678,13 +782,24 @@ static Inter plan_lstage(Context& c, const Env& E, const SiteT& ket, const Bond&
   }
   X.et = E.t.et;
   X.alloc(c.st, false);
-  for (int x = 0; x < (int)X.blocks.size(); ++x) {
-    const Inter::Blk& xb = X.blocks[x];
-    const Inter::Blk& eb = E.t.blocks[src[x].first];
-    int bet;
-    const void* bp = site_operand(c, ket, src[x].second, bet);
-    gb.task(X.ptr(x), X.et, xb.rows * xb.W, xb.cols, xb.cols, OP_N, E.t.et, OP_N, bet, false, 1.0);
-    gb.term(E.t.ptr(src[x].first), eb.cols, bp, xb.cols, eb.cols);
+  // the X blocks of one environment block (one per local state s') share
+  // that block as A: one task whose columns are the s' blocks side by side
+  for (int x0 = 0; x0 < (int)X.blocks.size();) {
+    int x1 = x0 + 1;
+    while (x1 < (int)X.blocks.size() && x1 - x0 < 4 && src[x1].first == src[x0].first) ++x1;
+    const Inter::Blk& eb = E.t.blocks[src[x0].first];
+    void* Cs[4];
+    int ld[4];
+    const void* bp[4];
+    int bet = 0;
+    for (int x = x0; x < x1; ++x) {
+      Cs[x - x0] = X.ptr(x);
+      ld[x - x0] = X.blocks[x].cols;
+      bp[x - x0] = site_operand(c, ket, src[x].second, bet);
+    }
+    gb.task_seg(1, x1 - x0, Cs, ld, ld, eb.rows * eb.W, X.et, OP_N, E.t.et, OP_N, bet, false, 1.0);
+    gb.term_seg(E.t.ptr(src[x0].first), eb.cols, bp, ld, eb.cols);
+    x0 = x1;
   }
   return X;
 }
@@ -809,44 +924,93 @@ struct ByRow {
   int hi(int rg) const { return rg + 1 < (int)start.size() ? start[rg + 1] : 0; }
 };
 
+// Output blocks of a site tensor grouped by their right sector (sb) or by
+// their row group (r), in groups of at most four (the segments one GEMM task
+// holds).  A plain tensor has at most four blocks per group, one per local
+// state; a two-site tensor, whose rows are fused (sector, state) pairs, can
+// have more, which then form several groups.
+static std::vector<std::vector<int>> blocks_by(const SiteT& out, bool by_right) {
+  int n = 0;
+  for (const auto& b : out.blocks) n = std::max(n, (by_right ? b.sb : b.r) + 1);
+  std::vector<std::vector<int>> g((size_t)n);
+  for (int o = 0; o < (int)out.blocks.size(); ++o)
+    g[(size_t)(by_right ? out.blocks[o].sb : out.blocks[o].r)].push_back(o);
+  std::vector<std::vector<int>> out4;
+  for (auto& v : g)
+    for (size_t i = 0; i < v.size(); i += 4)
+      out4.emplace_back(v.begin() + i, v.begin() + std::min(v.size(), i + 4));
+  return out4;
+}
+
+// The blocks (a, s) -> b of one right sector b share every R block: one
+// task whose rows are those blocks stacked (row segments).
 static void plan_rstage(const std::vector<LocalTerm>& ts, SiteT& out, GemmBatch& gb) {
   std::vector<ByRow> rby(ts.size());
   for (size_t t = 0; t < ts.size(); ++t) rby[t].build(ts[t].E->t);
-  for (int o = 0; o < (int)out.blocks.size(); ++o) {
-    const SiteT::Blk& ob = out.blocks[o];
-    gb.task(out.ptr(o), 0, ob.rows, ob.cols, ob.cols, OP_N, ts[0].Y->et, OP_T, ts[0].E->t.et,
-            false, 1.0);
+  for (const auto& grp : blocks_by(out, true)) {
+    if (grp.empty()) continue;
+    const int sb = out.blocks[grp[0]].sb, n = (int)grp.size();
+    void* Cs[4];
+    int ldc[4], rows[4];
+    for (int i = 0; i < n; ++i) {
+      Cs[i] = out.ptr(grp[i]);
+      ldc[i] = out.blocks[grp[i]].cols;
+      rows[i] = out.blocks[grp[i]].rows;
+    }
+    gb.task_seg(0, n, Cs, ldc, rows, out.blocks[grp[0]].cols, 0, OP_N, ts[0].Y->et, OP_T,
+                ts[0].E->t.et, false, 1.0);
     for (size_t t = 0; t < ts.size(); ++t) {
       const Inter& R = ts[t].E->t;
-      for (int q = rby[t].lo(ob.sb); q < rby[t].hi(ob.sb); ++q) {
+      for (int q = rby[t].lo(sb); q < rby[t].hi(sb); ++q) {
         const int rb = rby[t].list[q];
         const Inter::Blk& r = R.blocks[rb];
-        int y = ts[t].Y->find(ob.r, ob.sig, r.g, r.k);
-        if (y < 0) continue;
-        int K = r.W * r.cols;
-        gb.term(ts[t].Y->ptr(y), K, R.ptr(rb), K, K, ts[t].coef, ts[t].coef_dev);
+        const int K = r.W * r.cols;
+        const void* ap[4];
+        int lda[4];
+        for (int i = 0; i < n; ++i) {
+          const SiteT::Blk& ob = out.blocks[grp[i]];
+          const int y = ts[t].Y->find(ob.r, ob.sig, r.g, r.k);
+          ap[i] = y < 0 ? nullptr : ts[t].Y->ptr(y);
+          lda[i] = K;
+        }
+        gb.term_seg(R.ptr(rb), K, ap, lda, K, ts[t].coef, ts[t].coef_dev);
       }
     }
   }
 }
 
 // out[a][s][b] = sum_t coef_t sum_{w, a'} L_t[a][w][a'] Zp_t[b][s][w][a']
+// The blocks (a, s) of one left sector a share every L block: one task
+// whose columns are those blocks side by side (column segments).
 static void plan_lcontract(const std::vector<LocalTerm>& ts, SiteT& out, GemmBatch& gb) {
   std::vector<ByRow> lby(ts.size());
   for (size_t t = 0; t < ts.size(); ++t) lby[t].build(ts[t].E->t);
-  for (int o = 0; o < (int)out.blocks.size(); ++o) {
-    const SiteT::Blk& ob = out.blocks[o];
-    gb.task(out.ptr(o), 0, ob.rows, ob.cols, ob.cols, OP_N, ts[0].E->t.et, OP_T, ts[0].Y->et,
-            false, 1.0);
+  for (const auto& grp : blocks_by(out, false)) {
+    if (grp.empty()) continue;
+    const int r0 = out.blocks[grp[0]].r, n = (int)grp.size();
+    void* Cs[4];
+    int ldc[4];
+    for (int i = 0; i < n; ++i) {
+      Cs[i] = out.ptr(grp[i]);
+      ldc[i] = out.blocks[grp[i]].cols;
+    }
+    gb.task_seg(1, n, Cs, ldc, ldc, out.blocks[grp[0]].rows, 0, OP_N, ts[0].E->t.et, OP_T,
+                ts[0].Y->et, false, 1.0);
     for (size_t t = 0; t < ts.size(); ++t) {
       const Inter& Lt = ts[t].E->t;
-      for (int q = lby[t].lo(ob.r); q < lby[t].hi(ob.r); ++q) {
+      for (int q = lby[t].lo(r0); q < lby[t].hi(r0); ++q) {
         const int lb = lby[t].list[q];
         const Inter::Blk& l = Lt.blocks[lb];
-        int z = ts[t].Y->find(ob.sb, ob.sig, l.g, l.k);
-        if (z < 0) continue;
-        int K = l.W * l.cols;
-        gb.term(Lt.ptr(lb), K, ts[t].Y->ptr(z), K, K, ts[t].coef, ts[t].coef_dev);
+        const int K = l.W * l.cols;
+        const void* bp[4];
+        int ldb[4];
+        for (int i = 0; i < n; ++i) {
+          const SiteT::Blk& ob = out.blocks[grp[i]];
+          const int z = ts[t].Y->find(ob.sb, ob.sig, l.g, l.k);
+          bp[i] = z < 0 ? nullptr : ts[t].Y->ptr(z);
+          ldb[i] = K;
+        }
+        gb.term_seg(Lt.ptr(lb), K, bp, ldb, K, ts[t].coef, ts[t].coef_dev);
       }
     }
   }
@@ -948,13 +1112,25 @@ static Inter plan_r1(Context& c, const Env& R, const SiteT& A, const Bond& ket_l
   }
   Z.et = R.t.et;
   Z.alloc(c.st, false);
-  for (int z = 0; z < (int)Z.blocks.size(); ++z) {
-    const Inter::Blk& zb = Z.blocks[z];
-    const Inter::Blk& r = R.t.blocks[src[z].first];
-    int bet;
-    const void* bp = site_operand(c, A, src[z].second, bet);
-    gb.task(Z.ptr(z), Z.et, zb.rows * zb.W, zb.cols, zb.cols, OP_N, R.t.et, OP_T, bet, false, 1.0);
-    gb.term(R.t.ptr(src[z].first), r.cols, bp, r.cols, r.cols);
+  // the Z blocks of one environment block (one per local state s') share
+  // that block as A: one task with the s' blocks as column segments
+  for (int z0 = 0; z0 < (int)Z.blocks.size();) {
+    int z1 = z0 + 1;
+    while (z1 < (int)Z.blocks.size() && z1 - z0 < 4 && src[z1].first == src[z0].first) ++z1;
+    const Inter::Blk& r = R.t.blocks[src[z0].first];
+    void* Cs[4];
+    int ldc[4], ldb[4];
+    const void* bp[4];
+    int bet = 0;
+    for (int z = z0; z < z1; ++z) {
+      Cs[z - z0] = Z.ptr(z);
+      ldc[z - z0] = Z.blocks[z].cols;
+      ldb[z - z0] = r.cols;
+      bp[z - z0] = site_operand(c, A, src[z].second, bet);
+    }
+    gb.task_seg(1, z1 - z0, Cs, ldc, ldc, r.rows * r.W, Z.et, OP_N, R.t.et, OP_T, bet, false, 1.0);
+    gb.term_seg(R.t.ptr(src[z0].first), r.cols, bp, ldb, r.cols);
+    z0 = z1;
   }
   return Z;
 }

@@ -40,6 +40,28 @@ struct GemmTask {
   // (element type tc, task orientation) and launch_reduce_splits adds the
   // slices in split order into C, so results do not depend on timing
   void* part;
+  // tensor-core path: 1 + index of this task's GemmSeg (0: not segmented)
+  int seg1;
+};
+
+// A segmented task: the rows (dim 0) or the columns (dim 1) of C are the
+// concatenation of n <= 4 output blocks, segment s covering [off[s], off[s+1])
+// with its own output pointer C[s] and leading dimension ldc[s]; in every
+// term the operand along that dimension (A for rows, B for columns) is one
+// block per segment, listed in the term's SegOps (GemmTerm::pad = its index;
+// a null block is zero), while the other operand is shared.  Used for the
+// local states that share one operand of a contraction (e.g. the four
+// output blocks (a, s) -> b of one right sector b), so that the shared
+// operand is streamed once for all of them.
+struct GemmSeg {
+  int dim, n;
+  int off[5];
+  void* C[4];
+  int ldc[4];
+};
+struct SegOps {
+  const void* p[4];
+  int ld[4];
 };
 
 // Sparse MPO-tensor application.  Output block Y[r][w][c] (rows r, W_out
@@ -106,14 +128,16 @@ struct TcTile {
 // operands complex float, C complex double (tc = 0) or float (tc = 1);
 // persistent: min(ntiles, n_sm) CTAs walk the tile list
 void launch_gemm_tc(const GemmTask* d_tasks, const GemmTerm* d_terms, const TcTile* d_tiles,
-                    int ntiles, int mode, int n_sm, int* d_err, cudaStream_t st);
+                    const GemmSeg* d_segs, const SegOps* d_segops, int ntiles, int mode, int n_sm,
+                    int* d_err, cudaStream_t st);
 int tc_smem_bytes(int mode);
 int tc_tile_m();
 int tc_tile_n();
 int tc_stage_k();   // complex K per staged tile
 // C of each listed split task = sum over s in order of its part slices
 // (+ C when beta); d_ids: indices into d_tasks
-void launch_reduce_splits(const GemmTask* d_tasks, const int* d_ids, int n, cudaStream_t st);
+void launch_reduce_splits(const GemmTask* d_tasks, const GemmSeg* d_segs, const int* d_ids, int n,
+                          cudaStream_t st);
 // out (float2) = in (double2), n elements
 void launch_to_float(const double2* in, float2* out, size_t n, cudaStream_t st);
 // out (double2) = in (element type et), n elements

@@ -247,6 +247,8 @@ template <int MODE>   // 0: TF32, 1: 3xTF32, 2: BF16
 __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_tc(const GemmTask* __restrict__ tasks,
                                                          const GemmTerm* __restrict__ terms,
                                                          const TcTile* __restrict__ tiles,
+                                                         const GemmSeg* __restrict__ segs,
+                                                         const SegOps* __restrict__ segops,
                                                          int ntiles, int* err) {
   extern __shared__ __align__(1024) unsigned char sm[];
   constexpr int NSPLIT = MODE == 1 ? 2 : 1;   // operand tiles per stage (hi[, lo])
@@ -295,6 +297,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_tc(const GemmTask* __res
     Item cur{(int)blockIdx.x, 0, 0, 0};
     TcTile tl{};
     int tM = 0, topA = 0, topB = 0, tend = 0;
+    // segmented task: this thread's A row (dim 0) or B column (dim 1) lies in
+    // segment sseg at local index sidx; -1: not segmented
+    int sdim = -1, sseg = 0, sidx = 0;
     const void* gA = nullptr;
     const void* gB = nullptr;
     int gK = 0, glda = 0, gldb = 0;
@@ -306,6 +311,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_tc(const GemmTask* __res
       gK = g.K;
       glda = g.lda;
       gldb = g.ldb;
+      if (sdim >= 0) {   // this thread's segment block (null: zeros)
+        const SegOps& so = segops[g.pad];
+        if (sdim == 0) { gA = so.p[sseg]; glda = so.ld[sseg]; }
+        else { gB = so.p[sseg]; gldb = so.ld[sseg]; }
+      }
       gsc = g.fscale;
       if (g.scale_ptr) {   // a device coefficient: formed in FP64 by one lane
         float sx = 0.f, sy = 0.f;
@@ -326,6 +336,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_tc(const GemmTask* __res
       topA = t.opA;
       topB = t.opB;
       tend = t.term_end;
+      sdim = -1;
+      if (t.seg1) {
+        const GemmSeg& sg = segs[t.seg1 - 1];
+        sdim = sg.dim;
+        const int x = sdim == 0 ? tl.m0 + ra_r : tl.n0 + rb_n;
+        sseg = 0;
+        while (sseg + 1 < sg.n && x >= sg.off[sseg + 1]) ++sseg;
+        sidx = x - sg.off[sseg];
+      }
       cur.s = 0;
       cur.e = tl.e0;
       cur.k0 = tl.k0;
@@ -343,20 +362,24 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_tc(const GemmTask* __res
         pd.sc = gsc;
         const uint32_t base = smem_u32(raw + r * RAW_BYTES);
         if (pd.arow) {
+          const int row = sdim == 0 ? sidx : tl.m0 + ra_r;
+          const bool live = gA != nullptr;
 #pragma unroll
           for (int j = 0; j < TC_AEL; ++j) {
             const int k = cur.k0 + ra_k + j;
-            const bool in = k < gK;
-            const void* src = in ? (const void*)el_addr(gA, glda, topA, tl.m0 + ra_r, k) : gA;
+            const bool in = live && k < gK;
+            const void* src = in ? (const void*)el_addr(gA, glda, topA, row, k) : (const void*)tasks;
             cp_async8(base + (j * TC_PROD + p) * 8, src, in ? 8u : 0u);
           }
         }
         if (pd.bcol) {
+          const int col = sdim == 1 ? sidx : tl.n0 + rb_n;
+          const bool live = gB != nullptr;
 #pragma unroll
           for (int j = 0; j < TC_BEL; ++j) {
             const int k = cur.k0 + rb_k + j;
-            const bool in = k < gK;
-            const void* src = in ? (const void*)el_addr(gB, gldb, topB, k, tl.n0 + rb_n) : gB;
+            const bool in = live && k < gK;
+            const void* src = in ? (const void*)el_addr(gB, gldb, topB, k, col) : (const void*)tasks;
             cp_async8(base + ((TC_AEL + j) * TC_PROD + p) * 8, src, in ? 8u : 0u);
           }
         }
@@ -542,6 +565,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_tc(const GemmTask* __res
       }
       const int row = tl.m0 + 32 * ew + lane;
       const int nchunk = (2 * tl.ncols + 31) / 32;
+      // segmented output: the segment of this lane's row (dim 0), or of each
+      // column (dim 1)
+      const GemmSeg* sg = t.seg1 ? &segs[t.seg1 - 1] : nullptr;
+      int rseg = 0;
+      if (sg && sg->dim == 0)
+        while (rseg + 1 < sg->n && row >= sg->off[rseg + 1]) ++rseg;
       for (int c = 0; c < nchunk; ++c) {
         float vv[32];
         if (have) {
@@ -569,14 +598,25 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_tc(const GemmTask* __res
             else ((float2*)t.part)[o] = make_float2(ore, oim);
             continue;
           }
-          const size_t o = t.ct ? (size_t)col * t.ldc + row : (size_t)row * t.ldc + col;
+          void* Cb = t.C;
+          size_t o;
+          if (sg) {
+            int s = rseg;
+            if (sg->dim == 1)
+              while (s + 1 < sg->n && col >= sg->off[s + 1]) ++s;
+            Cb = sg->C[s];
+            o = sg->dim == 0 ? (size_t)(row - sg->off[s]) * sg->ldc[s] + col
+                             : (size_t)row * sg->ldc[s] + (col - sg->off[s]);
+          } else {
+            o = t.ct ? (size_t)col * t.ldc + row : (size_t)row * t.ldc + col;
+          }
           if (t.tc == 0) {
-            double2* C = (double2*)t.C + o;
+            double2* C = (double2*)Cb + o;
             double2 out = make_double2((double)ore, (double)oim);
             if (t.beta) { out.x += C->x; out.y += C->y; }
             *C = out;
           } else {
-            float2* C = (float2*)t.C + o;
+            float2* C = (float2*)Cb + o;
             float2 out = make_float2(ore, oim);
             if (t.beta) { out.x += C->x; out.y += C->y; }
             *C = out;
@@ -598,12 +638,25 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_tc(const GemmTask* __res
 
 // C of a split task = sum of its part slices in split order (+ C when beta):
 // one CTA per task, the same summation order on every run
-__global__ void k_reduce_splits(const GemmTask* __restrict__ tasks, const int* __restrict__ ids) {
+__global__ void k_reduce_splits(const GemmTask* __restrict__ tasks,
+                                const GemmSeg* __restrict__ segs, const int* __restrict__ ids) {
   const GemmTask& t = tasks[ids[blockIdx.x]];
+  const GemmSeg* sg = t.seg1 ? &segs[t.seg1 - 1] : nullptr;
   const size_t mn = (size_t)t.M * t.N;
   for (size_t i = threadIdx.x; i < mn; i += blockDim.x) {
     const int r = (int)(i / t.N), c = (int)(i % t.N);
-    const size_t o = t.ct ? (size_t)c * t.ldc + r : (size_t)r * t.ldc + c;
+    void* Cb = t.C;
+    size_t o;
+    if (sg) {
+      const int x = sg->dim == 0 ? r : c;
+      int s = 0;
+      while (s + 1 < sg->n && x >= sg->off[s + 1]) ++s;
+      Cb = sg->C[s];
+      o = sg->dim == 0 ? (size_t)(r - sg->off[s]) * sg->ldc[s] + c
+                       : (size_t)r * sg->ldc[s] + (c - sg->off[s]);
+    } else {
+      o = t.ct ? (size_t)c * t.ldc + r : (size_t)r * t.ldc + c;
+    }
     if (t.tc == 0) {
       const double2* P = (const double2*)t.part;
       double2 s = P[i];
@@ -612,7 +665,7 @@ __global__ void k_reduce_splits(const GemmTask* __restrict__ tasks, const int* _
         s.x += x.x;
         s.y += x.y;
       }
-      double2* C = (double2*)t.C + o;
+      double2* C = (double2*)Cb + o;
       if (t.beta) { s.x += C->x; s.y += C->y; }
       *C = s;
     } else {
@@ -623,7 +676,7 @@ __global__ void k_reduce_splits(const GemmTask* __restrict__ tasks, const int* _
         s.x += x.x;
         s.y += x.y;
       }
-      float2* C = (float2*)t.C + o;
+      float2* C = (float2*)Cb + o;
       if (t.beta) { s.x += C->x; s.y += C->y; }
       *C = s;
     }
@@ -640,25 +693,27 @@ int tc_smem_bytes(int mode) {
 }
 
 void launch_gemm_tc(const GemmTask* d_tasks, const GemmTerm* d_terms, const TcTile* d_tiles,
-                    int ntiles, int mode, int n_sm, int* d_err, cudaStream_t st) {
+                    const GemmSeg* d_segs, const SegOps* d_segops, int ntiles, int mode, int n_sm,
+                    int* d_err, cudaStream_t st) {
   if (ntiles <= 0) return;
   const int grid = ntiles < n_sm ? ntiles : n_sm;
   const int smem = tc_smem_bytes(mode);
   if (mode == 2) {
     set_smem_limit((const void*)k_gemm_tc<2>, smem);
-    k_gemm_tc<2><<<grid, TC_THREADS, smem, st>>>(d_tasks, d_terms, d_tiles, ntiles, d_err);
+    k_gemm_tc<2><<<grid, TC_THREADS, smem, st>>>(d_tasks, d_terms, d_tiles, d_segs, d_segops, ntiles, d_err);
   } else if (mode == 0) {
     set_smem_limit((const void*)k_gemm_tc<0>, smem);
-    k_gemm_tc<0><<<grid, TC_THREADS, smem, st>>>(d_tasks, d_terms, d_tiles, ntiles, d_err);
+    k_gemm_tc<0><<<grid, TC_THREADS, smem, st>>>(d_tasks, d_terms, d_tiles, d_segs, d_segops, ntiles, d_err);
   } else {
     set_smem_limit((const void*)k_gemm_tc<1>, smem);
-    k_gemm_tc<1><<<grid, TC_THREADS, smem, st>>>(d_tasks, d_terms, d_tiles, ntiles, d_err);
+    k_gemm_tc<1><<<grid, TC_THREADS, smem, st>>>(d_tasks, d_terms, d_tiles, d_segs, d_segops, ntiles, d_err);
   }
 }
 
-void launch_reduce_splits(const GemmTask* d_tasks, const int* d_ids, int n, cudaStream_t st) {
+void launch_reduce_splits(const GemmTask* d_tasks, const GemmSeg* d_segs, const int* d_ids, int n,
+                          cudaStream_t st) {
   if (n <= 0) return;
-  k_reduce_splits<<<n, 256, 0, st>>>(d_tasks, d_ids);
+  k_reduce_splits<<<n, 256, 0, st>>>(d_tasks, d_segs, d_ids);
 }
 
 int tc_stage_k() { return TC_BKC; }
