@@ -472,6 +472,11 @@ def main():
             out.free()
 
     state = td.mps_import(ctx, A, q)
+    if args.mode == "apply":
+        # the gauge every state produced by the library is in (a fit or an
+        # integrator step returns it right-canonical), so that the timed
+        # application is the one an integrator makes; no truncation at D
+        td.compress(ctx, state, D, 0.0)
     for _ in range(args.warmup):
         step(state)
     torch.cuda.synchronize()

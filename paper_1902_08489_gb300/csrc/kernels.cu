@@ -407,10 +407,19 @@ __global__ void __launch_bounds__(SVD_THREADS) k_svd(const FactTask* __restrict_
     V[e] = make_double2((e % n) == (e / n) ? 1.0 : 0.0, 0.0);
   __syncthreads();
   {
+    // Frobenius norm: warp partial sums added in warp order (the same
+    // rounding on every run, so the negligibility threshold is reproducible)
+    __shared__ double part[32];
     double s2 = 0.0;
     for (size_t e = threadIdx.x; e < (size_t)m * n; e += blockDim.x) s2 += cabs2(A[e]);
     s2 = warp_sum(s2);
-    if (lane == 0) atomicAdd(&fro2, s2);
+    if (lane == 0) part[warp] = s2;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double f = 0.0;
+      for (int w = 0; w < nwarp; ++w) f += part[w];
+      fro2 = f;
+    }
   }
   __syncthreads();
   const double negl = 1e-26 * fro2;

@@ -192,10 +192,11 @@ __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;\n" : : "n"(N) : "memory");
 }
 
-// TF32 head of x, rounded to nearest (ties away from zero) on the integer
-// ALU: the tensor pipe reads the top 19 bits of a 32-bit operand, so adding
-// half a unit of the 13 dropped bits to the magnitude and clearing them is
-// the rounding; the tail x - head is exact in FP32 and the pipe truncates it.
+// x rounded to TF32 (nearest, ties away from zero) on the integer ALU: the
+// tensor pipe reads the top 19 bits of a 32-bit operand, so adding half a
+// unit of the 13 dropped bits to the magnitude and clearing them is the
+// rounding.  The split of split TF32 is head = tf32(x), tail = tf32(x - head)
+// (x - head is exact in FP32).
 __device__ __forceinline__ float tf32_head(float x) {
   return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
 }
@@ -426,7 +427,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_tc(const GemmTask* __res
           const float2 hi = make_float2(tf32_head(a.x), tf32_head(a.y));
           *(float2*)(sA + canon_off(ra_r, 2 * kk)) = hi;
           if (MODE == 1)
-            *(float2*)(sA + A_BYTES + canon_off(ra_r, 2 * kk)) = make_float2(a.x - hi.x, a.y - hi.y);
+            *(float2*)(sA + A_BYTES + canon_off(ra_r, 2 * kk)) =
+                make_float2(tf32_head(a.x - hi.x), tf32_head(a.y - hi.y));
         }
       }
       // B-tilde (K-major, rows = real N): column n -> rows 2n (br, -bi), 2n+1 (bi, br)
@@ -448,9 +450,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_tc(const GemmTask* __res
           *(float2*)(sB + canon_off(2 * rb_n + 1, 2 * kk)) = h1;
           if (MODE == 1) {
             *(float2*)(sB + B_BYTES + canon_off(2 * rb_n, 2 * kk)) =
-                make_float2(r0.x - h0.x, r0.y - h0.y);
+                make_float2(tf32_head(r0.x - h0.x), tf32_head(r0.y - h0.y));
             *(float2*)(sB + B_BYTES + canon_off(2 * rb_n + 1, 2 * kk)) =
-                make_float2(r1.x - h1.x, r1.y - h1.y);
+                make_float2(tf32_head(r1.x - h1.x), tf32_head(r1.y - h1.y));
           }
         }
       }
