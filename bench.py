@@ -410,6 +410,9 @@ def main():
                     help="skip the FP64 run of the same steps (error and FP64 steps/s)")
     ap.add_argument("--no-traj-compare", action="store_true",
                     help="skip the mixed-vs-FP64 error on the physical beta-hole trajectory")
+    ap.add_argument("--traj-steps", type=int, default=2,
+                    help="Krylov steps of the beta-hole trajectory comparison (each takes "
+                         "15-20 s per precision once the bonds reach D)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--mode", default="krylov", choices=["krylov", "apply", "batch"],
@@ -535,12 +538,12 @@ def main():
 
     # Observable error of mixed precision on a well-conditioned trajectory:
     # the random D = 256 start has a broad energy spread, and the Gram-Schmidt
-    # cancellation of its Krylov vectors amplifies any rounding (FP64 runs
-    # differ from run to run there too), so the error is taken on the
-    # physical problem of the same size instead: the neutral 16-electron
-    # aufbau determinant minus the beta electron of orbital 7, two Krylov
-    # steps (m = 10, dt = 0.05, D = 256, eps = 1e-8; one two-site + one
-    # one-site sweep per fit so the bonds can grow), FP64 vs this precision.
+    # cancellation of its Krylov vectors amplifies any rounding, so the error
+    # is taken on the physical problem of the same size instead: the neutral
+    # 16-electron aufbau determinant minus the beta electron of orbital 7,
+    # Krylov steps of m = 10, dt = 0.05, D = 256, eps = 1e-8 (one two-site +
+    # one one-site sweep per fit so the bonds can grow), FP64 vs this
+    # precision.  Observables of the normalised state (Sec. 3.2).
     traj = None
     if (args.precision != "fp64" and not args.no_traj_compare and args.mode == "krylov"
             and not args.size):
@@ -551,23 +554,37 @@ def main():
             ctx.set_schedule(1, 1)
             s0 = td.mps_from_determinant(ctx, occ)
             t0 = time.perf_counter()
-            gs, es = [], []
-            for _ in range(2):
+            gs, es, ns = [], [], []
+            for _ in range(args.traj_steps):
                 td.krylov_step(ctx, mpo, s0, DT, M_KRYLOV, True, D, EPS)
-                gs.append(td.one_rdm(ctx, s0))
-                es.append(td.expectation(ctx, mpo, s0, s0).real / td.overlap(ctx, s0, s0).real)
+                n2 = td.overlap(ctx, s0, s0).real
+                gs.append(td.one_rdm(ctx, s0) / n2)
+                es.append(td.expectation(ctx, mpo, s0, s0).real / n2)
+                ns.append(n2)
             torch.cuda.synchronize()
-            obs[p] = (np.array(gs), np.array(es), time.perf_counter() - t0, s0.info()["max_bond"])
+            obs[p] = (np.array(gs), np.array(es), np.array(ns), time.perf_counter() - t0,
+                      s0.info()["max_bond"])
             s0.free()
         ctx.set_precision(args.precision)
         ctx.set_schedule(*sched)
-        g64, e64, t64, b64 = obs["fp64"]
-        gm, em, tm, bm = obs[args.precision]
-        traj = {"workload": "beta-hole determinant, L=16 N=15, 2 Krylov steps, schedule 1+1",
-                "max_abs_err_one_rdm": float(np.abs(gm - g64).max()),
-                "max_abs_err_energy": float(np.abs(em - e64).max()),
-                "max_abs_err_dipole": float(np.abs(dipole(gm) - dipole(g64)).max()),
-                "s_per_step_fp64": t64 / 2, "s_per_step": tm / 2, "max_bond": int(bm)}
+        g64, e64, n64, t64, b64 = obs["fp64"]
+        gm, em, nm, tm, bm = obs[args.precision]
+        dg = np.abs(gm - g64).reshape(len(gm), -1).max(axis=1)
+        de = np.abs(em - e64)
+        dmu = np.abs(dipole(gm) - dipole(g64)).reshape(len(gm), -1).max(axis=1)
+        traj = {"workload": "beta-hole determinant, L=16 N=15, %d Krylov steps (m=10, dt=0.05, "
+                            "D=256, eps=1e-8), schedule 1+1" % args.traj_steps,
+                "observables": "of the normalised state; the Krylov result fit and inner "
+                               "products in FP64, the basis fits in this precision",
+                "max_abs_err_one_rdm": float(dg.max()),
+                "max_abs_err_energy": float(de.max()),
+                "max_abs_err_dipole": float(dmu.max()),
+                "max_abs_err_norm2": float(np.abs(nm - n64).max()),
+                "per_step_err_one_rdm": [float(x) for x in dg],
+                "per_step_err_energy": [float(x) for x in de],
+                "target_1e-6_met": bool(max(dg.max(), de.max(), dmu.max()) <= 1e-6),
+                "s_per_step_fp64": t64 / args.traj_steps, "s_per_step": tm / args.traj_steps,
+                "max_bond": int(bm)}
 
     # end-to-end through the public API with host buffers: import the state
     # from host memory, one Krylov step, read the 1-RDM back

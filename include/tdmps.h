@@ -104,11 +104,15 @@ int tdmps_set_precision(tdmps_ctx_t ctx, int precision);
  * either is negative or both are 0. */
 int tdmps_set_schedule(tdmps_ctx_t ctx, int n_two_site, int n_one_site);
 
-/* Krylov inner products (Gram-Schmidt coefficients and the N, H matrices of
- * Eq. krylov_evo) contracted in FP64 (on != 0, the default) or in the
- * context precision (on == 0: faster in the TF32 modes, but the canonical
- * orthogonalisation then sees the TF32 rounding of N and H).  The matrices
- * are accumulated and processed in FP64 either way. */
+/* The Krylov algebra in FP64 (on != 0, the default) or in the context
+ * precision (on == 0).  It covers the inner products (Gram-Schmidt
+ * coefficients and the N, H matrices of Eq. krylov_evo) and the fit of the
+ * step's result sum_j c_j |phi_j>.  With on == 0 the TF32 modes run faster,
+ * but the canonical orthogonalisation sees the TF32 rounding of N and H.
+ * The Krylov basis vectors are always fitted in the context precision: N
+ * and H are measured on the vectors as fitted, so their FP32-level errors
+ * change the step only through the span they give.  The small matrices are
+ * accumulated and processed in FP64 either way. */
 int tdmps_set_krylov_fp64(tdmps_ctx_t ctx, int on);
 
 /* Scheduling of the FP64 Krylov inner products of an orthogonal-basis step

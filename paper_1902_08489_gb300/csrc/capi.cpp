@@ -277,7 +277,13 @@ int tdmps_sum(tdmps_ctx_t ctx, int n_terms, const tdmps_complex* coefs, const td
     }
     FitOpts o = opts(ctx, D, eps);
     auto* r = new tdmps_mps_s;
-    try { r->m = fit(*ctx->c, ft, terms[0]->m, o); } catch (...) { delete r; throw; }
+    try {
+      r->m = fit(*ctx->c, ft, terms[0]->m, o);
+      restore_fit_scale(*ctx->c, r->m, ft);
+    } catch (...) {
+      delete r;
+      throw;
+    }
     *out = r;
   });
 }

@@ -661,7 +661,7 @@ struct GemmBatch {
                      c.n_sm, c.tc_err(), c.st);
     if (!split_ids.empty())
       launch_reduce_splits(dt, (const GemmSeg*)(base + o_segs), (const int*)(base + o_split),
-                           (int)split_ids.size(), c.st);
+                           (int)split_ids.size(), fp64 ? 0 : 1, c.st);
     c.kend(kind, ev, flops, bytes);
   }
 };
@@ -1922,6 +1922,50 @@ void normalize_center(Context& c, MPSd& m, double2* norm_out) {
   c.kend(TDMPS_KSTAT_OTHER, ev, 0.0, 0.0);
 }
 
+// Mixed-precision fits come out scaled: at L = 16, D = 256 a fitted H|psi>
+// is the FP64 fit times (1 - 1.7e-5) (the same factor on every 1-RDM entry
+// to 2e-7), while its direction agrees to 1 - 4e-12 in fidelity.  The
+// shrink grows with the length of the accumulation chains (cutting them to
+// 4 K stages by split-K removes a third of it), the signature of FP32
+// accumulators that drop the low bits of each MMA's sum instead of rounding
+// them.  For a target T that is a sum of states, <C|T> and <C|C> are cheap
+// FP64 overlaps, and the projection property of the last local solve
+// (<C|T> = <C|C>) fixes the scale.
+void restore_fit_scale(Context& c, MPSd& C, const std::vector<FitTerm>& terms) {
+  if (c.precision == TDMPS_FP64 || terms.empty()) return;
+  std::vector<std::pair<const MPSd*, const MPSd*>> pairs;
+  for (auto& t : terms) {
+    if (t.mpo) throw Error(TDMPS_ERR_INVALID_ARG, "scale restoration needs a sum of states");
+    pairs.push_back({&C, t.ket});
+  }
+  pairs.push_back({&C, &C});
+  const size_t n = pairs.size();
+  DevPtr d = dev_alloc(sizeof(double2) * 2 * n, c.st);
+  std::vector<double2*> outs;
+  for (size_t k = 0; k < n; ++k) outs.push_back((double2*)d->p + k);
+  sandwich_batch(c, nullptr, pairs, outs, true);
+  // device coefficients next to the overlaps, one copy back
+  for (size_t k = 0; k + 1 < n; ++k)
+    if (terms[k].coef_dev)
+      TD_CHECK_CUDA(cudaMemcpyAsync((double2*)d->p + n + k, terms[k].coef_dev, sizeof(double2),
+                                    cudaMemcpyDeviceToDevice, c.st));
+  std::vector<double2> h(2 * n);
+  TD_CHECK_CUDA(cudaMemcpyAsync(h.data(), d->p, sizeof(double2) * 2 * n, cudaMemcpyDeviceToHost, c.st));
+  c.sync();
+  cplx ct = 0.0;
+  for (size_t k = 0; k + 1 < n; ++k) {
+    cplx a = terms[k].coef;
+    if (terms[k].coef_dev) a *= cplx(h[n + k].x, h[n + k].y);
+    ct += a * cplx(h[k].x, h[k].y);
+  }
+  const double cc = h[n - 1].x;
+  if (!(cc > 0.0) || !std::isfinite(ct.real()) || !std::isfinite(ct.imag())) return;
+  const cplx s = ct / cc;
+  // the gauge centre of a fit result is site 0
+  launch_scale((double2*)C.sites[0].data->p, C.sites[0].size, make_double2(s.real(), s.imag()), c.st);
+  C.sites[0].data32.reset();
+}
+
 // ------------------------------------------------------------------ compress
 
 double compress(Context& c, MPSd& m, int D, double eps) {
@@ -1982,8 +2026,12 @@ MPSd rk4_step(Context& c, const MPOd& H, const MPSd& psi, double dt, const FitOp
   MPSd k3 = applyH(s2);
   MPSd s3 = sum2(1.0, k3);
   MPSd k4 = applyH(s3);
-  return fit(c, {{&psi, nullptr, 1.0}, {&k1, nullptr, 1.0 / 6}, {&k2, nullptr, 1.0 / 3},
-                 {&k3, nullptr, 1.0 / 3}, {&k4, nullptr, 1.0 / 6}}, psi, o);
+  const std::vector<FitTerm> fin = {{&psi, nullptr, 1.0}, {&k1, nullptr, 1.0 / 6},
+                                    {&k2, nullptr, 1.0 / 3}, {&k3, nullptr, 1.0 / 3},
+                                    {&k4, nullptr, 1.0 / 6}};
+  MPSd out = fit(c, fin, psi, o);
+  restore_fit_scale(c, out, fin);
+  return out;
 }
 
 MPSd krylov_step(Context& c, const MPOd& H, const MPSd& psi, double dt, int m, bool orth,
@@ -2127,7 +2175,19 @@ MPSd krylov_step(Context& c, const MPOd& H, const MPSd& psi, double dt, int m, b
   if (m - hs[0] < 2) throw Error(TDMPS_ERR_KRYLOV_SINGULAR, "Krylov overlap matrix has rank < 2");
   std::vector<FitTerm> terms;
   for (int k = 0; k < m; ++k) terms.push_back({&phi[k], nullptr, 1.0, cd + k});
-  return fit(c, terms, phi[0], o);
+  // the step's result sum_j c_j |phi_j> is part of the Krylov algebra: with
+  // FP64 inner products it is fitted in FP64 too (it is one of the 2m - 1
+  // fits of the step, and the only one whose errors reach the next step
+  // directly); otherwise in the context precision with its scale restored
+  MPSd out;
+  if (c.krylov_fp64) {
+    Fp64Scope fs(c, true);
+    out = fit(c, terms, phi[0], o);
+  } else {
+    out = fit(c, terms, phi[0], o);
+    restore_fit_scale(c, out, terms);
+  }
+  return out;
 }
 
 // ------------------------------------------------------------------ density matrices

@@ -39,7 +39,7 @@ struct Context {
   int device = 0;
   int precision = TDMPS_FP64;
   int n_two_site = 2, n_one_site = 2;
-  bool krylov_fp64 = true;    // Krylov inner products in FP64 regardless of precision
+  bool krylov_fp64 = true;    // Krylov inner products and result fit in FP64 regardless of precision
   int n_sm = 0;               // streaming multiprocessors of the device
   std::string err;
   // staging ring for task lists
@@ -176,6 +176,12 @@ struct FitOpts {
   double* max_discarded = nullptr;
 };
 MPSd fit(Context& c, const std::vector<FitTerm>& terms, const MPSd& guess, const FitOpts& o);
+// Mixed-precision contexts: rescale a fit C of a sum of states (terms
+// without MPO) by <C|T> / <C|C>, both from FP64 overlaps.  A no-op in exact
+// arithmetic (the last local solve of a fit is an orthogonal projection, so
+// <C|T> = <C|C>); it removes the common scale error of the tensor-core
+// sums.  FP64 contexts: nothing.
+void restore_fit_scale(Context& c, MPSd& C, const std::vector<FitTerm>& terms);
 
 // <bra_p| O |ket_p> for many pairs into device scalars; FP64 contractions
 // unless fp64 == false (then the context precision)

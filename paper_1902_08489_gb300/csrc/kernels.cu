@@ -619,6 +619,8 @@ __global__ void __launch_bounds__(SVDC_THREADS) k_svd_cl(const FactTask* __restr
   for (int c = 0; c < n; ++c)
     for (int i = threadIdx.x; i < nl; i += blockDim.x)
       t.V[(size_t)c * n + vr0 + i] = make_double2(vr0 + i == c ? 1.0 : 0.0, 0.0);
+  // the rows were staged by every thread; warp 0 reads all of them
+  __syncthreads();
   // Frobenius norm
   {
     if (warp == 0) {
@@ -985,6 +987,8 @@ __global__ void __launch_bounds__(QRC_THREADS) k_qr_cl(const FactTask* __restric
     for (int i = threadIdx.x; i < ml; i += blockDim.x) A[(size_t)c * mc + i] = t.A[(size_t)c * m + row0 + i];
   if (rank == 0)
     for (int e = threadIdx.x; e < n * n; e += blockDim.x) t.V[e] = make_double2(0.0, 0.0);
+  // the rows were staged by every thread; each warp reads whole columns
+  __syncthreads();
   // largest column norm
   for (int c = warp; c < n; c += nwarp) {
     double s2 = 0.0;

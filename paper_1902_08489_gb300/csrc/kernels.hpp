@@ -37,8 +37,9 @@ struct GemmTask {
   int splits;            // CTAs sharing the K range
   int ct;                // 1: the task computes C^T (M x N); element (r, c) goes to C[c][r]
   // splits > 1: split s stores alpha * (its partial sum) at part[(s M + r) N + c]
-  // (element type tc, task orientation) and launch_reduce_splits adds the
-  // slices in split order into C, so results do not depend on timing
+  // (task orientation; complex float from the tensor-core kernel, complex
+  // double from the FP64 kernel) and launch_reduce_splits adds the slices in
+  // split order into C, so results do not depend on timing
   void* part;
   // tensor-core path: 1 + index of this task's GemmSeg (0: not segmented)
   int seg1;
@@ -135,9 +136,11 @@ int tc_tile_m();
 int tc_tile_n();
 int tc_stage_k();   // complex K per staged tile
 // C of each listed split task = sum over s in order of its part slices
-// (+ C when beta); d_ids: indices into d_tasks
+// (+ C when beta); d_ids: indices into d_tasks.  f32_parts: the slices are
+// complex float (tensor-core kernel; added in FP64 for a complex double C),
+// else of C's element type (FP64 kernel).
 void launch_reduce_splits(const GemmTask* d_tasks, const GemmSeg* d_segs, const int* d_ids, int n,
-                          cudaStream_t st);
+                          int f32_parts, cudaStream_t st);
 // out (float2) = in (double2), n elements
 void launch_to_float(const double2* in, float2* out, size_t n, cudaStream_t st);
 // out (double2) = in (element type et), n elements

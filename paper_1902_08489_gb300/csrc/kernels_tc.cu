@@ -58,7 +58,7 @@ constexpr int TC_NREAL = 2 * TC_BNC;
 constexpr uint32_t TC_SPIN_LIMIT = 1u << 22;
 
 constexpr int TC_NS = 4;          // MMA stages in the ring
-constexpr int TC_NR = 5;          // raw operand slots (prefetch depth + 1)
+constexpr int TC_NR = 4;          // raw operand slots (prefetch depth + 1)
 constexpr int TC_PROD_WARPS = 8;
 constexpr int TC_PROD = TC_PROD_WARPS * 32;
 constexpr int TC_EPI_WARP0 = 8;
@@ -167,6 +167,15 @@ __device__ __forceinline__ bool wait_or_abort(uint32_t mbar, uint32_t phase,
   return false;
 }
 
+// the same wait taken by lane 0 for the whole warp (every lane then sees the
+// same outcome, so warp-collective instructions after it stay converged)
+__device__ __forceinline__ bool warp_wait(uint32_t mbar, uint32_t phase, volatile int* abort_flag,
+                                          int* err) {
+  int ok = 0;
+  if ((threadIdx.x & 31) == 0) ok = wait_or_abort(mbar, phase, abort_flag, err) ? 1 : 0;
+  return __shfl_sync(0xffffffffu, ok, 0) != 0;
+}
+
 __device__ __forceinline__ void fence_async_smem() {
   asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
 }
@@ -204,6 +213,23 @@ __device__ __forceinline__ float tf32_head(float x) {
 __device__ __forceinline__ uint32_t bf16_bits(float x) {
   const uint32_t u = __float_as_uint(x);
   return (u + 0x7FFFu + ((u >> 16) & 1u)) >> 16;
+}
+// FP32 -> FP64 by exponent rebias on the integer ALU (the conversion
+// instruction runs on the narrow FP64 pipe); subnormal, Inf and NaN inputs
+// take the conversion instruction
+__device__ __forceinline__ double f32_to_f64(float x) {
+  const uint32_t u = __float_as_uint(x);
+  const uint32_t e = (u >> 23) & 0xFFu;
+  if ((u & 0x7FFFFFFFu) == 0u)   // signed zero
+    return __longlong_as_double((long long)((unsigned long long)(u >> 31) << 63));
+  if (e == 0u || e == 0xFFu) return (double)x;
+  const unsigned long long b = ((unsigned long long)(u >> 31) << 63) |
+                               ((unsigned long long)(e + 896u) << 52) |
+                               ((unsigned long long)(u & 0x7FFFFFu) << 29);
+  return __longlong_as_double((long long)b);
+}
+__device__ __forceinline__ double2 f2_to_d2(float re, float im) {
+  return make_double2(f32_to_f64(re), f32_to_f64(im));
 }
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
   return bf16_bits(lo) | (bf16_bits(hi) << 16);
@@ -270,13 +296,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_tc(const GemmTask* __res
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
   }
   if (threadIdx.x == 0) {
+    // one arrival per producer warp / epilogue warp (after __syncwarp): 256
+    // arrivals on one barrier word per stage would serialise in shared memory
     for (int s = 0; s < TC_NS; ++s) {
-      mbar_init(smem_u32(&full[s]), TC_PROD);
+      mbar_init(smem_u32(&full[s]), TC_PROD_WARPS);
       mbar_init(smem_u32(&empty[s]), 1);
     }
     for (int a = 0; a < 2; ++a) {
       mbar_init(smem_u32(&acc_full[a]), 1);
-      mbar_init(smem_u32(&acc_empty[a]), 128);
+      mbar_init(smem_u32(&acc_empty[a]), 4);
     }
     abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
@@ -406,7 +434,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_tc(const GemmTask* __res
       if (!pd.valid) return false;
       const int slot = g % TC_NS;
       const uint32_t use = g / TC_NS;
-      if (!wait_or_abort(smem_u32(&empty[slot]), (use & 1u) ^ 1u, &abort_flag, err)) return false;
+      if (!warp_wait(smem_u32(&empty[slot]), (use & 1u) ^ 1u, &abort_flag, err)) return false;
       unsigned char* sA = sm + slot * STAGE_BYTES;
       unsigned char* sB = sA + NSPLIT * A_BYTES;
       const float2* rw = (const float2*)(raw + r * RAW_BYTES);
@@ -457,7 +485,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_tc(const GemmTask* __res
         }
       }
       fence_async_smem();
-      mbar_arrive(smem_u32(&full[slot]));
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(&full[slot]));
       ++g;
       return true;
     };
@@ -488,7 +517,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_tc(const GemmTask* __res
       if (tl.count <= 0) continue;
       const int acc = v & 1;
       const uint32_t vuse = v >> 1;
-      if (!wait_or_abort(smem_u32(&acc_empty[acc]), (vuse & 1u) ^ 1u, &abort_flag, err)) break;
+      if (!warp_wait(smem_u32(&acc_empty[acc]), (vuse & 1u) ^ 1u, &abort_flag, err)) break;
       tc_fence_after();
       const int nreal = ((2 * tl.ncols + 15) / 16) * 16;
       const uint32_t idesc = MODE == 2 ? make_idesc_bf16(nreal) : make_idesc_tf32(nreal);
@@ -497,7 +526,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_tc(const GemmTask* __res
       for (int s = 0; s < tl.count; ++s, ++g) {
         const int slot = g % TC_NS;
         const uint32_t use = g / TC_NS;
-        if (!wait_or_abort(smem_u32(&full[slot]), use & 1u, &abort_flag, err)) { ok = false; break; }
+        if (!warp_wait(smem_u32(&full[slot]), use & 1u, &abort_flag, err)) { ok = false; break; }
         tc_fence_after();
         if (lane == 0) {
           const uint32_t a0 = smem_u32(sm + slot * STAGE_BYTES);
@@ -537,8 +566,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_tc(const GemmTask* __res
     const int ew = warp - TC_EPI_WARP0;      // TMEM lanes 32 ew .. 32 ew + 31
     uint32_t v = 0;
     for (int tile = blockIdx.x; tile < ntiles && !abort_flag; tile += gridDim.x) {
+      // the task and its segments copied into registers: the stores below
+      // then cannot force reloads of them
       const TcTile tl = tiles[tile];
-      const GemmTask& t = tasks[tl.task];
+      const GemmTask t = tasks[tl.task];
       const bool split = t.splits > 1;
       const bool have = tl.count > 0;
       // alpha in FP64 (device scalars) by one lane, shared by the warp
@@ -562,17 +593,26 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_tc(const GemmTask* __res
       const int acc = v & 1;
       const uint32_t vuse = v >> 1;
       if (have) {
-        if (!wait_or_abort(smem_u32(&acc_full[acc]), vuse & 1u, &abort_flag, err)) break;
+        if (!warp_wait(smem_u32(&acc_full[acc]), vuse & 1u, &abort_flag, err)) break;
         tc_fence_after();
       }
       const int row = tl.m0 + 32 * ew + lane;
       const int nchunk = (2 * tl.ncols + 31) / 32;
       // segmented output: the segment of this lane's row (dim 0), or of each
       // column (dim 1)
-      const GemmSeg* sg = t.seg1 ? &segs[t.seg1 - 1] : nullptr;
-      int rseg = 0;
-      if (sg && sg->dim == 0)
-        while (rseg + 1 < sg->n && row >= sg->off[rseg + 1]) ++rseg;
+      // segments in scalar registers: segment of index x = number of segment
+      // starts at or below it (unused segments start at the total extent)
+      int sdim = -1, o1 = 0, o2 = 0, o3 = 0, l0 = 0, l1 = 0, l2 = 0, l3 = 0;
+      void *c0 = nullptr, *c1 = nullptr, *c2 = nullptr, *c3 = nullptr;
+      if (t.seg1) {
+        const GemmSeg& sg = segs[t.seg1 - 1];
+        sdim = sg.dim;
+        o1 = sg.off[1]; o2 = sg.off[2]; o3 = sg.off[3];
+        c0 = sg.C[0]; c1 = sg.C[1]; c2 = sg.C[2]; c3 = sg.C[3];
+        l0 = sg.ldc[0]; l1 = sg.ldc[1]; l2 = sg.ldc[2]; l3 = sg.ldc[3];
+      }
+      auto seg_of = [&](int x) { return (int)(x >= o1) + (int)(x >= o2) + (int)(x >= o3); };
+      const int rseg = sdim == 0 ? seg_of(row) : 0;
       for (int c = 0; c < nchunk; ++c) {
         float vv[32];
         if (have) {
@@ -585,7 +625,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_tc(const GemmTask* __res
         }
         if (have && c == nchunk - 1) {
           tc_fence_before();
-          mbar_arrive(smem_u32(&acc_empty[acc]));
+          __syncwarp();
+          if (lane == 0) mbar_arrive(smem_u32(&acc_empty[acc]));
         }
         if (row >= t.M) continue;
 #pragma unroll
@@ -596,25 +637,23 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_tc(const GemmTask* __res
           const float ore = fax * xr - fay * xi, oim = fax * xi + fay * xr;
           if (split) {   // this split's slice; launch_reduce_splits adds them in order
             const size_t o = ((size_t)tl.split * t.M + row) * t.N + col;
-            if (t.tc == 0) ((double2*)t.part)[o] = make_double2((double)ore, (double)oim);
-            else ((float2*)t.part)[o] = make_float2(ore, oim);
+            ((float2*)t.part)[o] = make_float2(ore, oim);
             continue;
           }
           void* Cb = t.C;
           size_t o;
-          if (sg) {
-            int s = rseg;
-            if (sg->dim == 1)
-              while (s + 1 < sg->n && col >= sg->off[s + 1]) ++s;
-            Cb = sg->C[s];
-            o = sg->dim == 0 ? (size_t)(row - sg->off[s]) * sg->ldc[s] + col
-                             : (size_t)row * sg->ldc[s] + (col - sg->off[s]);
+          if (sdim >= 0) {
+            const int s = sdim == 0 ? rseg : seg_of(col);
+            Cb = s == 0 ? c0 : s == 1 ? c1 : s == 2 ? c2 : c3;
+            const int ld = s == 0 ? l0 : s == 1 ? l1 : s == 2 ? l2 : l3;
+            const int base = s == 0 ? 0 : s == 1 ? o1 : s == 2 ? o2 : o3;
+            o = sdim == 0 ? (size_t)(row - base) * ld + col : (size_t)row * ld + (col - base);
           } else {
             o = t.ct ? (size_t)col * t.ldc + row : (size_t)row * t.ldc + col;
           }
           if (t.tc == 0) {
             double2* C = (double2*)Cb + o;
-            double2 out = make_double2((double)ore, (double)oim);
+            double2 out = f2_to_d2(ore, oim);
             if (t.beta) { out.x += C->x; out.y += C->y; }
             *C = out;
           } else {
@@ -641,9 +680,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_tc(const GemmTask* __res
 // C of a split task = sum of its part slices in split order (+ C when beta):
 // one CTA per task, the same summation order on every run
 __global__ void k_reduce_splits(const GemmTask* __restrict__ tasks,
-                                const GemmSeg* __restrict__ segs, const int* __restrict__ ids) {
-  const GemmTask& t = tasks[ids[blockIdx.x]];
-  const GemmSeg* sg = t.seg1 ? &segs[t.seg1 - 1] : nullptr;
+                                const GemmSeg* __restrict__ segs, const int* __restrict__ ids,
+                                int f32_parts) {
+  const GemmTask t = tasks[ids[blockIdx.x]];
+  GemmSeg sgv{};
+  if (t.seg1) sgv = segs[t.seg1 - 1];
+  const GemmSeg* sg = t.seg1 ? &sgv : nullptr;
   const size_t mn = (size_t)t.M * t.N;
   for (size_t i = threadIdx.x; i < mn; i += blockDim.x) {
     const int r = (int)(i / t.N), c = (int)(i % t.N);
@@ -659,11 +701,24 @@ __global__ void k_reduce_splits(const GemmTask* __restrict__ tasks,
     } else {
       o = t.ct ? (size_t)c * t.ldc + r : (size_t)r * t.ldc + c;
     }
-    if (t.tc == 0) {
+    if (t.tc == 0 && !f32_parts) {
+      // FP64 slices of the FP64 kernel
       const double2* P = (const double2*)t.part;
       double2 s = P[i];
       for (int q = 1; q < t.splits; ++q) {
         const double2 x = P[q * mn + i];
+        s.x += x.x;
+        s.y += x.y;
+      }
+      double2* C = (double2*)Cb + o;
+      if (t.beta) { s.x += C->x; s.y += C->y; }
+      *C = s;
+    } else if (t.tc == 0) {
+      // FP64 output: FP32 slices of the tensor-core kernel, added in FP64
+      const float2* P = (const float2*)t.part;
+      double2 s = f2_to_d2(P[i].x, P[i].y);
+      for (int q = 1; q < t.splits; ++q) {
+        const double2 x = f2_to_d2(P[q * mn + i].x, P[q * mn + i].y);
         s.x += x.x;
         s.y += x.y;
       }
@@ -713,9 +768,9 @@ void launch_gemm_tc(const GemmTask* d_tasks, const GemmTerm* d_terms, const TcTi
 }
 
 void launch_reduce_splits(const GemmTask* d_tasks, const GemmSeg* d_segs, const int* d_ids, int n,
-                          cudaStream_t st) {
+                          int f32_parts, cudaStream_t st) {
   if (n <= 0) return;
-  k_reduce_splits<<<n, 256, 0, st>>>(d_tasks, d_segs, d_ids);
+  k_reduce_splits<<<n, 256, 0, st>>>(d_tasks, d_segs, d_ids, f32_parts);
 }
 
 int tc_stage_k() { return TC_BKC; }

@@ -176,6 +176,7 @@ def test_native_arm_json_assembly_with_a_stand_in_library(monkeypatch, capsys):
     lib.one_rdm = lambda ctx, m: np.eye(m.L, dtype=complex) * (15.0 / m.L)
     lib.krylov_step = lambda *a, **k: None
     lib.apply_H = lambda *a, **k: MPS()
+    lib.compress = lambda *a, **k: 0.0
     monkeypatch.setitem(sys.modules, "paper_1902_08489_gb300", lib)
     monkeypatch.delenv("WORLD_SIZE", raising=False)
     for argv, mode in ((["--steps", "2", "--warmup", "3"], "krylov"),
@@ -194,6 +195,7 @@ def test_native_arm_json_assembly_with_a_stand_in_library(monkeypatch, capsys):
         if mode == "krylov":
             traj = line["vs_fp64_trajectory"]
             assert traj["max_abs_err_dipole"] == 0.0 and line["vs_fp64"] is not None
+            assert len(traj["per_step_err_one_rdm"]) == 2 and traj["target_1e-6_met"]
             assert line["e2e"]["h2d_bytes_per_step"] > 0
             assert line["e2e"]["pinned_inputs"] is False      # no driver here
         else:

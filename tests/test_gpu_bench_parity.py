@@ -26,7 +26,11 @@ order agree to ~1e-9 there, not 1e-10; that step is bounded by 1e-8 and the
 strict 1e-10 comparison runs on the same configuration at m = 4
 (cond(N) = 2e3).
 Mixed precision: the observables target is 1e-6; where the split-TF32 run
-misses it the test is marked xfail with the measured error.
+misses it the test is marked xfail with the measured error.  A fitted
+H|psi> in split TF32 is the FP64 fit times one common factor (the FP32
+tensor-core sums shrink it); its direction and the observables of the
+normalised state are checked against the target, and its scale is reported
+on its own.
 """
 import json
 import os
@@ -115,19 +119,42 @@ def test_apply_H_at_bench_size_matches_block_sparse_oracle(td, inputs, oracle_ap
     assert ec < TOL and eg < TOL
 
 
-MIXED_APPLY_GAMMA = 1e-6   # the benchmark spec mixed-precision target for observables
+MIXED_TARGET = 1e-6   # the benchmark spec mixed-precision target for observables
 
 
-def test_apply_H_at_bench_size_split_tf32_error(td, inputs, oracle_apply):
+@pytest.fixture(scope="module")
+def split_tf32_apply(td, inputs):
+    return _fit_apply(td, "tf32x3", inputs, 1)
+
+
+def test_apply_H_at_bench_size_split_tf32_direction(split_tf32_apply, oracle_apply):
+    # the 1-RDM of the normalised fitted state (the observable Sec. 3.2 reads
+    # from a wave function) and the fidelity: the direction of the mixed fit
     C, g_ref, _ = oracle_apply
-    G, g = _fit_apply(td, "tf32x3", inputs, 1)
+    G, g = split_tf32_apply
+    nG2, nC2 = ob.norm(G) ** 2, ob.norm(C) ** 2
+    err = _relmax(g / nG2, g_ref / nC2)
+    fid = abs(ob.overlap(G, C)) ** 2 / (nG2 * nC2)
+    print("split-TF32 apply_H at L=16 D=256: normalised 1-RDM max rel error %.3e, "
+          "1 - fidelity %.3e" % (err, 1.0 - fid))
+    assert 1.0 - fid < 1e-10
+    assert err < MIXED_TARGET
+
+
+def test_apply_H_at_bench_size_split_tf32_scale(split_tf32_apply, oracle_apply):
+    # the norm of a fitted H|psi>: the tensor-core FP32 sums shrink it by one
+    # common factor that FP64 overlaps cannot restore here (the target has an
+    # MPO); the integrators restore it on their final sums
+    C, g_ref, _ = oracle_apply
+    G, g = split_tf32_apply
+    scale = ob.norm(G) ** 2 / ob.norm(C) ** 2 - 1.0
     err = _relmax(g, g_ref)
-    fid = abs(ob.overlap(G, C)) / (ob.norm(G) * ob.norm(C))
-    print("split-TF32 apply_H at L=16 D=256: max rel 1-RDM error %.3e, 1 - fidelity %.3e"
-          % (err, 1.0 - fid))
+    print("split-TF32 apply_H at L=16 D=256: norm^2 ratio - 1 %.3e, raw 1-RDM error %.3e"
+          % (scale, err))
     assert err < 1e-2, "gross failure, not a precision effect"
-    if err >= MIXED_APPLY_GAMMA:
-        pytest.xfail("split-TF32 1-RDM error %.2e misses the 1e-6 target" % err)
+    if err >= MIXED_TARGET:
+        pytest.xfail("split-TF32 fitted H|psi> is scaled by %.2e (1-RDM error %.2e): misses "
+                     "the 1e-6 target" % (scale, err))
 
 
 def _krylov(td, prec, inputs, m):
@@ -191,8 +218,8 @@ def test_krylov_step_at_bench_size_split_tf32_error(td, inputs):
     got = _krylov(td, "tf32x3", inputs, 4)
     errs = _krylov_errors(got, gold)
     print("split-TF32 Krylov step m=4 at L=16 D=256 vs oracle:", errs)
-    worst = max(errs["energy"], errs["one_rdm"])
+    worst = max(errs["energy"], errs["one_rdm"], errs["norm2"])
     assert worst < 1e-2, "gross failure, not a precision effect"
-    if worst >= 1e-6:
+    if worst >= MIXED_TARGET:
         pytest.xfail("split-TF32 Krylov step observables error %.2e misses the 1e-6 target"
                      % worst)
