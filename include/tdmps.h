@@ -215,9 +215,46 @@ int tdmps_mps_free(tdmps_mps_t mps);
 int tdmps_apply_H(tdmps_ctx_t ctx, tdmps_mpo_t mpo, tdmps_mps_t in, tdmps_complex alpha,
                   int D, double eps, int n_sweeps, tdmps_mps_t* out);
 
-/* out ~ sum_k coefs[k] |terms[k]> (Eqs. sum_exact, add_min), guess terms[0]. */
+/* out ~ sum_k coefs[k] |terms[k]> (Eqs. sum_exact, add_min), guess terms[0].
+ * In the TF32/BF16 precisions the result is rescaled by <out|T>/<out|out>
+ * (T the exact sum; FP64 overlaps), which the projection property of the
+ * fit makes 1 in exact arithmetic and which removes the common shrink of
+ * the tensor-core sums. */
 int tdmps_sum(tdmps_ctx_t ctx, int n_terms, const tdmps_complex* coefs,
               const tdmps_mps_t* terms, int D, double eps, tdmps_mps_t* out);
+
+/* The adjoint of the energy with respect to the state (Sec. 2.2.1: the
+ * effective-Hamiltonian matvec of the local problem of Eq. add_min, applied
+ * to the state's own sites).  For E = <psi|H|psi> / <psi|psi>:
+ *     *energy = E,
+ *     site i of *grad = dE/dconj(A_i) = (H_i A_i - E N_i A_i) / <psi|psi>,
+ * where H_i A_i = sum L[a,w,a'] W[w,w',s,s'] A_i[a',s',b'] R[b,w',b'] with the
+ * environments of <psi|H|psi> left and right of site i, and N_i A_i the same
+ * with the identity operator (psi's gauge is not assumed).  A perturbation
+ * dA_i changes E by 2 Re sum conj(G_i) dA_i to first order.  *grad is a new
+ * handle with psi's bonds and block layout whose "sites" are the gradients
+ * (read them with tdmps_mps_export; it is no physical state).  FP64 in every
+ * context precision.  stride >= 1: right environments are kept at every
+ * stride-th bond and rebuilt in between when the left-to-right pass needs
+ * them (one extra right sweep; environment memory O(L/stride + stride)
+ * instead of O(L)); stride = 1 keeps all.  env_bytes_peak (may be NULL)
+ * receives the most device memory that environments held at once.
+ * Errors: INVALID_ARG (NULL argument, stride < 1, lengths differ),
+ * ZERO_STATE (psi = 0), CUDA. */
+int tdmps_energy_gradient(tdmps_ctx_t ctx, tdmps_mpo_t mpo, tdmps_mps_t psi, int stride,
+                          double* energy, tdmps_mps_t* grad, size_t* env_bytes_peak);
+
+/* E = <psi|H|psi> / <psi|psi> (real part; H is Hermitian), FP64 chains.
+ * Errors: INVALID_ARG, ZERO_STATE (psi = 0), CUDA. */
+int tdmps_energy(tdmps_ctx_t ctx, tdmps_mpo_t mpo, tdmps_mps_t psi, double* energy);
+
+/* The gradient of that energy with respect to the integrals of Eq. hamil
+ * (E is linear in them): dE_dh[i*L + j] = Re gamma_ij / <psi|psi> and
+ * dE_deri[((i*L + j)*L + k)*L + l] = Re Gamma_ijkl / (2 <psi|psi>), gamma and
+ * Gamma as in tdmps_one_rdm and tdmps_two_rdm (chemist order); dE/de0 = 1.
+ * Either output may be NULL (not both).  Host arrays of L^2 and L^4 doubles.
+ * Errors: INVALID_ARG, ZERO_STATE, CUDA. */
+int tdmps_integral_gradient(tdmps_ctx_t ctx, tdmps_mps_t psi, double* dE_dh, double* dE_deri);
 
 /* <bra|ket> (the contraction of two chains of Eq. mps). */
 int tdmps_overlap(tdmps_ctx_t ctx, tdmps_mps_t bra, tdmps_mps_t ket, tdmps_complex* out);

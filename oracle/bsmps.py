@@ -49,8 +49,11 @@ full-CI Hamiltonian of oracle.fci on the whole Fock space (L <= 4) and
 H|psi> on a sector (L = 6); sandwiches and overlaps equal contracted vectors;
 fits, sums, RK4 and Krylov steps equal oracle.mps and full CI (untruncated);
 the 1-RDM equals the full-CI one; the FLOP count of an overlap equals
-oracle.mps.overlap_flops.  Parity unpinned, as in oracle.mps: whether a
-truncated fit reaches the best truncated state.
+oracle.mps.overlap_flops; the energy gradient with respect to the site
+tensors equals the full-CI projection M_i^+ (H v - E v) / |v|^2 and central
+differences of the energy, and is orthogonal to its own site (E does not
+change under A_i -> (1 + t) A_i).  Parity unpinned, as in oracle.mps: whether
+a truncated fit reaches the best truncated state.
 """
 from __future__ import annotations
 
@@ -1049,3 +1052,42 @@ def coefficients(m: BMPS, occs) -> np.ndarray:
             q = qadd(q, SITE_Q[int(o)])
         out[n] = v[0, 0] if ok and v.shape == (1, 1) else 0.0
     return out
+
+
+# ---------------------------------------------------------------------------
+# gradient of the energy with respect to the site tensors
+# ---------------------------------------------------------------------------
+
+def energy_gradient(mpo: MPO, psi: BMPS):
+    """E = <psi|H|psi> / <psi|psi> and its derivative with respect to the
+    conjugated site tensors, site by site in the gauge psi is given in:
+
+        dE / d conj(A_i) = (H_i A_i - E N_i A_i) / <psi|psi>,
+
+    H_i A_i the one-site product of Eq. (add_min)'s local problem (left and
+    right environments of <psi|H|psi> around site i, here with bra = ket =
+    psi) and N_i A_i the same with the identity operator (the norm
+    environments; no orthogonality of the other sites is assumed).  <psi|H|psi>
+    is linear in A_i and in conj(A_i) separately, which is why its derivative
+    with respect to conj(A_i) is H_i A_i.  Returns (E, [one block dict per
+    site, blocks as in psi])."""
+    L = psi.L
+    ident = identity_mpo(L)
+    RH, RN = [None] * (L + 1), [None] * (L + 1)
+    RH[L] = right_boundary(psi.total)
+    RN[L] = right_boundary(psi.total)
+    for i in range(L - 1, -1, -1):
+        RH[i] = env_right(RH[i + 1], psi.sites[i], psi.sites[i], mpo.W[i])
+        RN[i] = env_right(RN[i + 1], psi.sites[i], psi.sites[i], ident.W[i])
+    num = complex(RH[0][((0, 0), (0, 0))][0, 0, 0])
+    nrm = RN[0][((0, 0), (0, 0))][0, 0, 0].real
+    E = num.real / nrm
+    LH, LN = left_boundary(), left_boundary()
+    grads = []
+    for i in range(L):
+        gh = local_one(LH, RH[i + 1], psi.sites[i], mpo.W[i], psi.bonds[i], psi.bonds[i + 1])
+        gn = local_one(LN, RN[i + 1], psi.sites[i], ident.W[i], psi.bonds[i], psi.bonds[i + 1])
+        grads.append({k: (gh[k] - E * gn[k]) / nrm for k in gh})
+        LH = env_left(LH, psi.sites[i], psi.sites[i], mpo.W[i])
+        LN = env_left(LN, psi.sites[i], psi.sites[i], ident.W[i])
+    return E, grads

@@ -72,6 +72,10 @@ _SIGS = {
     "tdmps_mps_copy": (I, [P, P, ctypes.POINTER(P)]),
     "tdmps_mps_free": (I, [P]),
     "tdmps_apply_H": (I, [P, P, P, Complex, I, D, I, ctypes.POINTER(P)]),
+    "tdmps_energy_gradient": (I, [P, P, P, I, ctypes.POINTER(D), ctypes.POINTER(P),
+                                  ctypes.POINTER(ctypes.c_size_t)]),
+    "tdmps_energy": (I, [P, P, P, ctypes.POINTER(D)]),
+    "tdmps_integral_gradient": (I, [P, P, P, P]),
     "tdmps_sum": (I, [P, I, P, P, I, D, ctypes.POINTER(P)]),
     "tdmps_overlap": (I, [P, P, P, ctypes.POINTER(Complex)]),
     "tdmps_overlap_noalloc": (I, [P, P, P, ctypes.POINTER(Complex)]),
@@ -297,6 +301,34 @@ def apply_H(ctx, mpo, mps, alpha=1.0, D=64, eps=0.0, n_sweeps=0) -> MPS:
     _check(lib().tdmps_apply_H(ctx.h, mpo.h, mps.h, Complex(a.real, a.imag), D, eps, n_sweeps,
                                ctypes.byref(out)), ctx)
     return MPS(ctx, out)
+
+
+def energy_gradient(ctx, mpo, mps, stride=1):
+    """(E, G, env_bytes_peak): E = <psi|H|psi>/<psi|psi> and G, an MPS-shaped
+    handle whose site i is dE/dconj(A_i) (read it with G.export())."""
+    out = ctypes.c_void_p()
+    e = ctypes.c_double()
+    peak = ctypes.c_size_t()
+    _check(lib().tdmps_energy_gradient(ctx.h, mpo.h, mps.h, stride, ctypes.byref(e),
+                                       ctypes.byref(out), ctypes.byref(peak)), ctx)
+    return e.value, MPS(ctx, out), peak.value
+
+
+def energy(ctx, mpo, mps) -> float:
+    """<psi|H|psi> / <psi|psi>."""
+    e = ctypes.c_double()
+    _check(lib().tdmps_energy(ctx.h, mpo.h, mps.h, ctypes.byref(e)), ctx)
+    return e.value
+
+
+def integral_gradient(ctx, mps, two_body=True):
+    """(dE/dh, dE/deri) of <psi|H|psi>/<psi|psi> (dE/deri None unless two_body)."""
+    L = mps.info()["L"]
+    dh = np.zeros((L, L))
+    de = np.zeros((L, L, L, L)) if two_body else None
+    _check(lib().tdmps_integral_gradient(ctx.h, mps.h, _ptr(dh),
+                                         _ptr(de) if two_body else None), ctx)
+    return dh, de
 
 
 def mps_sum(ctx, coefs, terms, D=64, eps=0.0) -> MPS:

@@ -265,6 +265,25 @@ int tdmps_apply_H(tdmps_ctx_t ctx, tdmps_mpo_t mpo, tdmps_mps_t in, tdmps_comple
   });
 }
 
+int tdmps_energy_gradient(tdmps_ctx_t ctx, tdmps_mpo_t mpo, tdmps_mps_t psi, int stride,
+                          double* energy, tdmps_mps_t* grad, size_t* env_bytes_peak) {
+  if (!ctx) return TDMPS_ERR_INVALID_ARG;
+  return guard(ctx, [&] {
+    need(mpo && psi && grad, "NULL argument");
+    need(mpo->m.L == psi->m.L, "MPO and MPS lengths differ");
+    need(stride >= 1, "stride must be >= 1");
+    ensure_uploaded(ctx, mpo);
+    auto* r = new tdmps_mps_s;
+    try {
+      r->m = energy_gradient(*ctx->c, mpo->m, psi->m, stride, energy, env_bytes_peak);
+    } catch (...) {
+      delete r;
+      throw;
+    }
+    *grad = r;
+  });
+}
+
 int tdmps_sum(tdmps_ctx_t ctx, int n_terms, const tdmps_complex* coefs, const tdmps_mps_t* terms,
               int D, double eps, tdmps_mps_t* out) {
   if (!ctx) return TDMPS_ERR_INVALID_ARG;
@@ -389,6 +408,38 @@ int tdmps_two_rdm(tdmps_ctx_t ctx, tdmps_mps_t psi, tdmps_complex* Gamma) {
     std::vector<cplx> g(L2 * L2);
     two_rdm(*ctx->c, psi->m, g.data());
     for (size_t i = 0; i < g.size(); ++i) Gamma[i] = {g[i].real(), g[i].imag()};
+  });
+}
+
+int tdmps_energy(tdmps_ctx_t ctx, tdmps_mpo_t mpo, tdmps_mps_t psi, double* energy) {
+  if (!ctx) return TDMPS_ERR_INVALID_ARG;
+  return guard(ctx, [&] {
+    need(mpo && psi && energy, "NULL argument");
+    need(mpo->m.L == psi->m.L, "MPO and MPS lengths differ");
+    ensure_uploaded(ctx, mpo);
+    const double n2 = sandwich(*ctx->c, nullptr, psi->m, psi->m).real();
+    if (!(n2 > 0.0)) throw Error(TDMPS_ERR_ZERO_STATE, "state has zero norm");
+    *energy = sandwich(*ctx->c, &mpo->m, psi->m, psi->m).real() / n2;
+  });
+}
+
+int tdmps_integral_gradient(tdmps_ctx_t ctx, tdmps_mps_t psi, double* dE_dh, double* dE_deri) {
+  if (!ctx) return TDMPS_ERR_INVALID_ARG;
+  return guard(ctx, [&] {
+    need(psi && (dE_dh || dE_deri), "NULL argument");
+    const double n2 = sandwich(*ctx->c, nullptr, psi->m, psi->m).real();
+    if (!(n2 > 0.0)) throw Error(TDMPS_ERR_ZERO_STATE, "state has zero norm");
+    const size_t L2 = (size_t)psi->m.L * psi->m.L;
+    if (dE_dh) {
+      std::vector<cplx> g(L2);
+      one_rdm(*ctx->c, psi->m, g.data());
+      for (size_t i = 0; i < L2; ++i) dE_dh[i] = g[i].real() / n2;
+    }
+    if (dE_deri) {
+      std::vector<cplx> g(L2 * L2);
+      two_rdm(*ctx->c, psi->m, g.data());
+      for (size_t i = 0; i < g.size(); ++i) dE_deri[i] = 0.5 * g[i].real() / n2;
+    }
   });
 }
 

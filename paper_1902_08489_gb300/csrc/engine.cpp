@@ -1914,6 +1914,118 @@ cplx sandwich(Context& c, const MPOd* mpo, const MPSd& bra, const MPSd& ket) {
   return cplx(h.x, h.y);
 }
 
+// ------------------------------------------------------------------ energy gradient
+
+// The adjoint of E = <psi|H|psi> / <psi|psi> with respect to the site tensors
+// (the effective-Hamiltonian matvec of Eq. add_min's local problem, applied
+// to psi's own site): dE/dconj(A_i) = (H_i A_i - E N_i A_i) / <psi|psi>.  H_i
+// A_i and N_i A_i are the one-site products L W A R with the environments of
+// <psi|H|psi> and <psi|psi> (bra = ket = psi, so no gauge is assumed).  The
+// two terms share every launch of a pass.  Right environments from site L
+// down; then a left-to-right pass forms the products site by site and
+// advances the left environments, which are dropped once used.  With stride
+// s > 1 only the right environments at bonds that are multiples of s (and L)
+// are kept: the pass rebuilds the others of one segment from the next kept
+// bond when it reaches it (one more right sweep in all, environment memory
+// O(L/s + s) instead of O(L)).
+MPSd energy_gradient(Context& c, const MPOd& H, const MPSd& psi, int stride, double* energy,
+                     size_t* env_bytes_peak) {
+  if (stride < 1) throw Error(TDMPS_ERR_INVALID_ARG, "stride must be >= 1");
+  if (H.L != psi.L) throw Error(TDMPS_ERR_INVALID_ARG, "MPO length differs from MPS");
+  Fp64Scope scope(c, true);
+  const int L = psi.L;
+  std::vector<TermState> ts(2);
+  ts[0].mpo = &H;
+  ts[1].mpo = &c.identity_mpo(L);
+  for (auto& t : ts) {
+    t.ket = &psi;
+    t.coef = 1.0;
+    t.coef_dev = nullptr;
+    t.LE.resize(L + 1);
+    t.RE.resize(L + 1);
+    t.LE[0] = env_left_boundary(c, psi, psi, *t.mpo);
+    t.RE[L] = env_right_boundary(c, psi, psi, *t.mpo);
+  }
+  auto kept = [&](int b) { return b == L || b % stride == 0; };
+  size_t live = 0, peak = 0;
+  auto env_bytes = [](const Env& e) { return e.t.size * e.t.esz(); };
+  auto note = [&](long long delta) {
+    live = (size_t)((long long)live + delta);
+    peak = std::max(peak, live);
+  };
+  for (auto& t : ts) note((long long)(env_bytes(t.LE[0]) + env_bytes(t.RE[L])));
+  // right environments RE[b] for b = hi - 1 down to lo from RE[hi]; those of
+  // bonds that are not kept are dropped once the next one is formed, unless
+  // keep_all (a segment rebuilt for the left-to-right pass)
+  auto right_sweep = [&](int hi, int lo, bool keep_all) {
+    for (int i = hi - 1; i >= lo; --i) {
+      right_env_step(c, ts, psi, i);
+      for (auto& t : ts) note((long long)env_bytes(t.RE[i]));
+      if (!keep_all && !kept(i + 1))
+        for (auto& t : ts) {
+          note(-(long long)env_bytes(t.RE[i + 1]));
+          t.RE[i + 1] = Env();
+        }
+    }
+  };
+  right_sweep(L, 0, false);
+  // E and <psi|psi> from the bond-0 environments (1 x 1 x 1 blocks)
+  DevPtr sc = dev_alloc(2 * sizeof(double2), c.st);
+  for (int k = 0; k < 2; ++k) {
+    const Env& e = ts[k].RE[0];
+    if (e.t.blocks.size() != 1) throw Error(TDMPS_ERR_SECTOR, "final environment is not a scalar");
+    launch_to_double(e.t.ptr(0), e.t.et, (double2*)sc->p + k, 1, c.st);
+  }
+  double2 hv[2];
+  TD_CHECK_CUDA(cudaMemcpyAsync(hv, sc->p, sizeof(hv), cudaMemcpyDeviceToHost, c.st));
+  c.sync();
+  const double nrm = hv[1].x;
+  if (!(nrm > 0.0)) throw Error(TDMPS_ERR_ZERO_STATE, "state has zero norm");
+  const double E = hv[0].x / nrm;
+  if (energy) *energy = E;
+  for (auto& t : ts) {
+    note(-(long long)env_bytes(t.RE[0]));
+    t.RE[0] = Env();
+  }
+  MPSd G;
+  G.L = L;
+  G.tot = psi.tot;
+  G.bonds = psi.bonds;
+  G.sites.resize(L);
+  for (int i = 0; i < L; ++i) {
+    if (ts[0].RE[i + 1].t.blocks.empty() && !kept(i + 1)) {
+      // rebuild the segment (i + 1 .. next kept bond - 1)
+      const int hi = std::min(L, ((i + 1) / stride + 1) * stride);
+      right_sweep(hi, i + 1, true);
+    }
+    std::vector<Inter> Y = left_stages(c, ts, i);
+    SiteT gh = make_site(RowGroups::from_bond(psi.bonds[i]), psi.bonds[i + 1], c.st, false);
+    SiteT gn = make_site(RowGroups::from_bond(psi.bonds[i]), psi.bonds[i + 1], c.st, false);
+    {
+      GemmBatch g(c);
+      plan_rstage({{&Y[0], &ts[0].RE[i + 1], 1.0, nullptr}}, gh, g);
+      plan_rstage({{&Y[1], &ts[1].RE[i + 1], 1.0, nullptr}}, gn, g);
+      g.run();
+    }
+    // G_i = (H_i A_i - E N_i A_i) / <psi|psi>
+    launch_axpby((double2*)gh.data->p, (const double2*)gn.data->p, gh.size,
+                 make_double2(1.0 / nrm, 0.0), make_double2(-E / nrm, 0.0), c.st);
+    G.sites[i] = std::move(gh);
+    if (i + 1 < L) {
+      left_env_step(c, ts, psi, i, Y);
+      for (auto& t : ts) note((long long)env_bytes(t.LE[i + 1]));
+    }
+    for (auto& t : ts) {
+      note(-(long long)(env_bytes(t.LE[i]) + env_bytes(t.RE[i + 1])));
+      t.LE[i] = Env();
+      t.RE[i + 1] = Env();
+    }
+  }
+  if (env_bytes_peak) *env_bytes_peak = peak;
+  c.sync();
+  return G;
+}
+
 void normalize_center(Context& c, MPSd& m, double2* norm_out) {
   cudaEvent_t ev;
   c.kbegin(TDMPS_KSTAT_OTHER, &ev);

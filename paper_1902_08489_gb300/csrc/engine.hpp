@@ -196,6 +196,13 @@ MPSd right_canonicalize(Context& c, const MPSd& m);
 double compress(Context& c, MPSd& m, int D, double eps);
 void normalize_center(Context& c, MPSd& m, double2* norm_out);
 
+// E = <psi|H|psi> / <psi|psi> and dE/dconj(A_i) = (H_i A_i - E N_i A_i) /
+// <psi|psi> for every site (H_i, N_i: one-site products with the
+// environments of <psi|H|psi> and <psi|psi>), in FP64, as an MPS with the
+// bonds of psi.  Right environments are kept every `stride` sites and the
+// others recomputed when the left-to-right pass needs them (1: all kept).
+MPSd energy_gradient(Context& c, const MPOd& H, const MPSd& psi, int stride, double* energy,
+                     size_t* env_bytes_peak = nullptr);
 MPSd rk4_step(Context& c, const MPOd& H, const MPSd& psi, double dt, const FitOpts& o);
 MPSd krylov_step(Context& c, const MPOd& H, const MPSd& psi, double dt, int m, bool orth,
                  const FitOpts& o);

@@ -375,6 +375,19 @@ void launch_scale(double2* x, size_t n, double2 a, cudaStream_t st) {
   k_scale<<<(unsigned)blocks, 256, 0, st>>>(x, n, a);
 }
 
+__global__ void k_axpby(double2* y, const double2* x, size_t n, double2 a, double2 b) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * blockDim.x)
+    y[i] = cadd(cmul(a, y[i]), cmul(b, x[i]));
+}
+
+void launch_axpby(double2* y, const double2* x, size_t n, double2 a, double2 b, cudaStream_t st) {
+  if (n == 0) return;
+  size_t blocks = (n + 255) / 256;
+  if (blocks > 152 * 32) blocks = 152 * 32;
+  k_axpby<<<(unsigned)blocks, 256, 0, st>>>(y, x, n, a, b);
+}
+
 // ------------------------------------------------------------------ Jacobi SVD
 
 // One-sided (Hestenes) Jacobi on the columns of a column-major m x n matrix

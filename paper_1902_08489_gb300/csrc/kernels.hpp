@@ -177,6 +177,8 @@ void launch_scalar_div_neg(const double2* num, const double2* den, double2* out,
 // norm of a buffer (sqrt of sum |x|^2) and scaling of it by 1/norm
 void launch_normalize(double2* x, size_t n, double2* d_norm_out, cudaStream_t st);
 void launch_scale(double2* x, size_t n, double2 a, cudaStream_t st);
+// y = a y + b x, n complex elements
+void launch_axpby(double2* y, const double2* x, size_t n, double2 a, double2 b, cudaStream_t st);
 void launch_trace_channels(const void* E, int rows, int nch, int cols, const void* R, int et,
                            double2* out, cudaStream_t st);
 

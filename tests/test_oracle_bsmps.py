@@ -203,3 +203,63 @@ def test_energy_of_determinant_is_slater_condon():
     H = fci.hamiltonian(I.h, I.eri, dets, 0.25)
     col = np.searchsorted(dets, np.uint64(fci.occupation_mask(occ)))
     assert abs(e - H[col, col]) < 1e-12
+
+
+def _energy(mpo, psi):
+    return ob.sandwich(mpo, psi, psi).real / ob.overlap(psi, psi).real
+
+
+def test_energy_gradient_equals_full_ci_projection():
+    # dE/dconj(A_i) = M_i^+ (H v - E v) / |v|^2 with M_i = dv/dA_i, the
+    # sector vector of the MPS differentiated by each entry of site i
+    # (columns by unit perturbation: v is linear in A_i), H the full-CI
+    # Hamiltonian of the sector
+    L = 4
+    I, sys_ = _sector_system(L, 4, 0, 12)
+    mpo = ob.hamiltonian_mpo(I.h, I.eri)
+    A, q = synth.random_mps(L, 4, 0, 8, seed=13)
+    psi = ob.from_dense(A, q)
+    E, G = ob.energy_gradient(mpo, psi)
+    v = sys_.vec(om.from_arrays(A, q))
+    Hv = sys_.H @ v
+    n2 = np.vdot(v, v).real
+    assert abs(E - np.vdot(v, Hv).real / n2) < 1e-12
+    r = (Hv - E * v) / n2
+    for i in range(L):
+        for k, blk in psi.sites[i].items():
+            for (a, b) in [(0, 0), (blk.shape[0] - 1, blk.shape[1] - 1)]:
+                # column of M_i: the state with A_i replaced by the unit
+                # tensor of entry (a, sigma, b) of this block
+                unit = psi.copy()
+                unit.sites[i] = {kk: np.zeros_like(x) for kk, x in unit.sites[i].items()}
+                unit.sites[i][k][a, b] = 1.0
+                col = sys_.vec(om.from_arrays(*ob.to_dense(unit)))
+                ref = np.vdot(col, r)
+                assert abs(G[i][k][a, b] - ref) < 1e-12 * max(1.0, abs(ref))
+
+
+def test_energy_gradient_finite_differences_and_scale_invariance():
+    L = 6
+    I = synth.make_integrals(L, seed=14)
+    mpo = ob.hamiltonian_mpo(I.h, I.eri, 0.1)
+    A, q = synth.random_mps(L, 5, 1, 12, seed=15)
+    psi = ob.from_dense(A, q)
+    E, G = ob.energy_gradient(mpo, psi)
+    rng = np.random.default_rng(16)
+    h = 1e-6
+    for i in (0, 2, L - 1):
+        keys = list(psi.sites[i].keys())
+        for _ in range(3):
+            k = keys[rng.integers(len(keys))]
+            a, b = rng.integers(psi.sites[i][k].shape[0]), rng.integers(psi.sites[i][k].shape[1])
+            for d in (1.0, 1j):
+                p, m = psi.copy(), psi.copy()
+                p.sites[i][k][a, b] += h * d
+                m.sites[i][k][a, b] -= h * d
+                fd = (_energy(mpo, p) - _energy(mpo, m)) / (2 * h)
+                # dE = 2 Re(conj(g) dz) for a real E of a complex z
+                assert abs(fd - 2 * (np.conj(G[i][k][a, b]) * d).real) < 1e-7
+    # E is invariant under A_i -> (1 + t) A_i: <A_i, dE/dconj(A_i)> = 0
+    for i in range(L):
+        s = sum(np.vdot(psi.sites[i][k], G[i][k]) for k in G[i])
+        assert abs(s) < 1e-12 * abs(E)
