@@ -612,6 +612,17 @@ struct GemmBatch {
       for (int q = 0; q < t.tiles_m * tn * t.splits; ++q) tile_task.push_back(id);
     }
     if (tile_task.empty()) return;
+    // the reduction of the split tasks in chunks of at most 4096 elements
+    // (one CTA each), so that a few large tasks still spread over the SMs
+    std::vector<int> red;
+    for (int id : split_ids) {
+      const int mn = tk[id].M * tk[id].N;
+      for (int b = 0; b < mn; b += 4096) {
+        red.push_back(id);
+        red.push_back(b);
+        red.push_back(std::min(mn, b + 4096));
+      }
+    }
     // partial-sum slices of the split tasks (freed in stream order after use)
     DevPtr part;
     if (part_elems) {
@@ -627,7 +638,7 @@ struct GemmBatch {
     auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
     const size_t o_terms = al(tk.size() * sizeof(GemmTask));
     const size_t o_split = o_terms + al(terms.size() * sizeof(GemmTerm));
-    const size_t o_segs = o_split + al(split_ids.size() * sizeof(int));
+    const size_t o_segs = o_split + al(red.size() * sizeof(int));
     const size_t o_segops = o_segs + al(segs.size() * sizeof(GemmSeg));
     const size_t o_tiles = o_segops + al(segops.size() * sizeof(SegOps));
     const size_t pk_bytes =
@@ -636,8 +647,7 @@ struct GemmBatch {
     pk.resize(pk_bytes);
     std::memcpy(pk.data(), tk.data(), tk.size() * sizeof(GemmTask));
     if (!terms.empty()) std::memcpy(pk.data() + o_terms, terms.data(), terms.size() * sizeof(GemmTerm));
-    if (!split_ids.empty())
-      std::memcpy(pk.data() + o_split, split_ids.data(), split_ids.size() * sizeof(int));
+    if (!red.empty()) std::memcpy(pk.data() + o_split, red.data(), red.size() * sizeof(int));
     if (!segs.empty()) std::memcpy(pk.data() + o_segs, segs.data(), segs.size() * sizeof(GemmSeg));
     if (!segops.empty())
       std::memcpy(pk.data() + o_segops, segops.data(), segops.size() * sizeof(SegOps));
@@ -659,9 +669,9 @@ struct GemmBatch {
                      (const SegOps*)(base + o_segops), (int)tc_tiles.size(),
                      c.precision == TDMPS_TF32X3 ? 1 : c.precision == TDMPS_BF16 ? 2 : 0,
                      c.n_sm, c.tc_err(), c.st);
-    if (!split_ids.empty())
+    if (!red.empty())
       launch_reduce_splits(dt, (const GemmSeg*)(base + o_segs), (const int*)(base + o_split),
-                           (int)split_ids.size(), fp64 ? 0 : 1, c.st);
+                           (int)(red.size() / 3), fp64 ? 0 : 1, c.st);
     c.kend(kind, ev, flops, bytes);
   }
 };
@@ -889,7 +899,8 @@ static Inter plan_wstage(Context& c, Inter&& X, const MPOd& m, int site, bool le
     }
     int64_t n = (int64_t)yb.rows * yb.W * yb.cols;
     if (n >= ((int64_t)1 << 31)) throw Error(TDMPS_ERR_INVALID_ARG, "MPO-stage block too large");
-    wb.work += n;
+    const int rpi = wstage_rows_per_item();
+    wb.work += (int64_t)((yb.rows + rpi - 1) / rpi) * yb.W * yb.cols;
     wb.bytes += (double)Y.esz() * n;
     // one real x complex multiply-add per non-zero W entry, row and column
     wb.flops += 4.0 * (double)nnz * yb.rows * yb.cols;

@@ -190,14 +190,21 @@ template <class T> struct WAcc;
 template <> struct WAcc<double2> { using R = double; };
 template <> struct WAcc<float2> { using R = float; };
 
+// One thread per (output channel w, column b) and group of up to WS_ROWS
+// rows a of a block: the CSR row of w (entries w_in, value) is walked once
+// and applied to all of those rows, so the entry loads, the loop control and
+// the index arithmetic are shared by WS_ROWS outputs; consecutive threads
+// take consecutive columns, so every X read and Y write is coalesced along b.
+constexpr int WS_ROWS = 4;
+
 template <class T>
 __global__ void __launch_bounds__(256) k_wstage(const WTask* __restrict__ tasks, int ntasks,
                                                 int64_t total, const int* __restrict__ rowptr,
                                                 const int* __restrict__ ent_w,
                                                 const typename WAcc<T>::R* __restrict__ ent_v) {
   using R = typename WAcc<T>::R;
-  // each CTA owns one contiguous range of the flat output index, so a
-  // thread finds its task once (binary search) and then only steps forward
+  // each CTA owns one contiguous range of the flat work index, so a thread
+  // finds its task once (binary search) and then only steps forward
   const int64_t per = (total + gridDim.x - 1) / gridDim.x;
   const int64_t beg = (int64_t)blockIdx.x * per;
   const int64_t end = beg + per < total ? beg + per : total;
@@ -213,33 +220,54 @@ __global__ void __launch_bounds__(256) k_wstage(const WTask* __restrict__ tasks,
   for (int64_t idx = beg + threadIdx.x; idx < end; idx += blockDim.x) {
     while (lo + 1 < ntasks && tasks[lo + 1].work_base <= idx) ++lo;
     const WTask& t = tasks[lo];
-    // 32-bit index split (a task holds fewer than 2^31 outputs): 64-bit
-    // division is a long instruction sequence and this stage is issue-bound
+    // 32-bit index split (a task holds fewer than 2^31 work items)
     const int loc = (int)(idx - t.work_base);
     const int cols = t.cols, wout = t.wout;
     const int rw = loc / cols;
     const int b = loc - rw * cols;
-    const int a = rw / wout;
-    const int w = rw - a * wout;
-    R ax = 0, ay = 0;
+    const int q = rw / wout;            // row group
+    const int w = rw - q * wout;
+    const int a0 = q * WS_ROWS;
+    const int nr = t.rows - a0 < WS_ROWS ? t.rows - a0 : WS_ROWS;
+    R ax[WS_ROWS], ay[WS_ROWS];
+#pragma unroll
+    for (int r = 0; r < WS_ROWS; ++r) ax[r] = ay[r] = 0;
     for (int s = 0; s < 4; ++s) {
       if (t.csr[s] < 0) continue;
       const int* rp = rowptr + t.csr[s];
-      const T* X = (const T*)t.X[s];
-      int win = t.win[s];
-      for (int e = rp[w]; e < rp[w + 1]; ++e) {
+      const int win = t.win[s];
+      const size_t rstride = (size_t)win * cols;
+      const T* X = (const T*)t.X[s] + (size_t)a0 * rstride + b;
+      const int e1 = rp[w + 1];
+      for (int e = rp[w]; e < e1; ++e) {
         const R v = ent_v[e];
-        T x = X[((size_t)a * win + ent_w[e]) * t.cols + b];
-        ax = fma(v, (R)x.x, ax);
-        ay = fma(v, (R)x.y, ay);
+        const T* xp = X + (size_t)ent_w[e] * cols;
+#pragma unroll
+        for (int r = 0; r < WS_ROWS; ++r) {
+          if (r < nr) {   // constant indices: the accumulators stay in registers
+            const T x = xp[r * rstride];
+            ax[r] = fma(v, (R)x.x, ax[r]);
+            ay[r] = fma(v, (R)x.y, ay[r]);
+          }
+        }
       }
     }
-    T* y = (T*)t.Y + ((size_t)a * t.wout + w) * t.cols + b;
-    if (t.beta) { ax += (R)y->x; ay += (R)y->y; }
-    y->x = ax;
-    y->y = ay;
+    const size_t ystride = (size_t)wout * cols;
+    T* y = (T*)t.Y + (size_t)a0 * ystride + (size_t)w * cols + b;
+#pragma unroll
+    for (int r = 0; r < WS_ROWS; ++r) {
+      if (r < nr) {
+        T* yr = y + r * ystride;
+        R ox = ax[r], oy = ay[r];
+        if (t.beta) { ox += (R)yr->x; oy += (R)yr->y; }
+        yr->x = ox;
+        yr->y = oy;
+      }
+    }
   }
 }
+
+int wstage_rows_per_item() { return WS_ROWS; }
 
 void launch_wstage(const WTask* d_tasks, int ntasks, int64_t total_work, const int* d_rowptr,
                    const int* d_ent_w, const double* d_ent_v, const float* d_ent_vf, int et,

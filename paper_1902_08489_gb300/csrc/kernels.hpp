@@ -111,6 +111,9 @@ void launch_gemm(const GemmTask* d_tasks, int ntasks, const GemmTerm* d_terms,
                  const int* d_tile_task, int ntiles, cudaStream_t st);
 // et: element type of X and Y (0 double2 with the FP64 values, 1 float2 with
 // the FP32 copy of the values)
+// rows a of a W-stage block that one work item covers (work per block:
+// ceil(rows / this) x wout x cols)
+int wstage_rows_per_item();
 void launch_wstage(const WTask* d_tasks, int ntasks, int64_t total_work, const int* d_rowptr,
                    const int* d_ent_w, const double* d_ent_v, const float* d_ent_vf, int et,
                    cudaStream_t st);
@@ -136,11 +139,12 @@ int tc_tile_m();
 int tc_tile_n();
 int tc_stage_k();   // complex K per staged tile
 // C of each listed split task = sum over s in order of its part slices
-// (+ C when beta); d_ids: indices into d_tasks.  f32_parts: the slices are
+// (+ C when beta); d_chunks: n triples (index into d_tasks, first element,
+// end element) of the task's flat M x N range, one CTA each.  f32_parts: the slices are
 // complex float (tensor-core kernel; added in FP64 for a complex double C),
 // else of C's element type (FP64 kernel).
-void launch_reduce_splits(const GemmTask* d_tasks, const GemmSeg* d_segs, const int* d_ids, int n,
-                          int f32_parts, cudaStream_t st);
+void launch_reduce_splits(const GemmTask* d_tasks, const GemmSeg* d_segs, const int* d_chunks,
+                          int n, int f32_parts, cudaStream_t st);
 // out (float2) = in (double2), n elements
 void launch_to_float(const double2* in, float2* out, size_t n, cudaStream_t st);
 // out (double2) = in (element type et), n elements

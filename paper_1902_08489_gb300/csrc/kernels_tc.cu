@@ -678,16 +678,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_tc(const GemmTask* __res
 }
 
 // C of a split task = sum of its part slices in split order (+ C when beta):
-// one CTA per task, the same summation order on every run
+// one CTA per chunk of a task's elements, the same summation order on every run
 __global__ void k_reduce_splits(const GemmTask* __restrict__ tasks,
-                                const GemmSeg* __restrict__ segs, const int* __restrict__ ids,
+                                const GemmSeg* __restrict__ segs, const int* __restrict__ chunks,
                                 int f32_parts) {
-  const GemmTask t = tasks[ids[blockIdx.x]];
+  const int* ch = chunks + 3 * blockIdx.x;
+  const GemmTask t = tasks[ch[0]];
   GemmSeg sgv{};
   if (t.seg1) sgv = segs[t.seg1 - 1];
   const GemmSeg* sg = t.seg1 ? &sgv : nullptr;
   const size_t mn = (size_t)t.M * t.N;
-  for (size_t i = threadIdx.x; i < mn; i += blockDim.x) {
+  for (size_t i = (size_t)ch[1] + threadIdx.x; i < (size_t)ch[2]; i += blockDim.x) {
     const int r = (int)(i / t.N), c = (int)(i % t.N);
     void* Cb = t.C;
     size_t o;
@@ -767,10 +768,10 @@ void launch_gemm_tc(const GemmTask* d_tasks, const GemmTerm* d_terms, const TcTi
   }
 }
 
-void launch_reduce_splits(const GemmTask* d_tasks, const GemmSeg* d_segs, const int* d_ids, int n,
-                          int f32_parts, cudaStream_t st) {
+void launch_reduce_splits(const GemmTask* d_tasks, const GemmSeg* d_segs, const int* d_chunks,
+                          int n, int f32_parts, cudaStream_t st) {
   if (n <= 0) return;
-  k_reduce_splits<<<n, 256, 0, st>>>(d_tasks, d_segs, d_ids, f32_parts);
+  k_reduce_splits<<<n, 256, 0, st>>>(d_tasks, d_segs, d_chunks, f32_parts);
 }
 
 int tc_stage_k() { return TC_BKC; }
