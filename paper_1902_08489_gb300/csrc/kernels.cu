@@ -195,7 +195,7 @@ template <> struct WAcc<float2> { using R = float; };
 // and applied to all of those rows, so the entry loads, the loop control and
 // the index arithmetic are shared by WS_ROWS outputs; consecutive threads
 // take consecutive columns, so every X read and Y write is coalesced along b.
-constexpr int WS_ROWS = 4;
+constexpr int WS_ROWS = 2;
 
 template <class T>
 __global__ void __launch_bounds__(256) k_wstage(const WTask* __restrict__ tasks, int ntasks,

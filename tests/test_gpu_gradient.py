@@ -172,3 +172,28 @@ def test_differentiation_workload_L12_D128_trajectory(td):
     assert abs(holes[-1].sum()) < 1e-8          # particle number is conserved
     assert worst <= 1e-6
     ctx.close()
+
+
+def test_integral_gradient_equals_full_ci_rdms_L8(td):
+    # dE/dh = Re gamma / <psi|psi>, dE/d(ij|kl) = Re Gamma / (2 <psi|psi>) against
+    # the full-CI density matrices of the contracted state (L = 8, 7 electrons)
+    from oracle import fci
+    from oracle import mps as om
+    L = 8
+    I = synth.make_integrals(L, seed=37)
+    A, q = synth.random_mps(L, 7, 1, 40, seed=38)
+    ctx = td.Context("tf32x3")          # the density matrices are FP64 in every precision
+    psi = td.mps_import(ctx, A, q)
+    dh, deri = td.integral_gradient(ctx, psi)
+    dets = fci.basis(L, 4, 3)
+    v = om.to_sector(om.from_arrays(A, q), dets)
+    n2 = np.vdot(v, v).real
+    g = fci.one_rdm(v, dets, L).real / n2
+    G = 0.5 * fci.two_rdm(v, dets, L).real / n2
+    e1, e2 = np.abs(dh - g).max(), np.abs(deri - G).max()
+    print("integral gradient L=8 vs full CI: dE/dh %.2e, dE/deri %.2e" % (e1, e2))
+    assert e1 < 1e-11 * np.abs(g).max() and e2 < 1e-11 * np.abs(G).max()
+    mpo = td.build_mpo(ctx, I.h, I.eri, n_elec=7)
+    H = fci.hamiltonian(I.h, I.eri, dets)
+    assert abs(td.energy(ctx, mpo, psi) - np.vdot(v, H @ v).real / n2) < 1e-11
+    ctx.close()
