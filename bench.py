@@ -421,6 +421,10 @@ def main():
                          "RK4 step of each of 64 uneven instances (L in {8..14}, "
                          "D in {32, 64, 128}) on worker streams")
     ap.add_argument("--workers", type=int, default=16, help="batch mode: worker streams")
+    ap.add_argument("--compare-precisions", action="store_true",
+                    help="apply mode: also run the fitted application in FP64, split TF32 "
+                         "and BF16 and report each one's time and its error against FP64 "
+                         "(fidelity, norm, 1-RDM of the normalised state)")
     ap.add_argument("--size", default=None,
                     help="apply/krylov modes: L,N,D of another workload (e.g. 32,23,512 for "
                          "the large active space: 64 Cholesky vectors and the localised "
@@ -586,6 +590,40 @@ def main():
                 "s_per_step_fp64": t64 / args.traj_steps, "s_per_step": tm / args.traj_steps,
                 "max_bond": int(bm)}
 
+    # the same application in every precision against FP64 (apply mode)
+    prec_cmp = None
+    if args.compare_precisions and args.mode == "apply":
+        res = {}
+        for p in ("fp64", "tf32x3", "bf16"):
+            ctx.set_precision(p)
+            for rep in range(2):          # the first call carries one-time setup
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                out = td.apply_H(ctx, mpo, state, -1j * DT, D, EPS)
+                torch.cuda.synchronize()
+                dt_s = time.perf_counter() - t0
+                if rep == 0:
+                    out.free()
+            res[p] = (out, dt_s)
+        ctx.set_precision("fp64")
+        ref = res["fp64"][0]
+        n_ref = td.overlap(ctx, ref, ref).real
+        g_ref = td.one_rdm(ctx, ref) / n_ref
+        prec_cmp = {"fp64": {"s_per_apply": res["fp64"][1]}}
+        for p in ("tf32x3", "bf16"):
+            o = res[p][0]
+            n_o = td.overlap(ctx, o, o).real
+            x = td.overlap(ctx, ref, o)
+            prec_cmp[p] = {"s_per_apply": res[p][1],
+                           "speedup_vs_fp64": res["fp64"][1] / res[p][1],
+                           "one_minus_fidelity": float(1.0 - abs(x) ** 2 / (n_ref * n_o)),
+                           "norm2_ratio_minus_1": float(n_o / n_ref - 1.0),
+                           "max_abs_err_one_rdm_normalised":
+                               float(np.abs(td.one_rdm(ctx, o) / n_o - g_ref).max())}
+        for p in res:
+            res[p][0].free()
+        ctx.set_precision(args.precision)
+
     # end-to-end through the public API with host buffers: import the state
     # from host memory, one Krylov step, read the 1-RDM back
     e2e = None
@@ -617,6 +655,7 @@ def main():
         "steps_per_s": 1e3 * args.steps / ms,
         "vs_fp64": fp64_cmp,
         "vs_fp64_trajectory": traj,
+        "precision_compare": prec_cmp,
         "gpu_launches": int(sum(v["launches"] for k, v in st.items() if not k.startswith("host"))),
         "kernel_stats": {k: {"launches": v["launches"], "ms": round(v["ms"], 3),
                              "gflop": round(v["flops"] / 1e9, 3), "gb": round(v["bytes"] / 1e9, 3)}

@@ -181,6 +181,8 @@ def test_native_arm_json_assembly_with_a_stand_in_library(monkeypatch, capsys):
     monkeypatch.delenv("WORLD_SIZE", raising=False)
     for argv, mode in ((["--steps", "2", "--warmup", "3"], "krylov"),
                        (["--mode", "apply", "--steps", "2", "--warmup", "3"], "apply"),
+                       (["--mode", "apply", "--steps", "1", "--warmup", "3",
+                         "--compare-precisions"], "apply-cmp"),
                        (["--steps", "1", "--warmup", "3", "--serial-inner", "--no-traj-compare",
                          "--no-fp64-compare", "--no-e2e"], "serial")):
         monkeypatch.setattr(sys, "argv", ["bench.py", "--no-cpu-baseline", *argv])
@@ -200,4 +202,7 @@ def test_native_arm_json_assembly_with_a_stand_in_library(monkeypatch, capsys):
             assert line["e2e"]["pinned_inputs"] is False      # no driver here
         else:
             assert line["vs_fp64_trajectory"] is None
+        if mode == "apply-cmp":
+            assert set(line["precision_compare"]) == {"fp64", "tf32x3", "bf16"}
+            assert line["precision_compare"]["bf16"]["one_minus_fidelity"] == 0.0
     assert seen == [False]
