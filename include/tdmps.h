@@ -123,7 +123,10 @@ int tdmps_set_krylov_fp64(tdmps_ctx_t ctx, int on);
  * same values up to the summation order of split-K accumulation.  The
  * serial order is for tools that serialise kernels across threads, such as
  * profilers.  It applies when the inner products are FP64
- * (tdmps_set_krylov_fp64) and m > 2.  Errors: INVALID_ARG for a NULL ctx. */
+ * (tdmps_set_krylov_fp64) and m > 2.  The helper stream has the default,
+ * lowest, priority: a context bound to a higher-priority stream keeps its
+ * fits (the critical path of the step) ahead of the inner products.
+ * Errors: INVALID_ARG for a NULL ctx. */
 int tdmps_set_concurrent_inner(tdmps_ctx_t ctx, int on);
 
 /* ------------------------------------------------------- orbital order */

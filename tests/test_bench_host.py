@@ -125,8 +125,13 @@ def test_native_arm_json_assembly_with_a_stand_in_library(monkeypatch, capsys):
         def elapsed_time(self, other):
             return 1e3 * (other.t - self.t) + 1e-3
 
+    class Stream:
+        def __init__(self, priority=0):
+            self.priority = max(priority, -3)
+
     for name, fn in (("Event", Ev), ("synchronize", lambda *a, **k: None),
-                     ("set_device", lambda *a, **k: None),
+                     ("set_device", lambda *a, **k: None), ("Stream", Stream),
+                     ("set_stream", lambda *a, **k: None),
                      ("current_stream", lambda *a, **k: object())):
         monkeypatch.setattr(torch.cuda, name, fn)
     classes = ["gemm", "wstage", "qr", "svd", "other", "gemm_fp64", "host_plan", "host_launch",
@@ -193,6 +198,7 @@ def test_native_arm_json_assembly_with_a_stand_in_library(monkeypatch, capsys):
                   "roofline", "clocks", "e2e", "gpu_launches"):
             assert k in line, (mode, k)
         assert line["metric"] == bench.METRIC and line["gpu_launches"] > 0
+        assert line["config"]["stream_priority"] == -3
         assert line["config"]["inner_products"] == ("serial" if mode == "serial" else "concurrent")
         if mode == "krylov":
             traj = line["vs_fp64_trajectory"]
