@@ -320,7 +320,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_tc(const GemmTask* __res
     const int ra_r = p & (TC_BM - 1);            // A: row of this thread
     const int ra_k = (p >> 7) * TC_AEL;          //    first complex K of its 4
     const int rb_n = p & (TC_BNC - 1);           // B: column of this thread
-    const int rb_k = (p >> 6) * TC_BEL;          //    first complex K of its 2
+    const int rb_k = (p / TC_BNC) * TC_BEL;      //    first complex K of its TC_BEL
     // the stage being issued, with its tile's and term's fields kept in
     // registers while they stay the same (they are reloaded on a change only)
     Item cur{(int)blockIdx.x, 0, 0, 0};
