@@ -213,6 +213,10 @@ def workload_config(args, sched, size, world):
     else:
         w = ("apply_H fit, L=%d N=%d 2Sz=%d D=%d, schedule %d two-site + %d one-site sweeps, "
              "random seeded D=%d state" % (Ls, Ns, Ss, Ds, sched[0], sched[1], Ds))
+    if getattr(args, "start", "random") != "random":
+        w = w.replace("random seeded D=%d start" % Ds, "start " + args.start)
+        w = w.replace("random seeded D=%d state" % Ds, "state " + args.start)
+        w += " (beta-hole determinant evolved K Krylov steps, schedule 1+1)"
     return {"workload": w,
             "l2": "inputs larger than L2 (Krylov basis + environments, several GB)",
             "inner_products": "serial" if args.serial_inner else "concurrent",
@@ -430,6 +434,10 @@ def main():
                          "the large active space: 64 Cholesky vectors and the localised "
                          "orbital block); the default is the L=16 workload")
     ap.add_argument("--schedule", default=None, help="two-site,one-site sweeps per fit")
+    ap.add_argument("--start", default="random",
+                    help="random (the seeded random D state, default) or hole:K (the beta-hole "
+                         "determinant evolved K Krylov steps with schedule 1+1, the physical "
+                         "timing state; needs N = L - 1)")
     ap.add_argument("--serial-inner", action="store_true",
                     help="run the Krylov inner products after each fit on the context "
                          "stream instead of beside it on a helper thread (for profilers "
@@ -470,7 +478,19 @@ def main():
     I = synth.make_integrals(L, seed=0, n_chol=64 if big else 16, localised_block=big)
     mpo = td.build_mpo(ctx, I.h, I.eri, n_elec=N_ELEC)
     # replicas only: each rank evolves its own seeded state, no collective
-    A, q = synth.random_mps(L, N_ELEC, TWO_SZ, D, seed=rank)
+    if args.start.startswith("hole:"):
+        # the physical state: sudden beta hole in orbital L/2 - 1, evolved
+        if N_ELEC != L - 1 or TWO_SZ != 1:
+            raise SystemExit("--start hole:K needs N = L - 1 and 2Sz = 1")
+        ctx.set_schedule(1, 1)
+        s0 = td.mps_from_determinant(ctx, synth.hole_occupation(L, L, L // 2 - 1))
+        for _ in range(int(args.start.split(":")[1])):
+            td.krylov_step(ctx, mpo, s0, DT, M_KRYLOV, True, D, EPS)
+        ctx.set_schedule(*sched)
+        A, q = s0.export()
+        s0.free()
+    else:
+        A, q = synth.random_mps(L, N_ELEC, TWO_SZ, D, seed=rank)
     nrm = None
     psi = td.mps_import(ctx, A, q)
     nrm = abs(td.overlap(ctx, psi, psi)) ** 0.5

@@ -148,6 +148,10 @@ def test_native_arm_json_assembly_with_a_stand_in_library(monkeypatch, capsys):
         def free(self):
             pass
 
+        def export(self):
+            return ([np.ones((1, 4, 1), dtype=complex) for _ in range(self.L)],
+                    [np.zeros((1, 2), dtype=np.int64) for _ in range(self.L + 1)])
+
     class Ctx:
         def __init__(self, prec):
             self.prec = prec
@@ -188,6 +192,8 @@ def test_native_arm_json_assembly_with_a_stand_in_library(monkeypatch, capsys):
                        (["--mode", "apply", "--steps", "2", "--warmup", "3"], "apply"),
                        (["--mode", "apply", "--steps", "1", "--warmup", "3",
                          "--compare-precisions"], "apply-cmp"),
+                       (["--mode", "apply", "--steps", "1", "--warmup", "3",
+                         "--start", "hole:2"], "apply-hole"),
                        (["--steps", "1", "--warmup", "3", "--serial-inner", "--no-traj-compare",
                          "--no-fp64-compare", "--no-e2e"], "serial")):
         monkeypatch.setattr(sys, "argv", ["bench.py", "--no-cpu-baseline", *argv])
@@ -208,6 +214,8 @@ def test_native_arm_json_assembly_with_a_stand_in_library(monkeypatch, capsys):
             assert line["e2e"]["pinned_inputs"] is False      # no driver here
         else:
             assert line["vs_fp64_trajectory"] is None
+        if mode == "apply-hole":
+            assert "hole:2" in line["config"]["workload"]
         if mode == "apply-cmp":
             assert set(line["precision_compare"]) == {"fp64", "tf32x3", "bf16"}
             assert line["precision_compare"]["bf16"]["one_minus_fidelity"] == 0.0
