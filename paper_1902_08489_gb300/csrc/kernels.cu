@@ -967,7 +967,7 @@ __global__ void __launch_bounds__(QR_THREADS) k_qr(const FactTask* __restrict__ 
 // CTA has read the buffer of reduction r - 1, which reduction r + 1 reuses.
 // A sector's FP64 work is divided by the cluster size, which is what limits
 // the single-CTA kernel on large sectors (one SM's FP64 pipe).
-constexpr int QRC_CS = 8;
+constexpr int QRC_CS = 4;
 constexpr int QRC_THREADS = 256;
 
 __host__ __device__ inline int qrc_mc(int m) { return (m + QRC_CS - 1) / QRC_CS; }
