@@ -1310,6 +1310,8 @@ void run_qr(Context& c, FactWork& fw) {
 
 void run_svd(Context& c, FactWork& fw) {
   if (fw.tasks.empty()) return;
+  for (auto& t : fw.tasks)
+    if (t.n > 1024) throw Error(TDMPS_ERR_INVALID_ARG, "SVD block exceeds the supported size");
   const FactTask* d = c.stage(fw.tasks);
   cudaEvent_t ev;
   c.kbegin(TDMPS_KSTAT_SVD, &ev);

@@ -428,6 +428,25 @@ void launch_axpby(double2* y, const double2* x, size_t n, double2 a, double2 b, 
 constexpr int SVD_THREADS = 1024;
 constexpr int SVD_MAX_SWEEPS = 60;
 
+// Rotation of the column pair with squared norms al, be and inner product
+// gr + i gi (conj(a_p) a_q): c and s e^{i phi}, or false when the pair is
+// already orthogonal to tol or a column is numerically zero.  Taken by one
+// thread per pair: these square roots and divisions run on the FP64 pipe,
+// which is the scarce unit on this part, and a warp that computed them on
+// every lane would spend 32 times the pipe time.
+__device__ __forceinline__ bool jacobi_rotation(double al, double be, double gr, double gi,
+                                                double negl, double tol, double* c,
+                                                double2* sph) {
+  const double g = sqrt(gr * gr + gi * gi);
+  if (g == 0.0 || al <= negl || be <= negl || g <= tol * sqrt(al * be)) return false;
+  const double zeta = (be - al) / (2.0 * g);
+  const double tt = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+  const double cc = 1.0 / sqrt(1.0 + tt * tt), sn = cc * tt;
+  *c = cc;
+  *sph = cscale(make_double2(gr / g, gi / g), sn);   // s e^{i phi}
+  return true;
+}
+
 __global__ void __launch_bounds__(SVD_THREADS) k_svd(const FactTask* __restrict__ tasks,
                                                      int* status, int smem_budget) {
   extern __shared__ double2 svd_sh[];
@@ -441,6 +460,7 @@ __global__ void __launch_bounds__(SVD_THREADS) k_svd(const FactTask* __restrict_
   __shared__ int rotated;
   __shared__ double fro2;
   __shared__ int perm[1024];
+  __shared__ double2 pr[1024];   // per pair: sums, then rotation parameters
   if (threadIdx.x == 0) fro2 = 0.0;
   if (a_sh)
     for (size_t e = threadIdx.x; e < (size_t)m * n; e += blockDim.x) A[e] = t.A[e];
@@ -472,31 +492,57 @@ __global__ void __launch_bounds__(SVD_THREADS) k_svd(const FactTask* __restrict_
     if (threadIdx.x == 0) rotated = 0;
     __syncthreads();
     for (int r = 0; r < np - 1; ++r) {
+      // the pair sums (one warp per pair), then the rotation parameters (one
+      // thread per pair, in place), then the rotations (one warp per pair)
       for (int k = warp; k < np / 2; k += nwarp) {
         int pa = k, pb = np - 1 - k;
         int p = pa == 0 ? 0 : ((pa - 1 + r) % (np - 1)) + 1;
         int q = ((pb - 1 + r) % (np - 1)) + 1;
-        if (p >= n || q >= n) continue;
+        double al = 0.0, be = 0.0, gr = 0.0, gi = 0.0;
+        if (p < n && q < n) {
+          if (p > q) { int tmp = p; p = q; q = tmp; }
+          const double2* ap = A + (size_t)p * m;
+          const double2* aq = A + (size_t)q * m;
+          for (int i = lane; i < m; i += 32) {
+            double2 x = ap[i], y = aq[i];
+            al += cabs2(x);
+            be += cabs2(y);
+            gr += x.x * y.x + x.y * y.y;     // conj(x) * y
+            gi += x.x * y.y - x.y * y.x;
+          }
+          al = warp_sum(al); be = warp_sum(be); gr = warp_sum(gr); gi = warp_sum(gi);
+        }
+        if (lane == 0) {
+          pr[2 * k] = make_double2(al, be);
+          pr[2 * k + 1] = make_double2(gr, gi);
+        }
+      }
+      __syncthreads();
+      for (int k = threadIdx.x; k < np / 2; k += blockDim.x) {
+        int pa = k, pb = np - 1 - k;
+        int p = pa == 0 ? 0 : ((pa - 1 + r) % (np - 1)) + 1;
+        int q = ((pb - 1 + r) % (np - 1)) + 1;
+        double c = 1.0;
+        double2 sph = make_double2(0.0, 0.0);
+        const bool go = p < n && q < n &&
+                        jacobi_rotation(pr[2 * k].x, pr[2 * k].y, pr[2 * k + 1].x,
+                                        pr[2 * k + 1].y, negl, tol, &c, &sph);
+        pr[2 * k] = make_double2(c, go ? 1.0 : 0.0);
+        pr[2 * k + 1] = sph;
+        if (go) rotated = 1;
+      }
+      __syncthreads();
+      for (int k = warp; k < np / 2; k += nwarp) {
+        if (pr[2 * k].y == 0.0) continue;
+        int pa = k, pb = np - 1 - k;
+        int p = pa == 0 ? 0 : ((pa - 1 + r) % (np - 1)) + 1;
+        int q = ((pb - 1 + r) % (np - 1)) + 1;
         if (p > q) { int tmp = p; p = q; q = tmp; }
+        const double c = pr[2 * k].x;
+        const double2 sph = pr[2 * k + 1];                   // s e^{i phi}
+        const double2 sphc = cconj(sph);                     // s e^{-i phi}
         double2* ap = A + (size_t)p * m;
         double2* aq = A + (size_t)q * m;
-        double al = 0.0, be = 0.0, gr = 0.0, gi = 0.0;
-        for (int i = lane; i < m; i += 32) {
-          double2 x = ap[i], y = aq[i];
-          al += cabs2(x);
-          be += cabs2(y);
-          gr += x.x * y.x + x.y * y.y;     // conj(x) * y
-          gi += x.x * y.y - x.y * y.x;
-        }
-        al = warp_sum(al); be = warp_sum(be); gr = warp_sum(gr); gi = warp_sum(gi);
-        double g = sqrt(gr * gr + gi * gi);
-        if (g == 0.0 || al <= negl || be <= negl || g <= tol * sqrt(al * be)) continue;
-        double zeta = (be - al) / (2.0 * g);
-        double tt = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-        double c = 1.0 / sqrt(1.0 + tt * tt), s = c * tt;
-        double2 ph = make_double2(gr / g, gi / g);          // e^{i phi}
-        double2 sph = cscale(ph, s);                         // s e^{i phi}
-        double2 sphc = cconj(sph);                           // s e^{-i phi}
         for (int i = lane; i < m; i += 32) {
           double2 x = ap[i], y = aq[i];
           ap[i] = csub(cscale(x, c), cmul(sphc, y));
@@ -509,7 +555,6 @@ __global__ void __launch_bounds__(SVD_THREADS) k_svd(const FactTask* __restrict_
           vp[i] = csub(cscale(x, c), cmul(sphc, y));
           vq[i] = cadd(cmul(sph, x), cscale(y, c));
         }
-        if (lane == 0) rotated = 1;
       }
       __syncthreads();
     }
@@ -537,13 +582,12 @@ __global__ void __launch_bounds__(SVD_THREADS) k_svd(const FactTask* __restrict_
         rank += (sk > sj) || (sk == sj && k < j);
       }
       perm[rank] = j;
+      pr[j].x = sj > 0.0 ? 1.0 / sj : 0.0;   // 1/sigma once per column (pairs are done)
     }
     __syncthreads();
     for (size_t e = threadIdx.x; e < (size_t)m * n; e += blockDim.x) {
       int j = (int)(e / m), i = (int)(e % m);
-      double sj = t.s[perm[j]];
-      double inv = sj > 0.0 ? 1.0 / sj : 0.0;
-      t.A[e] = cscale(A[(size_t)perm[j] * m + i], inv);
+      t.A[e] = cscale(A[(size_t)perm[j] * m + i], pr[perm[j]].x);
     }
     __syncthreads();
     if (!v_sh) {   // A's shared buffer is free: stage V there (n*n <= m*n)
@@ -709,21 +753,29 @@ __global__ void __launch_bounds__(SVDC_THREADS) k_svd_cl(const FactTask* __restr
       }
       __syncthreads();
       allreduce(part, np);
-      for (int k = warp; k < np / 2; k += nwarp) {
+      // rotation parameters, one thread per pair, in place of the sums
+      for (int k = threadIdx.x; k < np / 2; k += blockDim.x) {
         int pa = k, pb = np - 1 - k;
         int p = pa == 0 ? 0 : ((pa - 1 + r) % (np - 1)) + 1;
         int q = ((pb - 1 + r) % (np - 1)) + 1;
-        if (p >= n || q >= n) continue;
+        double c = 1.0;
+        double2 sph = make_double2(0.0, 0.0);
+        const bool go = p < n && q < n &&
+                        jacobi_rotation(part[2 * k].x, part[2 * k].y, part[2 * k + 1].x,
+                                        part[2 * k + 1].y, negl, tol, &c, &sph);
+        part[2 * k] = make_double2(c, go ? 1.0 : 0.0);
+        part[2 * k + 1] = sph;
+        if (go) rotated = 1;
+      }
+      __syncthreads();
+      for (int k = warp; k < np / 2; k += nwarp) {
+        if (part[2 * k].y == 0.0) continue;
+        int pa = k, pb = np - 1 - k;
+        int p = pa == 0 ? 0 : ((pa - 1 + r) % (np - 1)) + 1;
+        int q = ((pb - 1 + r) % (np - 1)) + 1;
         if (p > q) { int tmp = p; p = q; q = tmp; }
-        const double al = part[2 * k].x, be = part[2 * k].y;
-        const double gr = part[2 * k + 1].x, gi = part[2 * k + 1].y;
-        const double g = sqrt(gr * gr + gi * gi);
-        if (g == 0.0 || al <= negl || be <= negl || g <= tol * sqrt(al * be)) continue;
-        const double zeta = (be - al) / (2.0 * g);
-        const double tt = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-        const double c = 1.0 / sqrt(1.0 + tt * tt), s = c * tt;
-        const double2 ph = make_double2(gr / g, gi / g);   // e^{i phi}
-        const double2 sph = cscale(ph, s);                  // s e^{i phi}
+        const double c = part[2 * k].x;
+        const double2 sph = part[2 * k + 1];                // s e^{i phi}
         const double2 sphc = cconj(sph);                    // s e^{-i phi}
         double2* ap = A + (size_t)p * mc;
         double2* aq = A + (size_t)q * mc;
@@ -739,7 +791,6 @@ __global__ void __launch_bounds__(SVDC_THREADS) k_svd_cl(const FactTask* __restr
           vp[i] = csub(cscale(x, c), cmul(sphc, y));
           vq[i] = cadd(cmul(sph, x), cscale(y, c));
         }
-        if (lane == 0) rotated = 1;
       }
       __syncthreads();
     }
@@ -766,11 +817,12 @@ __global__ void __launch_bounds__(SVDC_THREADS) k_svd_cl(const FactTask* __restr
     int rk = 0;
     for (int k = 0; k < n; ++k) rk += (sv[k] > sj) || (sv[k] == sj && k < j);
     perm[rk] = j;
+    part[j].x = sj > 0.0 ? 1.0 / sj : 0.0;   // 1/sigma once per column
   }
   __syncthreads();
   for (int j = 0; j < n; ++j) {
     const int pj = perm[j];
-    const double inv = sv[pj] > 0.0 ? 1.0 / sv[pj] : 0.0;
+    const double inv = part[pj].x;
     for (int i = threadIdx.x; i < ml; i += blockDim.x)
       t.A[(size_t)j * m + row0 + i] = cscale(A[(size_t)pj * mc + i], inv);
   }
@@ -822,8 +874,8 @@ void launch_svd(const FactTask* d_tasks, int ntasks, int* d_status, cudaStream_t
       return;
     }
   }
-  // static shared: perm (4 KB) + scalars
-  const size_t cap = 227 * 1024 - 5 * 1024;
+  // static shared: perm (4 KB), the pair array (16 KB) and scalars
+  const size_t cap = 227 * 1024 - 21 * 1024;
   size_t dyn = max_bytes < cap ? max_bytes : cap;
   set_smem_limit((const void*)k_svd, (int)cap);
   k_svd<<<ntasks, SVD_THREADS, dyn, st>>>(d_tasks, d_status, (int)dyn);
@@ -858,7 +910,7 @@ __global__ void __launch_bounds__(QR_THREADS) k_qr(const FactTask* __restrict__ 
   double2* A = a_sh ? sh + m + n : t.A;
   double2* R = a_sh ? sh + m + n + (size_t)m * n : t.V;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-  __shared__ double maxn, vn;
+  __shared__ double maxn, vn, vinv;
   __shared__ int nq;
   if (threadIdx.x == 0) { maxn = 0.0; nq = 0; }
   if (a_sh)
@@ -931,12 +983,15 @@ __global__ void __launch_bounds__(QR_THREADS) k_qr(const FactTask* __restrict__ 
       double s2 = 0.0;
       for (int i = lane; i < m; i += 32) s2 += cabs2(v[i]);
       s2 = warp_sum(s2);
-      if (lane == 0) vn = sqrt(s2);
+      if (lane == 0) {
+        vn = sqrt(s2);
+        vinv = vn > 0.0 ? 1.0 / vn : 0.0;   // once, not on every thread (FP64 pipe)
+      }
     }
     __syncthreads();
     const double nrm = vn;
     if (nrm > tol && q < kmax) {
-      double inv = 1.0 / nrm;
+      const double inv = vinv;
       for (int i = threadIdx.x; i < m; i += blockDim.x) A[(size_t)q * m + i] = cscale(v[i], inv);
       if (threadIdx.x == 0) {
         R[(size_t)j * n + q] = make_double2(nrm, 0.0);
@@ -967,7 +1022,7 @@ __global__ void __launch_bounds__(QR_THREADS) k_qr(const FactTask* __restrict__ 
 // CTA has read the buffer of reduction r - 1, which reduction r + 1 reuses.
 // A sector's FP64 work is divided by the cluster size, which is what limits
 // the single-CTA kernel on large sectors (one SM's FP64 pipe).
-constexpr int QRC_CS = 4;
+constexpr int QRC_CS = 8;
 constexpr int QRC_THREADS = 256;
 
 __host__ __device__ inline int qrc_mc(int m) { return (m + QRC_CS - 1) / QRC_CS; }
@@ -1039,10 +1094,15 @@ __global__ void __launch_bounds__(QRC_THREADS) k_qr_cl(const FactTask* __restric
   }
   __syncthreads();
   allreduce(coef, n, coef);
-  double maxn = 0.0;
-  for (int c = 0; c < n; ++c) maxn = fmax(maxn, sqrt(coef[c].x));
+  // sqrt is monotonic: the largest norm is the root of the largest square,
+  // taken once (FP64 square roots on every thread would load the narrow pipe)
+  if (threadIdx.x == 0) {
+    double m2 = 0.0;
+    for (int c = 0; c < n; ++c) m2 = fmax(m2, coef[c].x);
+    scal[4] = make_double2(sqrt(m2), 0.0);
+  }
   __syncthreads();
-  const double tol = 1e-12 * maxn;
+  const double tol = 1e-12 * scal[4].x;
   int nq = 0;
   for (int j = 0; j < n; ++j) {
     for (int i = threadIdx.x; i < ml; i += blockDim.x) v[i] = A[(size_t)j * mc + i];
@@ -1079,10 +1139,10 @@ __global__ void __launch_bounds__(QRC_THREADS) k_qr_cl(const FactTask* __restric
         }
         __syncthreads();
         allreduce(coef, pass == 0 ? q + 1 : q, coef);
-        double proj = 0.0;
-        if (pass == 0) {
-          before = coef[q].x;
+        if (pass == 0 && threadIdx.x == 0) {   // one thread; read after the barrier below
+          double proj = 0.0;
           for (int cc = 0; cc < q; ++cc) proj += cabs2(coef[cc]);
+          scal[2] = make_double2(coef[q].x, proj);
         }
         for (int i = threadIdx.x; i < ml; i += blockDim.x) {
           double2 acc = v[i];
@@ -1096,7 +1156,8 @@ __global__ void __launch_bounds__(QRC_THREADS) k_qr_cl(const FactTask* __restric
           }
         __syncthreads();
         if (pass == 0) {
-          const double est = before - proj;
+          before = scal[2].x;
+          const double est = before - scal[2].y;
           if (!(est < 0.5 * before)) {   // one pass was enough
             nrm2 = est;
             break;
@@ -1106,9 +1167,15 @@ __global__ void __launch_bounds__(QRC_THREADS) k_qr_cl(const FactTask* __restric
         }
       }
     }
-    const double nrm = sqrt(nrm2);
+    // the column norm and its inverse, once
+    if (threadIdx.x == 0) {
+      const double r0 = sqrt(nrm2);
+      scal[3] = make_double2(r0, r0 > 0.0 ? 1.0 / r0 : 0.0);
+    }
+    __syncthreads();
+    const double nrm = scal[3].x;
     if (nrm > tol && q < kmax) {
-      const double inv = 1.0 / nrm;
+      const double inv = scal[3].y;
       for (int i = threadIdx.x; i < ml; i += blockDim.x) A[(size_t)q * mc + i] = cscale(v[i], inv);
       if (rank == 0 && threadIdx.x == 0) t.V[(size_t)j * n + q] = make_double2(nrm, 0.0);
       nq = q + 1;
