@@ -728,7 +728,10 @@ __global__ void __launch_bounds__(SVDC_THREADS) k_svd_cl(const FactTask* __restr
     if (threadIdx.x == 0) rotated = 0;
     __syncthreads();
     for (int r = 0; r < np - 1; ++r) {
-      for (int k = warp; k < np / 2; k += nwarp) {
+      // the partial sums of every pair over the local rows, one thread per
+      // pair (the local rows are few: no warp reduction, whose shuffles and
+      // adds would cost the FP64 pipe on every lane)
+      for (int k = threadIdx.x; k < np / 2; k += blockDim.x) {
         int pa = k, pb = np - 1 - k;
         int p = pa == 0 ? 0 : ((pa - 1 + r) % (np - 1)) + 1;
         int q = ((pb - 1 + r) % (np - 1)) + 1;
@@ -737,19 +740,16 @@ __global__ void __launch_bounds__(SVDC_THREADS) k_svd_cl(const FactTask* __restr
           if (p > q) { int tmp = p; p = q; q = tmp; }
           const double2* ap = A + (size_t)p * mc;
           const double2* aq = A + (size_t)q * mc;
-          for (int i = lane; i < ml; i += 32) {
+          for (int i = 0; i < ml; ++i) {
             const double2 x = ap[i], y = aq[i];
             al += cabs2(x);
             be += cabs2(y);
             gr += x.x * y.x + x.y * y.y;     // conj(x) * y
             gi += x.x * y.y - x.y * y.x;
           }
-          al = warp_sum(al); be = warp_sum(be); gr = warp_sum(gr); gi = warp_sum(gi);
         }
-        if (lane == 0) {
-          part[2 * k] = make_double2(al, be);
-          part[2 * k + 1] = make_double2(gr, gi);
-        }
+        part[2 * k] = make_double2(al, be);
+        part[2 * k + 1] = make_double2(gr, gi);
       }
       __syncthreads();
       allreduce(part, np);
@@ -768,7 +768,10 @@ __global__ void __launch_bounds__(SVDC_THREADS) k_svd_cl(const FactTask* __restr
         if (go) rotated = 1;
       }
       __syncthreads();
-      for (int k = warp; k < np / 2; k += nwarp) {
+      // the rotations, one thread per (pair, local row of A or V)
+      const int per = ml + nl;
+      for (int idx = threadIdx.x; idx < (np / 2) * per; idx += blockDim.x) {
+        const int k = idx / per, i = idx - k * per;
         if (part[2 * k].y == 0.0) continue;
         int pa = k, pb = np - 1 - k;
         int p = pa == 0 ? 0 : ((pa - 1 + r) % (np - 1)) + 1;
@@ -777,20 +780,18 @@ __global__ void __launch_bounds__(SVDC_THREADS) k_svd_cl(const FactTask* __restr
         const double c = part[2 * k].x;
         const double2 sph = part[2 * k + 1];                // s e^{i phi}
         const double2 sphc = cconj(sph);                    // s e^{-i phi}
-        double2* ap = A + (size_t)p * mc;
-        double2* aq = A + (size_t)q * mc;
-        for (int i = lane; i < ml; i += 32) {
-          const double2 x = ap[i], y = aq[i];
-          ap[i] = csub(cscale(x, c), cmul(sphc, y));
-          aq[i] = cadd(cmul(sph, x), cscale(y, c));
+        double2* xp;
+        double2* yp;
+        if (i < ml) {
+          xp = A + (size_t)p * mc + i;
+          yp = A + (size_t)q * mc + i;
+        } else {
+          xp = t.V + (size_t)p * n + vr0 + (i - ml);
+          yp = t.V + (size_t)q * n + vr0 + (i - ml);
         }
-        double2* vp = t.V + (size_t)p * n + vr0;
-        double2* vq = t.V + (size_t)q * n + vr0;
-        for (int i = lane; i < nl; i += 32) {
-          const double2 x = vp[i], y = vq[i];
-          vp[i] = csub(cscale(x, c), cmul(sphc, y));
-          vq[i] = cadd(cmul(sph, x), cscale(y, c));
-        }
+        const double2 x = *xp, y = *yp;
+        *xp = csub(cscale(x, c), cmul(sphc, y));
+        *yp = cadd(cmul(sph, x), cscale(y, c));
       }
       __syncthreads();
     }
