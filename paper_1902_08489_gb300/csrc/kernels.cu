@@ -492,9 +492,11 @@ __global__ void __launch_bounds__(SVD_THREADS) k_svd(const FactTask* __restrict_
     if (threadIdx.x == 0) rotated = 0;
     __syncthreads();
     for (int r = 0; r < np - 1; ++r) {
-      // the pair sums (one warp per pair), then the rotation parameters (one
-      // thread per pair, in place), then the rotations (one warp per pair)
-      for (int k = warp; k < np / 2; k += nwarp) {
+      // the pair sums and the rotation parameters (one thread per pair),
+      // then the rotations (one thread per (pair, row)): no warp
+      // reductions and no FP64 work repeated across lanes; pr holds each
+      // pair's c and s e^{i phi}
+      for (int k = threadIdx.x; k < np / 2; k += blockDim.x) {
         int pa = k, pb = np - 1 - k;
         int p = pa == 0 ? 0 : ((pa - 1 + r) % (np - 1)) + 1;
         int q = ((pb - 1 + r) % (np - 1)) + 1;
@@ -503,36 +505,25 @@ __global__ void __launch_bounds__(SVD_THREADS) k_svd(const FactTask* __restrict_
           if (p > q) { int tmp = p; p = q; q = tmp; }
           const double2* ap = A + (size_t)p * m;
           const double2* aq = A + (size_t)q * m;
-          for (int i = lane; i < m; i += 32) {
+          for (int i = 0; i < m; ++i) {
             double2 x = ap[i], y = aq[i];
             al += cabs2(x);
             be += cabs2(y);
             gr += x.x * y.x + x.y * y.y;     // conj(x) * y
             gi += x.x * y.y - x.y * y.x;
           }
-          al = warp_sum(al); be = warp_sum(be); gr = warp_sum(gr); gi = warp_sum(gi);
         }
-        if (lane == 0) {
-          pr[2 * k] = make_double2(al, be);
-          pr[2 * k + 1] = make_double2(gr, gi);
-        }
-      }
-      __syncthreads();
-      for (int k = threadIdx.x; k < np / 2; k += blockDim.x) {
-        int pa = k, pb = np - 1 - k;
-        int p = pa == 0 ? 0 : ((pa - 1 + r) % (np - 1)) + 1;
-        int q = ((pb - 1 + r) % (np - 1)) + 1;
         double c = 1.0;
         double2 sph = make_double2(0.0, 0.0);
-        const bool go = p < n && q < n &&
-                        jacobi_rotation(pr[2 * k].x, pr[2 * k].y, pr[2 * k + 1].x,
-                                        pr[2 * k + 1].y, negl, tol, &c, &sph);
+        const bool go = p < n && q < n && jacobi_rotation(al, be, gr, gi, negl, tol, &c, &sph);
         pr[2 * k] = make_double2(c, go ? 1.0 : 0.0);
         pr[2 * k + 1] = sph;
         if (go) rotated = 1;
       }
       __syncthreads();
-      for (int k = warp; k < np / 2; k += nwarp) {
+      const int per = m + n;
+      for (int idx = threadIdx.x; idx < (np / 2) * per; idx += blockDim.x) {
+        const int k = idx / per, i = idx - k * per;
         if (pr[2 * k].y == 0.0) continue;
         int pa = k, pb = np - 1 - k;
         int p = pa == 0 ? 0 : ((pa - 1 + r) % (np - 1)) + 1;
@@ -541,20 +532,11 @@ __global__ void __launch_bounds__(SVD_THREADS) k_svd(const FactTask* __restrict_
         const double c = pr[2 * k].x;
         const double2 sph = pr[2 * k + 1];                   // s e^{i phi}
         const double2 sphc = cconj(sph);                     // s e^{-i phi}
-        double2* ap = A + (size_t)p * m;
-        double2* aq = A + (size_t)q * m;
-        for (int i = lane; i < m; i += 32) {
-          double2 x = ap[i], y = aq[i];
-          ap[i] = csub(cscale(x, c), cmul(sphc, y));
-          aq[i] = cadd(cmul(sph, x), cscale(y, c));
-        }
-        double2* vp = V + (size_t)p * n;
-        double2* vq = V + (size_t)q * n;
-        for (int i = lane; i < n; i += 32) {
-          double2 x = vp[i], y = vq[i];
-          vp[i] = csub(cscale(x, c), cmul(sphc, y));
-          vq[i] = cadd(cmul(sph, x), cscale(y, c));
-        }
+        double2* xp = i < m ? A + (size_t)p * m + i : V + (size_t)p * n + (i - m);
+        double2* yp = i < m ? A + (size_t)q * m + i : V + (size_t)q * n + (i - m);
+        const double2 x = *xp, y = *yp;
+        *xp = csub(cscale(x, c), cmul(sphc, y));
+        *yp = cadd(cmul(sph, x), cscale(y, c));
       }
       __syncthreads();
     }
