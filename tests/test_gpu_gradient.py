@@ -197,3 +197,25 @@ def test_integral_gradient_equals_full_ci_rdms_L8(td):
     H = fci.hamiltonian(I.h, I.eri, dets)
     assert abs(td.energy(ctx, mpo, psi) - np.vdot(v, H @ v).real / n2) < 1e-11
     ctx.close()
+
+
+@pytest.mark.parametrize("L,stride", [(1, 1), (2, 1), (3, 2), (4, 9)])
+def test_state_gradient_short_chains_and_wide_strides(td, L, stride):
+    # the boundaries of the adjoint: one and two sites, a checkpoint stride
+    # that does not divide L, one longer than the chain
+    I = synth.make_integrals(L, seed=40 + L)
+    n = max(1, L - 1)
+    A, q = synth.random_mps(L, n, n % 2, 8, seed=41 + L)
+    ctx = td.Context("fp64")
+    mpo = td.build_mpo(ctx, I.h, I.eri, n_elec=n)
+    psi = td.mps_import(ctx, A, q)
+    E, G, _ = td.energy_gradient(ctx, mpo, psi, stride=stride)
+    gt, gq = G.export()
+    Eo, Go = ob.energy_gradient(ob.hamiltonian_mpo(I.h, I.eri), ob.from_dense(A, q))
+    got = ob.from_dense(gt, gq)
+    assert abs(E - Eo) < 1e-12 * max(1.0, abs(Eo))
+    scale = max(np.abs(b).max() for s in Go for b in s.values())
+    err = max(np.abs(got.sites[i][k] - Go[i][k]).max() for i in range(L) for k in Go[i])
+    # (at L = 1 the one-dimensional sector makes the gradient vanish)
+    assert err <= 1e-11 * max(scale, abs(Eo))
+    ctx.close()
