@@ -119,8 +119,8 @@ int tdmps_set_krylov_fp64(tdmps_ctx_t ctx, int on);
  * (Eq. kry_orth).  Those of Gram-Schmidt step k depend on phi_0..phi_k only.
  * With on != 0 (the default) they run on a helper stream driven by a
  * second host thread, concurrently with the fit of H phi_k. With on == 0
- * they run after that fit, in order, on the context stream.  Both give the
- * same values up to the summation order of split-K accumulation.  The
+ * they run after that fit, in order, on the context stream.  Both run the
+ * same contractions with the same launch plans (fixed summation order).  The
  * serial order is for tools that serialise kernels across threads, such as
  * profilers.  It applies when the inner products are FP64
  * (tdmps_set_krylov_fp64) and m > 2.  The helper stream has the default,

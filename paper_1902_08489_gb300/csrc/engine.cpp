@@ -554,7 +554,7 @@ struct GemmBatch {
     // that the launch has about `per_sm` work units per SM (the FP64 pipe
     // and the tensor pipe are per-SM resources; a launch with fewer units
     // than SMs leaves the rest idle), with at least `min_chunks` K chunks
-    // per unit to amortise the atomic epilogue.
+    // per unit to amortise the partial-slice store and its reduction.
     const int kc = fp64 ? 8 : tc_stage_k();
     const int per_sm = fp64 ? 4 : 3, min_chunks = fp64 ? 2 : 4;
     std::vector<long long> stages(tasks.size(), 0);
