@@ -52,7 +52,9 @@ the 1-RDM equals the full-CI one; the FLOP count of an overlap equals
 oracle.mps.overlap_flops; the energy gradient with respect to the site
 tensors equals the full-CI projection M_i^+ (H v - E v) / |v|^2 and central
 differences of the energy, and is orthogonal to its own site (E does not
-change under A_i -> (1 + t) A_i).  Parity unpinned, as in oracle.mps: whether
+change under A_i -> (1 + t) A_i); the one-site local operator equals the
+full-CI projection M_i^+ H M_i, is Hermitian and gives <A_i, H_i A_i> =
+<psi|H|psi> at every site.  Parity unpinned, as in oracle.mps: whether
 a truncated fit reaches the best truncated state.
 """
 from __future__ import annotations
@@ -1091,3 +1093,24 @@ def energy_gradient(mpo: MPO, psi: BMPS):
         LH = env_left(LH, psi.sites[i], psi.sites[i], mpo.W[i])
         LN = env_left(LN, psi.sites[i], psi.sites[i], ident.W[i])
     return E, grads
+
+
+def local_matvec(mpo: MPO, psi: BMPS, i: int, x: dict, fl: Flops = _NOCOUNT) -> dict:
+    """The one-site effective Hamiltonian of Eq. (add_min)'s local problem at
+    site i, applied to x (a site tensor on psi's bonds i and i+1):
+
+        y[a, s, b] = sum L[a, w, a'] W_i[w, w', s, s'] x[a', s', b'] R[b, w', b'],
+
+    L and R the environments of <psi|H|psi> left of site i and right of it.
+    No gauge is assumed: <psi(x)|H|psi(z)> = <x, y(z)> for the states psi(x),
+    psi(z) with site i replaced, so in psi's mixed-canonical gauge at i this is
+    H projected onto the site's variational space.  The environments are
+    built by plain sweeps from both ends; only the application is counted in
+    ``fl``."""
+    Le = left_boundary()
+    for j in range(i):
+        Le = env_left(Le, psi.sites[j], psi.sites[j], mpo.W[j])
+    Re = right_boundary(psi.total)
+    for j in range(psi.L - 1, i, -1):
+        Re = env_right(Re, psi.sites[j], psi.sites[j], mpo.W[j])
+    return local_one(Le, Re, x, mpo.W[i], psi.bonds[i], psi.bonds[i + 1], fl=fl)

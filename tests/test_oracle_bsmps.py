@@ -263,3 +263,66 @@ def test_energy_gradient_finite_differences_and_scale_invariance():
     for i in range(L):
         s = sum(np.vdot(psi.sites[i][k], G[i][k]) for k in G[i])
         assert abs(s) < 1e-12 * abs(E)
+
+
+def _random_site(site: dict, rng) -> dict:
+    return {k: rng.standard_normal(b.shape) + 1j * rng.standard_normal(b.shape)
+            for k, b in site.items()}
+
+
+def _site_vectors(sys_, psi, i):
+    """M_i: the sector vectors of psi with site i replaced by each unit tensor
+    (one column per entry, entries in the order of _flat)."""
+    cols = []
+    for k, blk in psi.sites[i].items():
+        for a in range(blk.shape[0]):
+            for b in range(blk.shape[1]):
+                unit = psi.copy()
+                unit.sites[i] = {kk: np.zeros_like(x) for kk, x in unit.sites[i].items()}
+                unit.sites[i][k][a, b] = 1.0
+                cols.append(sys_.vec(om.from_arrays(*ob.to_dense(unit))))
+    return np.array(cols).T
+
+
+def _flat(site: dict, like: dict):
+    return np.concatenate([site[k].reshape(-1) for k in like])
+
+
+def test_local_matvec_equals_full_ci_projection():
+    # y = M_i^+ H M_i x: the local operator is H in the coordinates of site i
+    # (psi's other sites fixed, no gauge assumed), H the full-CI Hamiltonian
+    L = 4
+    I, sys_ = _sector_system(L, 4, 0, 40)
+    mpo = ob.hamiltonian_mpo(I.h, I.eri, 0.3)
+    A, q = synth.random_mps(L, 4, 0, 8, seed=41)
+    psi = ob.from_dense(A, q)
+    rng = np.random.default_rng(42)
+    for i in range(L):
+        x = _random_site(psi.sites[i], rng)
+        y = ob.local_matvec(mpo, psi, i, x)
+        assert set(y) == set(psi.sites[i])
+        M = _site_vectors(sys_, psi, i)
+        ref = M.conj().T @ ((sys_.H + 0.3 * np.eye(len(sys_.H))) @ (M @ _flat(x, psi.sites[i])))
+        got = _flat(y, psi.sites[i])
+        assert np.abs(got - ref).max() < 1e-12 * np.abs(ref).max()
+
+
+def test_local_matvec_hermitian_and_reproduces_the_energy():
+    # <z, H_i x> = conj(<x, H_i z>), and with x = A_i the site's own tensor
+    # <A_i, H_i A_i> = <psi|H|psi> at every site
+    L = 6
+    I = synth.make_integrals(L, seed=43)
+    mpo = ob.hamiltonian_mpo(I.h, I.eri)
+    A, q = synth.random_mps(L, 5, 1, 12, seed=44)
+    psi = ob.from_dense(A, q)
+    e = ob.sandwich(mpo, psi, psi)
+    rng = np.random.default_rng(45)
+    for i in range(L):
+        keys = psi.sites[i]
+        x, z = _random_site(keys, rng), _random_site(keys, rng)
+        hx, hz = ob.local_matvec(mpo, psi, i, x), ob.local_matvec(mpo, psi, i, z)
+        a = np.vdot(_flat(z, keys), _flat(hx, keys))
+        b = np.vdot(_flat(x, keys), _flat(hz, keys))
+        assert abs(a - np.conj(b)) < 1e-11 * abs(a)
+        ha = ob.local_matvec(mpo, psi, i, psi.sites[i])
+        assert abs(np.vdot(_flat(psi.sites[i], keys), _flat(ha, keys)) - e) < 1e-11 * abs(e)
