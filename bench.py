@@ -30,6 +30,7 @@ sys.path.insert(0, ROOT)
 import numpy as np  # noqa: E402
 
 METRIC = "apply_H TFLOP/s at L=16, D=256 (Krylov step)"
+METRIC_MATVEC = "local one-site matvec TFLOP/s at the centre site, L=16, D=256"
 L, N_ELEC, TWO_SZ, D = 16, 15, 1, 256
 M_KRYLOV, DT, EPS = 10, 0.05, 1e-8
 SCHEDULE = (0, 2)   # two-site sweeps, one-site sweeps per fit
@@ -210,6 +211,11 @@ def workload_config(args, sched, size, world):
         w = ("Krylov step, L=%d N=%d 2Sz=%d D=%d m=10 dt=0.05 eps=1e-8, fit schedule %d "
              "two-site + %d one-site sweeps, random seeded D=%d start"
              % (Ls, Ns, Ss, Ds, sched[0], sched[1], Ds))
+    elif args.mode == "matvec":
+        w = ("local one-site matvec L W x R (the fit's local product) at the centre site "
+             "i = %d, L=%d N=%d 2Sz=%d D=%d, environments of <psi|H|psi> built once "
+             "(untimed), %d applications per step, random seeded D=%d state"
+             % (Ls // 2, Ls, Ns, Ss, Ds, args.reps, Ds))
     else:
         w = ("apply_H fit, L=%d N=%d 2Sz=%d D=%d, schedule %d two-site + %d one-site sweeps, "
              "random seeded D=%d state" % (Ls, Ns, Ss, Ds, sched[0], sched[1], Ds))
@@ -218,7 +224,9 @@ def workload_config(args, sched, size, world):
         w = w.replace("random seeded D=%d state" % Ds, "state " + args.start)
         w += " (beta-hole determinant evolved K Krylov steps, schedule 1+1)"
     return {"workload": w,
-            "l2": "inputs larger than L2 (Krylov basis + environments, several GB)",
+            "l2": ("flushed before every application (a 256 MB write, outside the timed "
+                   "intervals)" if args.mode == "matvec" else
+                   "inputs larger than L2 (Krylov basis + environments, several GB)"),
             "inner_products": "serial" if args.serial_inner else "concurrent",
             "parallelism": "replicas" if world > 1 else "single"}
 
@@ -238,14 +246,24 @@ def run_reference(args):
     size = workload_size(args)
     o = _oracle_workload(size)
     ob, mpo, psi = o["ob"], o["mpo"], o["psi"]
+    if args.mode == "matvec":
+        # the local operator at the centre site: environments once, untimed
+        c = size[0] // 2
+        Le, Re = ob.local_environments(mpo, psi, c)
+
+        def unit(fl=ob.Flops()):
+            ob.local_one(Le, Re, psi.sites[c], mpo.W[c], psi.bonds[c], psi.bonds[c + 1], fl=fl)
+    else:
+        def unit(fl=ob.Flops()):
+            ob.sandwich(mpo, psi, psi, fl)
     for _ in range(args.warmup):
-        ob.sandwich(mpo, psi, psi)
+        unit()
     import resource
     fl = ob.Flops()
     r0 = resource.getrusage(resource.RUSAGE_SELF)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        ob.sandwich(mpo, psi, psi, fl)
+        unit(fl)
     dt = time.perf_counter() - t0
     r1 = resource.getrusage(resource.RUSAGE_SELF)
     cpu_s = (r1.ru_utime - r0.ru_utime) + (r1.ru_stime - r0.ru_stime)
@@ -254,12 +272,16 @@ def run_reference(args):
     cb = {"value": v, "unit": "TFLOP/s", "cores": int(threads), "kind": "oracle",
           "avg_busy_threads": round(cpu_s / dt, 2),
           "sample": "block-sparse FP64 oracle on the benchmark workload (L=%d N=%d 2Sz=%d "
-                    "D=%d): one exact <psi|H|psi> sandwich per step, %.1f GFLOP per step"
-                    % (size[0], size[1], size[2], size[3], fl.total / 1e9 / max(1, args.steps))}
+                    "D=%d): %s per step, %.1f GFLOP per step"
+                    % (size[0], size[1], size[2], size[3],
+                       "one application of the local operator at the centre site"
+                       if args.mode == "matvec" else "one exact <psi|H|psi> sandwich",
+                       fl.total / 1e9 / max(1, args.steps))}
     kf = _krylov_step_oracle_flops(size)
-    if kf:
+    if kf and args.mode != "matvec":
         cb["s_per_krylov_step_extrapolated"] = kf / (fl.total / dt)
-    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "TFLOP/s",
+    line = {"impl": "reference", "metric": METRIC_MATVEC if args.mode == "matvec" else METRIC,
+            "value": v, "unit": "TFLOP/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * dt / max(1, args.steps), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -273,9 +295,13 @@ def reference_config(args, size):
     """`config` of the oracle arm: the native arm's workload, with the sample
     each timed step takes."""
     cfg = workload_config(args, fit_schedule(args), size, int(os.environ.get("WORLD_SIZE", "1")))
-    cfg["sample_per_step"] = ("one exact <psi|H|psi> MPO sandwich of the seeded D=%d state "
-                              "(block-sparse FP64 oracle): the operation the Krylov step runs "
-                              "55 times for its Hamiltonian matrix" % size[3])
+    if args.mode == "matvec":
+        cfg["sample_per_step"] = ("one application of the local operator at the centre site "
+                                  "(block-sparse FP64 oracle; environments built once, untimed)")
+    else:
+        cfg["sample_per_step"] = ("one exact <psi|H|psi> MPO sandwich of the seeded D=%d state "
+                                  "(block-sparse FP64 oracle): the operation the Krylov step "
+                                  "runs 55 times for its Hamiltonian matrix" % size[3])
     cfg["inner_products"] = "n/a (oracle)"
     return cfg
 
@@ -419,11 +445,15 @@ def main():
                          "15-20 s per precision once the bonds reach D)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--mode", default="krylov", choices=["krylov", "apply", "batch"],
+    ap.add_argument("--mode", default="krylov", choices=["krylov", "apply", "matvec", "batch"],
                     help="krylov: one Krylov time step per step (default); apply: one "
-                         "fitted H application (one one-site sweep) per step; batch: one "
-                         "RK4 step of each of 64 uneven instances (L in {8..14}, "
+                         "fitted H application (one one-site sweep) per step; matvec: "
+                         "--reps applications of the local one-site operator at the "
+                         "centre site per step (L2 flushed between applications); batch: "
+                         "one RK4 step of each of 64 uneven instances (L in {8..14}, "
                          "D in {32, 64, 128}) on worker streams")
+    ap.add_argument("--reps", type=int, default=50,
+                    help="matvec mode: local operator applications per step")
     ap.add_argument("--workers", type=int, default=16, help="batch mode: worker streams")
     ap.add_argument("--compare-precisions", action="store_true",
                     help="apply mode: also run the fitted application in FP64, split TF32 "
@@ -497,14 +527,33 @@ def main():
     A[0] = A[0] / nrm
     h2d_bytes = sum(int(np.count_nonzero(t)) for t in A) * 16
 
+    # matvec mode: the operator, its output state, an L2 flush buffer (a write
+    # of twice the 129 MB L2 before every application) and the event pair of
+    # every application (the flush stays outside the timed intervals)
+    mv = {"op": None, "y": None, "flush": None, "events": []}
+
     def step(state):
         if args.mode == "krylov":
             td.krylov_step(ctx, mpo, state, DT, M_KRYLOV, True, D, EPS)
+        elif args.mode == "matvec":
+            for _ in range(args.reps):
+                mv["flush"].zero_()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record()
+                mv["op"].apply(state, mv["y"])
+                e1.record()
+                mv["events"].append((e0, e1))
         else:
             out = td.apply_H(ctx, mpo, state, -1j * DT, D, EPS)
             out.free()
 
     state = td.mps_import(ctx, A, q)
+    if args.mode == "matvec":
+        td.compress(ctx, state, D, 0.0)
+        mv["op"] = td.local_hamiltonian(ctx, mpo, state, L // 2)
+        mv["y"] = state.copy()
+        mv["flush"] = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     if args.mode == "apply":
         # the gauge every state produced by the library is in (a fit or an
         # integrator step returns it right-canonical), so that the timed
@@ -523,12 +572,15 @@ def main():
         torch.cuda.synchronize()
         if dist:
             dist.barrier()
+        mv["events"].clear()
         ev0.record(stream)
         for _ in range(args.steps):
             step(state)
         ev1.record(stream)
         torch.cuda.synchronize()
     ms = ev0.elapsed_time(ev1)
+    if args.mode == "matvec":   # the applications alone, without the L2 flushes
+        ms = sum(a.elapsed_time(b) for a, b in mv["events"])
     st = ctx.stats()
     ctx.stats_enable(False)
     flops = st["gemm"]["flops"] + st["gemm_fp64"]["flops"] + st["wstage"]["flops"]
@@ -653,7 +705,7 @@ def main():
     # end-to-end through the public API with host buffers: import the state
     # from host memory, one Krylov step, read the 1-RDM back
     e2e = None
-    if not args.no_e2e:
+    if not args.no_e2e and args.mode != "matvec":
         A_host, _keep, pinned = pinned_copies(A, torch)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -671,15 +723,25 @@ def main():
 
     # dominant kernel class: the largest live event time in the timed region
     roof = roofline(st, args.precision)
+    config = dict(workload_config(args, sched, (L, N_ELEC, TWO_SZ, D), world),
+                  stream_priority=int(hp_stream.priority))
+    matvec = None
+    if args.mode == "matvec":
+        matvec = {"site": L // 2, "env_bytes": mv["op"].env_bytes,
+                  "applications": len(mv["events"]),
+                  "us_per_application": 1e3 * ms / max(1, len(mv["events"])),
+                  "timed": "sum of per-application event intervals"}
+        mv["op"].free()
+        mv["y"].free()
     line = {
-        "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world,
+        "metric": METRIC_MATVEC if args.mode == "matvec" else METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": {"fp64": "f64", "tf32": "tf32", "tf32x3": "tf32x3", "bf16": "bf16"}[args.precision],
         "data": "synthetic",
-        "config": dict(workload_config(args, sched, (L, N_ELEC, TWO_SZ, D), world),
-                       stream_priority=int(hp_stream.priority)),
+        "config": config,
         "steps_per_s": 1e3 * args.steps / ms,
+        "matvec": matvec,
         "vs_fp64": fp64_cmp,
         "vs_fp64_trajectory": traj,
         "precision_compare": prec_cmp,

@@ -41,6 +41,7 @@ extern "C" {
 typedef struct tdmps_ctx_s* tdmps_ctx_t;
 typedef struct tdmps_mpo_s* tdmps_mpo_t;
 typedef struct tdmps_mps_s* tdmps_mps_t;
+typedef struct tdmps_heff_s* tdmps_heff_t;
 
 typedef struct {
   double re, im;
@@ -246,6 +247,36 @@ int tdmps_sum(tdmps_ctx_t ctx, int n_terms, const tdmps_complex* coefs,
  * ZERO_STATE (psi = 0), CUDA. */
 int tdmps_energy_gradient(tdmps_ctx_t ctx, tdmps_mpo_t mpo, tdmps_mps_t psi, int stride,
                           double* energy, tdmps_mps_t* grad, size_t* env_bytes_peak);
+
+/* The one-site effective Hamiltonian of the local problem of Eq. add_min
+ * (Sec. 2.2.1) at site `site` of psi, as an operator on that site's tensor:
+ *     y[a,s,b] = sum L[a,w,a'] W_site[w,w',s,s'] x[a',s',b'] R[b,w',b'],
+ * L and R the environments of <psi|H|psi> left and right of the site (the
+ * product every one-site fit step forms).  psi's gauge is not assumed:
+ * <psi(x)|H|psi(z)> = <x, H_site z> for psi with the site replaced, so in
+ * psi's mixed-canonical gauge at the site the operator is H projected onto
+ * the site's variational space.  Create builds the two environments once
+ * (one sweep in from each end, in the context's precision) and keeps them
+ * on the device; *env_bytes (may be NULL) receives their size.  The handle
+ * copies what it needs of mpo and psi: both may be freed before it.  Free
+ * it before its context.
+ * Errors: INVALID_ARG (NULL argument, lengths differ, site outside
+ * 0..L-1), SECTOR, CUDA. */
+int tdmps_heff_create(tdmps_ctx_t ctx, tdmps_mpo_t mpo, tdmps_mps_t psi, int site,
+                      tdmps_heff_t* out, size_t* env_bytes);
+
+/* Replace site `site` of y with the operator applied to site `site` of x.
+ * x and y need psi's (N, 2S_z), length and bonds at site and site + 1 (for
+ * instance copies of psi; x == y is allowed).  Only that site of y changes,
+ * and y is then in no canonical gauge.  One launch per stage (L-stage, MPO
+ * stage, R-stage; a GEMM with split K is followed by its ordered reduction),
+ * in the precision the operator was created in.
+ * Errors: INVALID_ARG (NULL argument, context precision changed since
+ * create), SECTOR (bonds differ), CUDA. */
+int tdmps_heff_apply(tdmps_ctx_t ctx, tdmps_heff_t op, tdmps_mps_t x, tdmps_mps_t y);
+
+/* Release the operator's environments (stream-ordered). */
+int tdmps_heff_free(tdmps_heff_t op);
 
 /* E = <psi|H|psi> / <psi|psi> (real part; H is Hermitian), FP64 chains.
  * Errors: INVALID_ARG, ZERO_STATE (psi = 0), CUDA. */

@@ -1107,10 +1107,16 @@ def local_matvec(mpo: MPO, psi: BMPS, i: int, x: dict, fl: Flops = _NOCOUNT) -> 
     H projected onto the site's variational space.  The environments are
     built by plain sweeps from both ends; only the application is counted in
     ``fl``."""
+    Le, Re = local_environments(mpo, psi, i)
+    return local_one(Le, Re, x, mpo.W[i], psi.bonds[i], psi.bonds[i + 1], fl=fl)
+
+
+def local_environments(mpo: MPO, psi: BMPS, i: int):
+    """The environments of <psi|H|psi> left of site i and right of it."""
     Le = left_boundary()
     for j in range(i):
         Le = env_left(Le, psi.sites[j], psi.sites[j], mpo.W[j])
     Re = right_boundary(psi.total)
     for j in range(psi.L - 1, i, -1):
         Re = env_right(Re, psi.sites[j], psi.sites[j], mpo.W[j])
-    return local_one(Le, Re, x, mpo.W[i], psi.bonds[i], psi.bonds[i + 1], fl=fl)
+    return Le, Re

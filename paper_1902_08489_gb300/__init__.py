@@ -74,6 +74,9 @@ _SIGS = {
     "tdmps_apply_H": (I, [P, P, P, Complex, I, D, I, ctypes.POINTER(P)]),
     "tdmps_energy_gradient": (I, [P, P, P, I, ctypes.POINTER(D), ctypes.POINTER(P),
                                   ctypes.POINTER(ctypes.c_size_t)]),
+    "tdmps_heff_create": (I, [P, P, P, I, ctypes.POINTER(P), ctypes.POINTER(ctypes.c_size_t)]),
+    "tdmps_heff_apply": (I, [P, P, P, P]),
+    "tdmps_heff_free": (I, [P]),
     "tdmps_energy": (I, [P, P, P, ctypes.POINTER(D)]),
     "tdmps_integral_gradient": (I, [P, P, P, P]),
     "tdmps_sum": (I, [P, I, P, P, I, D, ctypes.POINTER(P)]),
@@ -312,6 +315,42 @@ def energy_gradient(ctx, mpo, mps, stride=1):
     _check(lib().tdmps_energy_gradient(ctx.h, mpo.h, mps.h, stride, ctypes.byref(e),
                                        ctypes.byref(out), ctypes.byref(peak)), ctx)
     return e.value, MPS(ctx, out), peak.value
+
+
+class LocalHamiltonian:
+    """The one-site effective Hamiltonian of a state at one site (environments
+    held on the device); see local_hamiltonian."""
+
+    def __init__(self, ctx, handle, site, env_bytes):
+        self.ctx = ctx
+        self.h = handle
+        self.site = site
+        self.env_bytes = env_bytes
+
+    def apply(self, x, y):
+        """Site `site` of y <- the operator applied to site `site` of x."""
+        _check(lib().tdmps_heff_apply(self.ctx.h, self.h, x.h, y.h), self.ctx)
+
+    def free(self):
+        if self.h:
+            lib().tdmps_heff_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def local_hamiltonian(ctx, mpo, mps, site) -> LocalHamiltonian:
+    """H_site: x -> L W_site x R with the environments of <psi|H|psi> around
+    `site` (the local problem of a one-site fit step)."""
+    out = ctypes.c_void_p()
+    nb = ctypes.c_size_t()
+    _check(lib().tdmps_heff_create(ctx.h, mpo.h, mps.h, site, ctypes.byref(out),
+                                   ctypes.byref(nb)), ctx)
+    return LocalHamiltonian(ctx, out, site, nb.value)
 
 
 def energy(ctx, mpo, mps) -> float:

@@ -19,6 +19,9 @@ struct tdmps_mpo_s {
 struct tdmps_mps_s {
   MPSd m;
 };
+struct tdmps_heff_s {
+  std::unique_ptr<LocalOp> op;
+};
 
 namespace {
 
@@ -282,6 +285,39 @@ int tdmps_energy_gradient(tdmps_ctx_t ctx, tdmps_mpo_t mpo, tdmps_mps_t psi, int
     }
     *grad = r;
   });
+}
+
+int tdmps_heff_create(tdmps_ctx_t ctx, tdmps_mpo_t mpo, tdmps_mps_t psi, int site,
+                      tdmps_heff_t* out, size_t* env_bytes) {
+  if (!ctx) return TDMPS_ERR_INVALID_ARG;
+  return guard(ctx, [&] {
+    need(mpo && psi && out, "NULL argument");
+    need(mpo->m.L == psi->m.L, "MPO and MPS lengths differ");
+    need(site >= 0 && site < psi->m.L, "site out of range");
+    ensure_uploaded(ctx, mpo);
+    auto* r = new tdmps_heff_s;
+    try {
+      r->op = local_op_create(*ctx->c, mpo->m, psi->m, site);
+    } catch (...) {
+      delete r;
+      throw;
+    }
+    if (env_bytes) *env_bytes = r->op->env_bytes;
+    *out = r;
+  });
+}
+
+int tdmps_heff_apply(tdmps_ctx_t ctx, tdmps_heff_t op, tdmps_mps_t x, tdmps_mps_t y) {
+  if (!ctx) return TDMPS_ERR_INVALID_ARG;
+  return guard(ctx, [&] {
+    need(op && x && y, "NULL argument");
+    local_op_apply(*ctx->c, *op->op, x->m, y->m);
+  });
+}
+
+int tdmps_heff_free(tdmps_heff_t op) {
+  delete op;
+  return TDMPS_OK;
 }
 
 int tdmps_sum(tdmps_ctx_t ctx, int n_terms, const tdmps_complex* coefs, const tdmps_mps_t* terms,

@@ -2039,6 +2039,75 @@ MPSd energy_gradient(Context& c, const MPOd& H, const MPSd& psi, int stride, dou
   return G;
 }
 
+// ------------------------------------------------------------------ local operator
+
+// The local problem of Eq. add_min at one site, as an operator on that site's
+// tensor: L W x R, the product every one-site fit step forms, with the
+// environments of <psi|H|psi> (no gauge assumed: <psi(x)|H|psi(z)> = <x, H_i z>
+// for psi with site i replaced).  The environments come from one sweep in
+// from each end, exactly as a fit builds them, and stay on the device.
+std::unique_ptr<LocalOp> local_op_create(Context& c, const MPOd& H, const MPSd& psi, int site) {
+  if (H.L != psi.L) throw Error(TDMPS_ERR_INVALID_ARG, "MPO length differs from MPS");
+  if (site < 0 || site >= psi.L) throw Error(TDMPS_ERR_INVALID_ARG, "site out of range");
+  const int L = psi.L;
+  auto op = std::make_unique<LocalOp>();
+  op->H = H;
+  op->site = site;
+  op->L = L;
+  op->precision = c.precision;
+  op->tot = psi.tot;
+  op->left = psi.bonds[site];
+  op->right = psi.bonds[site + 1];
+  std::vector<TermState> ts(1);
+  TermState& t = ts[0];
+  t.ket = &psi;
+  t.mpo = &op->H;
+  t.coef = 1.0;
+  t.coef_dev = nullptr;
+  t.LE.resize(L + 1);
+  t.RE.resize(L + 1);
+  t.LE[0] = env_left_boundary(c, psi, psi, op->H);
+  for (int j = 0; j < site; ++j) {
+    std::vector<Inter> Y = left_stages(c, ts, j);
+    left_env_step(c, ts, psi, j, Y);
+    t.LE[j] = Env();
+  }
+  t.RE[L] = env_right_boundary(c, psi, psi, op->H);
+  for (int j = L - 1; j > site; --j) {
+    right_env_step(c, ts, psi, j);
+    t.RE[j + 1] = Env();
+  }
+  op->LE = std::move(t.LE[site]);
+  op->RE = std::move(t.RE[site + 1]);
+  op->env_bytes = op->LE.t.size * op->LE.t.esz() + op->RE.t.size * op->RE.t.esz();
+  return op;
+}
+
+void local_op_apply(Context& c, const LocalOp& op, const MPSd& x, MPSd& y) {
+  if (c.precision != op.precision)
+    throw Error(TDMPS_ERR_INVALID_ARG, "context precision differs from the operator's");
+  auto on_bonds = [&](const MPSd& m) {
+    const Bond& a = m.bonds[op.site];
+    const Bond& b = m.bonds[op.site + 1];
+    return m.L == op.L && m.tot == op.tot && a.q == op.left.q && a.d == op.left.d &&
+           b.q == op.right.q && b.d == op.right.d;
+  };
+  if (!on_bonds(x) || !on_bonds(y))
+    throw Error(TDMPS_ERR_SECTOR, "x and y must have the operator's bonds at its site");
+  GemmBatch g1(c);
+  Inter X = plan_lstage(c, op.LE, x.sites[op.site], op.right, g1);
+  g1.run();
+  WBatch wb;
+  Inter Y = plan_wstage(c, std::move(X), op.H, op.site, true, wb);
+  wb.run(c);
+  SiteT out = make_site(RowGroups::from_bond(op.left), op.right, c.st, false);
+  GemmBatch g2(c);
+  plan_rstage({{&Y, &op.RE, 1.0, nullptr}}, out, g2);
+  g2.run();
+  y.sites[op.site] = std::move(out);
+  y.rcanon = false;
+}
+
 void normalize_center(Context& c, MPSd& m, double2* norm_out) {
   cudaEvent_t ev;
   c.kbegin(TDMPS_KSTAT_OTHER, &ev);

@@ -203,6 +203,20 @@ void normalize_center(Context& c, MPSd& m, double2* norm_out);
 // others recomputed when the left-to-right pass needs them (1: all kept).
 MPSd energy_gradient(Context& c, const MPOd& H, const MPSd& psi, int stride, double* energy,
                      size_t* env_bytes_peak = nullptr);
+// The one-site effective Hamiltonian of Eq. add_min's local problem at one
+// site of psi: y = L W_site x R with the environments of <psi|H|psi> left
+// and right of the site, built once in the context's precision at creation.
+struct LocalOp {
+  MPOd H;            // a copy (device tables shared): the environments point into it
+  int site = 0, L = 0, precision = 0;
+  QN tot;
+  Bond left, right;  // psi's bonds at site and site + 1
+  Env LE, RE;
+  size_t env_bytes = 0;
+};
+std::unique_ptr<LocalOp> local_op_create(Context& c, const MPOd& H, const MPSd& psi, int site);
+// y's site <- the operator applied to x's site (x, y on psi's bonds there)
+void local_op_apply(Context& c, const LocalOp& op, const MPSd& x, MPSd& y);
 MPSd rk4_step(Context& c, const MPOd& H, const MPSd& psi, double dt, const FitOpts& o);
 MPSd krylov_step(Context& c, const MPOd& H, const MPSd& psi, double dt, int m, bool orth,
                  const FitOpts& o);

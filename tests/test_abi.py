@@ -152,7 +152,7 @@ def test_binding_signatures_match_the_header_prototypes():
 
     def kind_c(p):
         p = " ".join(p.split())
-        if "*" in p or re.search(r"\btdmps_(ctx|mpo|mps)_t\b", p):
+        if "*" in p or re.search(r"\btdmps_(ctx|mpo|mps|heff)_t\b", p):
             return "ptr"
         if re.search(r"\btdmps_complex\b", p):
             return "complex"

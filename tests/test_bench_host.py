@@ -106,7 +106,7 @@ def test_native_arm_json_assembly_with_a_stand_in_library(monkeypatch, capsys):
     """Runs bench.main() on the CPU with a stand-in for the library and for
     torch.cuda (test double only: every number it prints is meaningless).  It
     checks the control flow and the JSON line of the native arm in the krylov,
-    apply and serial-inner-product modes, so that a Python-level mistake there
+    apply, local-matvec and serial-inner-product modes, so that a Python-level mistake there
     shows up without a GPU.  The real library is exercised by the GPU tests."""
     import json
     import sys
@@ -148,6 +148,9 @@ def test_native_arm_json_assembly_with_a_stand_in_library(monkeypatch, capsys):
         def free(self):
             pass
 
+        def copy(self):
+            return MPS(self.L)
+
         def export(self):
             return ([np.ones((1, 4, 1), dtype=complex) for _ in range(self.L)],
                     [np.zeros((1, 2), dtype=np.int64) for _ in range(self.L + 1)])
@@ -186,6 +189,20 @@ def test_native_arm_json_assembly_with_a_stand_in_library(monkeypatch, capsys):
     lib.krylov_step = lambda *a, **k: None
     lib.apply_H = lambda *a, **k: MPS()
     lib.compress = lambda *a, **k: 0.0
+    applied = []
+
+    class Op:
+        env_bytes = 12345
+
+        def apply(self, x, y):
+            applied.append((x, y))
+
+        def free(self):
+            pass
+
+    lib.local_hamiltonian = lambda ctx, mpo, m, site: (applied.append(site), Op())[1]
+    empty = torch.empty
+    monkeypatch.setattr(torch, "empty", lambda *a, **k: empty(16, dtype=k.get("dtype")))
     monkeypatch.setitem(sys.modules, "paper_1902_08489_gb300", lib)
     monkeypatch.delenv("WORLD_SIZE", raising=False)
     for argv, mode in ((["--steps", "2", "--warmup", "3"], "krylov"),
@@ -194,6 +211,8 @@ def test_native_arm_json_assembly_with_a_stand_in_library(monkeypatch, capsys):
                          "--compare-precisions"], "apply-cmp"),
                        (["--mode", "apply", "--steps", "1", "--warmup", "3",
                          "--start", "hole:2"], "apply-hole"),
+                       (["--mode", "matvec", "--steps", "2", "--warmup", "3", "--reps", "2"],
+                        "matvec"),
                        (["--steps", "1", "--warmup", "3", "--serial-inner", "--no-traj-compare",
                          "--no-fp64-compare", "--no-e2e"], "serial")):
         monkeypatch.setattr(sys, "argv", ["bench.py", "--no-cpu-baseline", *argv])
@@ -203,7 +222,8 @@ def test_native_arm_json_assembly_with_a_stand_in_library(monkeypatch, capsys):
                   "higher_is_better", "scaling", "vs_baseline", "dtype", "data", "config",
                   "roofline", "clocks", "e2e", "gpu_launches"):
             assert k in line, (mode, k)
-        assert line["metric"] == bench.METRIC and line["gpu_launches"] > 0
+        assert line["metric"] == (bench.METRIC_MATVEC if mode == "matvec" else bench.METRIC)
+        assert line["gpu_launches"] > 0
         assert line["config"]["stream_priority"] == -3
         assert line["config"]["inner_products"] == ("serial" if mode == "serial" else "concurrent")
         if mode == "krylov":
@@ -214,9 +234,33 @@ def test_native_arm_json_assembly_with_a_stand_in_library(monkeypatch, capsys):
             assert line["e2e"]["pinned_inputs"] is False      # no driver here
         else:
             assert line["vs_fp64_trajectory"] is None
+        if mode == "matvec":
+            # the operator at the centre site, (3 warm-up + 2 timed) x 2 applications,
+            # only the timed ones in the line; no e2e in this mode
+            assert applied[0] == 8 and len(applied) == 1 + 5 * 2
+            assert line["matvec"]["applications"] == 4 and line["matvec"]["site"] == 8
+            assert line["matvec"]["env_bytes"] == 12345 and line["e2e"] is None
+            assert "flushed" in line["config"]["l2"]
         if mode == "apply-hole":
             assert "hole:2" in line["config"]["workload"]
         if mode == "apply-cmp":
             assert set(line["precision_compare"]) == {"fp64", "tf32x3", "bf16"}
             assert line["precision_compare"]["bf16"]["one_minus_fidelity"] == 0.0
     assert seen == [False]
+
+
+def test_reference_arm_of_the_local_matvec_mode():
+    """The oracle arm of --mode matvec times the oracle's local operator at
+    the centre site of the benchmark state (environments once, untimed)."""
+    import json
+    import subprocess
+    import sys
+    out = subprocess.run([sys.executable, bench.__file__, "--impl", "reference", "--mode", "matvec",
+                          "--steps", "1", "--warmup", "0"], capture_output=True, text=True,
+                         timeout=300)
+    assert out.returncode == 0, out.stderr[-2000:]
+    line = json.loads(out.stdout.strip().splitlines()[-1])
+    assert line["metric"] == bench.METRIC_MATVEC and line["value"] > 0
+    assert "centre site" in line["config"]["sample_per_step"]
+    assert "local operator at the centre site" in line["cpu_baseline"]["sample"]
+    assert "s_per_krylov_step_extrapolated" not in line["cpu_baseline"]
