@@ -66,6 +66,11 @@ def test_invalid_arguments_are_rejected_without_gpu(built):
     # context setters reject a NULL context
     assert td.ERRORS[built.tdmps_set_concurrent_inner(None, 0)] == "INVALID_ARG"
     assert td.ERRORS[built.tdmps_set_krylov_fp64(None, 1)] == "INVALID_ARG"
+    # the local operator: a NULL context is refused before anything else,
+    # and freeing a NULL operator is a no-op
+    assert td.ERRORS[built.tdmps_heff_create(None, mpo.h, None, 0, None, None)] == "INVALID_ARG"
+    assert td.ERRORS[built.tdmps_heff_apply(None, None, None, None)] == "INVALID_ARG"
+    assert built.tdmps_heff_free(None) == 0
 
 
 def _dense_mpo(mpo, L):
