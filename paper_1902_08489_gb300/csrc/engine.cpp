@@ -612,15 +612,19 @@ struct GemmBatch {
       for (int q = 0; q < t.tiles_m * tn * t.splits; ++q) tile_task.push_back(id);
     }
     if (tile_task.empty()) return;
-    // the reduction of the split tasks in chunks of at most 4096 elements
-    // (one CTA each), so that a few large tasks still spread over the SMs
+    // the reduction of the split tasks in chunks of at most 512 elements (one
+    // CTA of 256 threads each, two elements per thread): a few large tasks
+    // still spread over every SM, with enough independent slice loads in
+    // flight to cover their latency.  Every element is summed by one thread
+    // in split order, so the chunking does not change the result.
+    constexpr int red_chunk = 512;
     std::vector<int> red;
     for (int id : split_ids) {
       const int mn = tk[id].M * tk[id].N;
-      for (int b = 0; b < mn; b += 4096) {
+      for (int b = 0; b < mn; b += red_chunk) {
         red.push_back(id);
         red.push_back(b);
-        red.push_back(std::min(mn, b + 4096));
+        red.push_back(std::min(mn, b + red_chunk));
       }
     }
     // partial-sum slices of the split tasks (freed in stream order after use)
