@@ -326,3 +326,41 @@ def test_local_matvec_hermitian_and_reproduces_the_energy():
         assert abs(a - np.conj(b)) < 1e-11 * abs(a)
         ha = ob.local_matvec(mpo, psi, i, psi.sites[i])
         assert abs(np.vdot(_flat(psi.sites[i], keys), _flat(ha, keys)) - e) < 1e-11 * abs(e)
+
+
+def test_local_two_equals_full_ci_projection():
+    # the two-site local product of the fit (sites i, i+1 of psi, environments
+    # of <psi|H|psi> around them) = M_{i,i+1}^+ H v: each entry is the overlap
+    # of H v with the state whose two-site tensor is the unit tensor of that
+    # entry, built as a product through a one-dimensional middle bond
+    L = 4
+    I, sys_ = _sector_system(L, 4, 0, 46)
+    mpo = ob.hamiltonian_mpo(I.h, I.eri, 0.2)
+    A, q = synth.random_mps(L, 4, 0, 8, seed=47)
+    psi = ob.from_dense(A, q)
+    v = sys_.vec(om.from_arrays(A, q))
+    Hv = (sys_.H + 0.2 * np.eye(len(v))) @ v
+    for i in range(L - 1):
+        Le = ob.local_environments(mpo, psi, i)[0]
+        Re = ob.local_environments(mpo, psi, i + 1)[1]
+        Th = ob.local_two(Le, Re, psi.sites[i], psi.sites[i + 1], mpo.W[i], mpo.W[i + 1],
+                          psi.bonds[i], psi.bonds[i + 2])
+        scale = max(np.abs(b).max() for b in Th.values())
+        n = 0
+        for (qa, s1, s2), blk in Th.items():
+            qb = ob.qadd(ob.qadd(qa, ob.SITE_Q[s1]), ob.SITE_Q[s2])
+            rows = np.flatnonzero((q[i] == qa).all(axis=1))
+            cols = np.flatnonzero((q[i + 2] == qb).all(axis=1))
+            for a in range(blk.shape[0]):
+                for b in range(blk.shape[1]):
+                    At = [x.copy() for x in A]
+                    qt = [x.copy() for x in q]
+                    At[i] = np.zeros((len(q[i]), 4, 1), dtype=complex)
+                    At[i + 1] = np.zeros((1, 4, len(q[i + 2])), dtype=complex)
+                    At[i][rows[a], s1, 0] = 1.0
+                    At[i + 1][0, s2, cols[b]] = 1.0
+                    qt[i + 1] = np.array([ob.qadd(qa, ob.SITE_Q[s1])])
+                    col = sys_.vec(om.from_arrays(At, qt))
+                    assert abs(blk[a, b] - np.vdot(col, Hv)) < 1e-12 * scale
+                    n += 1
+        assert n == sum(b.size for b in Th.values()) > 0
