@@ -54,7 +54,10 @@ tensors equals the full-CI projection M_i^+ (H v - E v) / |v|^2 and central
 differences of the energy, and is orthogonal to its own site (E does not
 change under A_i -> (1 + t) A_i); the one-site local operator equals the
 full-CI projection M_i^+ H M_i, is Hermitian and gives <A_i, H_i A_i> =
-<psi|H|psi> at every site; the two-site local product equals M_{i,i+1}^+ H v.  Parity unpinned, as in oracle.mps: whether
+<psi|H|psi> at every site; the two-site local product equals M_{i,i+1}^+ H v;
+the sector QR / LQ factors reproduce their blocks with orthonormal factors,
+right canonicalisation keeps the state, and the two-site split is the
+truncated SVD of each middle sector (Eckart-Young).  Parity unpinned, as in oracle.mps: whether
 a truncated fit reaches the best truncated state.
 """
 from __future__ import annotations

@@ -364,3 +364,109 @@ def test_local_two_equals_full_ci_projection():
                     assert abs(blk[a, b] - np.vdot(col, Hv)) < 1e-12 * scale
                     n += 1
         assert n == sum(b.size for b in Th.values()) > 0
+
+
+def _stack_rows(site, left, qb):
+    rows = sorted((qa, s) for s in range(4) for qa in [ob.qsub(qb, ob.SITE_Q[s])] if qa in left
+                  and (qa, s) in site)
+    return rows, np.concatenate([site[k] for k in rows], axis=0)
+
+
+def test_qr_left_and_lq_right_factor_each_sector():
+    # Q R = C and orthonormal Q per right sector (QR); L Q = C and orthonormal
+    # rows per left sector (LQ); a sector with a repeated column keeps rank r
+    A, q = synth.random_mps(5, 5, 1, 12, seed=48)
+    psi = ob.from_dense(A, q)
+    i = 2
+    C = {k: v.copy() for k, v in psi.sites[i].items()}
+    left, right = psi.bonds[i], psi.bonds[i + 1]
+    # make one right sector rank deficient: its last column repeats the first
+    qb = max(right, key=lambda x: right[x])
+    for (qa, s), blk in C.items():
+        if ob.qadd(qa, ob.SITE_Q[s]) == qb:
+            blk[:, -1] = blk[:, 0]
+    Q, newb, Rs = ob.qr_left(C, left, right)
+    for qr_, r in newb.items():
+        rows, M = _stack_rows(C, left, qr_)
+        Qm = np.concatenate([Q[k] for k in rows], axis=0)
+        assert Qm.shape[1] == r == np.linalg.matrix_rank(M)
+        assert np.abs(Qm.conj().T @ Qm - np.eye(r)).max() < 1e-13
+        assert np.abs(Qm @ Rs[qr_] - M).max() < 1e-13 * np.abs(M).max()
+    assert newb[qb] == right[qb] - 1 if right[qb] > 1 else True
+    Q2, newl, Ls = ob.lq_right(C, left, right)
+    for qa, r in newl.items():
+        cols = [(qa, s) for s in range(4) if (qa, s) in C]
+        M = np.concatenate([C[k] for k in cols], axis=1)
+        Qr = np.concatenate([Q2[k] for k in cols], axis=1)
+        assert Qr.shape[0] == r == np.linalg.matrix_rank(M)
+        assert np.abs(Qr @ Qr.conj().T - np.eye(r)).max() < 1e-13
+        assert np.abs(Ls[qa] @ Qr - M).max() < 1e-13 * np.abs(M).max()
+
+
+def test_right_canonicalize_keeps_the_state_and_makes_sites_isometric():
+    L = 5
+    A, q = synth.random_mps(L, 5, 1, 12, seed=49)
+    psi = ob.from_dense(A, q)
+    rc = ob.right_canonicalize(psi)
+    sys_ = om.System.build(np.zeros((L, L)), np.zeros((L,) * 4), 3, 2)
+    v0 = sys_.vec(om.from_arrays(A, q))
+    v1 = sys_.vec(om.from_arrays(*ob.to_dense(rc)))
+    assert np.abs(v1 - v0).max() < 1e-12 * np.abs(v0).max()
+    for i in range(1, L):
+        for qa, da in rc.bonds[i].items():
+            acc = np.zeros((da, da), dtype=complex)
+            for s in range(4):
+                if (qa, s) in rc.sites[i]:
+                    b = rc.sites[i][(qa, s)]
+                    acc += b @ b.conj().T
+            assert np.abs(acc - np.eye(da)).max() < 1e-12
+
+
+def test_split_two_is_the_truncated_svd_of_each_middle_sector():
+    # untruncated: A B = Th exactly; truncated to D: per middle sector the
+    # best rank-k approximation (Eckart-Young) with the kept counts, and the
+    # discarded weight is the sum of the dropped squared singular values
+    A, q = synth.random_mps(5, 5, 1, 12, seed=50)
+    psi = ob.from_dense(A, q)
+    i = 1
+    left, right = psi.bonds[i], psi.bonds[i + 2]
+    Th = {}
+    for (qa, s1), B1 in psi.sites[i].items():
+        qm = ob.qadd(qa, ob.SITE_Q[s1])
+        for s2 in range(4):
+            B2 = psi.sites[i + 1].get((qm, s2))
+            if B2 is not None and ob.qadd(qm, ob.SITE_Q[s2]) in right:
+                Th[(qa, s1, s2)] = B1 @ B2
+    Dfull = sum(psi.bonds[i + 1].values())
+
+    def product(Aa, Bb):
+        out = {}
+        for (qa, s1, s2) in Th:
+            qm = ob.qadd(qa, ob.SITE_Q[s1])
+            if (qa, s1) in Aa and (qm, s2) in Bb:
+                out[(qa, s1, s2)] = Aa[(qa, s1)] @ Bb[(qm, s2)]
+            else:
+                out[(qa, s1, s2)] = np.zeros_like(Th[(qa, s1, s2)])
+        return out
+
+    Aa, Bb, mid, disc, total = ob.split_two(Th, left, right, Dfull, 0.0, "right")
+    P = product(Aa, Bb)
+    assert max(np.abs(P[k] - Th[k]).max() for k in Th) < 1e-12 * max(np.abs(t).max() for t in Th.values())
+    assert abs(total - sum(np.sum(np.abs(t) ** 2) for t in Th.values())) < 1e-10 * total
+    D = Dfull // 2
+    Aa, Bb, mid, disc, total = ob.split_two(Th, left, right, D, 0.0, "left")
+    assert sum(mid.values()) <= D
+    P = product(Aa, Bb)
+    dropped = 0.0
+    for qm in {ob.qadd(qa, ob.SITE_Q[s1]) for (qa, s1, s2) in Th}:
+        rows = sorted({(qa, s1) for (qa, s1, s2) in Th if ob.qadd(qa, ob.SITE_Q[s1]) == qm})
+        cols = sorted({(s2, ob.qadd(qm, ob.SITE_Q[s2])) for (qa, s1, s2) in Th
+                       if ob.qadd(qa, ob.SITE_Q[s1]) == qm})
+        M = np.block([[Th[(qa, s1, s2)] for (s2, qb) in cols] for (qa, s1) in rows])
+        Mp = np.block([[P[(qa, s1, s2)] for (s2, qb) in cols] for (qa, s1) in rows])
+        U, sv, Vh = np.linalg.svd(M, full_matrices=False)
+        k = mid.get(qm, 0)
+        best = (U[:, :k] * sv[:k]) @ Vh[:k]
+        assert np.abs(Mp - best).max() < 1e-10 * max(1.0, sv[0])
+        dropped += np.sum(sv[k:] ** 2)
+    assert abs(disc - dropped) < 1e-10 * total
