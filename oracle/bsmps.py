@@ -57,7 +57,9 @@ full-CI projection M_i^+ H M_i, is Hermitian and gives <A_i, H_i A_i> =
 <psi|H|psi> at every site; the two-site local product equals M_{i,i+1}^+ H v;
 the sector QR / LQ factors reproduce their blocks with orthonormal factors,
 right canonicalisation keeps the state, and the two-site split is the
-truncated SVD of each middle sector (Eckart-Young).  Parity unpinned, as in oracle.mps: whether
+truncated SVD of each middle sector (Eckart-Young); the identity MPO is the
+identity and the site-operator MPOs of c_{j,s} (with their Jordan-Wigner
+strings) obey the canonical anticommutation relations on the Fock space.  Parity unpinned, as in oracle.mps: whether
 a truncated fit reaches the best truncated state.
 """
 from __future__ import annotations

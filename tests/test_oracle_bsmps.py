@@ -470,3 +470,32 @@ def test_split_two_is_the_truncated_svd_of_each_middle_sector():
         assert np.abs(Mp - best).max() < 1e-10 * max(1.0, sv[0])
         dropped += np.sum(sv[k:] ** 2)
     assert abs(disc - dropped) < 1e-10 * total
+
+
+@pytest.mark.parametrize("L", [1, 2, 3])
+def test_identity_and_site_operator_mpos_on_the_fock_space(L):
+    # the identity MPO contracts to the identity; the site-operator MPOs of
+    # c_{j,s} with Jordan-Wigner parities on the sites before j satisfy the
+    # canonical anticommutation relations on the whole Fock space, and
+    # c+_{j,s} c_{j,s} is diagonal with the occupation of spin orbital (j, s)
+    # in the Fock index sum_i sigma_i 4^(L-1-i)
+    assert np.array_equal(ob.mpo_to_matrix(ob.identity_mpo(L)), np.eye(4 ** L))
+    C = {}
+    for j in range(L):
+        for s in range(2):
+            ops = {k: (ob.PARITY, (0, 0)) for k in range(j)}
+            ops[j] = (ob.local_op(s, False), ob.op_charge(s, False))
+            C[(j, s)] = ob.mpo_to_matrix(ob.site_operator_mpo(L, ops))
+            Cd = ob.mpo_to_matrix(ob.site_operator_mpo(
+                L, {**{k: (ob.PARITY, (0, 0)) for k in range(j)},
+                    j: (ob.local_op(s, True), ob.op_charge(s, True))}))
+            assert np.array_equal(Cd, C[(j, s)].T)
+    eye = np.eye(4 ** L)
+    for p, Cp in C.items():
+        for q_, Cq in C.items():
+            assert np.abs(Cp @ Cq.T + Cq.T @ Cp - (eye if p == q_ else 0)).max() < 1e-14
+            assert np.abs(Cp @ Cq + Cq @ Cp).max() < 1e-14
+        j, s = p
+        digit = (np.arange(4 ** L) // 4 ** (L - 1 - j)) % 4
+        occ = np.isin(digit, (1, 3) if s == 0 else (2, 3)).astype(float)
+        assert np.array_equal(Cp.T @ Cp, np.diag(occ))
