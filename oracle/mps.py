@@ -40,8 +40,11 @@ moves down to the cluster edge.
 
 Pins (tests/test_oracle_mps.py, test_oracle_observables.py,
 test_oracle_flops.py): untruncated fits and integrators equal the full-CI
-results, compression of two sites equals the library SVD, and the truncated
-fit lowers its residual at every local solve.  Parity unpinned: whether a
+results, compression of two sites equals the library SVD, the truncated
+fit lowers its residual at every local solve, the sector QR / LQ factors
+reproduce their blocks with orthonormal factors, the two-site split is the
+truncated SVD of each sector, right canonicalisation keeps the vector, and
+the local projections are the adjoints of the site maps.  Parity unpinned: whether a
 truncated fit (D below the exact bond dimension) reaches the best truncated
 state.  No closed form fixes that state, so the GPU is compared with this
 oracle on the same schedule instead.

@@ -163,3 +163,115 @@ def test_gram_schmidt_qr_against_library_qr():
     Q, R = om.gram_schmidt_qr(M)
     assert np.allclose(Q @ R, M, atol=1e-12)
     assert np.abs(Q[:, 2]).max() == 0.0
+
+
+def _row_labels(ql):
+    return (ql[:, None, :] + om.SITE_Q[None, :, :]).reshape(-1, 2)
+
+
+def test_sector_qr_and_lq_factor_each_sector_with_orthonormal_factors():
+    A, q = synth.random_mps(5, 5, 1, 12, seed=60)
+    i = 2
+    C = np.asarray(A[i], dtype=complex).copy()
+    ql, qr = np.asarray(q[i]), np.asarray(q[i + 1])
+    Dl, d, Dr = C.shape
+    M = C.reshape(Dl * d, Dr)
+    Q, lab, Rs = om.qr_left(C, ql, qr)
+    Qm = Q.reshape(Dl * d, -1)
+    assert np.abs(Qm.conj().T @ Qm - np.eye(Qm.shape[1])).max() < 1e-13
+    rowlab = _row_labels(ql)
+    for sec, (R, cols) in Rs.items():
+        k = np.flatnonzero((lab == sec).all(axis=1))
+        rows = np.flatnonzero((rowlab == sec).all(axis=1))
+        outside = np.setdiff1d(np.arange(Dl * d), rows)
+        assert np.abs(Qm[np.ix_(outside, k)]).max(initial=0.0) == 0.0
+        assert np.abs(Qm[:, k] @ R - M[:, cols]).max() < 1e-13 * np.abs(M).max()
+    Q2, lab2, Ls = om.lq_right(C, ql, qr)
+    Q2m = Q2.reshape(-1, d * Dr)
+    assert np.abs(Q2m @ Q2m.conj().T - np.eye(Q2m.shape[0])).max() < 1e-13
+    Mr = C.reshape(Dl, d * Dr)
+    for sec, (Lf, rows) in Ls.items():
+        k = np.flatnonzero((lab2 == sec).all(axis=1))
+        assert np.abs(Lf @ Q2m[k] - Mr[rows]).max() < 1e-13 * np.abs(Mr).max()
+
+
+def test_split_two_site_is_the_truncated_svd_of_each_sector():
+    A, q = synth.random_mps(5, 5, 1, 12, seed=61)
+    i = 1
+    Th = np.einsum("asx,xtb->astb", A[i], A[i + 1])
+    ql, qr = np.asarray(q[i]), np.asarray(q[i + 2])
+    Dl, _, _, Dr = Th.shape
+    M = Th.reshape(Dl * 4, 4 * Dr)
+    rowlab = _row_labels(ql)
+    collab = (qr[None, :, :] - om.SITE_Q[:, None, :]).reshape(4 * Dr, 2)
+    total = np.sum(np.abs(M) ** 2)
+    U, V, lab, disc, tot = om.split_two_site(Th, ql, qr, 10 ** 6, 0.0, "right")
+    assert np.abs(np.einsum("asx,xtb->astb", U, V) - Th).max() < 1e-12 * np.abs(Th).max()
+    assert abs(tot - total) < 1e-10 * total
+    D = len(q[i + 1]) // 2
+    U, V, lab, disc, tot = om.split_two_site(Th, ql, qr, D, 0.0, "left")
+    assert len(lab) <= D
+    P = np.einsum("asx,xtb->astb", U, V).reshape(Dl * 4, 4 * Dr)
+    dropped = 0.0
+    for sec in {tuple(x) for x in rowlab} & {tuple(x) for x in collab}:
+        rows = np.flatnonzero((rowlab == sec).all(axis=1))
+        cols = np.flatnonzero((collab == sec).all(axis=1))
+        u, s, vh = np.linalg.svd(M[np.ix_(rows, cols)], full_matrices=False)
+        k = int(np.sum((lab == sec).all(axis=1)))
+        best = (u[:, :k] * s[:k]) @ vh[:k]
+        assert np.abs(P[np.ix_(rows, cols)] - best).max() < 1e-10 * max(1.0, s[0])
+        dropped += np.sum(s[k:] ** 2)
+    assert abs(disc - dropped) < 1e-10 * total
+
+
+def test_right_canonicalize_keeps_the_vector_and_makes_sites_isometric():
+    A, q = synth.random_mps(5, 5, 1, 12, seed=62)
+    m = om.from_arrays(A, q)
+    rc = om.right_canonicalize(m)
+    v0, v1 = om.to_fock(m), om.to_fock(rc)
+    assert np.abs(v1 - v0).max() < 1e-12 * np.abs(v0).max()
+    for t in rc.tensors[1:]:
+        Dl = t.shape[0]
+        Mt = t.reshape(Dl, -1)
+        assert np.abs(Mt @ Mt.conj().T - np.eye(Dl)).max() < 1e-12
+
+
+def test_projections_are_the_adjoint_of_the_site_maps():
+    # project_one(T) = M_i^+ T and project_two(T) = M_{i,i+1}^+ T, M the
+    # linear maps from the site (pair) tensor to the Fock vector of C with
+    # that site (pair) replaced
+    L = 4
+    A, q = synth.random_mps(L, 4, 0, 6, seed=63)
+    C = om.from_arrays(A, q)
+    rng = np.random.default_rng(64)
+    T = rng.standard_normal(4 ** L) + 1j * rng.standard_normal(4 ** L)
+    for i in range(L):
+        P = om.project_one(T, C, i)
+        Dl, _, Dr = C.tensors[i].shape
+        for a, s, b in [(0, 0, 0), (Dl - 1, 3, Dr - 1), (Dl // 2, 1, Dr // 2)]:
+            U = C.copy()
+            U.tensors[i] = np.zeros_like(C.tensors[i])
+            U.tensors[i][a, s, b] = 1.0
+            assert abs(P[a, s, b] - np.vdot(om.to_fock(U), T)) < 1e-12 * np.abs(T).max()
+    for i in range(L - 1):
+        P2 = om.project_two(T, C, i)
+        Dl, Dr = C.tensors[i].shape[0], C.tensors[i + 1].shape[2]
+        for a, s, t, b in [(0, 0, 3, 0), (Dl - 1, 2, 1, Dr - 1)]:
+            U = C.copy()
+            U.tensors[i] = np.zeros((Dl, 4, 1), dtype=complex)
+            U.tensors[i + 1] = np.zeros((1, 4, Dr), dtype=complex)
+            U.tensors[i][a, s, 0] = 1.0
+            U.tensors[i + 1][0, t, b] = 1.0
+            assert abs(P2[a, s, t, b] - np.vdot(om.to_fock(U), T)) < 1e-12 * np.abs(T).max()
+
+
+def test_untruncated_sum_fit_is_the_exact_sum():
+    L = 4
+    sys_ = _system(L, 4, 0, 65)
+    A1, q1 = synth.random_mps(L, 4, 0, 6, seed=66)
+    A2, q2 = synth.random_mps(L, 4, 0, 6, seed=67)
+    m1, m2 = om.from_arrays(A1, q1), om.from_arrays(A2, q2)
+    c1, c2 = 0.7 - 0.2j, -1.1 + 0.4j
+    out = om.sum_fit(sys_, [(c1, m1), (c2, m2)], om.Schedule(D=36, n_two_site=3, n_one_site=1))
+    ref = c1 * sys_.vec(m1) + c2 * sys_.vec(m2)
+    assert np.abs(sys_.vec(out) - ref).max() < 1e-11 * np.abs(ref).max()
