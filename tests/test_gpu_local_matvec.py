@@ -8,8 +8,9 @@ Eq. add_min's local problem) on the GPU.
   environment chains of up to L - 1 sites, the case the fitted-state bounds
   of the mixed tests cover (2e-5 relative for split TF32, 5e-2 for BF16).
 * At the benchmark size (L = 16, 15 electrons, 2S_z = 1, D = 256, centre
-  site): <A_c, H_c A_c> = <psi|H|psi> (the FP64 sandwich), a property that
-  holds at any size, and split TF32 against FP64 on every element.
+  site): FP64 against the oracle on every element of the site (1e-10 of the
+  largest entry, the FP64 observable bound), <A_c, H_c A_c> = <psi|H|psi>
+  (the FP64 sandwich), and split TF32 against FP64 on every element.
 * Only the operator's site of y changes; wrong bonds and a changed context
   precision are refused before any work.
 """
@@ -135,6 +136,14 @@ def test_local_operator_at_bench_size_centre_site(td):
         ctx.close()
     y64, a64 = out["fp64"]
     keys = a64
+    # the oracle's local operator on the same state, every entry of the site
+    psi_o = ob.from_dense(A, q)
+    ref = ob.local_matvec(ob.hamiltonian_mpo(I.h, I.eri), psi_o, c, psi_o.sites[c])
+    err = np.abs(_flat(y64, keys) - _flat(ref, keys)).max()
+    scale = np.abs(_flat(ref, keys)).max()
+    print("centre site of L=16 D=256: FP64 vs oracle, max abs error %.2e (max |y| %.2e)"
+          % (err, scale))
+    assert err <= 1e-10 * scale
     ea = np.vdot(_flat(a64, keys), _flat(y64, keys))
     print("centre site of L=16 D=256: <A,H_c A> - <psi|H|psi> = %.2e (|E| %.3e), "
           "environments %.1f MB (FP64)" % (abs(ea - e), abs(e), env_mb))
