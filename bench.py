@@ -320,6 +320,48 @@ def replica_totals(ms, work, dist, device):
     return float(t.item()), float(w.item())
 
 
+def centre_site_matvec(td, ctx, mpo, A, q, torch, precision, reps=50, warmup=3):
+    """The local one-site operator L W x R of the fit at the centre site of the
+    seeded state (the K3 micro-benchmark), after the timed region: its
+    environments once, then `reps` applications, each after an L2 flush and
+    timed on its own with CUDA events on the context stream."""
+    L = len(A)
+    state = td.mps_import(ctx, A, q)
+    td.compress(ctx, state, max(len(x) for x in q), 0.0)
+    op = td.local_hamiltonian(ctx, mpo, state, L // 2)
+    y = state.copy()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    for _ in range(warmup):
+        op.apply(state, y)
+    torch.cuda.synchronize()
+    ctx.stats_enable(True)
+    ctx.stats_reset()
+    ev = []
+    for _ in range(reps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        op.apply(state, y)
+        e1.record()
+        ev.append((e0, e1))
+    torch.cuda.synchronize()
+    st = ctx.stats()
+    ctx.stats_enable(False)
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    flops = st["gemm"]["flops"] + st["gemm_fp64"]["flops"] + st["wstage"]["flops"]
+    out = {"site": L // 2, "applications": reps, "us_per_application": 1e3 * ms / reps,
+           "gflop_per_application": flops / reps / 1e9, "tflops": flops / (ms / 1e3) / 1e12,
+           "env_bytes": op.env_bytes, "l2": "flushed before every application",
+           "roofline": roofline(st, precision),
+           "class_us_per_application": {k: 1e3 * v["ms"] / reps for k, v in st.items()
+                                        if not k.startswith("host") and v["launches"]}}
+    op.free()
+    y.free()
+    state.free()
+    return out
+
+
 def roofline(st, precision):
     """Roofline entry of the kernel class with the largest live event time:
     achieved = its algorithmic work per launch / its average launch time."""
@@ -452,6 +494,8 @@ def main():
                          "centre site per step (L2 flushed between applications); batch: "
                          "one RK4 step of each of 64 uneven instances (L in {8..14}, "
                          "D in {32, 64, 128}) on worker streams")
+    ap.add_argument("--no-matvec", action="store_true",
+                    help="krylov mode: skip the centre-site local matvec timed after the steps")
     ap.add_argument("--reps", type=int, default=50,
                     help="matvec mode: local operator applications per step")
     ap.add_argument("--workers", type=int, default=16, help="batch mode: worker streams")
@@ -721,6 +765,13 @@ def main():
                "unit": "TFLOP/s", "h2d_bytes_per_step": h2d_bytes,
                "d2h_bytes_per_step": int(g.nbytes), "pinned_inputs": pinned}
 
+    # the K3 micro-benchmark beside the Krylov step (its own line in --mode matvec)
+    k3 = None
+    if args.mode == "krylov" and not args.size and not args.no_matvec:
+        try:
+            k3 = centre_site_matvec(td, ctx, mpo, A, q, torch, args.precision)
+        except Exception as e:   # reported, never at the cost of the main line
+            k3 = {"error": str(e)[:200]}
     # dominant kernel class: the largest live event time in the timed region
     roof = roofline(st, args.precision)
     config = dict(workload_config(args, sched, (L, N_ELEC, TWO_SZ, D), world),
@@ -742,6 +793,7 @@ def main():
         "config": config,
         "steps_per_s": 1e3 * args.steps / ms,
         "matvec": matvec,
+        "centre_site_matvec": k3,
         "vs_fp64": fp64_cmp,
         "vs_fp64_trajectory": traj,
         "precision_compare": prec_cmp,

@@ -216,6 +216,7 @@ def test_native_arm_json_assembly_with_a_stand_in_library(monkeypatch, capsys):
                        (["--steps", "1", "--warmup", "3", "--serial-inner", "--no-traj-compare",
                          "--no-fp64-compare", "--no-e2e"], "serial")):
         monkeypatch.setattr(sys, "argv", ["bench.py", "--no-cpu-baseline", *argv])
+        applied.clear()
         bench.main()
         line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
         for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
@@ -232,8 +233,14 @@ def test_native_arm_json_assembly_with_a_stand_in_library(monkeypatch, capsys):
             assert len(traj["per_step_err_one_rdm"]) == 2 and traj["target_1e-6_met"]
             assert line["e2e"]["h2d_bytes_per_step"] > 0
             assert line["e2e"]["pinned_inputs"] is False      # no driver here
+            # the centre-site local matvec after the steps: 3 warm-up + 50 timed
+            k3 = line["centre_site_matvec"]
+            assert k3["site"] == 8 and k3["applications"] == 50 and "roofline" in k3
+            assert applied[0] == 8 and len(applied) == 1 + 3 + 50
         else:
             assert line["vs_fp64_trajectory"] is None
+        if mode not in ("krylov", "serial"):      # the serial run is a Krylov run too
+            assert line["centre_site_matvec"] is None
         if mode == "matvec":
             # the operator at the centre site, (3 warm-up + 2 timed) x 2 applications,
             # only the timed ones in the line; no e2e in this mode
