@@ -322,7 +322,7 @@ def replica_totals(ms, work, dist, device):
 
 def centre_site_matvec(td, ctx, mpo, A, q, torch, precision, reps=50, warmup=3):
     """The local one-site operator L W x R of the fit at the centre site of the
-    seeded state (the K3 micro-benchmark), after the timed region: its
+    seeded state (a micro-benchmark of the local product), after the timed region: its
     environments once, then `reps` applications, each after an L2 flush and
     timed on its own with CUDA events on the context stream."""
     L = len(A)
@@ -765,7 +765,7 @@ def main():
                "unit": "TFLOP/s", "h2d_bytes_per_step": h2d_bytes,
                "d2h_bytes_per_step": int(g.nbytes), "pinned_inputs": pinned}
 
-    # the K3 micro-benchmark beside the Krylov step (its own line in --mode matvec)
+    # the local-product micro-benchmark beside the Krylov step (its own line in --mode matvec)
     k3 = None
     if args.mode == "krylov" and not args.size and not args.no_matvec:
         try:
