@@ -162,7 +162,9 @@ int tdmps_build_mpo(tdmps_ctx_t ctx, const double* h, const double* eri, int L,
 /* ctx may be NULL: the MPO is then built on the host only (no GPU needed);
  * its device tables are uploaded on first use by a context. */
 
-/* Channel count of every bond (bond_dims[L+1]) and total stored elements. */
+/* Channel count of every bond (bond_dims[L+1]) and total stored elements.
+ * Either output may be NULL.  Host only.  Errors: INVALID_ARG for a NULL
+ * mpo. */
 int tdmps_mpo_info(tdmps_mpo_t mpo, int* bond_dims, int64_t* n_elements);
 /* Host copy of the stored elements of W_site, 0 <= site < L: entry e is the
  * matrix element <sig|W[w_in, w_out]|sigp> = v[e] between channel w_in of
@@ -190,12 +192,16 @@ int tdmps_mps_from_determinant(tdmps_ctx_t ctx, int L, const uint8_t* occ,
  * bond_dims[L+1]: dimensions D_0..D_L (D_0 = 1 with label (0,0)).
  * labels: for k = 0..L, D_k pairs (N, 2S_z) concatenated (int32 pairs).
  * tensors[i]: host array D_i x 4 x D_{i+1}, row-major, complex.
- * Entries that violate charge conservation must be zero (INVALID_ARG
- * otherwise, SECTOR if D_L is not 1). */
+ * Entries that violate charge conservation must be zero.
+ * Errors: INVALID_ARG (NULL argument, L outside 1..63, a bond dimension
+ * below 1, bond 0 not one-dimensional with label (0, 0), a non-zero entry
+ * that violates charge conservation), SECTOR (D_L is not 1), NONFINITE (a
+ * NaN or Inf entry), CUDA, OOM. */
 int tdmps_mps_import(tdmps_ctx_t ctx, int L, const int* bond_dims, const int* labels,
                      const tdmps_complex* const* tensors, tdmps_mps_t* out);
 /* Export: with tensors == NULL only bond_dims (L+1 entries) is written; then
- * call again with labels (sum D_k pairs) and tensors[i] of D_i*4*D_{i+1}. */
+ * call again with labels (sum D_k pairs) and tensors[i] of D_i*4*D_{i+1}.
+ * Errors: INVALID_ARG (NULL mps or bond_dims, tensors without labels), CUDA. */
 int tdmps_mps_export(tdmps_ctx_t ctx, tdmps_mps_t mps, int* bond_dims, int* labels,
                      tdmps_complex* const* tensors);
 /* Length, total charge (N, 2S_z) and the largest bond dimension (sum over
@@ -215,7 +221,12 @@ int tdmps_mps_free(tdmps_mps_t mps);
  * bond dimension <= D, discarding at most a relative weight eps per
  * truncation; n_sweeps > 0 overrides the one-site sweep count of the
  * schedule (n_sweeps <= 0 keeps it).  The initial guess is `in`.
- * The result is right-canonical with its norm on site 0. */
+ * The result is right-canonical with its norm on site 0.
+ * Errors: INVALID_ARG (NULL argument, lengths differ, D < 1, eps outside [0,
+ * 1), a symmetry block beyond the supported QR/SVD size), ZERO_STATE (the
+ * fit target vanished on a sweep), NUMERIC (a Jacobi SVD did not converge,
+ * or a tensor-core wait timed out), NONFINITE (non-finite scalar argument or
+ * singular values), CUDA, OOM. */
 int tdmps_apply_H(tdmps_ctx_t ctx, tdmps_mpo_t mpo, tdmps_mps_t in, tdmps_complex alpha,
                   int D, double eps, int n_sweeps, tdmps_mps_t* out);
 
@@ -223,7 +234,13 @@ int tdmps_apply_H(tdmps_ctx_t ctx, tdmps_mpo_t mpo, tdmps_mps_t in, tdmps_comple
  * In the TF32/BF16 precisions the result is rescaled by <out|T>/<out|out>
  * (T the exact sum; FP64 overlaps), which the projection property of the
  * fit makes 1 in exact arithmetic and which removes the common shrink of
- * the tensor-core sums. */
+ * the tensor-core sums.
+ * Errors: INVALID_ARG (n_terms < 1, NULL argument or term, lengths differ, D
+ * < 1, eps outside [0, 1), a symmetry block beyond the supported QR/SVD
+ * size), SECTOR (terms of different (N, 2S_z)), ZERO_STATE (the fit target
+ * vanished on a sweep), NUMERIC (a Jacobi SVD did not converge, or a
+ * tensor-core wait timed out), NONFINITE (non-finite scalar argument or
+ * singular values), CUDA, OOM. */
 int tdmps_sum(tdmps_ctx_t ctx, int n_terms, const tdmps_complex* coefs,
               const tdmps_mps_t* terms, int D, double eps, tdmps_mps_t* out);
 
@@ -290,7 +307,9 @@ int tdmps_energy(tdmps_ctx_t ctx, tdmps_mpo_t mpo, tdmps_mps_t psi, double* ener
  * Errors: INVALID_ARG, ZERO_STATE, CUDA. */
 int tdmps_integral_gradient(tdmps_ctx_t ctx, tdmps_mps_t psi, double* dE_dh, double* dE_deri);
 
-/* <bra|ket> (the contraction of two chains of Eq. mps). */
+/* <bra|ket> (the contraction of two chains of Eq. mps), FP64.  Errors:
+ * INVALID_ARG (NULL argument, lengths differ), SECTOR (different (N, 2S_z)),
+ * CUDA, OOM. */
 int tdmps_overlap(tdmps_ctx_t ctx, tdmps_mps_t bra, tdmps_mps_t ket, tdmps_complex* out);
 
 /* Overlap that allocates no device memory.  The paper has no counterpart:
@@ -309,23 +328,33 @@ int tdmps_overlap(tdmps_ctx_t ctx, tdmps_mps_t bra, tdmps_mps_t ket, tdmps_compl
  * streams at once) race.  A pair whose environments do not fit, or whose
  * task list for one launch exceeds a segment of the staging ring, returns
  * TDMPS_ERR_INVALID_ARG before any work is enqueued on the GPU; so does a
- * context whose device is not the current device. */
+ * context whose device is not the current device.  Other errors: SECTOR
+ * (different (N, 2S_z)), CUDA. */
 #define TDMPS_NOALLOC_SCRATCH_BYTES (16u << 20)
 int tdmps_overlap_noalloc(tdmps_ctx_t ctx, tdmps_mps_t bra, tdmps_mps_t ket, tdmps_complex* out);
 
-/* <bra|H|ket> with the MPO (Sec. 2.2.3, H_ij of Eq. krylov_evo). */
+/* <bra|H|ket> with the MPO (Sec. 2.2.3, H_ij of Eq. krylov_evo), FP64.
+ * Errors: INVALID_ARG (NULL argument, lengths differ), SECTOR (different
+ * (N, 2S_z)), CUDA, OOM. */
 int tdmps_expectation(tdmps_ctx_t ctx, tdmps_mpo_t mpo, tdmps_mps_t bra, tdmps_mps_t ket,
                       tdmps_complex* out);
 
 /* SVD compression in place (Sec. 2.1: keep the D largest singular values):
  * right-canonicalise, one left-to-right pass of truncated SVDs, exact LQ pass
  * back.  discarded_weight (may be NULL): sum over bonds of the relative
- * discarded weight. */
+ * discarded weight.  Errors: INVALID_ARG (NULL argument, D < 1, eps outside
+ * [0, 1)), ZERO_STATE (a zero state), NUMERIC, NONFINITE (the SVD), CUDA,
+ * OOM; inout is unchanged on error. */
 int tdmps_compress(tdmps_ctx_t ctx, tdmps_mps_t inout, int D, double eps,
                    double* discarded_weight);
 
 /* One RK4 step in place (Sec. 2.2.2, stages k1..k4 with k = -i dt H(...),
- * Eq. rk_add): four fitted H applications and four fitted sums. */
+ * Eq. rk_add): four fitted H applications and four fitted sums.
+ * Errors: INVALID_ARG (NULL argument, lengths differ, D < 1, eps outside [0,
+ * 1), a symmetry block beyond the supported QR/SVD size), ZERO_STATE (the
+ * fit target vanished on a sweep), NUMERIC (a Jacobi SVD did not converge,
+ * or a tensor-core wait timed out), NONFINITE (non-finite scalar argument or
+ * singular values), CUDA, OOM; inout is unchanged on error. */
 int tdmps_rk4_step(tdmps_ctx_t ctx, tdmps_mpo_t mpo, tdmps_mps_t inout, double dt, int D,
                    double eps);
 
@@ -335,17 +364,25 @@ int tdmps_rk4_step(tdmps_ctx_t ctx, tdmps_mpo_t mpo, tdmps_mps_t inout, double d
  * Eq. (kry_non).  Each new vector is normalised.  The new state is the fitted
  * sum of Eq. (krylov_evo) with N and H measured exactly; exp(-i dt N^-1 H) e0
  * uses canonical orthogonalisation of N (eigenvalues below 1e-12 * max are
- * dropped; KRYLOV_SINGULAR if fewer than 2 remain, inout unchanged). */
+ * dropped; KRYLOV_SINGULAR if fewer than 2 remain, inout unchanged).
+ * Errors: INVALID_ARG (NULL argument, lengths differ, m outside [2, 16], D <
+ * 1, eps outside [0, 1), a symmetry block beyond the supported QR/SVD size),
+ * ZERO_STATE (the fit target vanished on a sweep), NUMERIC (a Jacobi SVD did
+ * not converge, or a tensor-core wait timed out), NONFINITE (non-finite
+ * scalar argument or singular values or Krylov matrices), CUDA, OOM,
+ * KRYLOV_SINGULAR; inout is unchanged on error. */
 int tdmps_krylov_step(tdmps_ctx_t ctx, tdmps_mpo_t mpo, tdmps_mps_t inout, double dt, int m,
                       int orthogonal, int D, double eps);
 
 /* gamma_ij = sum_s <psi| c+_is c_js |psi> (Sec. 3.2, the 1BRDM), not
- * normalised by <psi|psi>.  gamma: host array L*L row-major. */
+ * normalised by <psi|psi>.  gamma: host array L*L row-major.  FP64.
+ * Errors: INVALID_ARG (NULL argument), CUDA, OOM. */
 int tdmps_one_rdm(tdmps_ctx_t ctx, tdmps_mps_t psi, tdmps_complex* gamma);
 
 /* T_ij = sum_s <bra| c+_is c_js |ket>: the 1BRDM between two states of the
  * same (N, 2S_z) (TDMPS_ERR_SECTOR otherwise), not normalised.  T: host
- * array L*L row-major.  FP64. */
+ * array L*L row-major.  FP64.  Errors: INVALID_ARG (NULL argument, lengths
+ * differ), SECTOR, CUDA, OOM. */
 int tdmps_transition_rdm(tdmps_ctx_t ctx, tdmps_mps_t bra, tdmps_mps_t ket, tdmps_complex* T);
 
 /* Gamma_ijkl = sum_{s,t} <psi| c+_is c+_kt c_lt c_js |psi>, the partner of
@@ -354,7 +391,8 @@ int tdmps_transition_rdm(tdmps_ctx_t ctx, tdmps_mps_t bra, tdmps_mps_t ket, tdmp
  * and dE/dh_ij = gamma_ij, dE/d(ij|kl) = Gamma_ijkl / 2.  Not normalised.
  * Gamma: host array L^4 row-major (index ((i*L + j)*L + k)*L + l).  Computed
  * as sum_s T[c_is psi, c_js psi]_kl from 2 L^2 transition 1BRDMs of the
- * exactly ionised states (tdmps_apply_site_op).  FP64. */
+ * exactly ionised states (tdmps_apply_site_op).  FP64.  Errors: INVALID_ARG
+ * (NULL argument), CUDA, OOM. */
 int tdmps_two_rdm(tdmps_ctx_t ctx, tdmps_mps_t psi, tdmps_complex* Gamma);
 
 /* ------------------------------------------------------- site operators */
@@ -369,7 +407,9 @@ int tdmps_two_rdm(tdmps_ctx_t ctx, tdmps_mps_t psi, tdmps_complex* Gamma);
  * Green's function (Eq. green_time: c_js|psi0>, propagated with a negative
  * time step, projected on c_is|psi0>).  Returns TDMPS_ERR_ZERO_STATE, with
  * *out untouched, when the operator annihilates every configuration of
- * `in` (for example c_up on a state with that orbital empty). */
+ * `in` (for example c_up on a state with that orbital empty).  Other
+ * errors: INVALID_ARG (NULL argument, site outside [0, L), spin not 0 or 1),
+ * CUDA, OOM. */
 int tdmps_apply_site_op(tdmps_ctx_t ctx, tdmps_mps_t in, int site, int spin, int dagger,
                         tdmps_mps_t* out);
 
@@ -401,9 +441,8 @@ int tdmps_green_function(tdmps_ctx_t ctx, tdmps_mpo_t mpo, tdmps_mps_t psi0, int
  * from a shared counter, so the kernels of several items overlap on the GPU.
  * The context's stream is ordered before the first and after the last
  * kernel of the batch; the context's precision and sweep schedule apply to
- * every item.  Results equal those of separate tdmps_rk4_step /
- * tdmps_krylov_step calls up to the summation order of split-K partial
- * products.  status (may be NULL): n codes, 0 for every item that finished;
+ * every item.  Each item runs the launch plans a separate tdmps_rk4_step /
+ * tdmps_krylov_step call would run (the tests compare them to 1e-11).  status (may be NULL): n codes, 0 for every item that finished;
  * a failed item keeps its input state.  Returns 0 when every item finished,
  * else the code of the first failed item (message in tdmps_last_error with
  * its index).  The worker streams are created on the first call and live as
