@@ -362,9 +362,10 @@ def centre_site_matvec(td, ctx, mpo, A, q, torch, precision, reps=50, warmup=3):
     return out
 
 
-def roofline(st, precision):
-    """Roofline entry of the kernel class with the largest live event time:
-    achieved = its algorithmic work per launch / its average launch time."""
+def roofline(st, precision, cls=None):
+    """Roofline entry of the kernel class with the largest live event time
+    (or of class `cls`): achieved = its algorithmic work per launch / its
+    average launch time."""
     peaks = _peaks()
     # the kernels run inside seconds-long steps: the sustained bf16 figure;
     # without the measured file, the earlier GB300 measurement (fallback)
@@ -374,7 +375,7 @@ def roofline(st, precision):
     fp64_peak = bf16 * 1.25 / 2250.0
     tag = "measured" if measured else "fallback"
     dev = {k: v for k, v in st.items() if not k.startswith("host")}
-    top = max(dev, key=lambda k: dev[k]["ms"])
+    top = cls if cls is not None else max(dev, key=lambda k: dev[k]["ms"])
     ks = st[top]
     per_launch_s = ks["ms"] / max(1, ks["launches"]) / 1e3
     per_launch = lambda x: x / max(1, ks["launches"])
@@ -802,6 +803,10 @@ def main():
                              "gflop": round(v["flops"] / 1e9, 3), "gb": round(v["bytes"] / 1e9, 3)}
                          for k, v in st.items()},
         "roofline": roof,
+        # the tensor-core GEMM class on its own (the contraction kernel of the
+        # metric), whichever class dominates the step
+        "roofline_tensor_core": (roofline(st, args.precision, "gemm")
+                                 if args.precision != "fp64" and st["gemm"]["launches"] else None),
         "clocks": clk.summary(),
         "e2e": e2e,
     }

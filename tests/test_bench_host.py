@@ -227,6 +227,8 @@ def test_native_arm_json_assembly_with_a_stand_in_library(monkeypatch, capsys):
         assert line["gpu_launches"] > 0
         assert line["config"]["stream_priority"] == -3
         assert line["config"]["inner_products"] == ("serial" if mode == "serial" else "concurrent")
+        rt = line["roofline_tensor_core"]
+        assert rt["kernel"].startswith("k_gemm_tc") and rt["bound"] == "tensor"
         if mode == "krylov":
             traj = line["vs_fp64_trajectory"]
             assert traj["max_abs_err_dipole"] == 0.0 and line["vs_fp64"] is not None
