@@ -307,3 +307,20 @@ def test_krylov_error_decreases_with_time_step():
         errs.append(np.linalg.norm(fci.krylov_step(H, psi, dt, 4) - fci.exact_evolve(H, psi, dt)))
     # local error O(dt^m): halving dt shrinks it by ~2^4
     assert errs[1] < errs[0] / 8
+
+
+@pytest.mark.parametrize("L", [1, 2, 3])
+def test_apply_op_equals_kronecker_operators(L):
+    # a_p and a+_p on determinant bit strings (mask = sum_p n_p 2^p) equal the
+    # Jordan-Wigner Kronecker matrices of every spin orbital
+    ops = _spin_orbital_ops(L)
+    masks = np.arange(4 ** L, dtype=np.uint64)
+    for p in range(2 * L):
+        for dagger in (False, True):
+            new, amp = fci.apply_op(masks, np.ones(len(masks)), p, dagger)
+            M = np.zeros((4 ** L, 4 ** L))
+            for old, (n, a) in enumerate(zip(new, amp)):
+                if a != 0.0:
+                    M[int(n), old] += a
+            ref = ops[p].T if dagger else ops[p]
+            assert np.array_equal(M, ref), (p, dagger)

@@ -104,3 +104,17 @@ def test_library_rejects_bad_input_on_host():
     assert e.value.name == "INVALID_ARG"
     # one and two orbitals have a single ordering
     assert list(td.fiedler_order(I.h[:2, :2], I.eri[:2, :2, :2, :2])) == [0, 1]
+
+
+def test_weights_by_hand():
+    # w_ij = (|h_ij| + |h_ji| + |K_ij| + |K_ji|) / 2 with the exchange integral
+    # K_ij = (ij|ji), zero diagonal; the Coulomb integrals (ii|jj) do not enter
+    from oracle import ordering as oo
+    h = np.array([[-1.0, 0.3, 0.0], [0.3, -0.5, -0.2], [0.0, -0.2, 0.1]])
+    eri = np.zeros((3, 3, 3, 3))
+    eri[0, 1, 1, 0] = eri[1, 0, 0, 1] = 0.05
+    eri[0, 2, 2, 0] = 0.02
+    eri[2, 0, 0, 2] = -0.04
+    eri[1, 1, 2, 2] = eri[2, 2, 1, 1] = 0.7     # Coulomb: ignored
+    expect = np.array([[0.0, 0.35, 0.03], [0.35, 0.0, 0.2], [0.03, 0.2, 0.0]])
+    assert np.allclose(oo.weights(h, eri), expect, atol=1e-15, rtol=0)
